@@ -1,0 +1,255 @@
+"""Plain FP64 CPU oracle of the BHEM hot path (ctypes wrapper around ``bhem_oracle.c``).
+
+TEST INFRASTRUCTURE: only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. The CUDA library and its Python binding never do, and the
+two share no code.
+
+The C source follows the paper's formulas step by step (Sec. 3, Sec. 4, Sec. 6.1, App. A, App. B);
+this wrapper only marshals numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bhem_oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class Grid(C.Structure):
+    _fields_ = [("nu", C.c_int), ("nv", C.c_int), ("periodic_u", C.c_int), ("periodic_v", C.c_int),
+                ("dxi1", C.c_double), ("dxi2", C.c_double)]
+
+
+class Material(C.Structure):
+    _fields_ = [("young", C.c_double), ("poisson", C.c_double), ("thickness", C.c_double),
+                ("density", C.c_double)]
+
+
+class StepParams(C.Structure):
+    _fields_ = [("dt", C.c_double), ("gravity", C.c_double * 3), ("newton_rtol", C.c_double),
+                ("newton_max", C.c_int), ("pcg_rtol", C.c_double), ("pcg_max", C.c_int),
+                ("pcg_fixed_iters", C.c_int)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("newton_iters", C.c_int), ("pcg_iters_total", C.c_int),
+                ("ls_backtracks", C.c_int), ("regularizations", C.c_int), ("status", C.c_int),
+                ("res0", C.c_double), ("res_final", C.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no target-specific flags) into oracle/_lib."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            os.makedirs(_LIBDIR, exist_ok=True)
+            tmp = _LIB + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        d, i, p = C.c_double, C.c_int, C.c_void_p
+        lib.og_hermite_w.restype = d
+        lib.og_hermite_w.argtypes = [i, i, d, i]
+        lib.og_gauss4.argtypes = [p, p]
+        lib.og_shape.argtypes = [d, d, d, d, p]
+        lib.og_n_nodes.restype = i
+        lib.og_n_nodes.argtypes = [p]
+        lib.og_patch_nodes.argtypes = [p, i, p]
+        lib.og_element_energy.restype = d
+        lib.og_element_energy.argtypes = [p, p, d, d, p]
+        lib.og_element_egh.argtypes = [p, p, d, d, p, p, p, p]
+        lib.og_element_mass.argtypes = [p, d, d, p, p, p]
+        lib.og_elements.argtypes = [p, p, p, p, i, i, p, p, p]
+        lib.og_bsr_pattern.restype = i
+        lib.og_bsr_pattern.argtypes = [p, p, p]
+        lib.og_assemble.argtypes = [p, p, p, p, p, p, d, p, p, p]
+        lib.og_mass.argtypes = [p, p, p, p, p, p, p]
+        lib.og_pcg.restype = i
+        lib.og_pcg.argtypes = [i, p, p, p, p, d, p, d, i, i, p, p]
+        lib.og_newton_step.restype = i
+        lib.og_newton_step.argtypes = [p, p, p, p, p, p, p, p, p, p]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _grid(g) -> Grid:
+    return Grid(int(g.nu), int(g.nv), int(bool(g.periodic_u)), int(bool(g.periodic_v)),
+                float(g.dxi1), float(g.dxi2))
+
+
+def _mat(m) -> Material:
+    return Material(float(m.young), float(m.poisson), float(m.thickness), float(m.density))
+
+
+# ------------------------------------------------------------------------------------------
+# App. A
+# ------------------------------------------------------------------------------------------
+def hermite_w(p: int, r: int, t: float, d: int = 0) -> float:
+    return _load().og_hermite_w(p, r, float(t), d)
+
+
+def gauss4():
+    x, w = np.zeros(4), np.zeros(4)
+    _load().og_gauss4(_ptr(x), _ptr(w))
+    return x, w
+
+
+def shape(dxi1, dxi2, t1, t2):
+    """[16, 6] values Phi, Phi_1, Phi_2, Phi_11, Phi_22, Phi_12 of the 16 shape functions."""
+    out = np.zeros((16, 6))
+    _load().og_shape(float(dxi1), float(dxi2), float(t1), float(t2), _ptr(out))
+    return out
+
+
+def patch_nodes(g, patch: int):
+    nd = np.zeros(4, dtype=np.int32)
+    _load().og_patch_nodes(C.byref(_grid(g)), int(patch), _ptr(nd))
+    return nd
+
+
+def gather(g, nodal, patch: int):
+    """Patch-local 48-vector: the 12 DOFs of the corners 00, 10, 01, 11."""
+    nodal = np.asarray(nodal).reshape(-1, 12)
+    return nodal[patch_nodes(g, patch)].reshape(48)
+
+
+# ------------------------------------------------------------------------------------------
+# Element level
+# ------------------------------------------------------------------------------------------
+def element_energy(q48, qb48, dxi1, dxi2, mat) -> float:
+    q48, qb48 = _f64(q48), _f64(qb48)
+    return _load().og_element_energy(_ptr(q48), _ptr(qb48), float(dxi1), float(dxi2),
+                                     C.byref(_mat(mat)))
+
+
+def element_egh(q48, qb48, dxi1, dxi2, mat):
+    """(E, grad[48], hess[48, 48]) of one patch; local order corner*12 + kind*3 + component."""
+    q48, qb48 = _f64(q48), _f64(qb48)
+    E = np.zeros(1)
+    g = np.zeros(48)
+    H = np.zeros((48, 48))
+    _load().og_element_egh(_ptr(q48), _ptr(qb48), float(dxi1), float(dxi2), C.byref(_mat(mat)),
+                           _ptr(E), _ptr(g), _ptr(H))
+    return float(E[0]), g, H
+
+
+def element_mass(qb48, dxi1, dxi2, mat):
+    qb48 = _f64(qb48)
+    m, f = np.zeros((16, 16)), np.zeros(16)
+    _load().og_element_mass(_ptr(qb48), float(dxi1), float(dxi2), C.byref(_mat(mat)), _ptr(m), _ptr(f))
+    return m, f
+
+
+def elements(g, mat, rest, q, p0: int = 0, p1: int | None = None, want_hess: bool = True):
+    """Per-patch (E[np], grad[np, 48], hess[np, 48, 48]) for patches p0..p1-1."""
+    p1 = g.n_patches if p1 is None else p1
+    rest, q = _f64(rest).reshape(-1), _f64(q).reshape(-1)
+    n = p1 - p0
+    E, G = np.zeros(n), np.zeros((n, 48))
+    H = np.zeros((n, 48, 48)) if want_hess else None
+    _load().og_elements(C.byref(_grid(g)), C.byref(_mat(mat)), _ptr(rest), _ptr(q), p0, p1,
+                        _ptr(E), _ptr(G), _ptr(H))
+    return E, G, H
+
+
+# ------------------------------------------------------------------------------------------
+# Assembly and solver
+# ------------------------------------------------------------------------------------------
+def bsr_pattern(g):
+    lib = _load()
+    gg = _grid(g)
+    nb = lib.og_bsr_pattern(C.byref(gg), None, None)
+    row_ptr = np.zeros(g.n_nodes + 1, dtype=np.int32)
+    col = np.zeros(nb, dtype=np.int32)
+    lib.og_bsr_pattern(C.byref(gg), _ptr(row_ptr), _ptr(col))
+    return row_ptr, col
+
+
+def assemble(g, mat, rest, q, mass_scale: float = 0.0, want_hess: bool = True, pattern=None):
+    """(energy, grad[n_dof], (row_ptr, col, val[nb, 12, 12]) or None): K + mass_scale * M."""
+    row_ptr, col = pattern if pattern is not None else bsr_pattern(g)
+    rest, q = _f64(rest).reshape(-1), _f64(q).reshape(-1)
+    E = np.zeros(1)
+    grad = np.zeros(g.n_dof)
+    val = np.zeros((col.size, 12, 12)) if want_hess else None
+    _load().og_assemble(C.byref(_grid(g)), C.byref(_mat(mat)), _ptr(rest), _ptr(q), _ptr(row_ptr),
+                        _ptr(col), float(mass_scale), _ptr(E), _ptr(grad), _ptr(val))
+    return float(E[0]), grad, ((row_ptr, col, val) if want_hess else None)
+
+
+def mass(g, mat, rest, pattern=None):
+    """Nodal mass as 4x4 scalar blocks [nb, 4, 4] (M = m (x) I3) and gravity factors [n, 4]."""
+    row_ptr, col = pattern if pattern is not None else bsr_pattern(g)
+    rest = _f64(rest).reshape(-1)
+    mval = np.zeros((col.size, 4, 4))
+    fs = np.zeros((g.n_nodes, 4))
+    _load().og_mass(C.byref(_grid(g)), C.byref(_mat(mat)), _ptr(rest), _ptr(row_ptr), _ptr(col),
+                    _ptr(mval), _ptr(fs))
+    return mval, fs
+
+
+def bsr_to_dense(row_ptr, col, val):
+    n = row_ptr.size - 1
+    bs = val.shape[1]
+    A = np.zeros((n * bs, n * bs))
+    for i in range(n):
+        for k in range(row_ptr[i], row_ptr[i + 1]):
+            j = col[k]
+            A[i * bs:(i + 1) * bs, j * bs:(j + 1) * bs] += val[k]
+    return A
+
+
+def pcg(row_ptr, col, val, b, mask=None, tau=0.0, rtol=1e-6, max_iter=1000, fixed_iters=0):
+    """Block-Jacobi PCG from x = 0 on the 12x12 BSR; returns (x, iters, status)."""
+    n = row_ptr.size - 1
+    val = _f64(val)
+    b = _f64(b).reshape(-1)
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    x = np.zeros(n * 12)
+    it = C.c_int(0)
+    st = _load().og_pcg(n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(m), float(tau), _ptr(b),
+                        float(rtol), int(max_iter), int(fixed_iters), _ptr(x), C.byref(it))
+    return x, it.value, st
+
+
+def step_params(dt=1e-3, gravity=(0.0, 0.0, -9.81), newton_rtol=1e-8, newton_max=50,
+                pcg_rtol=1e-6, pcg_max=1000, pcg_fixed_iters=0) -> StepParams:
+    return StepParams(float(dt), (C.c_double * 3)(*gravity), float(newton_rtol), int(newton_max),
+                      float(pcg_rtol), int(pcg_max), int(pcg_fixed_iters))
+
+
+def newton_step(g, mat, rest, q, v, params: StepParams, mask=None, qfix=None, warm=None):
+    """One implicit-Euler step. Returns (q_new, v_new, stats dict)."""
+    rest = _f64(rest).reshape(-1)
+    q = _f64(q).reshape(-1).copy()
+    v = _f64(v).reshape(-1).copy()
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    qf = None if qfix is None else _f64(qfix).reshape(-1)
+    w = None if warm is None else _f64(warm).reshape(-1)
+    st = StepStats()
+    _load().og_newton_step(C.byref(_grid(g)), C.byref(_mat(mat)), _ptr(rest), C.byref(params),
+                           _ptr(m), _ptr(qf), _ptr(q), _ptr(v), _ptr(w), C.byref(st))
+    stats = {f: getattr(st, f) for f, _ in StepStats._fields_}
+    return q, v, stats
