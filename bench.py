@@ -1,0 +1,344 @@
+"""Benchmark of the BHEM hot path on GB300: Newton iterations of the implicit-Euler step on a
+256 x 256-patch sheet (66,049 nodes, 792,588 DOF) displaced by the seeded 8-term sinusoid field.
+
+One step = one Newton iteration through shell_newton_step (newton_max = 1): FP64 residual
+(energy + gradient kernels, mass product), FP32 element Hessians of every patch assembled into
+the 12x12 BSR (+ M / dt^2), block-Jacobi set-up, exactly 50 PCG iterations (FP32 SpMV, FP64
+dots), line search with FP64 per-patch energy differences, update and velocity. The metric is
+patch-Hessians/s: patches whose E, 48-gradient and exact 48x48 Hessian were evaluated and
+assembled, per second, with everything else the Newton iteration needs included in the time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload W]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "patch-Hessians/s and Newton steps/s at 1e-8 residual; batched/learned vs plain"
+UNIT = "patch-Hessians/s"
+WORKLOADS = {
+    "sheet256": "256x256-patch 1 m sheet, 8-term sinusoid displacement (5 cm), FP32 element eval "
+                "+ BSR assembly + 50-iteration block-Jacobi PCG, FP64 residual/reductions",
+    "annulus280x5": "280x5-patch periodic annular strip, 8-term sinusoid displacement (5 cm), "
+                    "FP32 element eval + BSR assembly + 50-iteration block-Jacobi PCG, FP64 "
+                    "residual/reductions",
+}
+
+
+def make_workload(name):
+    from paper_2312_14839_gb300 import scenes as S
+    if name == "sheet256":
+        g, rest, q = S.sheet_sinusoid(256, 3)
+    elif name == "annulus280x5":
+        g, rest, q = S.annulus_sinusoid(280, 5, 3)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return g, S.SHEET_MATERIAL, rest, q
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel_src: str, workload: str):
+    """DRAM bytes per SpMV launch from the committed ncu summary, when it was taken on the
+    current kernel source (sha256 recorded in the summary); else None."""
+    path = os.path.join(ROOT, "profiles", f"spmv_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- `"):
+            k, _, v = line.strip()[3:].partition("`:")
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("solver_cu_sha256_16") != h:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(workload: str, n_steps: int = 2, n: int = 48):
+    """The oracle (plain FP64 C, single thread) on a bounded sample of the same workload: the
+    same sinusoid recipe on an n x n sheet, one Newton iteration with exactly 50 PCG iterations
+    per step."""
+    import oracle as O
+    from paper_2312_14839_gb300 import scenes as S
+    if workload == "annulus280x5":
+        g, rest, q = S.annulus_sinusoid(70, 5, 3)
+        sample = "70x5-patch periodic annulus, same recipe"
+    else:
+        g, rest, q = S.sheet_sinusoid(n, 3)
+        sample = f"{n}x{n}-patch sheet, same recipe"
+    P = O.step_params(dt=1e-3, newton_max=1, pcg_fixed_iters=50)
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        O.newton_step(g, S.SHEET_MATERIAL, rest, q.reshape(-1), np.zeros(g.n_dof), P)
+    dt = (time.perf_counter() - t0) / n_steps
+    return {"value": g.n_patches / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample}, {n_steps} x one Newton iteration (50 PCG iterations), "
+                      f"{dt:.2f} s each"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2312_14839_gb300 import scenes as S
+    O.build()
+    n = 32
+    g, rest, q = S.sheet_sinusoid(n, 3) if args.workload == "sheet256" else S.annulus_sinusoid(70, 5, 3)
+    P = O.step_params(dt=1e-3, newton_max=1, pcg_fixed_iters=50)
+    for _ in range(args.warmup):
+        O.newton_step(g, S.SHEET_MATERIAL, rest, q.reshape(-1), np.zeros(g.n_dof), P)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.newton_step(g, S.SHEET_MATERIAL, rest, q.reshape(-1), np.zeros(g.n_dof), P)
+    el = time.perf_counter() - t0
+    v = g.n_patches * args.steps / el
+    sample = (f"{g.nu}x{g.nv}-patch sample of the {args.workload} recipe, one Newton iteration "
+              f"(50 PCG iterations) per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="sheet256", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--spmv-reps", type=int, default=50)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2312_14839_gb300 import bhem
+    bhem.load()
+
+    g, mat, rest, q0 = make_workload(args.workload)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    rest_d = torch.as_tensor(rest.reshape(-1), device=dev)
+    q0_d = torch.as_tensor(q0.reshape(-1), device=dev)
+    sh = bhem.Shell(g, mat, rest_d, precision="mixed", stream=stream)
+    P = bhem.step_params(dt=1e-3, newton_max=1, pcg_fixed_iters=50)
+    q = q0_d.clone()
+    v = torch.zeros_like(q)
+    v0 = torch.zeros_like(q)
+
+    def step():
+        q.copy_(q0_d)
+        v.copy_(v0)
+        return sh.newton_step(q, v, P)
+
+    stats = None
+    for _ in range(args.warmup):
+        stats = step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches0 = sh.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        newton_iters = 0
+        for _ in range(args.steps):
+            stats = step()
+            newton_iters += stats["newton_iters"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = sh.kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        it = torch.tensor([newton_iters], device=dev, dtype=torch.float64)
+        dist.all_reduce(it)
+        total_iters = float(it.item())
+    else:
+        total_iters = float(newton_iters)
+    sec = ms / 1e3
+    value = g.n_patches * total_iters / sec
+
+    # e2e: the same Newton iteration through the C ABI with pinned host buffers (H2D of q, v and
+    # D2H of q, v inside the timed region); the host state evolves step to step.
+    qh = torch.empty(g.n_dof, dtype=torch.float64, pin_memory=True)
+    vh = torch.empty(g.n_dof, dtype=torch.float64, pin_memory=True)
+    qh.copy_(torch.as_tensor(q0.reshape(-1)))
+    vh.zero_()
+    qh_np, vh_np = qh.numpy(), vh.numpy()
+    for _ in range(2):
+        sh.newton_step(qh_np, vh_np, P)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(args.steps):
+        e2e_iters += sh.newton_step(qh_np, vh_np, P)["newton_iters"]
+    torch.cuda.synchronize()
+    e2e_sec = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_sec], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_sec = float(t.item())
+    e2e_value = g.n_patches * e2e_iters * world / e2e_sec
+
+    # roofline of the dominant kernel (the FP32 BSR SpMV: 50 launches per step), timed live with
+    # CUDA events on the shell's stream over back-to-back launches on the assembled matrix
+    sh.energy_grad_hess(q0_d, mass_scale=1.0 / P.dt ** 2, want_energy=False, want_grad=False)
+    x = torch.randn(g.n_dof, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(5):
+        sh.spmv(x, y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.spmv_reps):
+        sh.spmv(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    spmv_s = e0.elapsed_time(e1) / 1e3 / args.spmv_reps
+    nb, n, m = sh.n_blocks, sh.n_nodes, sh.n_dof
+    spmv_bytes = nb * 144 * 4 + nb * 4 + (n + 1) * 4 + m * 8 + m * 8
+    peak, peak_kind = measured_peaks()
+    achieved = spmv_bytes / spmv_s / 1e9
+    traffic = recorded_traffic(os.path.join(ROOT, "paper_2312_14839_gb300", "csrc", "solver.cu"), args.workload)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded sinusoid displacement, no external data)",
+        "config": {"workload": WORKLOADS[args.workload], "patches": g.n_patches, "nodes": g.n_nodes,
+                   "dof": g.n_dof, "bsr_blocks": nb, "newton_iterations_per_step": 1,
+                   "pcg_iterations_per_newton": 50, "precision": "mixed",
+                   "l2": "inputs larger than L2 (FP32 BSR 340 MB)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single GPU"},
+        "newton_steps_per_s": total_iters / sec,
+        "gpu_launches": launches,
+        "last_step_stats": stats,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * m * 8,
+                "d2h_bytes_per_step": 2 * m * 8},
+        "roofline": {"kernel": "k_spmv<float> (FP32 12x12 BSR SpMV)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "traffic": traffic, "algorithmic_bytes_per_launch": spmv_bytes,
+                     "avg_launch_us": spmv_s * 1e6},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sh.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

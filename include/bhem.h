@@ -1,0 +1,191 @@
+/*
+ * bhem.h - C ABI of the GB300 (sm_103a) BHEM shell library (libbhem.so).
+ *
+ * Bicubic Hermite element method for Kirchhoff-Love thin shells (arXiv 2312.14839): per-patch
+ * 4x4 Gauss-point evaluation of the membrane + bending energy, its 48-DOF gradient and 48x48
+ * Hessian, assembly into a 12x12-block sparse (BSR) matrix, and implicit-Euler Newton steps
+ * whose linear systems are solved by block-Jacobi PCG. All compute runs in CUDA kernels of
+ * this library; there is no CPU fallback.
+ *
+ * Conventions used by every entry point
+ *  - Node arrays hold 12 doubles per node, [x, x_,1, x_,2, x_,12] (each in R^3), the
+ *    generalised coordinates of Sec. 4.1 (Eq. hermite): derivative DOFs are derivatives with
+ *    respect to the global parameters xi^1, xi^2. Node (i, j) has id j * n1 + i, i along xi^1,
+ *    n1 = nu + 1 (nu when periodic in u), n2 = nv + 1 (nv when periodic in v).
+ *  - Patch (pu, pv) has id pv * nu + pu; its corners 00, 10, 01, 11 are nodes (pu+p, pv+q)
+ *    (indices wrap when periodic, Sec. 4.2). Patch-local DOF order is corner * 12 + kind * 3 +
+ *    component, kind in {x, x_,1, x_,2, x_,12}.
+ *  - "device" pointers are CUDA device (or managed) memory owned by the caller. Entry points
+ *    that accept "host or device" detect the kind with cudaPointerGetAttributes and stage host
+ *    buffers through library-owned device memory.
+ *  - All GPU work is enqueued on the stream given to shell_create (a cudaStream_t passed as
+ *    void*; NULL means the legacy default stream). Entry points that return host values
+ *    (stats, flags) synchronise that stream; the others are asynchronous.
+ *  - Errors are returned as shell_status codes, never thrown. shell_last_error() gives a
+ *    thread-local message for the last failing call. Outputs are unspecified after an error,
+ *    except where stated.
+ */
+#ifndef BHEM_H
+#define BHEM_H
+
+#if defined(__GNUC__)
+#define SHELL_API __attribute__((visibility("default")))
+#else
+#define SHELL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct shell_s shell_t;
+
+typedef enum {
+  SHELL_OK = 0,
+  SHELL_ERR_ARG = 1,            /* invalid argument (NULL, size, enum value)                   */
+  SHELL_ERR_CUDA = 2,           /* a CUDA runtime call failed                                   */
+  SHELL_ERR_OOM = 3,            /* device allocation failed                                     */
+  SHELL_ERR_DEGENERATE = 4,     /* |a_1 x a_2| <= 1e-300 at a Gauss point (no normal, Sec. 3.1) */
+  SHELL_ERR_NONFINITE = 5,      /* a non-finite energy, gradient or residual was produced      */
+  SHELL_ERR_NOT_CONVERGED = 6,  /* Newton hit newton_max; q, v hold the last iterate            */
+  SHELL_ERR_LINESEARCH = 7,     /* no step satisfied the Armijo test in 20 trials               */
+  SHELL_ERR_INDEFINITE = 8,     /* negative curvature persisted up to tau = 1e4                 */
+  SHELL_ERR_TIMEOUT = 9         /* reserved: a bounded device-side wait expired                 */
+} shell_status;
+
+/* Patch grid (Sec. 4.1, Fig. regular; periodic boundary conditions of Sec. 4.2). dxi1, dxi2
+   are the parameter extents of one patch (uniform grid). */
+typedef struct {
+  int nu, nv;
+  int periodic_u, periodic_v;
+  double dxi1, dxi2;
+} shell_grid;
+
+/* Material (Sec. 3.3): Young's modulus Y, Poisson ratio nu, thickness h, density rho.
+   lambda = Y nu / (1 - nu^2), mu = Y / (2 (1 + nu)). */
+typedef struct {
+  double young, poisson, thickness, density;
+} shell_material;
+
+enum { SHELL_PREC_FP64 = 0, SHELL_PREC_MIXED = 1 };
+enum { SHELL_HESS_EXACT = 0, SHELL_HESS_PSEUDO = 1 };
+enum { SHELL_ASM_ATOMIC = 0, SHELL_ASM_COLOR = 1 };
+
+/* precision: SHELL_PREC_FP64 = every quantity in FP64; SHELL_PREC_MIXED = element Hessian,
+   BSR values, SpMV and block-Jacobi in FP32, while the energy, gradient/residual, line-search
+   energy differences and PCG dot products stay FP64.
+   hessian: exact (App. B.2) or the pseudo Hessian of App. B.2 without the second derivative of
+   beta. assembly: atomic scatter or 4-colour ordered scatter of the element blocks. */
+typedef struct {
+  int precision;
+  int hessian;
+  int assembly;
+  int reserved;
+} shell_options;
+
+/* One implicit-Euler step (Eq. implicit, Sec. 6.1). Newton stops when |g_free| <= newton_rtol *
+   |g_free(zero guess)|; PCG stops when |r| <= pcg_rtol |b| or after pcg_max iterations, or
+   runs exactly pcg_fixed_iters iterations when that is > 0. */
+typedef struct {
+  double dt;
+  double gravity[3];
+  double newton_rtol;
+  int newton_max;
+  double pcg_rtol;
+  int pcg_max;
+  int pcg_fixed_iters;
+} shell_step_params;
+
+typedef struct {
+  int newton_iters;       /* Newton updates applied                                         */
+  int pcg_iters_total;    /* PCG iterations over all solves (regularised restarts included) */
+  int ls_backtracks;      /* rejected line-search trials                                    */
+  int regularizations;    /* restarts with tau |diag(A)| added (Sec. 6.1 regulariser)       */
+  int status;             /* shell_status of the step                                       */
+  double res0;            /* |g_free| at the zero guess                                     */
+  double res_final;       /* |g_free| at the returned state                                 */
+} shell_step_stats;
+
+typedef struct {
+  int n_nodes, n_patches, n_blocks, n_dof;
+} shell_info_t;
+
+/* Creates a shell on the current CUDA device. rest_dofs: host or device, [n_nodes * 12] FP64,
+   the reference configuration (copied). Builds the BSR pattern (Sec. 4.3 "Properties of the mass
+   matrix": two nodes couple iff they share a patch), the consistent mass M (Eq. mass) and the
+   gravity load factors (Sec. 4.3), all with the 4x4 Gauss rule of App. A.2. *out receives an
+   opaque handle owned by the caller (release with shell_destroy). stream: cudaStream_t. */
+SHELL_API shell_status shell_create(const shell_grid* grid, const shell_material* material,
+                          const double* rest_dofs, const shell_options* options, void* stream,
+                          shell_t** out);
+
+/* Frees every device buffer of the shell (synchronises its stream first). NULL is allowed. */
+SHELL_API shell_status shell_destroy(shell_t* shell);
+
+/* Sizes of the shell (host output). */
+SHELL_API shell_status shell_info(const shell_t* shell, shell_info_t* info);
+
+/* Element-by-element evaluation, unassembled (App. B): for every patch p, energy_p[p] (FP64),
+   grad_p[p * 48 + l] (FP64) and hess_p[p * 2304 + l * 48 + m] (FP32 when precision is
+   SHELL_PREC_MIXED, FP64 when SHELL_PREC_FP64), l, m patch-local DOF indices. q: device
+   [n_nodes * 12]. Any output may be NULL. Asynchronous. */
+SHELL_API shell_status shell_element_egh(shell_t* shell, const double* q, int precision, double* energy_p,
+                               double* grad_p, void* hess_p);
+
+/* Assembled elastic energy V_e (device, 1 double), elastic gradient dV_e/dq (device
+   [n_nodes * 12], App. B.1) and, when want_hessian != 0, the BSR matrix K + mass_scale * M
+   (App. B.2 Hessian, Eq. mass) into the shell's internal BSR (read with shell_get_bsr).
+   energy or grad may be NULL. Asynchronous. */
+SHELL_API shell_status shell_energy_grad_hess(shell_t* shell, const double* q, double mass_scale,
+                                    double* energy, double* grad, int want_hessian);
+
+/* Internal BSR arrays (device, valid until the next call that assembles or shell_destroy):
+   row_ptr[n_nodes + 1], col[n_blocks] (sorted per row), val[n_blocks * 144] 12x12 row-major
+   blocks, FP32 (*val_is_fp64 = 0) or FP64 (*val_is_fp64 = 1). Both triangles are stored. */
+SHELL_API shell_status shell_get_bsr(shell_t* shell, const int** row_ptr, const int** col,
+                           const void** val, int* val_is_fp64);
+
+/* Consistent mass as 4x4 scalar blocks on the same pattern (device, [n_blocks * 16], M =
+   mass (x) I3 per node pair, Eq. mass) and gravity load factors (device, [n_nodes * 4],
+   F = factors (x) g, Sec. 4.3). */
+SHELL_API shell_status shell_get_mass(shell_t* shell, const double** mass_blocks,
+                            const double** gravity_factors);
+
+/* Block-Jacobi PCG on the currently assembled BSR A: solves (A + tau |diag(A)|) x = rhs with
+   fixed DOFs (mask != 0) held at zero (identity rows/columns). rhs, x: device [n_dof];
+   fixed_mask: device [n_dof] or NULL. Runs until |r| <= rtol |rhs| or max_iter, or exactly
+   fixed_iters (> 0) iterations. *iters receives the iterations done, *neg_curv 1 when
+   p^T A p <= 0 stopped it. Synchronises. */
+SHELL_API shell_status shell_pcg_solve(shell_t* shell, const unsigned char* fixed_mask, double tau,
+                             const double* rhs, double* x, double rtol, int max_iter,
+                             int fixed_iters, int* iters, int* neg_curv);
+
+/* y = A x with the currently assembled BSR A (the product inside every PCG iteration of
+   Sec. 6.1's linear solve; FP32 arithmetic with FP32 accumulation per row chunk when the shell
+   is SHELL_PREC_MIXED, FP64 otherwise). x (16-byte aligned), y (8-byte aligned): device
+   [n_dof] FP64. No mask, no regulariser. Asynchronous; one kernel launch. */
+SHELL_API shell_status shell_spmv(shell_t* shell, const double* x, double* y);
+
+/* One implicit-Euler step (Eq. implicit) by Newton with line search (Sec. 6.1):
+   minimises Pi(q) = (q - y)^T M (q - y) / (2 dt^2) + V_e(q) - F^T q, y = q^n + dt v^n, over the
+   free DOFs; fixed DOFs (fixed_mask[k] != 0) take q_fixed[k] (Sec. 4.2 positional constraints).
+   q, v: [n_dof] FP64 in/out (host or device); fixed_mask [n_dof] uint8 and q_fixed [n_dof]
+   (host or device, may be NULL together); warm_start [n_dof] or NULL: initial Newton iterate
+   (the residual reference stays the zero guess q^n). stats: host. Returns stats->status. On
+   SHELL_ERR_NOT_CONVERGED q and v hold the last iterate; on other errors they are unchanged. */
+SHELL_API shell_status shell_newton_step(shell_t* shell, const shell_step_params* params,
+                               const unsigned char* fixed_mask, const double* q_fixed,
+                               double* q, double* v, const double* warm_start,
+                               shell_step_stats* stats);
+
+/* Number of CUDA kernels this shell has launched since shell_create (host counter; counts the
+   launches of the library's own kernels, not memset/memcpy operations). */
+SHELL_API shell_status shell_kernel_launches(const shell_t* shell, long long* count);
+
+/* Thread-local message describing the last error ("" if none). */
+SHELL_API const char* shell_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BHEM_H */

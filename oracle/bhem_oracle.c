@@ -28,9 +28,11 @@
  *   - Line search: Armijo (c1 = 1e-4) from alpha = 1, then a quadratic and afterwards cubic
  *     interpolation (Nocedal-Wright Sec. 3.5), each clamped to [0.1, 0.5] of the last step, at
  *     most 20 trials; alpha = 1 is accepted without a test once |g| <= 1e-6 |g_ref|.
- *   - Regulariser: PCG stops on p^T A p <= 0; the solve restarts on A + tau diag(A) with
- *     tau = 1e-8, 1e-7, ..., 1e-2, then gives up. A 12x12 block that is not SPD is replaced by
- *     the inverse of its diagonal in the block-Jacobi preconditioner.
+ *   - Regulariser (Sec. 6.1 gives no form or magnitude): PCG stops on p^T A p <= 0; the solve
+ *     restarts on A + tau |diag(A)| with tau = 1e-8, 1e-6, ..., 1e4 (x100 per restart), then
+ *     gives up. |diag(A)| rather than diag(A) because A may have negative diagonal entries
+ *     under compression, which tau diag(A) would make more negative. A 12x12 block that is not
+ *     SPD is replaced by the inverse of its diagonal in the block-Jacobi preconditioner.
  */
 #include <math.h>
 #include <stdint.h>
@@ -523,7 +525,7 @@ static void mass_mult(int n, const int* row_ptr, const int* col, const double* m
 /* ------------------------------------------------------------------------------------------ */
 /* Block-Jacobi PCG (replaces the direct LDL^T solve of Sec. 6.1).                              */
 /* A is the 12x12 BSR; fixed DOFs (mask != 0) get identity rows and columns. tau adds           */
-/* tau * diag(A) to the free diagonal (the regulariser).                                       */
+/* tau * |diag(A)| to the free diagonal (the regulariser).                                     */
 /* ------------------------------------------------------------------------------------------ */
 static void bsr_mult(int n, const int* row_ptr, const int* col, const double* val,
                      const unsigned char* mask, double tau, const double* diag,
@@ -541,7 +543,7 @@ static void bsr_mult(int n, const int* row_ptr, const int* col, const double* va
           acc += val[(size_t)k*144 + r*12 + s] * x[gj];
         }
       }
-      y[gi] = acc + tau * diag[gi] * x[gi];
+      y[gi] = acc + tau * fabs(diag[gi]) * x[gi];
     }
   }
 }
@@ -587,7 +589,7 @@ static void block_jacobi(int n, const int* row_ptr, const int* col, const double
       int fr = mask && mask[i*12 + r], fs = mask && mask[i*12 + s];
       double v = val[(size_t)k*144 + r*12 + s];
       if (fr || fs) v = (r == s) ? 1.0 : 0.0;
-      else if (r == s) v += tau * diag[i*12 + r];
+      else if (r == s) v += tau * fabs(diag[i*12 + r]);
       A[r*12 + s] = v;
     }
     if (!chol_inverse12(A, &D[(size_t)i*144])) {
@@ -743,7 +745,7 @@ int og_newton_step(const og_grid* g, const og_material* mat, const double* rest,
     if (it >= P->newton_max) { status = OG_ERR_NOT_CONVERGED; break; }
     og_assemble(g, mat, rest, q, row_ptr, col, 1.0 / (P->dt * P->dt), NULL, NULL, val);
     for (int i = 0; i < m; ++i) rhs[i] = -gr[i];
-    /* tau = 0, then 1e-8, 1e-7, ..., 1e-2 */
+    /* tau = 0, then 1e-8, 1e-6, ..., 1e4 */
     double tau = 0.0;
     int piters = 0, ps;
     for (int reg = 0;; ++reg) {
@@ -753,7 +755,7 @@ int og_newton_step(const og_grid* g, const og_material* mat, const double* rest,
       if (ps != OG_PCG_NEG_CURV) break;
       if (reg == 7) { status = OG_ERR_INDEFINITE; break; }
       st->regularizations++;
-      tau = 1e-8 * pow(10.0, reg);
+      tau = 1e-8 * pow(100.0, reg);
     }
     if (status != OG_OK) break;
 

@@ -1,0 +1,259 @@
+"""Thin ctypes binding of libbhem (include/bhem.h): argument marshalling only.
+
+Every step of the BHEM hot path runs in the library's CUDA kernels; this module passes pointers
+(torch CUDA tensors, or host numpy arrays where the C ABI accepts host buffers) and sizes. There
+is no CPU fallback: if the library cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+PREC = {"fp64": 0, "mixed": 1}
+HESS = {"exact": 0, "pseudo": 1}
+ASM = {"atomic": 0, "color": 1}
+STATUS = {0: "SHELL_OK", 1: "SHELL_ERR_ARG", 2: "SHELL_ERR_CUDA", 3: "SHELL_ERR_OOM",
+          4: "SHELL_ERR_DEGENERATE", 5: "SHELL_ERR_NONFINITE", 6: "SHELL_ERR_NOT_CONVERGED",
+          7: "SHELL_ERR_LINESEARCH", 8: "SHELL_ERR_INDEFINITE", 9: "SHELL_ERR_TIMEOUT"}
+
+
+class ShellError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class shell_grid(C.Structure):
+    _fields_ = [("nu", C.c_int), ("nv", C.c_int), ("periodic_u", C.c_int), ("periodic_v", C.c_int),
+                ("dxi1", C.c_double), ("dxi2", C.c_double)]
+
+
+class shell_material(C.Structure):
+    _fields_ = [("young", C.c_double), ("poisson", C.c_double), ("thickness", C.c_double),
+                ("density", C.c_double)]
+
+
+class shell_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("hessian", C.c_int), ("assembly", C.c_int),
+                ("reserved", C.c_int)]
+
+
+class shell_step_params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("gravity", C.c_double * 3), ("newton_rtol", C.c_double),
+                ("newton_max", C.c_int), ("pcg_rtol", C.c_double), ("pcg_max", C.c_int),
+                ("pcg_fixed_iters", C.c_int)]
+
+
+class shell_step_stats(C.Structure):
+    _fields_ = [("newton_iters", C.c_int), ("pcg_iters_total", C.c_int),
+                ("ls_backtracks", C.c_int), ("regularizations", C.c_int), ("status", C.c_int),
+                ("res0", C.c_double), ("res_final", C.c_double)]
+
+
+class shell_info_t(C.Structure):
+    _fields_ = [("n_nodes", C.c_int), ("n_patches", C.c_int), ("n_blocks", C.c_int),
+                ("n_dof", C.c_int)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads libbhem.so, building it with nvcc first when it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libbhem.so not found at {path}")
+            lib = C.CDLL(path)
+            p, i, d = C.c_void_p, C.c_int, C.c_double
+            sigs = {
+                "shell_create": [p, p, p, p, p, p],
+                "shell_destroy": [p],
+                "shell_info": [p, p],
+                "shell_element_egh": [p, p, i, p, p, p],
+                "shell_energy_grad_hess": [p, p, d, p, p, i],
+                "shell_get_bsr": [p, p, p, p, p],
+                "shell_get_mass": [p, p, p],
+                "shell_pcg_solve": [p, p, d, p, p, d, i, i, p, p],
+                "shell_newton_step": [p, p, p, p, p, p, p, p],
+                "shell_spmv": [p, p, p],
+                "shell_kernel_launches": [p, p],
+            }
+            for name, args in sigs.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = C.c_int
+            lib.shell_last_error.restype = C.c_char_p
+            lib.shell_last_error.argtypes = []
+            _lib = lib
+        return _lib
+
+
+def _check(st: int):
+    if st != 0:
+        raise ShellError(st, load().shell_last_error().decode())
+
+
+def _ptr(t):
+    """Raw pointer of a torch tensor (device or host) or numpy array; None stays NULL."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(t.data_ptr())
+
+
+class _DevArray:
+    """Zero-copy view of library-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), True), "version": 3, "strides": None}
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream, C.c_void_p(stream.cuda_stream)
+
+
+def step_params(dt=1e-3, gravity=(0.0, 0.0, -9.81), newton_rtol=1e-8, newton_max=50,
+                pcg_rtol=1e-6, pcg_max=1000, pcg_fixed_iters=0) -> shell_step_params:
+    return shell_step_params(float(dt), (C.c_double * 3)(*gravity), float(newton_rtol),
+                             int(newton_max), float(pcg_rtol), int(pcg_max), int(pcg_fixed_iters))
+
+
+class Shell:
+    """One BHEM shell on the current CUDA device (wraps shell_create ... shell_destroy)."""
+
+    def __init__(self, grid, material, rest, precision="mixed", hessian="exact",
+                 assembly="atomic", stream=None):
+        import torch
+        lib = load()
+        self.grid = grid
+        self.material = material
+        self.precision = precision
+        self.stream, sh = _stream_handle(stream)
+        g = shell_grid(int(grid.nu), int(grid.nv), int(bool(grid.periodic_u)),
+                       int(bool(grid.periodic_v)), float(grid.dxi1), float(grid.dxi2))
+        m = shell_material(float(material.young), float(material.poisson),
+                           float(material.thickness), float(material.density))
+        o = shell_options(PREC[precision], HESS[hessian], ASM[assembly], 0)
+        if isinstance(rest, np.ndarray):
+            rest = np.ascontiguousarray(rest, dtype=np.float64)
+        else:
+            rest = rest.contiguous().to(torch.float64)
+        self._h = C.c_void_p()
+        _check(lib.shell_create(C.byref(g), C.byref(m), _ptr(rest), C.byref(o), sh, C.byref(self._h)))
+        info = shell_info_t()
+        _check(lib.shell_info(self._h, C.byref(info)))
+        self.n_nodes, self.n_patches = info.n_nodes, info.n_patches
+        self.n_blocks, self.n_dof = info.n_blocks, info.n_dof
+
+    # ------------------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            load().shell_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------------------------------
+    def element_egh(self, q, precision=None, want=("e", "g", "h")):
+        """Unassembled per-patch (E [np], grad [np, 48], hess [np, 48, 48]) as torch tensors."""
+        import torch
+        prec = PREC[precision or self.precision]
+        dev = q.device
+        E = torch.empty(self.n_patches, dtype=torch.float64, device=dev) if "e" in want else None
+        G = torch.empty(self.n_patches, 48, dtype=torch.float64, device=dev) if "g" in want else None
+        hd = torch.float64 if prec == 0 else torch.float32
+        H = torch.empty(self.n_patches, 48, 48, dtype=hd, device=dev) if "h" in want else None
+        _check(load().shell_element_egh(self._h, _ptr(q), prec, _ptr(E), _ptr(G), _ptr(H)))
+        return E, G, H
+
+    def energy_grad_hess(self, q, mass_scale=0.0, want_hessian=True, want_energy=True,
+                         want_grad=True):
+        """Assembled elastic energy (device scalar), gradient [n_dof]; Hessian into the BSR."""
+        import torch
+        dev = q.device
+        E = torch.empty(1, dtype=torch.float64, device=dev) if want_energy else None
+        G = torch.empty(self.n_dof, dtype=torch.float64, device=dev) if want_grad else None
+        _check(load().shell_energy_grad_hess(self._h, _ptr(q), float(mass_scale), _ptr(E), _ptr(G),
+                                             int(bool(want_hessian))))
+        return E, G
+
+    def bsr(self):
+        """Copies of (row_ptr [n+1], col [nb], val [nb, 12, 12]) of the assembled matrix."""
+        import torch
+        rp, col, val, f64 = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_int()
+        _check(load().shell_get_bsr(self._h, C.byref(rp), C.byref(col), C.byref(val), C.byref(f64)))
+        dev = torch.device("cuda", torch.cuda.current_device())
+        t_rp = torch.as_tensor(_DevArray(rp.value, (self.n_nodes + 1,), "<i4"), device=dev).clone()
+        t_col = torch.as_tensor(_DevArray(col.value, (self.n_blocks,), "<i4"), device=dev).clone()
+        t_val = torch.as_tensor(_DevArray(val.value, (self.n_blocks, 12, 12), "<f8" if f64.value else "<f4"),
+                                device=dev).clone()
+        return t_rp, t_col, t_val
+
+    def mass(self):
+        """Copies of the 4x4-block consistent mass [nb, 4, 4] and gravity factors [n, 4]."""
+        import torch
+        mb, fg = C.c_void_p(), C.c_void_p()
+        _check(load().shell_get_mass(self._h, C.byref(mb), C.byref(fg)))
+        dev = torch.device("cuda", torch.cuda.current_device())
+        M = torch.as_tensor(_DevArray(mb.value, (self.n_blocks, 4, 4), "<f8"), device=dev).clone()
+        F = torch.as_tensor(_DevArray(fg.value, (self.n_nodes, 4), "<f8"), device=dev).clone()
+        return M, F
+
+    def pcg_solve(self, rhs, mask=None, tau=0.0, rtol=1e-6, max_iter=1000, fixed_iters=0):
+        import torch
+        x = torch.empty_like(rhs)
+        it, neg = C.c_int(), C.c_int()
+        _check(load().shell_pcg_solve(self._h, _ptr(mask), float(tau), _ptr(rhs), _ptr(x), float(rtol),
+                                      int(max_iter), int(fixed_iters), C.byref(it), C.byref(neg)))
+        return x, it.value, neg.value
+
+    def kernel_launches(self) -> int:
+        n = C.c_longlong()
+        _check(load().shell_kernel_launches(self._h, C.byref(n)))
+        return n.value
+
+    def spmv(self, x, y=None):
+        """y = A x with the assembled BSR (one kernel launch on the shell's stream)."""
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        _check(load().shell_spmv(self._h, _ptr(x), _ptr(y)))
+        return y
+
+    def newton_step(self, q, v, params: shell_step_params, mask=None, q_fixed=None, warm=None,
+                    raise_on_error=False):
+        """In-place implicit-Euler step on q, v (torch CUDA tensors or host numpy arrays)."""
+        st = shell_step_stats()
+        rc = load().shell_newton_step(self._h, C.byref(params), _ptr(mask), _ptr(q_fixed), _ptr(q),
+                                      _ptr(v), _ptr(warm), C.byref(st))
+        stats = {f: getattr(st, f) for f, _ in shell_step_stats._fields_}
+        if rc != 0 and (raise_on_error or rc not in (6, 7, 8)):
+            raise ShellError(rc, load().shell_last_error().decode())
+        return stats

@@ -1,0 +1,218 @@
+// Internal declarations of libbhem (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "bhem.h"
+
+namespace bhem {
+
+// ------------------------------------------------------------------------------------------
+// Error handling: every entry point returns a shell_status and records a thread-local message.
+// ------------------------------------------------------------------------------------------
+void set_error(const std::string& msg);
+shell_status fail(shell_status st, const std::string& msg);
+
+#define BHEM_CUDA(call)                                                                   \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return ::bhem::fail(SHELL_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define BHEM_TRY(call)                          \
+  do {                                          \
+    shell_status s_ = (call);                   \
+    if (s_ != SHELL_OK) return s_;              \
+  } while (0)
+
+// Device-side error bits (OR-ed into Shell::d_err, read back at synchronising calls).
+enum : int { ERRBIT_DEGENERATE = 1, ERRBIT_NONFINITE = 2 };
+
+// ------------------------------------------------------------------------------------------
+// Deterministic grid reductions: each CTA writes a partial, the last CTA to arrive (atomic
+// ticket, no waiting) sums the partials in CTA order and resets the ticket.
+// ------------------------------------------------------------------------------------------
+constexpr int kMaxRed = 4;              // values reduced together
+constexpr int kMaxPartials = 1 << 17;   // CTAs per reduced kernel (checked at launch)
+
+struct Reduce {
+  double* partials;    // [kMaxRed * kMaxPartials]
+  unsigned* ticket;    // one counter
+};
+
+// Scalars of one PCG solve, resident in device memory.
+struct PcgState {
+  double rz, pq, alpha, beta, rr, bb;
+  double rtol2;        // rtol^2 (0 disables the residual test)
+  int iters, done, negcurv, fixed;
+};
+
+// Scalars of one Newton step.
+struct NewtonScalars {
+  double gnorm2;       // |g_free|^2
+  double dots[3];      // d.Md, d.g_inert, d.g
+  double dV;           // sum_p (E_p(q + a d) - E_p(q))
+  double energy;       // assembled elastic energy
+};
+
+// ------------------------------------------------------------------------------------------
+// Shell: everything lives in device memory owned by the library.
+// ------------------------------------------------------------------------------------------
+struct Shell {
+  shell_grid grid;
+  shell_material mat;
+  shell_options opt;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int n1 = 0, n2 = 0, n_nodes = 0, n_patches = 0, n_blocks = 0, n_dof = 0;
+  double lam = 0, mu = 0;
+
+  // topology
+  int4* d_patch_nodes = nullptr;    // [np] corner node ids 00, 10, 01, 11
+  int* d_patch_blocks = nullptr;    // [np * 16] BSR block of corner pair (a, b) at a * 4 + b
+  int* d_row_ptr = nullptr;         // [n_nodes + 1]
+  int* d_col = nullptr;             // [n_blocks]
+  int* d_diag_block = nullptr;      // [n_nodes]
+  int* d_color_start = nullptr;     // unused by the atomic path
+  int* h_color_patches = nullptr;   // host copy of colour offsets (5 ints)
+  int* d_color_list = nullptr;      // [np] patches ordered by colour
+
+  // reference configuration
+  double* d_rest = nullptr;         // [n_dof]
+  double* d_restgp = nullptr;       // [13 * np * 16] per-Gauss-point rest data (SoA)
+  double* d_mass = nullptr;         // [n_blocks * 16] consistent mass, 4x4 scalar blocks
+  double* d_fgrav = nullptr;        // [n_nodes * 4] gravity load factors
+
+  // assembled matrix
+  void* d_val = nullptr;            // [n_blocks * 144] FP32 or FP64
+  int val_fp64 = 0;
+
+  // PCG workspace
+  double *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_Ap = nullptr;
+  double* d_diagA = nullptr;        // [n_dof] diagonal of A (regulariser)
+  void* d_Dinv = nullptr;           // [n_nodes * 144] block-Jacobi inverses (FP32 or FP64)
+  PcgState* d_pcg = nullptr;
+
+  // Newton workspace
+  double *d_qn = nullptr, *d_y = nullptr, *d_g = nullptr, *d_gin = nullptr, *d_d = nullptr;
+  double *d_Md = nullptr, *d_Ep = nullptr, *d_qwork = nullptr, *d_vwork = nullptr;
+  double *d_qfix = nullptr, *d_warm = nullptr, *d_rhs = nullptr;
+  unsigned char* d_mask = nullptr;
+  NewtonScalars* d_ns = nullptr;
+  NewtonScalars* h_ns = nullptr;    // pinned
+  PcgState* h_pcg = nullptr;        // pinned
+  int* d_err = nullptr;
+  int* h_err = nullptr;             // pinned
+  double* d_energy_tmp = nullptr;
+
+  Reduce red{};
+  long long launches = 0;           // kernels launched by this shell (introspection)
+};
+
+// ------------------------------------------------------------------------------------------
+// Kernels launchers (element.cu, solver.cu)
+// ------------------------------------------------------------------------------------------
+// rest per-Gauss-point data, mass, gravity factors (once per shell)
+shell_status launch_rest_setup(Shell& s);
+
+// Heavy element kernel: energy/gradient/Hessian per patch (one warp per patch).
+//   hess_out: unassembled [np*2304] of R, or nullptr; bsr: assembled BSR (R) or nullptr.
+struct ElemOutputs {
+  double* energy_p = nullptr;   // [np]
+  double* grad_p = nullptr;     // [np * 48]
+  void* hess_p = nullptr;       // [np * 2304]
+  void* bsr = nullptr;          // assembled values
+  double mass_scale = 0.0;      // adds mass_scale * M to the assembled / unassembled Hessian
+  int pseudo = 0;               // drop the second derivative of beta
+};
+shell_status launch_element_full(Shell& s, const double* q, bool fp64, const ElemOutputs& out);
+
+// Light FP64 kernel: per-patch energy (and assembled gradient) at q + step * dir.
+//   mode 0: energy_p[p] = E_p, grad += dE/dq (grad may be null), total -> scal_out
+//   mode 1: total of (E_p(q + step dir) - energy_ref[p]) -> scal_out (no gradient)
+shell_status launch_energy_grad64(Shell& s, const double* q, const double* dir, double step,
+                                  double* energy_p, const double* energy_ref, double* grad,
+                                  double* scal_out);
+
+// Solver kernels (solver.cu)
+shell_status launch_grad_finish(Shell& s, const double* q, const double* y, double dt,
+                                const double grav[3], const unsigned char* mask, double* g,
+                                double* gin, double* gnorm2_out);
+shell_status launch_mass_mult(Shell& s, const double* x, double* y);
+shell_status launch_dots3(Shell& s, int n, const double* a0, const double* b0, const double* a1,
+                          const double* b1, const double* a2, const double* b2, double* out3);
+shell_status launch_precond_setup(Shell& s, const unsigned char* mask, double tau);
+shell_status launch_pcg_init(Shell& s, const unsigned char* mask, const double* rhs,
+                             double rtol, int fixed);
+shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, double tau);
+shell_status launch_spmv(Shell& s, const double* x, double* y);
+shell_status launch_axpy_fixed(Shell& s, double* q, const double* d, double alpha);
+shell_status launch_overwrite_fixed(Shell& s, double* dst, const double* src,
+                                    const unsigned char* mask, const double* fixed_vals);
+shell_status launch_predictor(Shell& s, const double* qn, const double* v, double dt, double* y);
+shell_status launch_velocity(Shell& s, const double* q, const double* qn, double dt, double* v);
+shell_status launch_negate(Shell& s, const double* a, double* b);
+
+int grid_for(long long work, int per_block);
+
+// ------------------------------------------------------------------------------------------
+// Deterministic grid reduction of NV doubles (every thread of every CTA must call it): the
+// per-CTA sums go to red.partials; the last CTA to take a ticket sums them in CTA order into
+// out[0..NV) and returns true (in all of its threads). Nothing waits on other CTAs.
+// ------------------------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(const double (&v)[NV], Reduce red, double* out,
+                                            int nblocks) {
+  __shared__ double sred[NV][32];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  double x[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    x[i] = v[i];
+    for (int o = 16; o > 0; o >>= 1) x[i] += __shfl_xor_sync(0xffffffffu, x[i], o);
+  }
+  if (lane == 0)
+    for (int i = 0; i < NV; ++i) sred[i][wid] = x[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NV; ++i) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += sred[i][w];
+      red.partials[(size_t)i * kMaxPartials + blockIdx.x] = s;
+    }
+    __threadfence();
+    unsigned t = atomicAdd(red.ticket, 1u);
+    last = (t == (unsigned)nblocks - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  for (int i = 0; i < NV; ++i) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+      s += ((volatile double*)red.partials)[(size_t)i * kMaxPartials + b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if (lane == 0) sred[i][wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < nw; ++w) tot += sred[i][w];
+      out[i] = tot;
+    }
+  }
+  if (threadIdx.x == 0) *red.ticket = 0u;
+  __syncthreads();
+  return true;
+}
+
+}  // namespace bhem
+
+// The opaque handle of the C ABI.
+struct shell_s : public bhem::Shell {};

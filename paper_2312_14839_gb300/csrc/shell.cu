@@ -1,0 +1,543 @@
+// C ABI of libbhem: shell set-up, element evaluation, assembly, PCG and the implicit-Euler Newton
+// step (Sec. 6.1). Host code here only orchestrates; every arithmetic step of the hot path runs
+// in the kernels of element.cu and solver.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace bhem {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+shell_status fail(shell_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+template <typename T>
+static shell_status dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(SHELL_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return SHELL_OK;
+}
+
+static void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// ------------------------------------------------------------------------------------------
+// Topology of the structured patch grid (Sec. 4.1) with periodic wrap (Sec. 4.2).
+// ------------------------------------------------------------------------------------------
+struct HostTopo {
+  std::vector<int4> pnodes;
+  std::vector<int> row_ptr, col, pblocks, diag, color_list;
+  int color_off[10];
+};
+
+static void build_topology(const shell_grid& g, int n1, int n2, HostTopo& T) {
+  const int np = g.nu * g.nv, n = n1 * n2;
+  T.pnodes.resize(np);
+  for (int pv = 0; pv < g.nv; ++pv)
+    for (int pu = 0; pu < g.nu; ++pu) {
+      int i0 = pu % n1, i1 = (pu + 1) % n1, j0 = pv % n2, j1 = (pv + 1) % n2;
+      T.pnodes[pv * g.nu + pu] = make_int4(j0 * n1 + i0, j0 * n1 + i1, j1 * n1 + i0, j1 * n1 + i1);
+    }
+  std::vector<std::vector<int>> nb(n);
+  for (int p = 0; p < np; ++p) {
+    int nd[4] = {T.pnodes[p].x, T.pnodes[p].y, T.pnodes[p].z, T.pnodes[p].w};
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) nb[nd[a]].push_back(nd[b]);
+  }
+  T.row_ptr.assign(n + 1, 0);
+  T.col.clear();
+  for (int i = 0; i < n; ++i) {
+    auto& v = nb[i];
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+    T.row_ptr[i] = (int)T.col.size();
+    T.col.insert(T.col.end(), v.begin(), v.end());
+  }
+  T.row_ptr[n] = (int)T.col.size();
+  auto find = [&](int r, int c) {
+    auto b = T.col.begin() + T.row_ptr[r], e = T.col.begin() + T.row_ptr[r + 1];
+    return (int)(std::lower_bound(b, e, c) - T.col.begin());
+  };
+  T.pblocks.resize((size_t)np * 16);
+  for (int p = 0; p < np; ++p) {
+    int nd[4] = {T.pnodes[p].x, T.pnodes[p].y, T.pnodes[p].z, T.pnodes[p].w};
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) T.pblocks[(size_t)p * 16 + a * 4 + b] = find(nd[a], nd[b]);
+  }
+  T.diag.resize(n);
+  for (int i = 0; i < n; ++i) T.diag[i] = find(i, i);
+  // colours: patches of one colour share no node (3 colours along a periodic odd direction)
+  int cu = (g.periodic_u && (g.nu % 2)) ? 3 : 2, cv = (g.periodic_v && (g.nv % 2)) ? 3 : 2;
+  std::vector<int> cnt(10, 0);
+  std::vector<int> colr(np);
+  for (int p = 0; p < np; ++p) {
+    int pu = p % g.nu, pv = p / g.nu;
+    colr[p] = (pu % cu) + cu * (pv % cv);
+    cnt[colr[p] + 1]++;
+  }
+  for (int c = 0; c < 9; ++c) cnt[c + 1] += cnt[c];
+  for (int c = 0; c < 10; ++c) T.color_off[c] = cnt[c];
+  T.color_list.assign(np, 0);
+  std::vector<int> pos(cnt.begin(), cnt.begin() + 9);
+  for (int p = 0; p < np; ++p) T.color_list[pos[colr[p]]++] = p;
+}
+
+static void destroy_shell(shell_s* s) {
+  if (!s) return;
+  void* ptrs[] = {s->d_patch_nodes, s->d_patch_blocks, s->d_row_ptr, s->d_col, s->d_diag_block,
+                  s->d_color_list, s->d_rest, s->d_restgp, s->d_mass, s->d_fgrav, s->d_val,
+                  s->d_x, s->d_r, s->d_z, s->d_p, s->d_Ap, s->d_diagA, s->d_Dinv,
+                  s->d_pcg, s->d_qn, s->d_y, s->d_g, s->d_gin, s->d_d, s->d_Md, s->d_Ep,
+                  s->d_qwork, s->d_vwork, s->d_qfix, s->d_warm, s->d_mask, s->d_ns, s->d_err,
+                  s->d_energy_tmp, s->red.partials, s->red.ticket, s->d_rhs};
+  for (void* p : ptrs) dfree(p);
+  if (s->h_ns) cudaFreeHost(s->h_ns);
+  if (s->h_pcg) cudaFreeHost(s->h_pcg);
+  if (s->h_err) cudaFreeHost(s->h_err);
+  delete[] s->h_color_patches;
+  delete s;
+}
+
+static shell_status sync_and_check(Shell& s) {
+  BHEM_CUDA(cudaMemcpyAsync(s.h_err, s.d_err, sizeof(int), cudaMemcpyDeviceToHost, s.stream));
+  BHEM_CUDA(cudaStreamSynchronize(s.stream));
+  const int bits = *s.h_err;
+  if (bits) {
+    BHEM_CUDA(cudaMemsetAsync(s.d_err, 0, sizeof(int), s.stream));
+    BHEM_CUDA(cudaStreamSynchronize(s.stream));
+  }
+  if (bits & ERRBIT_DEGENERATE) return fail(SHELL_ERR_DEGENERATE, "degenerate surface normal at a Gauss point");
+  if (bits & ERRBIT_NONFINITE) return fail(SHELL_ERR_NONFINITE, "non-finite energy or residual");
+  return SHELL_OK;
+}
+
+}  // namespace bhem
+
+using namespace bhem;
+
+// ==========================================================================================
+// C ABI
+// ==========================================================================================
+extern "C" const char* shell_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" shell_status shell_create(const shell_grid* grid, const shell_material* material,
+                                     const double* rest_dofs, const shell_options* options,
+                                     void* stream, shell_t** out) {
+  if (!grid || !material || !rest_dofs || !out) return fail(SHELL_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  const shell_grid& g = *grid;
+  if (g.nu < 1 || g.nv < 1 || (g.periodic_u && g.nu < 2) || (g.periodic_v && g.nv < 2))
+    return fail(SHELL_ERR_ARG, "grid needs nu, nv >= 1 (>= 2 along a periodic direction)");
+  if (!(g.dxi1 > 0) || !(g.dxi2 > 0)) return fail(SHELL_ERR_ARG, "dxi1, dxi2 must be > 0");
+  if (!(material->thickness > 0) || !(material->young > 0) || !(material->density >= 0) ||
+      !(material->poisson > -1.0 && material->poisson < 1.0))
+    return fail(SHELL_ERR_ARG, "invalid material");
+  shell_options opt{SHELL_PREC_MIXED, SHELL_HESS_EXACT, SHELL_ASM_ATOMIC, 0};
+  if (options) opt = *options;
+  if ((opt.precision != SHELL_PREC_FP64 && opt.precision != SHELL_PREC_MIXED) ||
+      (opt.hessian != SHELL_HESS_EXACT && opt.hessian != SHELL_HESS_PSEUDO) ||
+      (opt.assembly != SHELL_ASM_ATOMIC && opt.assembly != SHELL_ASM_COLOR))
+    return fail(SHELL_ERR_ARG, "invalid options");
+  long long np_ll = (long long)g.nu * g.nv;
+  if (np_ll > (1LL << 26)) return fail(SHELL_ERR_ARG, "grid too large");
+
+  shell_s* s = new shell_s();
+  s->grid = g;
+  s->mat = *material;
+  s->opt = opt;
+  s->stream = (cudaStream_t)stream;
+  cudaGetDevice(&s->device);
+  s->n1 = g.periodic_u ? g.nu : g.nu + 1;
+  s->n2 = g.periodic_v ? g.nv : g.nv + 1;
+  s->n_nodes = s->n1 * s->n2;
+  s->n_patches = (int)np_ll;
+  s->n_dof = 12 * s->n_nodes;
+  s->lam = material->young * material->poisson / (1.0 - material->poisson * material->poisson);
+  s->mu = material->young / (2.0 * (1.0 + material->poisson));
+  s->val_fp64 = opt.precision == SHELL_PREC_FP64;
+
+  HostTopo T;
+  build_topology(g, s->n1, s->n2, T);
+  s->n_blocks = (int)T.col.size();
+  s->h_color_patches = new int[10];
+  std::memcpy(s->h_color_patches, T.color_off, sizeof(int) * 10);
+
+  const int n = s->n_nodes, np = s->n_patches, nb = s->n_blocks, m = s->n_dof;
+  shell_status st = SHELL_OK;
+#define A(ptr, count) \
+  if (st == SHELL_OK) st = dalloc(&(ptr), (size_t)(count))
+  A(s->d_patch_nodes, np);
+  A(s->d_patch_blocks, (size_t)np * 16);
+  A(s->d_row_ptr, n + 1);
+  A(s->d_col, nb);
+  A(s->d_diag_block, n);
+  A(s->d_color_list, np);
+  A(s->d_rest, m);
+  A(s->d_restgp, (size_t)13 * np * 16);
+  A(s->d_mass, (size_t)nb * 16);
+  A(s->d_fgrav, (size_t)n * 4);
+  if (st == SHELL_OK) {
+    if (s->val_fp64) {
+      double* v = nullptr;
+      st = dalloc(&v, (size_t)nb * 144);
+      s->d_val = v;
+      double* d = nullptr;
+      if (st == SHELL_OK) st = dalloc(&d, (size_t)n * 144);
+      s->d_Dinv = d;
+    } else {
+      float* v = nullptr;
+      st = dalloc(&v, (size_t)nb * 144);
+      s->d_val = v;
+      float* d = nullptr;
+      if (st == SHELL_OK) st = dalloc(&d, (size_t)n * 144);
+      s->d_Dinv = d;
+    }
+  }
+  A(s->d_x, m); A(s->d_r, m); A(s->d_z, m); A(s->d_p, m); A(s->d_Ap, m);
+  A(s->d_diagA, m); A(s->d_pcg, 1);
+  A(s->d_qn, m); A(s->d_y, m); A(s->d_g, m); A(s->d_gin, m); A(s->d_d, m); A(s->d_Md, m);
+  A(s->d_rhs, m); A(s->d_Ep, np); A(s->d_qwork, m); A(s->d_vwork, m); A(s->d_qfix, m);
+  A(s->d_warm, m); A(s->d_mask, m); A(s->d_ns, 1); A(s->d_err, 1); A(s->d_energy_tmp, 1);
+  A(s->red.partials, (size_t)kMaxRed * kMaxPartials);
+  A(s->red.ticket, 1);
+#undef A
+  if (st == SHELL_OK) {
+    cudaError_t e1 = cudaMallocHost((void**)&s->h_ns, sizeof(NewtonScalars));
+    cudaError_t e2 = cudaMallocHost((void**)&s->h_pcg, sizeof(PcgState));
+    cudaError_t e3 = cudaMallocHost((void**)&s->h_err, sizeof(int));
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) st = fail(SHELL_ERR_OOM, "cudaMallocHost failed");
+  }
+  if (st != SHELL_OK) {
+    destroy_shell(s);
+    return st;
+  }
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream);
+  };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = up(s->d_patch_nodes, T.pnodes.data(), sizeof(int4) * np);
+  if (e == cudaSuccess) e = up(s->d_patch_blocks, T.pblocks.data(), sizeof(int) * T.pblocks.size());
+  if (e == cudaSuccess) e = up(s->d_row_ptr, T.row_ptr.data(), sizeof(int) * (n + 1));
+  if (e == cudaSuccess) e = up(s->d_col, T.col.data(), sizeof(int) * nb);
+  if (e == cudaSuccess) e = up(s->d_diag_block, T.diag.data(), sizeof(int) * n);
+  if (e == cudaSuccess) e = up(s->d_color_list, T.color_list.data(), sizeof(int) * np);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_rest, rest_dofs, sizeof(double) * m, cudaMemcpyDefault, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->red.ticket, 0, sizeof(unsigned), s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_pcg, 0, sizeof(PcgState), s->stream);
+  if (e != cudaSuccess) {
+    destroy_shell(s);
+    return fail(SHELL_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+  }
+  st = launch_rest_setup(*s);
+  if (st == SHELL_OK) st = sync_and_check(*s);
+  if (st != SHELL_OK) {
+    destroy_shell(s);
+    return st;
+  }
+  *out = s;
+  return SHELL_OK;
+}
+
+extern "C" shell_status shell_destroy(shell_t* shell) {
+  if (!shell) return SHELL_OK;
+  cudaStreamSynchronize(shell->stream);
+  destroy_shell(shell);
+  return SHELL_OK;
+}
+
+extern "C" shell_status shell_info(const shell_t* shell, shell_info_t* info) {
+  if (!shell || !info) return fail(SHELL_ERR_ARG, "NULL argument");
+  info->n_nodes = shell->n_nodes;
+  info->n_patches = shell->n_patches;
+  info->n_blocks = shell->n_blocks;
+  info->n_dof = shell->n_dof;
+  return SHELL_OK;
+}
+
+extern "C" shell_status shell_element_egh(shell_t* shell, const double* q, int precision,
+                                          double* energy_p, double* grad_p, void* hess_p) {
+  if (!shell || !q) return fail(SHELL_ERR_ARG, "NULL argument");
+  if (precision != SHELL_PREC_FP64 && precision != SHELL_PREC_MIXED) return fail(SHELL_ERR_ARG, "precision");
+  ElemOutputs o;
+  o.energy_p = energy_p;
+  o.grad_p = grad_p;
+  o.hess_p = hess_p;
+  o.pseudo = shell->opt.hessian == SHELL_HESS_PSEUDO;
+  return launch_element_full(*shell, q, precision == SHELL_PREC_FP64, o);
+}
+
+namespace bhem {
+static shell_status assemble_hessian(Shell& s, const double* q, double mass_scale) {
+  size_t bytes = (size_t)s.n_blocks * 144 * (s.val_fp64 ? sizeof(double) : sizeof(float));
+  BHEM_CUDA(cudaMemsetAsync(s.d_val, 0, bytes, s.stream));
+  ElemOutputs o;
+  o.bsr = s.d_val;
+  o.mass_scale = mass_scale;
+  o.pseudo = s.opt.hessian == SHELL_HESS_PSEUDO;
+  return launch_element_full(s, q, s.val_fp64 != 0, o);
+}
+
+static shell_status elastic_energy_grad(Shell& s, const double* q, double* energy, double* grad) {
+  if (grad) BHEM_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * s.n_dof, s.stream));
+  return launch_energy_grad64(s, q, nullptr, 0.0, s.d_Ep, nullptr, grad, energy ? energy : s.d_energy_tmp);
+}
+}  // namespace bhem
+
+extern "C" shell_status shell_energy_grad_hess(shell_t* shell, const double* q, double mass_scale,
+                                               double* energy, double* grad, int want_hessian) {
+  if (!shell || !q) return fail(SHELL_ERR_ARG, "NULL argument");
+  if (energy || grad) BHEM_TRY(elastic_energy_grad(*shell, q, energy, grad));
+  if (want_hessian) BHEM_TRY(assemble_hessian(*shell, q, mass_scale));
+  return SHELL_OK;
+}
+
+extern "C" shell_status shell_get_bsr(shell_t* shell, const int** row_ptr, const int** col,
+                                      const void** val, int* val_is_fp64) {
+  if (!shell) return fail(SHELL_ERR_ARG, "NULL argument");
+  if (row_ptr) *row_ptr = shell->d_row_ptr;
+  if (col) *col = shell->d_col;
+  if (val) *val = shell->d_val;
+  if (val_is_fp64) *val_is_fp64 = shell->val_fp64;
+  return SHELL_OK;
+}
+
+extern "C" shell_status shell_get_mass(shell_t* shell, const double** mass_blocks,
+                                       const double** gravity_factors) {
+  if (!shell) return fail(SHELL_ERR_ARG, "NULL argument");
+  if (mass_blocks) *mass_blocks = shell->d_mass;
+  if (gravity_factors) *gravity_factors = shell->d_fgrav;
+  return SHELL_OK;
+}
+
+namespace bhem {
+// Runs the PCG kernels on the assembled matrix; the solution is left in s.d_x.
+static shell_status run_pcg(Shell& s, const unsigned char* mask, double tau, const double* rhs,
+                            double rtol, int max_iter, int fixed, int* iters, int* neg) {
+  BHEM_TRY(launch_precond_setup(s, mask, tau));
+  BHEM_TRY(launch_pcg_init(s, mask, rhs, rtol, fixed));
+  const int limit = fixed > 0 ? fixed : max_iter;
+  int launched = 0, chunk = fixed > 0 ? limit : 8;
+  *s.h_pcg = PcgState{};
+  BHEM_CUDA(cudaMemcpyAsync(s.h_pcg, s.d_pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s.stream));
+  BHEM_CUDA(cudaStreamSynchronize(s.stream));
+  while (launched < limit && !s.h_pcg->done) {
+    int c = std::min(chunk, limit - launched);
+    for (int k = 0; k < c; ++k) BHEM_TRY(launch_pcg_iteration(s, mask, tau));
+    launched += c;
+    BHEM_CUDA(cudaMemcpyAsync(s.h_pcg, s.d_pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s.stream));
+    BHEM_CUDA(cudaStreamSynchronize(s.stream));
+    chunk = std::min(chunk * 2, 64);
+  }
+  *iters = s.h_pcg->iters;
+  *neg = s.h_pcg->negcurv;
+  return SHELL_OK;
+}
+}  // namespace bhem
+
+extern "C" shell_status shell_pcg_solve(shell_t* shell, const unsigned char* fixed_mask, double tau,
+                                        const double* rhs, double* x, double rtol, int max_iter,
+                                        int fixed_iters, int* iters, int* neg_curv) {
+  if (!shell || !rhs || !x) return fail(SHELL_ERR_ARG, "NULL argument");
+  if (max_iter < 0 || fixed_iters < 0 || !(tau >= 0.0)) return fail(SHELL_ERR_ARG, "invalid PCG limits");
+  int it = 0, neg = 0;
+  BHEM_TRY(run_pcg(*shell, fixed_mask, tau, rhs, rtol, max_iter, fixed_iters, &it, &neg));
+  BHEM_CUDA(cudaMemcpyAsync(x, shell->d_x, sizeof(double) * shell->n_dof, cudaMemcpyDeviceToDevice, shell->stream));
+  BHEM_TRY(sync_and_check(*shell));
+  if (iters) *iters = it;
+  if (neg_curv) *neg_curv = neg;
+  return SHELL_OK;
+}
+
+namespace bhem {
+// |g| at q; leaves g in s.d_g, the inertial part in s.d_gin and E_p(q) in s.d_Ep.
+static shell_status residual(Shell& s, const double* q, const shell_step_params& P,
+                             const unsigned char* mask, double* gnorm) {
+  BHEM_CUDA(cudaMemsetAsync(s.d_g, 0, sizeof(double) * s.n_dof, s.stream));
+  BHEM_TRY(launch_energy_grad64(s, q, nullptr, 0.0, s.d_Ep, nullptr, s.d_g, &s.d_ns->energy));
+  BHEM_TRY(launch_grad_finish(s, q, s.d_y, P.dt, P.gravity, mask, s.d_g, s.d_gin, &s.d_ns->gnorm2));
+  BHEM_CUDA(cudaMemcpyAsync(s.h_ns, s.d_ns, sizeof(NewtonScalars), cudaMemcpyDeviceToHost, s.stream));
+  BHEM_TRY(sync_and_check(s));
+  *gnorm = std::sqrt(s.h_ns->gnorm2);
+  return SHELL_OK;
+}
+
+static shell_status newton_core(Shell& s, const shell_step_params& P, const unsigned char* mask,
+                                const double* qfix, double* q, const double* v_in,
+                                const double* warm, double* v_out, shell_step_stats& st) {
+  const int m = s.n_dof;
+  BHEM_CUDA(cudaMemcpyAsync(s.d_qn, q, sizeof(double) * m, cudaMemcpyDeviceToDevice, s.stream));
+  BHEM_TRY(launch_predictor(s, s.d_qn, v_in, P.dt, s.d_y));
+  if (mask) BHEM_TRY(launch_overwrite_fixed(s, q, s.d_qn, mask, qfix));
+  double gref = 0.0, gn = 0.0;
+  BHEM_TRY(residual(s, q, P, mask, &gref));
+  st.res0 = gref;
+  if (warm) BHEM_TRY(launch_overwrite_fixed(s, q, warm, mask, qfix));
+  shell_status status = SHELL_OK;
+  const double inv_dt2 = 1.0 / (P.dt * P.dt);
+  for (int it = 0;; ++it) {
+    if (it > 0 || warm) BHEM_TRY(residual(s, q, P, mask, &gn));
+    else gn = gref;
+    if (gn <= P.newton_rtol * gref) break;
+    if (it >= P.newton_max) { status = SHELL_ERR_NOT_CONVERGED; break; }
+    BHEM_TRY(assemble_hessian(s, q, inv_dt2));
+    BHEM_TRY(launch_negate(s, s.d_g, s.d_rhs));
+    // Sec. 6.1 diagonal regulariser: tau = 0, then A + tau |diag(A)| with tau = 1e-8, 1e-6, ...,
+    // 1e4 (x100 per restart) while PCG meets negative curvature
+    double tau = 0.0;
+    for (int reg = 0;; ++reg) {
+      int pit = 0, neg = 0;
+      BHEM_TRY(run_pcg(s, mask, tau, s.d_rhs, P.pcg_rtol, P.pcg_max, P.pcg_fixed_iters, &pit, &neg));
+      st.pcg_iters_total += pit;
+      if (!neg) break;
+      if (reg == 7) { status = SHELL_ERR_INDEFINITE; break; }
+      st.regularizations++;
+      tau = 1e-8 * std::pow(100.0, reg);
+    }
+    if (status != SHELL_OK) break;
+    BHEM_CUDA(cudaMemcpyAsync(s.d_d, s.d_x, sizeof(double) * m, cudaMemcpyDeviceToDevice, s.stream));
+    // line search on phi(a) = Pi(q + a d) - Pi(q) = dV(a) + a d.g_in + a^2/2 d^T M d / dt^2
+    double alpha = 1.0;
+    if (gn > 1e-6 * gref) {
+      BHEM_TRY(launch_mass_mult(s, s.d_d, s.d_Md));
+      BHEM_TRY(launch_dots3(s, m, s.d_d, s.d_Md, s.d_d, s.d_gin, s.d_g, s.d_d, s.d_ns->dots));
+      BHEM_CUDA(cudaMemcpyAsync(s.h_ns, s.d_ns, sizeof(NewtonScalars), cudaMemcpyDeviceToHost, s.stream));
+      BHEM_CUDA(cudaStreamSynchronize(s.stream));
+      const double dMd = s.h_ns->dots[0] * inv_dt2, dgin = s.h_ns->dots[1], gd = s.h_ns->dots[2];
+      if (!(gd < 0.0)) { status = SHELL_ERR_LINESEARCH; break; }
+      double a_prev = 0.0, f_prev = 0.0;
+      bool ok = false;
+      for (int trial = 0; trial < 20; ++trial) {
+        BHEM_TRY(launch_energy_grad64(s, q, s.d_d, alpha, nullptr, s.d_Ep, nullptr, &s.d_ns->dV));
+        BHEM_CUDA(cudaMemcpyAsync(&s.h_ns->dV, &s.d_ns->dV, sizeof(double), cudaMemcpyDeviceToHost, s.stream));
+        BHEM_CUDA(cudaStreamSynchronize(s.stream));
+        const double phi = s.h_ns->dV + alpha * dgin + 0.5 * alpha * alpha * dMd;
+        if (std::isfinite(phi) && phi <= 1e-4 * alpha * gd) { ok = true; break; }
+        st.ls_backtracks++;
+        double a_new;
+        if (!std::isfinite(phi)) {
+          a_new = 0.5 * alpha;
+        } else if (trial == 0) {
+          a_new = -gd * alpha * alpha / (2.0 * (phi - gd * alpha));   // quadratic model minimiser
+        } else {
+          // cubic through phi(0), phi'(0), phi(a_prev), phi(alpha) (Nocedal-Wright Sec. 3.5)
+          const double a0 = a_prev, a1 = alpha;
+          const double r1 = phi - gd * a1, r0 = f_prev - gd * a0;
+          const double den = a0 * a0 * a1 * a1 * (a1 - a0);
+          const double ca = (a0 * a0 * r1 - a1 * a1 * r0) / den;
+          const double cb = (-a0 * a0 * a0 * r1 + a1 * a1 * a1 * r0) / den;
+          const double disc = cb * cb - 3.0 * ca * gd;
+          a_new = (ca == 0.0 || disc < 0.0) ? 0.5 * alpha : (-cb + std::sqrt(disc)) / (3.0 * ca);
+        }
+        if (!(a_new >= 0.1 * alpha)) a_new = 0.1 * alpha;
+        if (a_new > 0.5 * alpha) a_new = 0.5 * alpha;
+        a_prev = alpha;
+        f_prev = phi;
+        alpha = a_new;
+      }
+      if (!ok) { status = SHELL_ERR_LINESEARCH; break; }
+    }
+    BHEM_TRY(launch_axpy_fixed(s, q, s.d_d, alpha));
+    st.newton_iters++;
+  }
+  st.res_final = gn;
+  if (status == SHELL_OK || status == SHELL_ERR_NOT_CONVERGED) {
+    BHEM_TRY(launch_velocity(s, q, s.d_qn, P.dt, v_out));
+  } else {
+    // leave q unchanged on failure
+    BHEM_CUDA(cudaMemcpyAsync(q, s.d_qn, sizeof(double) * m, cudaMemcpyDeviceToDevice, s.stream));
+  }
+  return status;
+}
+}  // namespace bhem
+
+extern "C" shell_status shell_newton_step(shell_t* shell, const shell_step_params* params,
+                                          const unsigned char* fixed_mask, const double* q_fixed,
+                                          double* q, double* v, const double* warm_start,
+                                          shell_step_stats* stats) {
+  if (!shell || !params || !q || !v || !stats) return fail(SHELL_ERR_ARG, "NULL argument");
+  if ((fixed_mask == nullptr) != (q_fixed == nullptr)) return fail(SHELL_ERR_ARG, "fixed_mask and q_fixed go together");
+  const shell_step_params& P = *params;
+  if (!(P.dt > 0) || P.newton_max < 0 || P.pcg_max < 0 || P.pcg_fixed_iters < 0 || !(P.newton_rtol >= 0))
+    return fail(SHELL_ERR_ARG, "invalid step parameters");
+  Shell& s = *shell;
+  std::memset(stats, 0, sizeof(*stats));
+  const size_t bytes = sizeof(double) * s.n_dof;
+  const bool q_dev = is_device_ptr(q), v_dev = is_device_ptr(v);
+  double* dq = q;
+  double* dv = v;
+  if (!q_dev) {
+    dq = s.d_qwork;
+    BHEM_CUDA(cudaMemcpyAsync(dq, q, bytes, cudaMemcpyHostToDevice, s.stream));
+  }
+  if (!v_dev) {
+    dv = s.d_vwork;
+    BHEM_CUDA(cudaMemcpyAsync(dv, v, bytes, cudaMemcpyHostToDevice, s.stream));
+  }
+  const unsigned char* dmask = fixed_mask;
+  const double* dqfix = q_fixed;
+  if (fixed_mask && !is_device_ptr(fixed_mask)) {
+    BHEM_CUDA(cudaMemcpyAsync(s.d_mask, fixed_mask, s.n_dof, cudaMemcpyHostToDevice, s.stream));
+    dmask = s.d_mask;
+  }
+  if (q_fixed && !is_device_ptr(q_fixed)) {
+    BHEM_CUDA(cudaMemcpyAsync(s.d_qfix, q_fixed, bytes, cudaMemcpyHostToDevice, s.stream));
+    dqfix = s.d_qfix;
+  }
+  const double* dwarm = warm_start;
+  if (warm_start && !is_device_ptr(warm_start)) {
+    BHEM_CUDA(cudaMemcpyAsync(s.d_warm, warm_start, bytes, cudaMemcpyHostToDevice, s.stream));
+    dwarm = s.d_warm;
+  }
+  shell_status st = newton_core(s, P, dmask, dqfix, dq, dv, dwarm, dv, *stats);
+  stats->status = st;
+  if (!q_dev) BHEM_CUDA(cudaMemcpyAsync(q, dq, bytes, cudaMemcpyDeviceToHost, s.stream));
+  if (!v_dev) BHEM_CUDA(cudaMemcpyAsync(v, dv, bytes, cudaMemcpyDeviceToHost, s.stream));
+  BHEM_CUDA(cudaStreamSynchronize(s.stream));
+  if (st != SHELL_OK) {
+    if (st == SHELL_ERR_NOT_CONVERGED) set_error("Newton did not reach the residual tolerance");
+    else if (st == SHELL_ERR_LINESEARCH) set_error("line search failed");
+    else if (st == SHELL_ERR_INDEFINITE) set_error("negative curvature persisted up to tau = 1e4");
+  }
+  return st;
+}
+
+extern "C" shell_status shell_spmv(shell_t* shell, const double* x, double* y) {
+  if (!shell || !x || !y) return fail(SHELL_ERR_ARG, "NULL argument");
+  if ((reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(y) & 7))
+    return fail(SHELL_ERR_ARG, "x must be 16-byte aligned and y 8-byte aligned");
+  return launch_spmv(*shell, x, y);
+}
+
+extern "C" shell_status shell_kernel_launches(const shell_t* shell, long long* count) {
+  if (!shell || !count) return fail(SHELL_ERR_ARG, "NULL argument");
+  *count = shell->launches;
+  return SHELL_OK;
+}

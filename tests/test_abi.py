@@ -1,0 +1,39 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/bhem.h declares
+(no GPU needed: nothing here launches a kernel)."""
+import os
+import re
+import subprocess
+
+from paper_2312_14839_gb300 import bhem, build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "bhem.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"SHELL_API\s+[\w\s\*]+?\b(shell_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ("shell_create", "shell_destroy", "shell_energy_grad_hess", "shell_newton_step",
+                 "shell_element_egh", "shell_pcg_solve", "shell_spmv", "shell_last_error"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol():
+    path = build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (shell_\w+)", out))
+    missing = [s for s in declared_symbols() if s not in exported]
+    assert not missing, missing
+    lib = bhem.load()
+    for s in declared_symbols():
+        assert getattr(lib, s) is not None
+
+
+def test_argument_errors_need_no_gpu():
+    lib = bhem.load()
+    assert lib.shell_create(None, None, None, None, None, None) == 1   # SHELL_ERR_ARG
+    assert b"NULL" in lib.shell_last_error()
+    assert lib.shell_destroy(None) == 0

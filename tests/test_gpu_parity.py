@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle, element by element.
+
+Tolerances (normwise relative, per patch / per quantity): <= 1e-11 for FP64 results, <= 1e-5 for
+FP32 element quantities; index work (BSR pattern) bit-exact; Newton iteration counts identical
+for the FP64 path.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2312_14839_gb300 import scenes as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-11, "mixed": 1e-5}
+
+
+def dev(a, dtype=None):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64, device="cuda")
+
+
+def host(t):
+    return t.detach().double().cpu().numpy()
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def make_shell(g, mat, rest, **kw):
+    from paper_2312_14839_gb300.bhem import Shell
+    return Shell(g, mat, dev(rest.reshape(-1)), **kw)
+
+
+THIN = S.SHEET_MATERIAL
+THICK = S.Material(1e5, 0.3, 0.05, 200.0)
+
+CASES = {
+    "sheet10x10-noisy": lambda: (*S.sheet_noisy(10, 1e-3, 1), THIN),
+    "sheet1x1": lambda: (*S.sheet_noisy(1, 1e-2, 2), THIN),
+    "sheet3x2-rect-thick": lambda: (lambda g, r: (g, r, S.noisy(r, 2e-2, 3), THICK))(*S.flat_sheet(3, 2, 0.6, 0.4)),
+    "annulus12x3": lambda: (lambda g, r: (g, r, S.noisy(r, 1e-2, 4), THIN))(*S.annulus(12, 3)),
+    "annulus7x2-odd-thick": lambda: (lambda g, r: (g, r, S.noisy(r, 1e-2, 5), THICK))(*S.annulus(7, 2)),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_element_parity(case, prec):
+    g, rest, q, mat = CASES[case]()
+    E0, G0, H0 = O.elements(g, mat, rest, q)
+    sh = make_shell(g, mat, rest, precision=prec)
+    E, G, H = sh.element_egh(dev(q.reshape(-1)), precision=prec)
+    torch.cuda.synchronize()
+    E, G, H = host(E), host(G), host(H)
+    tol = TOL[prec]
+    assert np.abs(E - E0).max() <= tol * np.abs(E0).sum()
+    for p in range(g.n_patches):
+        assert rel(G[p], G0[p]) <= tol, (p, rel(G[p], G0[p]))
+        assert rel(H[p], H0[p]) <= tol, (p, rel(H[p], H0[p]))
+        assert np.abs(H[p] - H[p].T).max() <= tol * np.abs(H0[p]).max() * 4
+
+
+@pytest.mark.parametrize("case", ["sheet10x10-noisy", "annulus12x3", "annulus7x2-odd-thick", "sheet1x1"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("assembly", ["atomic", "color"])
+def test_assembled_parity(case, prec, assembly):
+    g, rest, q, mat = CASES[case]()
+    ms = 1e6
+    pat = O.bsr_pattern(g)
+    E0, g0, (rp0, col0, val0) = O.assemble(g, mat, rest, q, mass_scale=ms, pattern=pat)
+    sh = make_shell(g, mat, rest, precision=prec, assembly=assembly)
+    E, G = sh.energy_grad_hess(dev(q.reshape(-1)), mass_scale=ms)
+    rp, col, val = sh.bsr()
+    torch.cuda.synchronize()
+    assert np.array_equal(host(rp).astype(np.int64), rp0) and np.array_equal(host(col).astype(np.int64), col0)
+    # energy and gradient are FP64 in both precisions
+    assert abs(host(E)[0] - E0) <= 1e-11 * abs(E0)
+    assert rel(host(G), g0) <= 1e-11
+    val = host(val)
+    assert rel(val, val0) <= TOL[prec]
+    for i in range(g.n_nodes):   # every block row
+        a, b = rp0[i], rp0[i + 1]
+        assert rel(val[a:b], val0[a:b]) <= TOL[prec] * 4, i
+
+
+@pytest.mark.parametrize("case", ["sheet10x10-noisy", "annulus7x2-odd-thick"])
+def test_mass_and_gravity_parity(case):
+    g, rest, q, mat = CASES[case]()
+    M0, F0 = O.mass(g, mat, rest)
+    sh = make_shell(g, mat, rest)
+    M, F = sh.mass()
+    torch.cuda.synchronize()
+    assert rel(host(M), M0) <= 1e-13
+    assert rel(host(F), F0) <= 1e-13
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_spmv_matches_dense_product(prec):
+    g, rest, q, mat = CASES["annulus12x3"]()
+    sh = make_shell(g, mat, rest, precision=prec)
+    sh.energy_grad_hess(dev(q.reshape(-1)), mass_scale=1e6)
+    rp, col, val = sh.bsr()
+    A = O.bsr_to_dense(host(rp).astype(np.int64), host(col).astype(np.int64), host(val))
+    x = np.random.default_rng(0).normal(size=g.n_dof)
+    y = host(sh.spmv(dev(x)))
+    assert rel(y, A @ x) <= (1e-13 if prec == "fp64" else 1e-5)
+
+
+def test_pcg_parity_fp64():
+    g, rest, q, mat = CASES["sheet10x10-noisy"]()
+    dt = 1e-3
+    pat = O.bsr_pattern(g)
+    _, grad0, (rp0, col0, val0) = O.assemble(g, mat, rest, q, mass_scale=1 / dt ** 2, pattern=pat)
+    mask = S.pinned_mask(g, [0, g.n_nodes - 1])
+    x0, it0, st0 = O.pcg(rp0, col0, val0, -grad0, mask=mask, rtol=1e-6, max_iter=1000)
+    sh = make_shell(g, mat, rest, precision="fp64")
+    _, G = sh.energy_grad_hess(dev(q.reshape(-1)), mass_scale=1 / dt ** 2)
+    x, it, neg = sh.pcg_solve(-G, mask=dev(mask, torch.uint8), rtol=1e-6, max_iter=1000)
+    assert st0 == 0 and neg == 0
+    assert it == it0
+    assert rel(host(x), x0) <= 1e-9
+
+
+def _config1_run(prec, steps=10, host_buffers=False):
+    g, rest, q0 = S.sheet_noisy(10, 1e-3, 1)
+    mat = THIN
+    c = S.corner_nodes(g)
+    mask = S.pinned_mask(g, [c[0], c[3]])
+    qfix = q0.reshape(-1).copy()
+    sh = make_shell(g, mat, rest, precision=prec)
+    P = __import__("paper_2312_14839_gb300.bhem", fromlist=["step_params"]).step_params(dt=1e-3)
+    if host_buffers:
+        q, v = q0.reshape(-1).copy(), np.zeros(g.n_dof)
+        m, qf = mask, qfix
+    else:
+        q, v = dev(q0.reshape(-1)), torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        m, qf = dev(mask, torch.uint8), dev(qfix)
+    out = []
+    for _ in range(steps):
+        st = sh.newton_step(q, v, P, mask=m, q_fixed=qf)
+        qq = q.copy() if host_buffers else host(q)
+        vv = v.copy() if host_buffers else host(v)
+        out.append((st, qq, vv))
+    return g, mat, rest, q0, mask, qfix, out
+
+
+def test_newton_config1_fp64_identical_iteration_counts():
+    g, mat, rest, q0, mask, qfix, out = _config1_run("fp64")
+    Po = O.step_params(dt=1e-3)
+    q, v = q0.reshape(-1).copy(), np.zeros(g.n_dof)
+    for st, qg, vg in out:
+        q, v, so = O.newton_step(g, mat, rest, q, v, Po, mask=mask, qfix=qfix)
+        assert st["status"] == 0 and so["status"] == 0
+        assert st["newton_iters"] == so["newton_iters"]
+        assert st["pcg_iters_total"] == so["pcg_iters_total"]
+        assert st["res_final"] <= 1e-8 * st["res0"]
+        assert rel(qg, q) <= 1e-11
+        assert rel(vg, v) <= 1e-7
+
+
+def test_newton_config1_mixed_precision():
+    g, mat, rest, q0, mask, qfix, out = _config1_run("mixed")
+    Po = O.step_params(dt=1e-3)
+    q, v = q0.reshape(-1).copy(), np.zeros(g.n_dof)
+    for st, qg, vg in out:
+        q, v, so = O.newton_step(g, mat, rest, q, v, Po, mask=mask, qfix=qfix)
+        assert st["status"] == 0
+        assert abs(st["newton_iters"] - so["newton_iters"]) <= 1
+        assert st["res_final"] <= 1e-8 * st["res0"]
+        assert rel(vg, v) <= 1e-5
+        q, v = qg.copy(), vg.copy()   # continue the oracle from the GPU state (no drift)
+
+
+def test_newton_host_buffers_match_device_buffers():
+    *_, out_d = _config1_run("fp64", steps=3)
+    *_, out_h = _config1_run("fp64", steps=3, host_buffers=True)
+    for (sd, qd, vd), (sh_, qh, vh) in zip(out_d, out_h):
+        assert sd["newton_iters"] == sh_["newton_iters"]
+        assert rel(qh, qd) <= 1e-13 and rel(vh, vd) <= 1e-9
+
+
+@pytest.mark.parametrize("maker", [lambda: S.sheet_sinusoid(256, 3), lambda: S.annulus_sinusoid(280, 5, 3)])
+def test_full_size_sampled_element_parity(maker):
+    """Full-size sheets in the bench's configuration: FP32 element outputs of sampled patches
+    against the oracle computed patch by patch."""
+    g, rest, q = maker()
+    mat = THIN
+    sh = make_shell(g, mat, rest, precision="mixed")
+    E, G, H = sh.element_egh(dev(q.reshape(-1)))
+    idx = np.unique(np.concatenate([[0, g.n_patches - 1], np.random.default_rng(7).integers(0, g.n_patches, 40)]))
+    ti = torch.as_tensor(idx, device="cuda")
+    Es, Gs, Hs = host(E[ti]), host(G[ti]), host(H[ti])
+    for k, p in enumerate(idx):
+        e0, g0, h0 = O.element_egh(O.gather(g, q, p), O.gather(g, rest, p), g.dxi1, g.dxi2, mat)
+        assert abs(Es[k] - e0) <= 1e-5 * abs(e0)
+        assert rel(Gs[k], g0) <= 1e-5
+        assert rel(Hs[k], h0) <= 1e-5
+
+
+def test_full_size_sampled_assembly_rows():
+    """256x256 BSR: sampled block rows against the sum of the oracle's element blocks of the
+    (up to 4) patches around the node."""
+    g, rest, q = S.sheet_sinusoid(256, 3)
+    mat = THIN
+    ms = 1e6
+    sh = make_shell(g, mat, rest, precision="mixed")
+    sh.energy_grad_hess(dev(q.reshape(-1)), mass_scale=ms)
+    rp, col, val = sh.bsr()
+    rp, col = host(rp).astype(np.int64), host(col).astype(np.int64)
+    for node in [0, 257, 33000, g.n_nodes - 1, 12345]:
+        i, j = node % g.n1, node // g.n1
+        want = {}
+        for pv in (j - 1, j):
+            for pu in (i - 1, i):
+                if not (0 <= pu < g.nu and 0 <= pv < g.nv):
+                    continue
+                p = pv * g.nu + pu
+                nd = O.patch_nodes(g, p)
+                _, _, H = O.element_egh(O.gather(g, q, p), O.gather(g, rest, p), g.dxi1, g.dxi2, mat)
+                m, _ = O.element_mass(O.gather(g, rest, p), g.dxi1, g.dxi2, mat)
+                H = H + ms * np.kron(m, np.eye(3))
+                a = list(nd).index(node)
+                for b in range(4):
+                    blk = H[a * 12:(a + 1) * 12, b * 12:(b + 1) * 12]
+                    want[nd[b]] = want.get(nd[b], 0) + blk
+        ks = range(rp[node], rp[node + 1])
+        assert sorted(want) == [col[k] for k in ks]
+        got = np.concatenate([host(val[k]) for k in ks])
+        ref = np.concatenate([want[col[k]] for k in ks])
+        assert rel(got, ref) <= 1e-5
+
+
+def test_degenerate_and_nonfinite_inputs_are_reported():
+    from paper_2312_14839_gb300.bhem import ShellError, step_params
+    g, rest, q, mat = CASES["sheet1x1"]()
+    sh = make_shell(g, mat, rest, precision="fp64")
+    P = step_params()
+    zero = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    with pytest.raises(ShellError) as e:
+        sh.newton_step(zero.clone(), zero.clone(), P)
+    assert e.value.status == 4
+    bad = dev(q.reshape(-1)).clone()
+    bad[5] = float("nan")
+    with pytest.raises(ShellError) as e:
+        sh.newton_step(bad, zero.clone(), P)
+    assert e.value.status in (4, 5)
+    # the shell stays usable afterwards
+    st = sh.newton_step(dev(q.reshape(-1)), zero.clone(), P)
+    assert st["status"] == 0
