@@ -100,7 +100,7 @@ typedef struct {
   int newton_iters;       /* Newton updates applied                                         */
   int pcg_iters_total;    /* PCG iterations over all solves (regularised restarts included) */
   int ls_backtracks;      /* rejected line-search trials                                    */
-  int regularizations;    /* restarts with tau |diag(A)| added (Sec. 6.1 regulariser)       */
+  int regularizations;    /* regulariser levels tried (tau D added, Sec. 6.1)               */
   int status;             /* shell_status of the step                                       */
   double res0;            /* |g_free| at the zero guess                                     */
   double res_final;       /* |g_free| at the returned state                                 */
@@ -151,7 +151,8 @@ SHELL_API shell_status shell_get_bsr(shell_t* shell, const int** row_ptr, const 
 SHELL_API shell_status shell_get_mass(shell_t* shell, const double** mass_blocks,
                             const double** gravity_factors);
 
-/* Block-Jacobi PCG on the currently assembled BSR A: solves (A + tau |diag(A)|) x = rhs with
+/* Block-Jacobi PCG on the currently assembled BSR A: solves (A + tau D) x = rhs, D diagonal with
+   D_ii = mean of |A_jj| over the free DOFs j of DOF i's kind (x, x_,1, x_,2 or x_,12), with
    fixed DOFs (mask != 0) held at zero (identity rows/columns). rhs, x: device [n_dof];
    fixed_mask: device [n_dof] or NULL. Runs until |r| <= rtol |rhs| or max_iter, or exactly
    fixed_iters (> 0) iterations. *iters receives the iterations done, *neg_curv 1 when
@@ -162,9 +163,11 @@ SHELL_API shell_status shell_pcg_solve(shell_t* shell, const unsigned char* fixe
 
 /* y = A x with the currently assembled BSR A (the product inside every PCG iteration of
    Sec. 6.1's linear solve; FP32 arithmetic with FP32 accumulation per row chunk when the shell
-   is SHELL_PREC_MIXED, FP64 otherwise). x (16-byte aligned), y (8-byte aligned): device
-   [n_dof] FP64. No mask, no regulariser. Asynchronous; one kernel launch. */
-SHELL_API shell_status shell_spmv(shell_t* shell, const double* x, double* y);
+   is SHELL_PREC_MIXED, FP64 otherwise). x: device [n_dof], 16-byte aligned, FP32 when
+   x_is_fp32 != 0 (SHELL_PREC_MIXED shells only: one kernel launch) else FP64 (a mixed shell
+   first converts it to FP32 in its own buffer: two launches); y: device [n_dof] FP64, 8-byte
+   aligned. No mask, no regulariser. Asynchronous. */
+SHELL_API shell_status shell_spmv(shell_t* shell, const void* x, int x_is_fp32, double* y);
 
 /* One implicit-Euler step (Eq. implicit) by Newton with line search (Sec. 6.1):
    minimises Pi(q) = (q - y)^T M (q - y) / (2 dt^2) + V_e(q) - F^T q, y = q^n + dt v^n, over the

@@ -79,7 +79,8 @@ def _load():
         lib.og_assemble.argtypes = [p, p, p, p, p, p, d, p, p, p]
         lib.og_mass.argtypes = [p, p, p, p, p, p, p]
         lib.og_pcg.restype = i
-        lib.og_pcg.argtypes = [i, p, p, p, p, d, p, d, i, i, p, p]
+        lib.og_pcg.argtypes = [i, p, p, p, p, d, p, p, d, i, i, p, p]
+        lib.og_kind_scale.argtypes = [i, p, p, p, p, p]
         lib.og_newton_step.restype = i
         lib.og_newton_step.argtypes = [p, p, p, p, p, p, p, p, p, p]
         _lib = lib
@@ -221,16 +222,27 @@ def bsr_to_dense(row_ptr, col, val):
     return A
 
 
+def kind_scale(row_ptr, col, val, mask=None):
+    """Regulariser scale per DOF kind: mean |A_ii| over free DOFs of each kind [4]."""
+    n = row_ptr.size - 1
+    val = _f64(val)
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    out = np.zeros(4)
+    _load().og_kind_scale(n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(m), _ptr(out))
+    return out
+
+
 def pcg(row_ptr, col, val, b, mask=None, tau=0.0, rtol=1e-6, max_iter=1000, fixed_iters=0):
-    """Block-Jacobi PCG from x = 0 on the 12x12 BSR; returns (x, iters, status)."""
+    """Block-Jacobi PCG from x = 0 on A + tau D (12x12 BSR); returns (x, iters, status)."""
     n = row_ptr.size - 1
     val = _f64(val)
     b = _f64(b).reshape(-1)
     m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    dbar = kind_scale(row_ptr, col, val, m)
     x = np.zeros(n * 12)
     it = C.c_int(0)
-    st = _load().og_pcg(n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(m), float(tau), _ptr(b),
-                        float(rtol), int(max_iter), int(fixed_iters), _ptr(x), C.byref(it))
+    st = _load().og_pcg(n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(m), float(tau), _ptr(dbar),
+                        _ptr(b), float(rtol), int(max_iter), int(fixed_iters), _ptr(x), C.byref(it))
     return x, it.value, st
 
 

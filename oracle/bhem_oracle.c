@@ -29,10 +29,14 @@
  *     interpolation (Nocedal-Wright Sec. 3.5), each clamped to [0.1, 0.5] of the last step, at
  *     most 20 trials; alpha = 1 is accepted without a test once |g| <= 1e-6 |g_ref|.
  *   - Regulariser (Sec. 6.1 gives no form or magnitude): PCG stops on p^T A p <= 0; the solve
- *     restarts on A + tau |diag(A)| with tau = 1e-8, 1e-6, ..., 1e4 (x100 per restart), then
- *     gives up. |diag(A)| rather than diag(A) because A may have negative diagonal entries
- *     under compression, which tau diag(A) would make more negative. A 12x12 block that is not
- *     SPD is replaced by the inverse of its diagonal in the block-Jacobi preconditioner.
+ *     restarts on A + tau D with tau = 1e-8, 1e-6, ..., 1e4 (x100 per restart), then gives up.
+ *     D is diagonal: for each DOF kind (x, x_,1, x_,2, x_,12) the mean of |A_ii| over the free
+ *     DOFs of that kind. It is positive and scales like each kind's stiffness (the shape
+ *     functions of derivative DOFs carry powers of dxi), where diag(A) itself may be negative
+ *     or near zero under compression. A level whose regularised matrix has a free diagonal
+ *     entry <= 0 cannot be positive definite and is skipped without running PCG. A 12x12
+ *     block that is not SPD is replaced by the inverse of its diagonal in the block-Jacobi
+ *     preconditioner.
  */
 #include <math.h>
 #include <stdint.h>
@@ -525,10 +529,10 @@ static void mass_mult(int n, const int* row_ptr, const int* col, const double* m
 /* ------------------------------------------------------------------------------------------ */
 /* Block-Jacobi PCG (replaces the direct LDL^T solve of Sec. 6.1).                              */
 /* A is the 12x12 BSR; fixed DOFs (mask != 0) get identity rows and columns. tau adds           */
-/* tau * |diag(A)| to the free diagonal (the regulariser).                                     */
+/* tau * dbar[kind] to the free diagonal (the regulariser; dbar[k] = mean |A_ii| of kind k).    */
 /* ------------------------------------------------------------------------------------------ */
 static void bsr_mult(int n, const int* row_ptr, const int* col, const double* val,
-                     const unsigned char* mask, double tau, const double* diag,
+                     const unsigned char* mask, double tau, const double* dbar,
                      const double* x, double* y) {
   for (int i = 0; i < n; ++i) {
     for (int r = 0; r < 12; ++r) {
@@ -543,7 +547,7 @@ static void bsr_mult(int n, const int* row_ptr, const int* col, const double* va
           acc += val[(size_t)k*144 + r*12 + s] * x[gj];
         }
       }
-      y[gi] = acc + tau * fabs(diag[gi]) * x[gi];
+      y[gi] = acc + (tau != 0.0 ? tau * dbar[r / 3] * x[gi] : 0.0);
     }
   }
 }
@@ -581,7 +585,7 @@ static int chol_inverse12(const double* A, double* Ainv) {
 
 /* Block-Jacobi inverses D[n*144] of the masked, regularised diagonal blocks. */
 static void block_jacobi(int n, const int* row_ptr, const int* col, const double* val,
-                         const unsigned char* mask, double tau, const double* diag, double* D) {
+                         const unsigned char* mask, double tau, const double* dbar, double* D) {
   for (int i = 0; i < n; ++i) {
     int k = find_block(row_ptr, col, i, i);
     double A[144];
@@ -589,7 +593,7 @@ static void block_jacobi(int n, const int* row_ptr, const int* col, const double
       int fr = mask && mask[i*12 + r], fs = mask && mask[i*12 + s];
       double v = val[(size_t)k*144 + r*12 + s];
       if (fr || fs) v = (r == s) ? 1.0 : 0.0;
-      else if (r == s) v += tau * fabs(diag[i*12 + r]);
+      else if (r == s && tau != 0.0) v += tau * dbar[r / 3];
       A[r*12 + s] = v;
     }
     if (!chol_inverse12(A, &D[(size_t)i*144])) {
@@ -608,19 +612,30 @@ static double vdot(int m, const double* a, const double* b) {
 /* Solves A x = b from x = 0. Stops when |r| <= rtol |b| (or after exactly fixed_iters
    iterations when fixed_iters > 0), or after max_iter. Returns OG_OK, or OG_PCG_NEG_CURV when
    p^T A p <= 0. *iters receives the iterations done. */
+/* Per-kind regulariser scale: dbar[k] = mean over free DOFs of kind k of |A_ii| (1 if none). */
+void og_kind_scale(int n, const int* row_ptr, const int* col, const double* val,
+                   const unsigned char* mask, double dbar[4]) {
+  double sum[4] = {0, 0, 0, 0};
+  long cnt[4] = {0, 0, 0, 0};
+  for (int i = 0; i < n; ++i) {
+    int k = find_block(row_ptr, col, i, i);
+    for (int a = 0; a < 12; ++a) {
+      if (mask && mask[i*12 + a]) continue;
+      sum[a / 3] += fabs(val[(size_t)k*144 + a*13]);
+      cnt[a / 3] += 1;
+    }
+  }
+  for (int q = 0; q < 4; ++q) dbar[q] = cnt[q] ? sum[q] / (double)cnt[q] : 1.0;
+}
+
 int og_pcg(int n, const int* row_ptr, const int* col, const double* val,
-           const unsigned char* mask, double tau, const double* b, double rtol,
-           int max_iter, int fixed_iters, double* x, int* iters) {
+           const unsigned char* mask, double tau, const double* dbar, const double* b,
+           double rtol, int max_iter, int fixed_iters, double* x, int* iters) {
   int m = n * 12;
-  double* diag = (double*)malloc(m * sizeof(double));
   double* D = (double*)malloc((size_t)n * 144 * sizeof(double));
   double *r = (double*)malloc(m * sizeof(double)), *z = (double*)malloc(m * sizeof(double));
   double *p = (double*)malloc(m * sizeof(double)), *Ap = (double*)malloc(m * sizeof(double));
-  for (int i = 0; i < n; ++i) {
-    int k = find_block(row_ptr, col, i, i);
-    for (int s = 0; s < 12; ++s) diag[i*12 + s] = val[(size_t)k*144 + s*13];
-  }
-  block_jacobi(n, row_ptr, col, val, mask, tau, diag, D);
+  block_jacobi(n, row_ptr, col, val, mask, tau, dbar, D);
   for (int i = 0; i < m; ++i) { x[i] = 0.0; r[i] = (mask && mask[i]) ? 0.0 : b[i]; }
   double bnorm = sqrt(vdot(m, r, r));
   int status = OG_OK, it = 0;
@@ -634,7 +649,7 @@ int og_pcg(int n, const int* row_ptr, const int* col, const double* val,
   memcpy(p, z, m * sizeof(double));
   double rz = vdot(m, r, z);
   while (it < limit) {
-    bsr_mult(n, row_ptr, col, val, mask, tau, diag, p, Ap);
+    bsr_mult(n, row_ptr, col, val, mask, tau, dbar, p, Ap);
     for (int i = 0; i < m; ++i) if (mask && mask[i]) Ap[i] = 0.0;
     double pAp = vdot(m, p, Ap);
     if (!(pAp > 0.0)) { status = OG_PCG_NEG_CURV; break; }
@@ -656,7 +671,7 @@ int og_pcg(int n, const int* row_ptr, const int* col, const double* val,
   }
 done:
   *iters = it;
-  free(diag); free(D); free(r); free(z); free(p); free(Ap);
+  free(D); free(r); free(z); free(p); free(Ap);
   return status;
 }
 
@@ -746,12 +761,27 @@ int og_newton_step(const og_grid* g, const og_material* mat, const double* rest,
     og_assemble(g, mat, rest, q, row_ptr, col, 1.0 / (P->dt * P->dt), NULL, NULL, val);
     for (int i = 0; i < m; ++i) rhs[i] = -gr[i];
     /* tau = 0, then 1e-8, 1e-6, ..., 1e4 */
-    double tau = 0.0;
+    double tau = 0.0, dbar[4];
+    og_kind_scale(n, row_ptr, col, val, mask, dbar);
     int piters = 0, ps;
     for (int reg = 0;; ++reg) {
-      ps = og_pcg(n, row_ptr, col, val, mask, tau, rhs, P->pcg_rtol, P->pcg_max,
-                  P->pcg_fixed_iters, d, &piters);
-      st->pcg_iters_total += piters;
+      /* a free diagonal entry <= 0 of A + tau D rules out positive definiteness */
+      int diag_ok = 1;
+      for (int i = 0; i < n && diag_ok; ++i) {
+        int k = find_block(row_ptr, col, i, i);
+        for (int a = 0; a < 12; ++a) {
+          if (mask && mask[i*12 + a]) continue;
+          double dv = val[(size_t)k*144 + a*13];
+          if (!(dv + tau * dbar[a / 3] > 0.0)) { diag_ok = 0; break; }
+        }
+      }
+      if (diag_ok) {
+        ps = og_pcg(n, row_ptr, col, val, mask, tau, dbar, rhs, P->pcg_rtol, P->pcg_max,
+                    P->pcg_fixed_iters, d, &piters);
+        st->pcg_iters_total += piters;
+      } else {
+        ps = OG_PCG_NEG_CURV;
+      }
       if (ps != OG_PCG_NEG_CURV) break;
       if (reg == 7) { status = OG_ERR_INDEFINITE; break; }
       st->regularizations++;

@@ -87,7 +87,7 @@ def load():
                 "shell_get_mass": [p, p, p],
                 "shell_pcg_solve": [p, p, d, p, p, d, i, i, p, p],
                 "shell_newton_step": [p, p, p, p, p, p, p, p],
-                "shell_spmv": [p, p, p],
+                "shell_spmv": [p, p, i, p],
                 "shell_kernel_launches": [p, p],
             }
             for name, args in sigs.items():
@@ -119,7 +119,7 @@ class _DevArray:
 
     def __init__(self, ptr: int, shape, typestr: str):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
-                                         "data": (int(ptr), True), "version": 3, "strides": None}
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
 
 
 def _stream_handle(stream):
@@ -240,11 +240,12 @@ class Shell:
         return n.value
 
     def spmv(self, x, y=None):
-        """y = A x with the assembled BSR (one kernel launch on the shell's stream)."""
+        """y = A x with the assembled BSR on the shell's stream; x FP64, or FP32 for a mixed shell
+        (then one kernel launch)."""
         import torch
         if y is None:
-            y = torch.empty_like(x)
-        _check(load().shell_spmv(self._h, _ptr(x), _ptr(y)))
+            y = torch.empty(x.shape, dtype=torch.float64, device=x.device)
+        _check(load().shell_spmv(self._h, _ptr(x), int(x.dtype == torch.float32), _ptr(y)))
         return y
 
     def newton_step(self, q, v, params: shell_step_params, mask=None, q_fixed=None, warm=None,

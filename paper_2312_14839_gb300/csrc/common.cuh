@@ -37,7 +37,7 @@ enum : int { ERRBIT_DEGENERATE = 1, ERRBIT_NONFINITE = 2 };
 // Deterministic grid reductions: each CTA writes a partial, the last CTA to arrive (atomic
 // ticket, no waiting) sums the partials in CTA order and resets the ticket.
 // ------------------------------------------------------------------------------------------
-constexpr int kMaxRed = 4;              // values reduced together
+constexpr int kMaxRed = 16;             // values reduced together
 constexpr int kMaxPartials = 1 << 17;   // CTAs per reduced kernel (checked at launch)
 
 struct Reduce {
@@ -58,6 +58,7 @@ struct NewtonScalars {
   double dots[3];      // d.Md, d.g_inert, d.g
   double dV;           // sum_p (E_p(q + a d) - E_p(q))
   double energy;       // assembled elastic energy
+  double diag_stats[12];  // per DOF kind: sum |A_ii|, count, min A_ii over free DOFs
 };
 
 // ------------------------------------------------------------------------------------------
@@ -85,6 +86,8 @@ struct Shell {
   // reference configuration
   double* d_rest = nullptr;         // [n_dof]
   double* d_restgp = nullptr;       // [13 * np * 16] per-Gauss-point rest data (SoA)
+  double* d_phi64 = nullptr;        // shape table + Gauss weights (kPhiTable doubles)
+  float* d_phi32 = nullptr;         // the same in FP32
   double* d_mass = nullptr;         // [n_blocks * 16] consistent mass, 4x4 scalar blocks
   double* d_fgrav = nullptr;        // [n_nodes * 4] gravity load factors
 
@@ -94,7 +97,7 @@ struct Shell {
 
   // PCG workspace
   double *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_Ap = nullptr;
-  double* d_diagA = nullptr;        // [n_dof] diagonal of A (regulariser)
+  float* d_p32 = nullptr;           // FP32 copy of p read by the FP32 SpMV
   void* d_Dinv = nullptr;           // [n_nodes * 144] block-Jacobi inverses (FP32 or FP64)
   PcgState* d_pcg = nullptr;
 
@@ -119,6 +122,8 @@ struct Shell {
 // ------------------------------------------------------------------------------------------
 // rest per-Gauss-point data, mass, gravity factors (once per shell)
 shell_status launch_rest_setup(Shell& s);
+// regulariser shift tau * dbar per DOF kind, as kernel argument
+struct Shift4 { double v[4]; };
 
 // Heavy element kernel: energy/gradient/Hessian per patch (one warp per patch).
 //   hess_out: unassembled [np*2304] of R, or nullptr; bsr: assembled BSR (R) or nullptr.
@@ -146,11 +151,12 @@ shell_status launch_grad_finish(Shell& s, const double* q, const double* y, doub
 shell_status launch_mass_mult(Shell& s, const double* x, double* y);
 shell_status launch_dots3(Shell& s, int n, const double* a0, const double* b0, const double* a1,
                           const double* b1, const double* a2, const double* b2, double* out3);
-shell_status launch_precond_setup(Shell& s, const unsigned char* mask, double tau);
+shell_status launch_precond_setup(Shell& s, const unsigned char* mask, const double td[4]);
 shell_status launch_pcg_init(Shell& s, const unsigned char* mask, const double* rhs,
                              double rtol, int fixed);
-shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, double tau);
-shell_status launch_spmv(Shell& s, const double* x, double* y);
+shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, const double td[4]);
+shell_status launch_spmv(Shell& s, const void* x, int x_fp32, double* y);
+shell_status launch_diag_check(Shell& s, const unsigned char* mask, double* out12);
 shell_status launch_axpy_fixed(Shell& s, double* q, const double* d, double alpha);
 shell_status launch_overwrite_fixed(Shell& s, double* dst, const double* src,
                                     const unsigned char* mask, const double* fixed_vals);
@@ -167,23 +173,28 @@ int grid_for(long long work, int per_block);
 // ------------------------------------------------------------------------------------------
 template <int NV>
 __device__ __forceinline__ bool grid_reduce(const double (&v)[NV], Reduce red, double* out,
-                                            int nblocks) {
+                                            int nblocks, unsigned minmask = 0u) {
   __shared__ double sred[NV][32];
   __shared__ int last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   double x[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
+    const bool mn = (minmask >> i) & 1u;
     x[i] = v[i];
-    for (int o = 16; o > 0; o >>= 1) x[i] += __shfl_xor_sync(0xffffffffu, x[i], o);
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_xor_sync(0xffffffffu, x[i], o);
+      x[i] = mn ? fmin(x[i], y) : x[i] + y;
+    }
   }
   if (lane == 0)
     for (int i = 0; i < NV; ++i) sred[i][wid] = x[i];
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int i = 0; i < NV; ++i) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += sred[i][w];
+      const bool mn = (minmask >> i) & 1u;
+      double s = sred[i][0];
+      for (int w = 1; w < nw; ++w) s = mn ? fmin(s, sred[i][w]) : s + sred[i][w];
       red.partials[(size_t)i * kMaxPartials + blockIdx.x] = s;
     }
     __threadfence();
@@ -194,16 +205,22 @@ __device__ __forceinline__ bool grid_reduce(const double (&v)[NV], Reduce red, d
   if (!last) return false;
   __threadfence();
   for (int i = 0; i < NV; ++i) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-      s += ((volatile double*)red.partials)[(size_t)i * kMaxPartials + b];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const bool mn = (minmask >> i) & 1u;
+    double s = mn ? INFINITY : 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+      const double y = ((volatile double*)red.partials)[(size_t)i * kMaxPartials + b];
+      s = mn ? fmin(s, y) : s + y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_xor_sync(0xffffffffu, s, o);
+      s = mn ? fmin(s, y) : s + y;
+    }
     __syncthreads();
     if (lane == 0) sred[i][wid] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double tot = 0.0;
-      for (int w = 0; w < nw; ++w) tot += sred[i][w];
+      double tot = sred[i][0];
+      for (int w = 1; w < nw; ++w) tot = mn ? fmin(tot, sred[i][w]) : tot + sred[i][w];
       out[i] = tot;
     }
   }

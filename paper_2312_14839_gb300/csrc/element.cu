@@ -42,6 +42,7 @@ __device__ __forceinline__ void gauss_unit(double th[4], double wt[4]) {
 // access patterns (lanes over g, lanes over I) free of bank conflicts.
 constexpr int kPhiStride = 97;
 constexpr int kPhiSize = 16 * kPhiStride;
+constexpr int kPhiTable = kPhiSize + 16;   // + the 16 Gauss weights W_g = dxi1 dxi2 w_g1 w_g2
 
 template <typename R>
 __device__ void build_shape_table(R* sphi, double d1, double d2) {
@@ -65,6 +66,25 @@ __device__ __forceinline__ double gauss_weight(int g, double d1, double d2) {
   double th[4], wt[4];
   gauss_unit(th, wt);
   return d1 * d2 * wt[g & 3] * wt[g >> 2];
+}
+
+// Shape table and Gauss weights of one shell, built once (FP64 arithmetic) into global memory.
+__global__ void k_shape_table(double d1, double d2, double* __restrict__ t64, float* __restrict__ t32) {
+  __shared__ double sphi[kPhiSize];
+  for (int e = threadIdx.x; e < kPhiSize; e += blockDim.x) sphi[e] = 0.0;
+  __syncthreads();
+  build_shape_table<double>(sphi, d1, d2);
+  __syncthreads();
+  for (int e = threadIdx.x; e < kPhiTable; e += blockDim.x) {
+    double v = e < kPhiSize ? sphi[e] : gauss_weight(e - kPhiSize, d1, d2);
+    t64[e] = v;
+    t32[e] = (float)v;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void load_shape_table(R* sphi, const R* __restrict__ table) {
+  for (int e = threadIdx.x; e < kPhiTable; e += blockDim.x) sphi[e] = table[e];
 }
 
 // ------------------------------------------------------------------------------------------
@@ -102,10 +122,10 @@ __device__ __forceinline__ void interp5(const R* sphi, const S* qv, int g, V3<R>
 constexpr int kRestFields = 13;
 
 __global__ void k_rest_setup(int np, const int4* __restrict__ pnodes, const double* __restrict__ rest,
-                             double d1, double d2, double lam, double mu, double* __restrict__ restgp,
-                             int* err) {
-  __shared__ double sphi[kPhiSize];
-  build_shape_table<double>(sphi, d1, d2);
+                             const double* __restrict__ table, double lam, double mu,
+                             double* __restrict__ restgp, int* err) {
+  __shared__ double sphi[kPhiTable];
+  load_shape_table<double>(sphi, table);
   __syncthreads();
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)np * 16) return;
@@ -137,16 +157,16 @@ __global__ void k_rest_setup(int np, const int4* __restrict__ pnodes, const doub
   restgp[9 * S + o] = (lam + 2 * mu) * ai22 * ai22;
   restgp[10 * S + o] = (lam + 2 * mu) * ai12 * ai22;
   restgp[11 * S + o] = (lam + mu) * ai12 * ai12 + mu * ai11 * ai22;
-  restgp[12 * S + o] = gauss_weight(g, d1, d2) * sq;
+  restgp[12 * S + o] = sphi[kPhiSize + g] * sq;
 }
 
 // Consistent mass (Eq. mass) as 4x4 scalar blocks and gravity load factors (Sec. 4.3).
 // One warp per patch; atomic scatter (once per shell).
 __global__ void k_mass(int np, const int* __restrict__ pblocks, const int4* __restrict__ pnodes,
-                       const double* __restrict__ restgp, double d1, double d2, double rho_h,
-                       double* __restrict__ mass, double* __restrict__ fgrav) {
-  __shared__ double sphi[kPhiSize];
-  build_shape_table<double>(sphi, d1, d2);
+                       const double* __restrict__ restgp, const double* __restrict__ table,
+                       double rho_h, double* __restrict__ mass, double* __restrict__ fgrav) {
+  __shared__ double sphi[kPhiTable];
+  load_shape_table<double>(sphi, table);
   __syncthreads();
   int lane = threadIdx.x & 31;
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -178,16 +198,19 @@ shell_status launch_rest_setup(Shell& s) {
   int np = s.n_patches;
   long long threads = (long long)np * 16;
   int blocks = (int)((threads + 255) / 256);
-  k_rest_setup<<<blocks, 256, 0, s.stream>>>(np, s.d_patch_nodes, s.d_rest, s.grid.dxi1,
-                                             s.grid.dxi2, s.lam, s.mu, s.d_restgp, s.d_err);
+  k_shape_table<<<1, 256, 0, s.stream>>>(s.grid.dxi1, s.grid.dxi2, s.d_phi64, s.d_phi32);
+  BHEM_CUDA(cudaGetLastError());
+  ++s.launches;
+  k_rest_setup<<<blocks, 256, 0, s.stream>>>(np, s.d_patch_nodes, s.d_rest, s.d_phi64, s.lam, s.mu,
+                                             s.d_restgp, s.d_err);
   BHEM_CUDA(cudaGetLastError());
   ++s.launches;
   BHEM_CUDA(cudaMemsetAsync(s.d_mass, 0, sizeof(double) * 16 * (size_t)s.n_blocks, s.stream));
   BHEM_CUDA(cudaMemsetAsync(s.d_fgrav, 0, sizeof(double) * 4 * (size_t)s.n_nodes, s.stream));
   int mblocks = grid_for((long long)np * 32, 256);
   k_mass<<<mblocks, 256, 0, s.stream>>>(np, s.d_patch_blocks, s.d_patch_nodes, s.d_restgp,
-                                        s.grid.dxi1, s.grid.dxi2,
-                                        s.mat.density * s.mat.thickness, s.d_mass, s.d_fgrav);
+                                        s.d_phi64, s.mat.density * s.mat.thickness, s.d_mass,
+                                        s.d_fgrav);
   BHEM_CUDA(cudaGetLastError());
   ++s.launches;
   return SHELL_OK;
@@ -201,13 +224,13 @@ constexpr int kEgPatches = 8;   // patches per CTA (128 threads)
 __global__ void __launch_bounds__(128)
 k_energy_grad64(int np, const int4* __restrict__ pnodes, const double* __restrict__ q,
                 const double* __restrict__ dir, double step, const double* __restrict__ restgp,
-                double d1, double d2, double h, double* __restrict__ energy_p,
+                const double* __restrict__ table, double h, double* __restrict__ energy_p,
                 const double* __restrict__ energy_ref, double* __restrict__ grad, Reduce red,
                 double* scal_out, int* err) {
-  __shared__ double sphi[kPhiSize];
+  __shared__ double sphi[kPhiTable];
   __shared__ double sq[kEgPatches][48];
   __shared__ double sG[kEgPatches][16][15];
-  build_shape_table<double>(sphi, d1, d2);
+  load_shape_table<double>(sphi, table);
   __syncthreads();
   const int hw = threadIdx.x >> 4, g = threadIdx.x & 15;
   const int p = blockIdx.x * kEgPatches + hw;
@@ -305,7 +328,7 @@ shell_status launch_energy_grad64(Shell& s, const double* q, const double* dir, 
   int blocks = (s.n_patches + kEgPatches - 1) / kEgPatches;
   if (blocks > kMaxPartials) return fail(SHELL_ERR_ARG, "too many patches for one reduction");
   k_energy_grad64<<<blocks, 128, 0, s.stream>>>(s.n_patches, s.d_patch_nodes, q, dir, step,
-                                                s.d_restgp, s.grid.dxi1, s.grid.dxi2,
+                                                s.d_restgp, s.d_phi64,
                                                 s.mat.thickness, energy_p, energy_ref, grad, s.red,
                                                 scal_out, s.d_err);
   BHEM_CUDA(cudaGetLastError());
@@ -333,6 +356,7 @@ struct WarpSmem {
 
 struct ElemArgs {
   int np;
+  const void* phi;         // shape table + Gauss weights in the kernel's precision
   const int4* pnodes;
   const int* plist;        // optional patch list (colour order), else identity
   int plist_n;
@@ -395,7 +419,7 @@ __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W
     sg[i] = H[i][0] * al[0] + H[i][1] * al[1] + H[i][2] * al[2];
     mm[i] = H[i][0] * be[0] + H[i][1] * be[1] + H[i][2] * be[2];
   }
-  const R wgt = (R)gauss_weight(g, A.d1, A.d2) * sqab;
+  const R wgt = sphi[kPhiSize + g] * sqab;
   const R s = h * h * h / (R)12;
   W.en[g] = wgt * ((R)0.5 * h * (al[0] * sg[0] + al[1] * sg[1] + al[2] * sg[2]) +
                    s * (R)0.5 * (be[0] * mm[0] + be[1] * mm[1] + be[2] * mm[2]));
@@ -527,8 +551,8 @@ k_element_full(ElemArgs A) {
   constexpr int JP = ElemCfg<R>::kJP;          // J columns per pass (16 / 2 / JP passes)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sphi = reinterpret_cast<R*>(smem_raw);
-  WarpSmem<R>* Ws = reinterpret_cast<WarpSmem<R>*>(smem_raw + sizeof(R) * ((kPhiSize + 3) & ~3));
-  build_shape_table<R>(sphi, A.d1, A.d2);
+  WarpSmem<R>* Ws = reinterpret_cast<WarpSmem<R>*>(smem_raw + sizeof(R) * ((kPhiTable + 3) & ~3));
+  load_shape_table<R>(sphi, reinterpret_cast<const R*>(A.phi));
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpSmem<R>& W = Ws[wid];
@@ -539,11 +563,22 @@ k_element_full(ElemArgs A) {
     const int p = A.plist ? A.plist[it] : it;
     const int4 pn = A.pnodes[p];
     const int nd[4] = {pn.x, pn.y, pn.z, pn.w};
+    // Value DOFs enter only through derivatives, whose value-kind shape functions sum to zero
+    // (partition of unity); subtracting corner 00's value in FP64 before rounding removes the
+    // O(|x| / dxi) cancellation of the derivative interpolation from the R arithmetic.
     for (int l = lane; l < 48; l += 32) {
-      size_t a = (size_t)nd[l / 12] * 12 + (l % 12);
+      const int kk = l % 12;
+      size_t a = (size_t)nd[l / 12] * 12 + kk;
       double qv = A.q[a], rv = A.rest[a];
-      W.u[l] = (R)(qv - rv);
-      W.qb[l] = (R)rv;
+      if (kk < 3) {
+        const size_t a0 = (size_t)nd[0] * 12 + kk;
+        const double q0 = A.q[a0], r0 = A.rest[a0];
+        W.u[l] = (R)((qv - rv) - (q0 - r0));
+        W.qb[l] = (R)(rv - r0);
+      } else {
+        W.u[l] = (R)(qv - rv);
+        W.qb[l] = (R)rv;
+      }
     }
     __syncwarp();
     if (lane < 16) gauss_point_matrix<R>(sphi, W, lane, A);
@@ -663,7 +698,7 @@ k_element_full(ElemArgs A) {
 
 template <typename R>
 static size_t elem_smem_bytes() {
-  return sizeof(R) * ((kPhiSize + 3) & ~3) + sizeof(WarpSmem<R>) * ElemCfg<R>::kWarps;
+  return sizeof(R) * ((kPhiTable + 3) & ~3) + sizeof(WarpSmem<R>) * ElemCfg<R>::kWarps;
 }
 
 template <typename R>
@@ -693,6 +728,7 @@ static shell_status launch_full_t(Shell& s, const ElemArgs& A, int work) {
 shell_status launch_element_full(Shell& s, const double* q, bool fp64, const ElemOutputs& out) {
   ElemArgs A{};
   A.np = s.n_patches;
+  A.phi = fp64 ? (const void*)s.d_phi64 : (const void*)s.d_phi32;
   A.pnodes = s.d_patch_nodes;
   A.pblocks = s.d_patch_blocks;
   A.q = q;

@@ -112,7 +112,7 @@ static void destroy_shell(shell_s* s) {
   if (!s) return;
   void* ptrs[] = {s->d_patch_nodes, s->d_patch_blocks, s->d_row_ptr, s->d_col, s->d_diag_block,
                   s->d_color_list, s->d_rest, s->d_restgp, s->d_mass, s->d_fgrav, s->d_val,
-                  s->d_x, s->d_r, s->d_z, s->d_p, s->d_Ap, s->d_diagA, s->d_Dinv,
+                  s->d_x, s->d_r, s->d_z, s->d_p, s->d_Ap, s->d_p32, s->d_Dinv, s->d_phi64, s->d_phi32,
                   s->d_pcg, s->d_qn, s->d_y, s->d_g, s->d_gin, s->d_d, s->d_Md, s->d_Ep,
                   s->d_qwork, s->d_vwork, s->d_qfix, s->d_warm, s->d_mask, s->d_ns, s->d_err,
                   s->d_energy_tmp, s->red.partials, s->red.ticket, s->d_rhs};
@@ -220,7 +220,8 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
     }
   }
   A(s->d_x, m); A(s->d_r, m); A(s->d_z, m); A(s->d_p, m); A(s->d_Ap, m);
-  A(s->d_diagA, m); A(s->d_pcg, 1);
+  A(s->d_pcg, 1); A(s->d_p32, m);
+  A(s->d_phi64, 1568); A(s->d_phi32, 1568);
   A(s->d_qn, m); A(s->d_y, m); A(s->d_g, m); A(s->d_gin, m); A(s->d_d, m); A(s->d_Md, m);
   A(s->d_rhs, m); A(s->d_Ep, np); A(s->d_qwork, m); A(s->d_vwork, m); A(s->d_qfix, m);
   A(s->d_warm, m); A(s->d_mask, m); A(s->d_ns, 1); A(s->d_err, 1); A(s->d_energy_tmp, 1);
@@ -339,18 +340,19 @@ extern "C" shell_status shell_get_mass(shell_t* shell, const double** mass_block
 
 namespace bhem {
 // Runs the PCG kernels on the assembled matrix; the solution is left in s.d_x.
-static shell_status run_pcg(Shell& s, const unsigned char* mask, double tau, const double* rhs,
-                            double rtol, int max_iter, int fixed, int* iters, int* neg) {
-  BHEM_TRY(launch_precond_setup(s, mask, tau));
+static shell_status run_pcg(Shell& s, const unsigned char* mask, const double td[4],
+                            const double* rhs, double rtol, int max_iter, int fixed, int* iters,
+                            int* neg) {
+  BHEM_TRY(launch_precond_setup(s, mask, td));
   BHEM_TRY(launch_pcg_init(s, mask, rhs, rtol, fixed));
   const int limit = fixed > 0 ? fixed : max_iter;
-  int launched = 0, chunk = fixed > 0 ? limit : 8;
+  int launched = 0, chunk = 4;
   *s.h_pcg = PcgState{};
   BHEM_CUDA(cudaMemcpyAsync(s.h_pcg, s.d_pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s.stream));
   BHEM_CUDA(cudaStreamSynchronize(s.stream));
   while (launched < limit && !s.h_pcg->done) {
     int c = std::min(chunk, limit - launched);
-    for (int k = 0; k < c; ++k) BHEM_TRY(launch_pcg_iteration(s, mask, tau));
+    for (int k = 0; k < c; ++k) BHEM_TRY(launch_pcg_iteration(s, mask, td));
     launched += c;
     BHEM_CUDA(cudaMemcpyAsync(s.h_pcg, s.d_pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s.stream));
     BHEM_CUDA(cudaStreamSynchronize(s.stream));
@@ -362,13 +364,39 @@ static shell_status run_pcg(Shell& s, const unsigned char* mask, double tau, con
 }
 }  // namespace bhem
 
+namespace bhem {
+// Per-kind regulariser scale dbar[k] = mean |A_ii| over free DOFs of kind k (1 if none) and the
+// per-kind minimum of A_ii, from the assembled matrix.
+struct KindStats { double dbar[4], dmin[4], count[4]; };
+static shell_status kind_stats(Shell& s, const unsigned char* mask, KindStats& K) {
+  BHEM_TRY(launch_diag_check(s, mask, s.d_ns->diag_stats));
+  BHEM_CUDA(cudaMemcpyAsync(s.h_ns, s.d_ns, sizeof(NewtonScalars), cudaMemcpyDeviceToHost, s.stream));
+  BHEM_CUDA(cudaStreamSynchronize(s.stream));
+  for (int q = 0; q < 4; ++q) {
+    K.count[q] = s.h_ns->diag_stats[3 * q + 1];
+    K.dbar[q] = K.count[q] > 0 ? s.h_ns->diag_stats[3 * q] / K.count[q] : 1.0;
+    K.dmin[q] = s.h_ns->diag_stats[3 * q + 2];
+  }
+  return SHELL_OK;
+}
+// A + tau D can only be positive definite if every free diagonal entry stays positive.
+static bool diag_positive(const KindStats& K, double tau) {
+  for (int q = 0; q < 4; ++q)
+    if (K.count[q] > 0 && !(K.dmin[q] + tau * K.dbar[q] > 0.0)) return false;
+  return true;
+}
+}  // namespace bhem
+
 extern "C" shell_status shell_pcg_solve(shell_t* shell, const unsigned char* fixed_mask, double tau,
                                         const double* rhs, double* x, double rtol, int max_iter,
                                         int fixed_iters, int* iters, int* neg_curv) {
   if (!shell || !rhs || !x) return fail(SHELL_ERR_ARG, "NULL argument");
   if (max_iter < 0 || fixed_iters < 0 || !(tau >= 0.0)) return fail(SHELL_ERR_ARG, "invalid PCG limits");
   int it = 0, neg = 0;
-  BHEM_TRY(run_pcg(*shell, fixed_mask, tau, rhs, rtol, max_iter, fixed_iters, &it, &neg));
+  KindStats K;
+  BHEM_TRY(kind_stats(*shell, fixed_mask, K));
+  const double td[4] = {tau * K.dbar[0], tau * K.dbar[1], tau * K.dbar[2], tau * K.dbar[3]};
+  BHEM_TRY(run_pcg(*shell, fixed_mask, td, rhs, rtol, max_iter, fixed_iters, &it, &neg));
   BHEM_CUDA(cudaMemcpyAsync(x, shell->d_x, sizeof(double) * shell->n_dof, cudaMemcpyDeviceToDevice, shell->stream));
   BHEM_TRY(sync_and_check(*shell));
   if (iters) *iters = it;
@@ -409,13 +437,21 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
     if (it >= P.newton_max) { status = SHELL_ERR_NOT_CONVERGED; break; }
     BHEM_TRY(assemble_hessian(s, q, inv_dt2));
     BHEM_TRY(launch_negate(s, s.d_g, s.d_rhs));
-    // Sec. 6.1 diagonal regulariser: tau = 0, then A + tau |diag(A)| with tau = 1e-8, 1e-6, ...,
-    // 1e4 (x100 per restart) while PCG meets negative curvature
+    // Sec. 6.1 diagonal regulariser: tau = 0, then A + tau D with tau = 1e-8, 1e-6, ..., 1e4
+    // (x100 per restart) while PCG meets negative curvature; D = per-kind mean |A_ii|. A level
+    // whose diagonal has a free entry <= 0 cannot be positive definite and is skipped.
+    KindStats K;
+    BHEM_TRY(kind_stats(s, mask, K));
     double tau = 0.0;
     for (int reg = 0;; ++reg) {
       int pit = 0, neg = 0;
-      BHEM_TRY(run_pcg(s, mask, tau, s.d_rhs, P.pcg_rtol, P.pcg_max, P.pcg_fixed_iters, &pit, &neg));
-      st.pcg_iters_total += pit;
+      if (diag_positive(K, tau)) {
+        const double td[4] = {tau * K.dbar[0], tau * K.dbar[1], tau * K.dbar[2], tau * K.dbar[3]};
+        BHEM_TRY(run_pcg(s, mask, td, s.d_rhs, P.pcg_rtol, P.pcg_max, P.pcg_fixed_iters, &pit, &neg));
+        st.pcg_iters_total += pit;
+      } else {
+        neg = 1;
+      }
       if (!neg) break;
       if (reg == 7) { status = SHELL_ERR_INDEFINITE; break; }
       st.regularizations++;
@@ -529,11 +565,12 @@ extern "C" shell_status shell_newton_step(shell_t* shell, const shell_step_param
   return st;
 }
 
-extern "C" shell_status shell_spmv(shell_t* shell, const double* x, double* y) {
+extern "C" shell_status shell_spmv(shell_t* shell, const void* x, int x_is_fp32, double* y) {
   if (!shell || !x || !y) return fail(SHELL_ERR_ARG, "NULL argument");
+  if (x_is_fp32 && shell->val_fp64) return fail(SHELL_ERR_ARG, "an FP64 shell takes FP64 x");
   if ((reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(y) & 7))
     return fail(SHELL_ERR_ARG, "x must be 16-byte aligned and y 8-byte aligned");
-  return launch_spmv(*shell, x, y);
+  return launch_spmv(*shell, x, x_is_fp32, y);
 }
 
 extern "C" shell_status shell_kernel_launches(const shell_t* shell, long long* count) {

@@ -14,7 +14,8 @@ int grid_for(long long work, int per_block) {
 }
 
 // ------------------------------------------------------------------------------------------
-// BSR SpMV  y = (A + tau |diag(A)|) p on free DOFs (y = 0 on fixed DOFs), fused with p . y.
+// BSR SpMV  y = (A + tau D) p on free DOFs (y = 0 on fixed DOFs), fused with p . y; tau D is
+// the regulariser shift per DOF kind (zero without regularisation).
 // Each 12x12 block row is read by TPR threads, one 16-byte chunk of one row per thread, so the
 // threads of a block row stream the block's 576 (FP32) or 1152 (FP64) bytes contiguously.
 // ------------------------------------------------------------------------------------------
@@ -22,11 +23,12 @@ template <typename Rm> struct Chunk;
 template <> struct Chunk<float> { using T = float4; static constexpr int E = 4; };
 template <> struct Chunk<double> { using T = double2; static constexpr int E = 2; };
 
-// dot of one 16-byte matrix chunk with the matching FP64 entries of x, in the matrix precision
-__device__ __forceinline__ float chunk_dot(float4 a, const double* __restrict__ x) {
-  const double2 x0 = *reinterpret_cast<const double2*>(x);
-  const double2 x1 = *reinterpret_cast<const double2*>(x + 2);
-  return a.x * (float)x0.x + a.y * (float)x0.y + a.z * (float)x1.x + a.w * (float)x1.y;
+// dot of one 16-byte matrix chunk with the matching entries of x, both in the matrix precision
+// (x is an FP32 copy for FP32 matrices: an FP64->FP32 conversion per product would run on the
+// narrow FP64 pipe)
+__device__ __forceinline__ float chunk_dot(float4 a, const float* __restrict__ x) {
+  const float4 xv = *reinterpret_cast<const float4*>(x);
+  return a.x * xv.x + a.y * xv.y + a.z * xv.z + a.w * xv.w;
 }
 __device__ __forceinline__ double chunk_dot(double2 a, const double* __restrict__ x) {
   const double2 x0 = *reinterpret_cast<const double2*>(x);
@@ -38,7 +40,7 @@ constexpr int kSpmvThreads = 288;
 template <typename Rm>
 __global__ void __launch_bounds__(kSpmvThreads)
 k_spmv(int n, const int* __restrict__ rp, const int* __restrict__ col, const Rm* __restrict__ val,
-       const double* __restrict__ x, const double* __restrict__ diagA, double tau,
+       const Rm* __restrict__ x, const double* __restrict__ xd, Shift4 td,
        const unsigned char* __restrict__ mask, double* __restrict__ y, PcgState* st, Reduce red) {
   using CT = typename Chunk<Rm>::T;
   constexpr int E = Chunk<Rm>::E;
@@ -53,10 +55,24 @@ k_spmv(int n, const int* __restrict__ rp, const int* __restrict__ col, const Rm*
   Rm acc = 0;
   if (i < n) {
     const int k0 = rp[i], k1 = rp[i + 1];
-    for (int k = k0; k < k1; ++k) {
-      const int j = col[k];
-      CT v = __ldcs(reinterpret_cast<const CT*>(val + (size_t)k * 144 + r * 12 + cc * E));
-      acc += chunk_dot(v, x + (size_t)j * 12 + cc * E);
+    // a node of the structured grid couples to at most 9 nodes: issue all block loads first
+    constexpr int U = 9;
+    CT v[U];
+    int j[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u;
+      if (k < k1) {
+        j[u] = col[k];
+        v[u] = __ldcs(reinterpret_cast<const CT*>(val + (size_t)k * 144 + r * 12 + cc * E));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (k0 + u < k1) acc += chunk_dot(v[u], x + (size_t)j[u] * 12 + cc * E);
+    for (int k = k0 + U; k < k1; ++k) {
+      CT w = __ldcs(reinterpret_cast<const CT*>(val + (size_t)k * 144 + r * 12 + cc * E));
+      acc += chunk_dot(w, x + (size_t)col[k] * 12 + cc * E);
     }
   }
   sacc[t] = acc;
@@ -67,9 +83,9 @@ k_spmv(int n, const int* __restrict__ rp, const int* __restrict__ col, const Rm*
 #pragma unroll
     for (int c = 0; c < NC; ++c) s += (double)sacc[t + c];
     const size_t gi = (size_t)i * 12 + r;
-    const double xi = x[gi];
+    const double xi = xd ? xd[gi] : (double)x[gi];
     double yi = s;
-    if (tau != 0.0) yi += tau * fabs(diagA[gi]) * xi;
+    yi += td.v[r / 3] * xi;
     if (mask && mask[gi]) yi = 0.0;
     y[gi] = yi;
     part = xi * yi;
@@ -90,70 +106,92 @@ k_spmv(int n, const int* __restrict__ rp, const int* __restrict__ col, const Rm*
 }
 
 // ------------------------------------------------------------------------------------------
-// Block-Jacobi: D_i = (A_ii masked + tau |diag|)^{-1} by Cholesky; a block that is not SPD falls
-// back to the inverse of its diagonal. Also records diag(A). One thread per node.
+// Block-Jacobi: D_i = (A_ii masked + tau D)^{-1} by Cholesky; a block that is not SPD falls back
+// to the inverse of its diagonal. 12 threads per node (one row each), 16 nodes per CTA.
 // ------------------------------------------------------------------------------------------
 template <typename Rm, typename Rd>
-__global__ void k_precond(int n, const int* __restrict__ diag_block, const Rm* __restrict__ val,
-                          const unsigned char* __restrict__ mask, double tau,
-                          double* __restrict__ diagA, Rd* __restrict__ Dinv) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const Rm* B = val + (size_t)diag_block[i] * 144;
-  Rd L[144];
-  bool fixed[12];
-  for (int a = 0; a < 12; ++a) {
-    fixed[a] = mask && mask[(size_t)i * 12 + a];
-    diagA[(size_t)i * 12 + a] = (double)B[a * 13];
-  }
-  for (int a = 0; a < 12; ++a)
+__global__ void __launch_bounds__(192)
+k_precond(int n, const int* __restrict__ diag_block, const Rm* __restrict__ val,
+          const unsigned char* __restrict__ mask, Shift4 td, Rd* __restrict__ Dinv) {
+  __shared__ Rd sL[16][12][13];
+  __shared__ Rd sW[16][12][13];
+  __shared__ Rd sdiag[16][12];
+  __shared__ int sok[16];
+  const int ln = threadIdx.x / 12, a = threadIdx.x % 12;
+  const int i = blockIdx.x * 16 + ln;
+  const bool active = i < n;
+  if (active) {
+    const Rm* B = val + (size_t)diag_block[i] * 144;
+    const bool fa = mask && mask[(size_t)i * 12 + a];
     for (int b = 0; b < 12; ++b) {
+      const bool fb = mask && mask[(size_t)i * 12 + b];
       Rd v = (Rd)B[a * 12 + b];
-      if (fixed[a] || fixed[b]) v = (a == b) ? (Rd)1 : (Rd)0;
-      else if (a == b) v += (Rd)(tau * fabs((double)B[a * 13]));
-      L[a * 12 + b] = v;
+      if (fa || fb) v = (a == b) ? (Rd)1 : (Rd)0;
+      else if (a == b) v += (Rd)td.v[a / 3];
+      sL[ln][a][b] = v;
     }
-  Rd diag[12];
-  for (int a = 0; a < 12; ++a) diag[a] = L[a * 13];
-  bool ok = true;
-  // in-place Cholesky, lower triangle
-  for (int j = 0; j < 12 && ok; ++j) {
-    Rd s = L[j * 13];
-    for (int k = 0; k < j; ++k) s -= L[j * 12 + k] * L[j * 12 + k];
-    if (!(s > (Rd)0)) { ok = false; break; }
-    Rd d = sqrt(s);
-    L[j * 13] = d;
-    for (int a = j + 1; a < 12; ++a) {
-      Rd u = L[a * 12 + j];
-      for (int k = 0; k < j; ++k) u -= L[a * 12 + k] * L[j * 12 + k];
-      L[a * 12 + j] = u / d;
+    sdiag[ln][a] = sL[ln][a][a];
+  }
+  if (a == 0) sok[ln] = 1;
+  __syncthreads();
+  for (int j = 0; j < 12; ++j) {
+    if (active && a == j && sok[ln]) {
+      Rd sacc = sL[ln][j][j];
+      for (int k = 0; k < j; ++k) sacc -= sL[ln][j][k] * sL[ln][j][k];
+      if (!(sacc > (Rd)0)) sok[ln] = 0;
+      else sL[ln][j][j] = sqrt(sacc);
+    }
+    __syncthreads();
+    if (active && a > j && sok[ln]) {
+      Rd u = sL[ln][a][j];
+      for (int k = 0; k < j; ++k) u -= sL[ln][a][k] * sL[ln][j][k];
+      sL[ln][a][j] = u / sL[ln][j][j];
+    }
+    __syncthreads();
+  }
+  const bool ok = active && sok[ln];
+  if (ok) {
+    // column a of W = L^{-1} (lower triangular) by forward substitution
+    for (int r = 0; r < 12; ++r) {
+      if (r < a) { sW[ln][r][a] = 0; continue; }
+      Rd u = (r == a) ? (Rd)1 : (Rd)0;
+      for (int k = a; k < r; ++k) u -= sL[ln][r][k] * sW[ln][k][a];
+      sW[ln][r][a] = u / sL[ln][r][r];
     }
   }
-  Rd* D = Dinv + (size_t)i * 144;
-  if (!ok) {
-    for (int a = 0; a < 12; ++a)
-      for (int b = 0; b < 12; ++b)
-        D[a * 12 + b] = (a == b) ? (diag[a] > (Rd)0 ? (Rd)1 / diag[a] : (Rd)1) : (Rd)0;
-    return;
-  }
-  // W = L^{-1} (lower), stored in the upper triangle's mirror: compute column by column
-  Rd Wm[144];
-  for (int c = 0; c < 12; ++c) {
-    for (int a = 0; a < 12; ++a) {
-      if (a < c) { Wm[a * 12 + c] = 0; continue; }
-      Rd u = (a == c) ? (Rd)1 : (Rd)0;
-      for (int k = c; k < a; ++k) u -= L[a * 12 + k] * Wm[k * 12 + c];
-      Wm[a * 12 + c] = u / L[a * 13];
+  __syncthreads();
+  if (!active) return;
+  Rd* D = Dinv + (size_t)i * 144 + a * 12;
+  if (ok) {
+    for (int b = 0; b < 12; ++b) {   // D = W^T W, row a
+      Rd sacc = 0;
+      for (int k = (a > b ? a : b); k < 12; ++k) sacc += sW[ln][k][a] * sW[ln][k][b];
+      D[b] = sacc;
     }
+  } else {
+    const Rd d = sdiag[ln][a];
+    for (int b = 0; b < 12; ++b) D[b] = (a == b) ? (d > (Rd)0 ? (Rd)1 / d : (Rd)1) : (Rd)0;
   }
-  // D = W^T W
-  for (int a = 0; a < 12; ++a)
-    for (int b = a; b < 12; ++b) {
-      Rd s = 0;
-      for (int k = (a > b ? a : b); k < 12; ++k) s += Wm[k * 12 + a] * Wm[k * 12 + b];
-      D[a * 12 + b] = s;
-      D[b * 12 + a] = s;
-    }
+}
+
+// Per DOF kind k (x, x_,1, x_,2, x_,12), over free DOFs: sum |A_ii|, count, min A_ii. They give the
+// regulariser scale (mean |A_ii| of the kind) and tell which regulariser levels leave a
+// non-positive diagonal entry (such a matrix cannot be positive definite).
+template <typename Rm>
+__global__ void k_diag_check(int n, const int* __restrict__ diag_block, const Rm* __restrict__ val,
+                             const unsigned char* __restrict__ mask, double* out12, Reduce red) {
+  double v[12];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) { v[3 * q] = 0.0; v[3 * q + 1] = 0.0; v[3 * q + 2] = INFINITY; }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n * 12; k += gridDim.x * blockDim.x) {
+    if (mask && mask[k]) continue;
+    const int i = k / 12, a = k % 12, q = a / 3;
+    const double d = (double)val[(size_t)diag_block[i] * 144 + a * 13];
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq)
+      if (qq == q) { v[3 * qq] += fabs(d); v[3 * qq + 1] += 1.0; v[3 * qq + 2] = fmin(v[3 * qq + 2], d); }
+  }
+  grid_reduce<12>(v, red, out12, gridDim.x, 0x924u);   // the min entries: 2, 5, 8, 11
 }
 
 // ------------------------------------------------------------------------------------------
@@ -162,10 +200,10 @@ __global__ void k_precond(int n, const int* __restrict__ diag_block, const Rm* _
 constexpr int kNodeThreads = 192;
 
 template <typename Rd>
-__device__ __forceinline__ double apply_block(const Rd* __restrict__ D, const double* sr, int a) {
+__device__ __forceinline__ double apply_block(const Rd* __restrict__ D, const Rd* sr, int a) {
   Rd s = 0;
 #pragma unroll
-  for (int c = 0; c < 12; ++c) s += D[a * 12 + c] * (Rd)sr[c];
+  for (int c = 0; c < 12; ++c) s += D[a * 12 + c] * sr[c];
   return (double)s;
 }
 
@@ -173,9 +211,9 @@ template <typename Rd>
 __global__ void __launch_bounds__(kNodeThreads)
 k_pcg_init(int n, const double* __restrict__ rhs, const Rd* __restrict__ Dinv,
            const unsigned char* __restrict__ mask, double* __restrict__ x, double* __restrict__ r,
-           double* __restrict__ z, double* __restrict__ p, double rtol2,
+           double* __restrict__ z, double* __restrict__ p, Rd* __restrict__ pr, double rtol2,
            int fixed, PcgState* st, Reduce red) {
-  __shared__ double sr[16][12];
+  __shared__ Rd sr[16][12];
   const int ln = threadIdx.x / 12, a = threadIdx.x % 12;
   const int i = blockIdx.x * 16 + ln;
   const size_t gi = (size_t)i * 12 + a;
@@ -184,13 +222,14 @@ k_pcg_init(int n, const double* __restrict__ rhs, const Rd* __restrict__ Dinv,
     ri = (mask && mask[gi]) ? 0.0 : rhs[gi];
     x[gi] = 0.0;
     r[gi] = ri;
-    sr[ln][a] = ri;
+    sr[ln][a] = (Rd)ri;
   }
   __syncthreads();
   if (i < n) {
     zi = (mask && mask[gi]) ? 0.0 : apply_block<Rd>(Dinv + (size_t)i * 144, sr[ln], a);
     z[gi] = zi;
     p[gi] = zi;
+    if (pr) pr[gi] = (Rd)zi;
   }
   double v[2] = {ri * zi, ri * ri};
   double out[2];
@@ -216,7 +255,7 @@ k_pcg_update(int n, double* __restrict__ x, double* __restrict__ r, double* __re
              const Rd* __restrict__ Dinv, const unsigned char* __restrict__ mask, PcgState* st,
              Reduce red) {
   if (st->done) return;
-  __shared__ double sr[16][12];
+  __shared__ Rd sr[16][12];
   const int ln = threadIdx.x / 12, a = threadIdx.x % 12;
   const int i = blockIdx.x * 16 + ln;
   const size_t gi = (size_t)i * 12 + a;
@@ -226,7 +265,7 @@ k_pcg_update(int n, double* __restrict__ x, double* __restrict__ r, double* __re
     x[gi] += alpha * p[gi];
     ri = r[gi] - alpha * Ap[gi];
     r[gi] = ri;
-    sr[ln][a] = ri;
+    sr[ln][a] = (Rd)ri;
   }
   __syncthreads();
   if (i < n) {
@@ -247,11 +286,18 @@ k_pcg_update(int n, double* __restrict__ x, double* __restrict__ r, double* __re
 }
 
 __global__ void k_pcg_pupdate(int m, const double* __restrict__ z, double* __restrict__ p,
-                              const PcgState* st) {
+                              float* __restrict__ p32, const PcgState* st) {
   if (st->done) return;
   const double beta = st->beta;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x)
-    p[k] = z[k] + beta * p[k];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+    const double v = z[k] + beta * p[k];
+    p[k] = v;
+    if (p32) p32[k] = (float)v;
+  }
+}
+
+__global__ void k_to_float(int m, const double* __restrict__ a, float* __restrict__ b) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) b[k] = (float)a[k];
 }
 
 // ------------------------------------------------------------------------------------------
@@ -388,14 +434,29 @@ shell_status launch_dots3(Shell& s, int m, const double* a0, const double* b0, c
   return SHELL_OK;
 }
 
-shell_status launch_precond_setup(Shell& s, const unsigned char* mask, double tau) {
-  int blocks = grid_for(s.n_nodes, 64);
+shell_status launch_precond_setup(Shell& s, const unsigned char* mask, const double td[4]) {
+  int blocks = grid_for(s.n_nodes, 16);
+  Shift4 sh{{td[0], td[1], td[2], td[3]}};
   if (s.val_fp64)
-    k_precond<double, double><<<blocks, 64, 0, s.stream>>>(s.n_nodes, s.d_diag_block,
-        (const double*)s.d_val, mask, tau, s.d_diagA, (double*)s.d_Dinv);
+    k_precond<double, double><<<blocks, 192, 0, s.stream>>>(s.n_nodes, s.d_diag_block,
+        (const double*)s.d_val, mask, sh, (double*)s.d_Dinv);
   else
-    k_precond<float, float><<<blocks, 64, 0, s.stream>>>(s.n_nodes, s.d_diag_block,
-        (const float*)s.d_val, mask, tau, s.d_diagA, (float*)s.d_Dinv);
+    k_precond<float, float><<<blocks, 192, 0, s.stream>>>(s.n_nodes, s.d_diag_block,
+        (const float*)s.d_val, mask, sh, (float*)s.d_Dinv);
+  BHEM_CUDA(cudaGetLastError());
+  ++s.launches;
+  return SHELL_OK;
+}
+
+shell_status launch_diag_check(Shell& s, const unsigned char* mask, double* out12) {
+  int blocks = vec_blocks(s.n_dof);
+  if (blocks > 1024) blocks = 1024;
+  if (s.val_fp64)
+    k_diag_check<double><<<blocks, 256, 0, s.stream>>>(s.n_nodes, s.d_diag_block,
+        (const double*)s.d_val, mask, out12, s.red);
+  else
+    k_diag_check<float><<<blocks, 256, 0, s.stream>>>(s.n_nodes, s.d_diag_block,
+        (const float*)s.d_val, mask, out12, s.red);
   BHEM_CUDA(cudaGetLastError());
   ++s.launches;
   return SHELL_OK;
@@ -408,45 +469,56 @@ shell_status launch_pcg_init(Shell& s, const unsigned char* mask, const double* 
   double rtol2 = fixed > 0 ? 0.0 : rtol * rtol;
   if (s.val_fp64)
     k_pcg_init<double><<<blocks, kNodeThreads, 0, s.stream>>>(
-        s.n_nodes, rhs, (const double*)s.d_Dinv, mask, s.d_x, s.d_r, s.d_z, s.d_p, rtol2, fixed,
-        s.d_pcg, s.red);
+        s.n_nodes, rhs, (const double*)s.d_Dinv, mask, s.d_x, s.d_r, s.d_z, s.d_p, nullptr, rtol2,
+        fixed, s.d_pcg, s.red);
   else
     k_pcg_init<float><<<blocks, kNodeThreads, 0, s.stream>>>(
-        s.n_nodes, rhs, (const float*)s.d_Dinv, mask, s.d_x, s.d_r, s.d_z, s.d_p, rtol2, fixed,
-        s.d_pcg, s.red);
+        s.n_nodes, rhs, (const float*)s.d_Dinv, mask, s.d_x, s.d_r, s.d_z, s.d_p, s.d_p32, rtol2,
+        fixed, s.d_pcg, s.red);
   BHEM_CUDA(cudaGetLastError());
   ++s.launches;
   return SHELL_OK;
 }
 
-static shell_status launch_spmv_impl(Shell& s, const double* x, const unsigned char* mask,
-                                     double tau, double* y, PcgState* st) {
+static shell_status launch_spmv_impl(Shell& s, const void* x, const double* xd,
+                                     const unsigned char* mask, const double td[4], double* y,
+                                     PcgState* st) {
+  Shift4 sh{{td[0], td[1], td[2], td[3]}};
   const int n = s.n_nodes;
   if (s.val_fp64) {
     constexpr int RPC = kSpmvThreads / 72;
     int blocks = grid_for(n, RPC);
     if (st && blocks > kMaxPartials) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
     k_spmv<double><<<blocks, kSpmvThreads, 0, s.stream>>>(n, s.d_row_ptr, s.d_col,
-        (const double*)s.d_val, x, s.d_diagA, tau, mask, y, st, s.red);
+        (const double*)s.d_val, (const double*)x, xd, sh, mask, y, st, s.red);
   } else {
     constexpr int RPC = kSpmvThreads / 36;
     int blocks = grid_for(n, RPC);
     if (st && blocks > kMaxPartials) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
     k_spmv<float><<<blocks, kSpmvThreads, 0, s.stream>>>(n, s.d_row_ptr, s.d_col,
-        (const float*)s.d_val, x, s.d_diagA, tau, mask, y, st, s.red);
+        (const float*)s.d_val, (const float*)x, xd, sh, mask, y, st, s.red);
   }
   BHEM_CUDA(cudaGetLastError());
   ++s.launches;
   return SHELL_OK;
 }
 
-shell_status launch_spmv(Shell& s, const double* x, double* y) {
-  return launch_spmv_impl(s, x, nullptr, 0.0, y, nullptr);
+shell_status launch_spmv(Shell& s, const void* x, int x_fp32, double* y) {
+  const double zero[4] = {0.0, 0.0, 0.0, 0.0};
+  if (!s.val_fp64 && !x_fp32) {
+    // FP32 matrix, FP64 input: one conversion pass into the shell's FP32 vector first
+    k_to_float<<<vec_blocks(s.n_dof), 256, 0, s.stream>>>(s.n_dof, (const double*)x, s.d_p32);
+    BHEM_CUDA(cudaGetLastError());
+    ++s.launches;
+    x = s.d_p32;
+  }
+  return launch_spmv_impl(s, x, nullptr, nullptr, zero, y, nullptr);
 }
 
-shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, double tau) {
+shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, const double td[4]) {
   const int n = s.n_nodes, m = s.n_dof;
-  BHEM_TRY(launch_spmv_impl(s, s.d_p, mask, tau, s.d_Ap, s.d_pcg));
+  const void* px = s.val_fp64 ? (const void*)s.d_p : (const void*)s.d_p32;
+  BHEM_TRY(launch_spmv_impl(s, px, s.d_p, mask, td, s.d_Ap, s.d_pcg));
   if (s.val_fp64)
     k_pcg_update<double><<<grid_for(n, 16), kNodeThreads, 0, s.stream>>>(
         n, s.d_x, s.d_r, s.d_z, s.d_p, s.d_Ap, (const double*)s.d_Dinv, mask, s.d_pcg, s.red);
@@ -455,7 +527,8 @@ shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, double ta
         n, s.d_x, s.d_r, s.d_z, s.d_p, s.d_Ap, (const float*)s.d_Dinv, mask, s.d_pcg, s.red);
   BHEM_CUDA(cudaGetLastError());
   ++s.launches;
-  k_pcg_pupdate<<<vec_blocks(m), 256, 0, s.stream>>>(m, s.d_z, s.d_p, s.d_pcg);
+  k_pcg_pupdate<<<vec_blocks(m), 256, 0, s.stream>>>(m, s.d_z, s.d_p, s.val_fp64 ? nullptr : s.d_p32,
+                                                     s.d_pcg);
   BHEM_CUDA(cudaGetLastError());
   ++s.launches;
   return SHELL_OK;

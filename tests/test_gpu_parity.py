@@ -107,6 +107,10 @@ def test_spmv_matches_dense_product(prec):
     x = np.random.default_rng(0).normal(size=g.n_dof)
     y = host(sh.spmv(dev(x)))
     assert rel(y, A @ x) <= (1e-13 if prec == "fp64" else 1e-5)
+    if prec == "mixed":   # FP32 input: the single-launch form
+        x32 = x.astype(np.float32)
+        y32 = host(sh.spmv(dev(x32, torch.float32)))
+        assert rel(y32, A @ x32.astype(np.float64)) <= 1e-5
 
 
 def test_pcg_parity_fp64():
