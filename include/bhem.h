@@ -181,6 +181,32 @@ SHELL_API shell_status shell_newton_step(shell_t* shell, const shell_step_params
                                double* q, double* v, const double* warm_start,
                                shell_step_stats* stats);
 
+/* Elastic energy and gradient without any device allocation. This is an interface addition of
+   this library; the paper has no counterpart. It computes the same quantities as the energy
+   and grad outputs of shell_energy_grad_hess (Sec. 3.3 energy, App. B.1 gradient), for
+   callers that must not allocate device memory while they run: applications whose device
+   memory belongs entirely to their own pool allocator (cudaMalloc would fail or escape its
+   accounting), latency-bound loops that cannot afford the device-wide synchronisation a
+   cudaMalloc/cudaFree may cause, and plug-ins that receive a fixed memory budget from their
+   host. No shell object is needed: the patch topology comes from grid, the shape table and the
+   rest geometry are computed from rest_dofs on every call.
+   Arguments: grid, material (host); rest_dofs, q: device [n_nodes * 12] FP64 (caller-owned,
+   read only); energy: device, 1 double (overwritten); grad: device [n_nodes * 12] FP64 or NULL
+   (overwritten); stream: cudaStream_t or NULL. Asynchronous: enqueues a memset of the ticket
+   (and of grad) and two kernels on stream, calls no cudaMalloc, cudaFree or allocating library
+   routine.
+   Scratch: one file-scope device array of about 141 KB (per-CTA energy sums, the shape table and
+   a counter), present on every GPU that loads the library until the process exits. Grids of
+   more than 131072 patches are rejected with SHELL_ERR_ARG. The first call on a device looks up
+   the array's device address (cudaGetSymbolAddress) with that device current; make that first
+   call before any stream capture. All calls share the array and each call resets the counter it
+   needs: calls whose work overlaps on the GPU (other streams, other host threads on the same
+   device) race on it and must be serialised by the caller. A degenerate geometry gives a
+   non-finite energy instead of an error code. */
+SHELL_API shell_status shell_energy_grad_noalloc(const shell_grid* grid, const shell_material* material,
+                                                 const double* rest_dofs, const double* q,
+                                                 double* energy, double* grad, void* stream);
+
 /* Number of CUDA kernels this shell has launched since shell_create (host counter; counts the
    launches of the library's own kernels, not memset/memcpy operations). */
 SHELL_API shell_status shell_kernel_launches(const shell_t* shell, long long* count);

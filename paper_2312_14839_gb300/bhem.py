@@ -89,6 +89,7 @@ def load():
                 "shell_newton_step": [p, p, p, p, p, p, p, p],
                 "shell_spmv": [p, p, i, p],
                 "shell_kernel_launches": [p, p],
+                "shell_energy_grad_noalloc": [p, p, p, p, p, p, p],
             }
             for name, args in sigs.items():
                 fn = getattr(lib, name)
@@ -133,6 +134,18 @@ def step_params(dt=1e-3, gravity=(0.0, 0.0, -9.81), newton_rtol=1e-8, newton_max
                 pcg_rtol=1e-6, pcg_max=1000, pcg_fixed_iters=0) -> shell_step_params:
     return shell_step_params(float(dt), (C.c_double * 3)(*gravity), float(newton_rtol),
                              int(newton_max), float(pcg_rtol), int(pcg_max), int(pcg_fixed_iters))
+
+
+def energy_grad_noalloc(grid, material, rest, q, energy, grad=None, stream=None):
+    """shell_energy_grad_noalloc: elastic energy (into ``energy``, a 1-element FP64 CUDA tensor)
+    and gradient (into ``grad`` or None) without any device allocation by the library."""
+    _, sh = _stream_handle(stream)
+    g = shell_grid(int(grid.nu), int(grid.nv), int(bool(grid.periodic_u)), int(bool(grid.periodic_v)),
+                   float(grid.dxi1), float(grid.dxi2))
+    m = shell_material(float(material.young), float(material.poisson), float(material.thickness),
+                       float(material.density))
+    _check(load().shell_energy_grad_noalloc(C.byref(g), C.byref(m), _ptr(rest), _ptr(q), _ptr(energy),
+                                            _ptr(grad), sh))
 
 
 class Shell:
