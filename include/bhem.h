@@ -163,11 +163,11 @@ SHELL_API shell_status shell_pcg_solve(shell_t* shell, const unsigned char* fixe
 
 /* y = A x with the currently assembled BSR A (the product inside every PCG iteration of
    Sec. 6.1's linear solve; FP32 arithmetic with FP32 accumulation per row chunk when the shell
-   is SHELL_PREC_MIXED, FP64 otherwise). x: device [n_dof], 16-byte aligned, FP32 when
-   x_is_fp32 != 0 (SHELL_PREC_MIXED shells only: one kernel launch) else FP64 (a mixed shell
-   first converts it to FP32 in its own buffer: two launches); y: device [n_dof] FP64, 8-byte
-   aligned. No mask, no regulariser. Asynchronous. */
-SHELL_API shell_status shell_spmv(shell_t* shell, const void* x, int x_is_fp32, double* y);
+   is SHELL_PREC_MIXED, FP64 otherwise). x, y: device [n_dof], x 16-byte and y 8-byte aligned.
+   x_is_fp32 != 0 (SHELL_PREC_MIXED shells only): x and y are FP32 and the call is one launch of
+   the kernel every PCG iteration runs. Otherwise x and y are FP64 (a mixed shell converts
+   through its own FP32 vectors: three launches). No mask, no regulariser. Asynchronous. */
+SHELL_API shell_status shell_spmv(shell_t* shell, const void* x, int x_is_fp32, void* y);
 
 /* One implicit-Euler step (Eq. implicit) by Newton with line search (Sec. 6.1):
    minimises Pi(q) = (q - y)^T M (q - y) / (2 dt^2) + V_e(q) - F^T q, y = q^n + dt v^n, over the

@@ -253,11 +253,11 @@ class Shell:
         return n.value
 
     def spmv(self, x, y=None):
-        """y = A x with the assembled BSR on the shell's stream; x FP64, or FP32 for a mixed shell
-        (then one kernel launch)."""
+        """y = A x with the assembled BSR on the shell's stream; x, y FP64, or FP32 for a mixed
+        shell (then one kernel launch)."""
         import torch
         if y is None:
-            y = torch.empty(x.shape, dtype=torch.float64, device=x.device)
+            y = torch.empty(x.shape, dtype=x.dtype, device=x.device)
         _check(load().shell_spmv(self._h, _ptr(x), int(x.dtype == torch.float32), _ptr(y)))
         return y
 

@@ -97,7 +97,8 @@ struct Shell {
 
   // PCG workspace
   double *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_Ap = nullptr;
-  float* d_p32 = nullptr;           // FP32 copy of p read by the FP32 SpMV
+  float* d_p32 = nullptr;           // FP32 PCG vectors of a mixed-precision shell
+  float *d_x32 = nullptr, *d_r32 = nullptr, *d_z32 = nullptr, *d_Ap32 = nullptr;
   void* d_Dinv = nullptr;           // [n_nodes * 144] block-Jacobi inverses (FP32 or FP64)
   PcgState* d_pcg = nullptr;
 
@@ -155,7 +156,8 @@ shell_status launch_precond_setup(Shell& s, const unsigned char* mask, const dou
 shell_status launch_pcg_init(Shell& s, const unsigned char* mask, const double* rhs,
                              double rtol, int fixed);
 shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, const double td[4]);
-shell_status launch_spmv(Shell& s, const void* x, int x_fp32, double* y);
+shell_status launch_spmv(Shell& s, const void* x, int x_fp32, void* y);
+shell_status launch_pcg_result(Shell& s);
 shell_status launch_diag_check(Shell& s, const unsigned char* mask, double* out12);
 shell_status launch_axpy_fixed(Shell& s, double* q, const double* d, double alpha);
 shell_status launch_overwrite_fixed(Shell& s, double* dst, const double* src,
@@ -165,6 +167,80 @@ shell_status launch_velocity(Shell& s, const double* q, const double* qn, double
 shell_status launch_negate(Shell& s, const double* a, double* b);
 
 int grid_for(long long work, int per_block);
+
+// ------------------------------------------------------------------------------------------
+// Double-float arithmetic on the FP32 pipe (GB300's FP64 pipe is narrow): a value is hi + lo.
+// Products of two floats are exact as (p, fma(a, b, -p)); sums use two-sum.
+// ------------------------------------------------------------------------------------------
+struct F2 { float hi, lo; };
+
+__device__ __forceinline__ F2 f2_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  const F2 s = f2_two_sum(a.hi, b.hi);
+  const float lo = __fadd_rn(__fadd_rn(s.lo, a.lo), b.lo);
+  const float hi = __fadd_rn(s.hi, lo);
+  return {hi, __fsub_rn(lo, __fsub_rn(hi, s.hi))};
+}
+__device__ __forceinline__ F2 f2_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, fmaf(a, b, -p)};
+}
+
+// Grid reduction of NV double-float sums, entirely on the FP32 pipe: per-CTA partials are stored
+// as (hi, lo) pairs and the last CTA (ticket, no waiting) combines them in a fixed order; only the
+// final value is converted to FP64. Same contract as grid_reduce.
+__device__ __forceinline__ F2 f2_block_sum(F2 x, F2 (*sred)[32], int i) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    F2 y;
+    y.hi = __shfl_xor_sync(0xffffffffu, x.hi, o);
+    y.lo = __shfl_xor_sync(0xffffffffu, x.lo, o);
+    x = f2_add(x, y);
+  }
+  if (lane == 0) sred[i][wid] = x;
+  __syncthreads();
+  F2 s = sred[i][0];
+  for (int w = 1; w < nw; ++w) s = f2_add(s, sred[i][w]);
+  __syncthreads();
+  return s;
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_reduce_f2(const F2 (&v)[NV], Reduce red, double* out,
+                                               int nblocks) {
+  __shared__ F2 sred2[NV][32];
+  __shared__ int last2;
+  float2* part = reinterpret_cast<float2*>(red.partials);
+  for (int i = 0; i < NV; ++i) {
+    const F2 s = f2_block_sum(v[i], sred2, i);
+    if (threadIdx.x == 0) part[(size_t)i * kMaxPartials + blockIdx.x] = make_float2(s.hi, s.lo);
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned t = atomicAdd(red.ticket, 1u);
+    last2 = (t == (unsigned)nblocks - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!last2) return false;
+  __threadfence();
+  for (int i = 0; i < NV; ++i) {
+    F2 s{0.f, 0.f};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+      const float2 y = __ldcg(part + (size_t)i * kMaxPartials + b);   // L2: other CTAs' writes
+      s = f2_add(s, F2{y.x, y.y});
+    }
+    const F2 t = f2_block_sum(s, sred2, i);
+    if (threadIdx.x == 0) out[i] = (double)t.hi + (double)t.lo;
+  }
+  if (threadIdx.x == 0) *red.ticket = 0u;
+  __syncthreads();
+  return true;
+}
 
 // ------------------------------------------------------------------------------------------
 // Deterministic grid reduction of NV doubles (every thread of every CTA must call it): the

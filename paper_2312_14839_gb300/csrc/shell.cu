@@ -112,7 +112,7 @@ static void destroy_shell(shell_s* s) {
   if (!s) return;
   void* ptrs[] = {s->d_patch_nodes, s->d_patch_blocks, s->d_row_ptr, s->d_col, s->d_diag_block,
                   s->d_color_list, s->d_rest, s->d_restgp, s->d_mass, s->d_fgrav, s->d_val,
-                  s->d_x, s->d_r, s->d_z, s->d_p, s->d_Ap, s->d_p32, s->d_Dinv, s->d_phi64, s->d_phi32,
+                  s->d_x, s->d_r, s->d_z, s->d_p, s->d_Ap, s->d_p32, s->d_x32, s->d_r32, s->d_z32, s->d_Ap32, s->d_Dinv, s->d_phi64, s->d_phi32,
                   s->d_pcg, s->d_qn, s->d_y, s->d_g, s->d_gin, s->d_d, s->d_Md, s->d_Ep,
                   s->d_qwork, s->d_vwork, s->d_qfix, s->d_warm, s->d_mask, s->d_ns, s->d_err,
                   s->d_energy_tmp, s->red.partials, s->red.ticket, s->d_rhs};
@@ -220,7 +220,7 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
     }
   }
   A(s->d_x, m); A(s->d_r, m); A(s->d_z, m); A(s->d_p, m); A(s->d_Ap, m);
-  A(s->d_pcg, 1); A(s->d_p32, m);
+  A(s->d_pcg, 1); A(s->d_p32, m); A(s->d_x32, m); A(s->d_r32, m); A(s->d_z32, m); A(s->d_Ap32, m);
   A(s->d_phi64, 1568); A(s->d_phi32, 1568);
   A(s->d_qn, m); A(s->d_y, m); A(s->d_g, m); A(s->d_gin, m); A(s->d_d, m); A(s->d_Md, m);
   A(s->d_rhs, m); A(s->d_Ep, np); A(s->d_qwork, m); A(s->d_vwork, m); A(s->d_qfix, m);
@@ -360,7 +360,7 @@ static shell_status run_pcg(Shell& s, const unsigned char* mask, const double td
   }
   *iters = s.h_pcg->iters;
   *neg = s.h_pcg->negcurv;
-  return SHELL_OK;
+  return launch_pcg_result(s);
 }
 }  // namespace bhem
 
@@ -565,7 +565,7 @@ extern "C" shell_status shell_newton_step(shell_t* shell, const shell_step_param
   return st;
 }
 
-extern "C" shell_status shell_spmv(shell_t* shell, const void* x, int x_is_fp32, double* y) {
+extern "C" shell_status shell_spmv(shell_t* shell, const void* x, int x_is_fp32, void* y) {
   if (!shell || !x || !y) return fail(SHELL_ERR_ARG, "NULL argument");
   if (x_is_fp32 && shell->val_fp64) return fail(SHELL_ERR_ARG, "an FP64 shell takes FP64 x");
   if ((reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(y) & 7))

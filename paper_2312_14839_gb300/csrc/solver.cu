@@ -301,6 +301,170 @@ __global__ void k_to_float(int m, const double* __restrict__ a, float* __restric
 }
 
 // ------------------------------------------------------------------------------------------
+// Mixed-precision PCG (FP32 matrix, FP32 vectors, dot products as exact FP32 products summed in
+// double-float): no FP64-pipe work per element. 36 threads per block row as in k_spmv.
+// ------------------------------------------------------------------------------------------
+struct Shift4f { float v[4]; };
+
+__global__ void __launch_bounds__(kSpmvThreads)
+k_spmv32(int n, const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ val,
+         const float* __restrict__ x, Shift4f td, const unsigned char* __restrict__ mask,
+         float* __restrict__ y, PcgState* st, Reduce red) {
+  constexpr int NC = 3, TPR = 36, RPC = kSpmvThreads / TPR;
+  if (st && st->done) return;
+  __shared__ float sacc[kSpmvThreads];
+  const int t = threadIdx.x;
+  const int br = t / TPR, w = t % TPR, r = w / NC, cc = w % NC;
+  const int i = blockIdx.x * RPC + br;
+  float acc = 0.f;
+  if (i < n) {
+    const int k0 = rp[i], k1 = rp[i + 1];
+    constexpr int U = 9;
+    float4 v[U];
+    int j[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u;
+      if (k < k1) {
+        j[u] = col[k];
+        v[u] = __ldcs(reinterpret_cast<const float4*>(val + (size_t)k * 144 + r * 12 + cc * 4));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (k0 + u < k1) {
+        const float4 xv = *reinterpret_cast<const float4*>(x + (size_t)j[u] * 12 + cc * 4);
+        acc += v[u].x * xv.x + v[u].y * xv.y + v[u].z * xv.z + v[u].w * xv.w;
+      }
+    for (int k = k0 + U; k < k1; ++k) {
+      const float4 a = __ldcs(reinterpret_cast<const float4*>(val + (size_t)k * 144 + r * 12 + cc * 4));
+      const float4 xv = *reinterpret_cast<const float4*>(x + (size_t)col[k] * 12 + cc * 4);
+      acc += a.x * xv.x + a.y * xv.y + a.z * xv.z + a.w * xv.w;
+    }
+  }
+  sacc[t] = acc;
+  __syncthreads();
+  F2 part{0.f, 0.f};
+  if (i < n && cc == 0) {
+    const size_t gi = (size_t)i * 12 + r;
+    const float xi = x[gi];
+    float yi = (sacc[t] + sacc[t + 1]) + sacc[t + 2];
+    yi += td.v[r / 3] * xi;
+    if (mask && mask[gi]) yi = 0.f;
+    y[gi] = yi;
+    part = f2_prod(xi, yi);
+  }
+  if (st) {
+    F2 v1[1] = {part};
+    double out[1];
+    if (grid_reduce_f2<1>(v1, red, out, gridDim.x) && threadIdx.x == 0) {
+      st->pq = out[0];
+      if (!(out[0] > 0.0)) {
+        st->negcurv = 1;
+        st->done = 1;
+        st->alpha = 0.0;
+      } else {
+        st->alpha = st->rz / out[0];
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float apply_block32(const float* __restrict__ D, const float* sr, int a) {
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) s += D[a * 12 + c] * sr[c];
+  return s;
+}
+
+__global__ void __launch_bounds__(kNodeThreads)
+k_pcg32_init(int n, const double* __restrict__ rhs, const float* __restrict__ Dinv,
+             const unsigned char* __restrict__ mask, float* __restrict__ x, float* __restrict__ r,
+             float* __restrict__ z, float* __restrict__ p, double rtol2, int fixed, PcgState* st,
+             Reduce red) {
+  __shared__ float sr[16][12];
+  const int ln = threadIdx.x / 12, a = threadIdx.x % 12;
+  const int i = blockIdx.x * 16 + ln;
+  const size_t gi = (size_t)i * 12 + a;
+  float ri = 0.f, zi = 0.f;
+  if (i < n) {
+    ri = (mask && mask[gi]) ? 0.f : (float)rhs[gi];
+    x[gi] = 0.f;
+    r[gi] = ri;
+    sr[ln][a] = ri;
+  }
+  __syncthreads();
+  if (i < n) {
+    zi = (mask && mask[gi]) ? 0.f : apply_block32(Dinv + (size_t)i * 144, sr[ln], a);
+    z[gi] = zi;
+    p[gi] = zi;
+  }
+  F2 v[2] = {f2_prod(ri, zi), f2_prod(ri, ri)};
+  double out[2];
+  if (grid_reduce_f2<2>(v, red, out, gridDim.x) && threadIdx.x == 0) {
+    st->rz = out[0];
+    st->bb = out[1];
+    st->rr = out[1];
+    st->rtol2 = rtol2;
+    st->fixed = fixed;
+    st->iters = 0;
+    st->negcurv = 0;
+    st->alpha = 0.0;
+    st->beta = 0.0;
+    st->pq = 0.0;
+    st->done = (out[1] == 0.0) ? 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(kNodeThreads)
+k_pcg32_update(int n, float* __restrict__ x, float* __restrict__ r, float* __restrict__ z,
+               const float* __restrict__ p, const float* __restrict__ Ap,
+               const float* __restrict__ Dinv, const unsigned char* __restrict__ mask, PcgState* st,
+               Reduce red) {
+  if (st->done) return;
+  __shared__ float sr[16][12];
+  const int ln = threadIdx.x / 12, a = threadIdx.x % 12;
+  const int i = blockIdx.x * 16 + ln;
+  const size_t gi = (size_t)i * 12 + a;
+  const float alpha = (float)st->alpha;
+  float ri = 0.f, zi = 0.f;
+  if (i < n) {
+    x[gi] = fmaf(alpha, p[gi], x[gi]);
+    ri = fmaf(-alpha, Ap[gi], r[gi]);
+    r[gi] = ri;
+    sr[ln][a] = ri;
+  }
+  __syncthreads();
+  if (i < n) {
+    zi = (mask && mask[gi]) ? 0.f : apply_block32(Dinv + (size_t)i * 144, sr[ln], a);
+    z[gi] = zi;
+  }
+  F2 v[2] = {f2_prod(ri, zi), f2_prod(ri, ri)};
+  double out[2];
+  if (grid_reduce_f2<2>(v, red, out, gridDim.x) && threadIdx.x == 0) {
+    const double rz_new = out[0];
+    st->rr = out[1];
+    st->iters += 1;
+    st->beta = rz_new / st->rz;
+    st->rz = rz_new;
+    if (st->fixed == 0 && out[1] <= st->rtol2 * st->bb) st->done = 1;
+    if (rz_new == 0.0) st->done = 1;
+  }
+}
+
+__global__ void k_pcg32_pupdate(int m, const float* __restrict__ z, float* __restrict__ p,
+                                const PcgState* st) {
+  if (st->done) return;
+  const float beta = (float)st->beta;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x)
+    p[k] = fmaf(beta, p[k], z[k]);
+}
+
+__global__ void k_to_double(int m, const float* __restrict__ a, double* __restrict__ b) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) b[k] = (double)a[k];
+}
+
+// ------------------------------------------------------------------------------------------
 // Consistent mass products (4x4 scalar blocks (x) I3), FP64.
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ double mass_row(const int* __restrict__ rp, const int* __restrict__ col,
@@ -467,6 +631,13 @@ shell_status launch_pcg_init(Shell& s, const unsigned char* mask, const double* 
   int blocks = grid_for(s.n_nodes, 16);
   if (blocks > kMaxPartials) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
   double rtol2 = fixed > 0 ? 0.0 : rtol * rtol;
+  if (!s.val_fp64) {
+    k_pcg32_init<<<blocks, kNodeThreads, 0, s.stream>>>(s.n_nodes, rhs, (const float*)s.d_Dinv, mask,
+        s.d_x32, s.d_r32, s.d_z32, s.d_p32, rtol2, fixed, s.d_pcg, s.red);
+    BHEM_CUDA(cudaGetLastError());
+    ++s.launches;
+    return SHELL_OK;
+  }
   if (s.val_fp64)
     k_pcg_init<double><<<blocks, kNodeThreads, 0, s.stream>>>(
         s.n_nodes, rhs, (const double*)s.d_Dinv, mask, s.d_x, s.d_r, s.d_z, s.d_p, nullptr, rtol2,
@@ -503,32 +674,68 @@ static shell_status launch_spmv_impl(Shell& s, const void* x, const double* xd,
   return SHELL_OK;
 }
 
-shell_status launch_spmv(Shell& s, const void* x, int x_fp32, double* y) {
+shell_status launch_spmv(Shell& s, const void* x, int x_fp32, void* y) {
   const double zero[4] = {0.0, 0.0, 0.0, 0.0};
-  if (!s.val_fp64 && !x_fp32) {
-    // FP32 matrix, FP64 input: one conversion pass into the shell's FP32 vector first
-    k_to_float<<<vec_blocks(s.n_dof), 256, 0, s.stream>>>(s.n_dof, (const double*)x, s.d_p32);
+  if (s.val_fp64) return launch_spmv_impl(s, x, nullptr, nullptr, zero, (double*)y, nullptr);
+  const float* xs = (const float*)x;
+  float* ys = (float*)y;
+  if (!x_fp32) {
+    // FP64 in and out: convert through the shell's FP32 vectors
+    k_to_float<<<vec_blocks(s.n_dof), 256, 0, s.stream>>>(s.n_dof, (const double*)x, s.d_z32);
     BHEM_CUDA(cudaGetLastError());
     ++s.launches;
-    x = s.d_p32;
+    xs = s.d_z32;
+    ys = s.d_Ap32;
   }
-  return launch_spmv_impl(s, x, nullptr, nullptr, zero, y, nullptr);
+  k_spmv32<<<grid_for(s.n_nodes, kSpmvThreads / 36), kSpmvThreads, 0, s.stream>>>(
+      s.n_nodes, s.d_row_ptr, s.d_col, (const float*)s.d_val, xs, Shift4f{{0.f, 0.f, 0.f, 0.f}},
+      nullptr, ys, nullptr, s.red);
+  BHEM_CUDA(cudaGetLastError());
+  ++s.launches;
+  if (!x_fp32) {
+    k_to_double<<<vec_blocks(s.n_dof), 256, 0, s.stream>>>(s.n_dof, s.d_Ap32, (double*)y);
+    BHEM_CUDA(cudaGetLastError());
+    ++s.launches;
+  }
+  return SHELL_OK;
 }
 
 shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, const double td[4]) {
   const int n = s.n_nodes, m = s.n_dof;
-  const void* px = s.val_fp64 ? (const void*)s.d_p : (const void*)s.d_p32;
+  if (!s.val_fp64) {
+    const int blocks = grid_for(n, kSpmvThreads / 36);
+    if (blocks > kMaxPartials) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
+    Shift4f sh{{(float)td[0], (float)td[1], (float)td[2], (float)td[3]}};
+    k_spmv32<<<blocks, kSpmvThreads, 0, s.stream>>>(n, s.d_row_ptr, s.d_col, (const float*)s.d_val,
+                                                    s.d_p32, sh, mask, s.d_Ap32, s.d_pcg, s.red);
+    BHEM_CUDA(cudaGetLastError());
+    ++s.launches;
+    k_pcg32_update<<<grid_for(n, 16), kNodeThreads, 0, s.stream>>>(
+        n, s.d_x32, s.d_r32, s.d_z32, s.d_p32, s.d_Ap32, (const float*)s.d_Dinv, mask, s.d_pcg, s.red);
+    BHEM_CUDA(cudaGetLastError());
+    ++s.launches;
+    k_pcg32_pupdate<<<vec_blocks(m), 256, 0, s.stream>>>(m, s.d_z32, s.d_p32, s.d_pcg);
+    BHEM_CUDA(cudaGetLastError());
+    ++s.launches;
+    return SHELL_OK;
+  }
+  const void* px = (const void*)s.d_p;
   BHEM_TRY(launch_spmv_impl(s, px, s.d_p, mask, td, s.d_Ap, s.d_pcg));
-  if (s.val_fp64)
-    k_pcg_update<double><<<grid_for(n, 16), kNodeThreads, 0, s.stream>>>(
-        n, s.d_x, s.d_r, s.d_z, s.d_p, s.d_Ap, (const double*)s.d_Dinv, mask, s.d_pcg, s.red);
-  else
-    k_pcg_update<float><<<grid_for(n, 16), kNodeThreads, 0, s.stream>>>(
-        n, s.d_x, s.d_r, s.d_z, s.d_p, s.d_Ap, (const float*)s.d_Dinv, mask, s.d_pcg, s.red);
+  k_pcg_update<double><<<grid_for(n, 16), kNodeThreads, 0, s.stream>>>(
+      n, s.d_x, s.d_r, s.d_z, s.d_p, s.d_Ap, (const double*)s.d_Dinv, mask, s.d_pcg, s.red);
   BHEM_CUDA(cudaGetLastError());
   ++s.launches;
-  k_pcg_pupdate<<<vec_blocks(m), 256, 0, s.stream>>>(m, s.d_z, s.d_p, s.val_fp64 ? nullptr : s.d_p32,
-                                                     s.d_pcg);
+  k_pcg_pupdate<<<vec_blocks(m), 256, 0, s.stream>>>(m, s.d_z, s.d_p, nullptr, s.d_pcg);
+  BHEM_CUDA(cudaGetLastError());
+  ++s.launches;
+  return SHELL_OK;
+}
+
+// Solution of the last PCG solve as FP64 in s.d_x (converted from the FP32 vector of a mixed
+// shell).
+shell_status launch_pcg_result(Shell& s) {
+  if (s.val_fp64) return SHELL_OK;
+  k_to_double<<<vec_blocks(s.n_dof), 256, 0, s.stream>>>(s.n_dof, s.d_x32, s.d_x);
   BHEM_CUDA(cudaGetLastError());
   ++s.launches;
   return SHELL_OK;
