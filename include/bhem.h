@@ -207,6 +207,48 @@ SHELL_API shell_status shell_energy_grad_noalloc(const shell_grid* grid, const s
                                                  const double* rest_dofs, const double* q,
                                                  double* energy, double* grad, void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+   Batches: many independent shells of uneven sizes and materials stepped together (every shell
+   runs its own Newton to its own residual tolerance, with the same policies as
+   shell_newton_step). Shells are concatenated: node k of shell s is node node_offsets[s] + k of
+   the batch, and q, v, masks are the shells' arrays one after the other. Precision is
+   SHELL_PREC_MIXED. Each phase of a Newton iteration is one launch over all shells; PCG
+   iterations are replayed from a CUDA graph.
+   --------------------------------------------------------------------------------------------- */
+typedef struct shell_batch_s shell_batch_t;
+
+typedef struct {
+  int n_shells, n_nodes, n_patches, n_blocks, n_dof;
+  int patches_per_item;   /* patches per element work item (set by shell_batch_autotune)   */
+  int assembly;           /* SHELL_ASM_ATOMIC or SHELL_ASM_COLOR                           */
+  long long kernel_launches;
+} shell_batch_info_t;
+
+/* Creates a batch of n_shells shells (grids[s], materials[s]; rest_dofs: host or device, the
+   shells' rest DOFs concatenated). options may be NULL (mixed precision, atomic assembly); a
+   precision other than SHELL_PREC_MIXED is rejected. Every shell needs at least 16 nodes.
+   stream: cudaStream_t (NULL: the batch creates its own blocking stream). */
+SHELL_API shell_status shell_batch_create(int n_shells, const shell_grid* grids,
+                                          const shell_material* materials, const double* rest_dofs,
+                                          const shell_options* options, void* stream,
+                                          shell_batch_t** out);
+SHELL_API shell_status shell_batch_destroy(shell_batch_t* batch);
+/* Sizes and the current tuning; node_offsets (host, [n_shells + 1]) may be NULL. */
+SHELL_API shell_status shell_batch_info(const shell_batch_t* batch, shell_batch_info_t* info,
+                                        int* node_offsets);
+/* Times the element Hessian assembly at the state q (device [n_dof]) for patches-per-item
+   4, 8, 16, 32 and atomic / colour-ordered scatter (repeats timed runs each, CUDA events) and
+   keeps the fastest. Synchronises. */
+SHELL_API shell_status shell_batch_autotune(shell_batch_t* batch, const double* q, int repeats);
+/* One implicit-Euler step of every shell (same contract as shell_newton_step, on the
+   concatenated arrays; host or device). stats: host [n_shells]. Returns SHELL_OK when every
+   shell succeeded, else the status of the first shell that did not (stats[s].status holds
+   each shell's). */
+SHELL_API shell_status shell_batch_newton_step(shell_batch_t* batch, const shell_step_params* params,
+                                               const unsigned char* fixed_mask, const double* q_fixed,
+                                               double* q, double* v, const double* warm_start,
+                                               shell_step_stats* stats);
+
 /* Number of CUDA kernels this shell has launched since shell_create (host counter; counts the
    launches of the library's own kernels, not memset/memcpy operations). */
 SHELL_API shell_status shell_kernel_launches(const shell_t* shell, long long* count);

@@ -58,6 +58,12 @@ class shell_step_stats(C.Structure):
                 ("res0", C.c_double), ("res_final", C.c_double)]
 
 
+class shell_batch_info_t(C.Structure):
+    _fields_ = [("n_shells", C.c_int), ("n_nodes", C.c_int), ("n_patches", C.c_int), ("n_blocks", C.c_int),
+                ("n_dof", C.c_int), ("patches_per_item", C.c_int), ("assembly", C.c_int),
+                ("kernel_launches", C.c_longlong)]
+
+
 class shell_info_t(C.Structure):
     _fields_ = [("n_nodes", C.c_int), ("n_patches", C.c_int), ("n_blocks", C.c_int),
                 ("n_dof", C.c_int)]
@@ -90,6 +96,11 @@ def load():
                 "shell_spmv": [p, p, i, p],
                 "shell_kernel_launches": [p, p],
                 "shell_energy_grad_noalloc": [p, p, p, p, p, p, p],
+                "shell_batch_create": [i, p, p, p, p, p, p],
+                "shell_batch_destroy": [p],
+                "shell_batch_info": [p, p, p],
+                "shell_batch_autotune": [p, p, i],
+                "shell_batch_newton_step": [p, p, p, p, p, p, p, p],
             }
             for name, args in sigs.items():
                 fn = getattr(lib, name)
@@ -271,3 +282,65 @@ class Shell:
         if rc != 0 and (raise_on_error or rc not in (6, 7, 8)):
             raise ShellError(rc, load().shell_last_error().decode())
         return stats
+
+
+class Batch:
+    """Many shells stepped together (shell_batch_*): shells = [(grid, material, rest), ...].
+    State arrays are the shells' arrays concatenated; ``node_offsets[s]`` is shell s's first node."""
+
+    def __init__(self, shells, stream=None):
+        import torch
+        lib = load()
+        S = len(shells)
+        self.grids = (shell_grid * S)()
+        self.mats = (shell_material * S)()
+        for k, (g, m, _) in enumerate(shells):
+            self.grids[k] = shell_grid(int(g.nu), int(g.nv), int(bool(g.periodic_u)), int(bool(g.periodic_v)),
+                                       float(g.dxi1), float(g.dxi2))
+            self.mats[k] = shell_material(float(m.young), float(m.poisson), float(m.thickness), float(m.density))
+        rest = np.concatenate([np.ascontiguousarray(r, dtype=np.float64).reshape(-1) for _, _, r in shells])
+        stream_obj, sh = (None, C.c_void_p(None)) if stream is None else _stream_handle(stream)
+        self.stream = stream_obj
+        self._h = C.c_void_p()
+        opts = shell_options(PREC["mixed"], HESS["exact"], ASM["atomic"], 0)
+        _check(lib.shell_batch_create(S, self.grids, self.mats, _ptr(rest), C.byref(opts), sh, C.byref(self._h)))
+        self.n_shells = S
+        self.node_offsets = np.zeros(S + 1, dtype=np.int32)
+        info = self.info()
+        self.n_nodes, self.n_patches, self.n_dof = info["n_nodes"], info["n_patches"], info["n_dof"]
+
+    def info(self):
+        inf = shell_batch_info_t()
+        _check(load().shell_batch_info(self._h, C.byref(inf), _ptr(self.node_offsets)))
+        return {f: getattr(inf, f) for f, _ in shell_batch_info_t._fields_}
+
+    def autotune(self, q, repeats=3):
+        _check(load().shell_batch_autotune(self._h, _ptr(q), int(repeats)))
+        return self.info()
+
+    def newton_step(self, q, v, params: shell_step_params, mask=None, q_fixed=None, warm=None,
+                    raise_on_error=False):
+        stats = (shell_step_stats * self.n_shells)()
+        rc = load().shell_batch_newton_step(self._h, C.byref(params), _ptr(mask), _ptr(q_fixed), _ptr(q),
+                                            _ptr(v), _ptr(warm), stats)
+        out = [{f: getattr(s, f) for f, _ in shell_step_stats._fields_} for s in stats]
+        if rc != 0 and (raise_on_error or rc not in (6, 7, 8)):
+            raise ShellError(rc, load().shell_last_error().decode())
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().shell_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

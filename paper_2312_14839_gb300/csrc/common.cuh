@@ -41,8 +41,9 @@ constexpr int kMaxRed = 16;             // values reduced together
 constexpr int kMaxPartials = 1 << 17;   // CTAs per reduced kernel (checked at launch)
 
 struct Reduce {
-  double* partials;    // [kMaxRed * kMaxPartials]
+  double* partials;    // [kMaxRed * stride]
   unsigned* ticket;    // one counter
+  int stride;          // partials per reduced value (>= the CTAs of any reducing launch)
 };
 
 // Scalars of one PCG solve, resident in device memory.
@@ -218,7 +219,7 @@ __device__ __forceinline__ bool grid_reduce_f2(const F2 (&v)[NV], Reduce red, do
   float2* part = reinterpret_cast<float2*>(red.partials);
   for (int i = 0; i < NV; ++i) {
     const F2 s = f2_block_sum(v[i], sred2, i);
-    if (threadIdx.x == 0) part[(size_t)i * kMaxPartials + blockIdx.x] = make_float2(s.hi, s.lo);
+    if (threadIdx.x == 0) part[(size_t)i * red.stride + blockIdx.x] = make_float2(s.hi, s.lo);
   }
   if (threadIdx.x == 0) {
     __threadfence();
@@ -231,7 +232,7 @@ __device__ __forceinline__ bool grid_reduce_f2(const F2 (&v)[NV], Reduce red, do
   for (int i = 0; i < NV; ++i) {
     F2 s{0.f, 0.f};
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-      const float2 y = __ldcg(part + (size_t)i * kMaxPartials + b);   // L2: other CTAs' writes
+      const float2 y = __ldcg(part + (size_t)i * red.stride + b);   // L2: other CTAs' writes
       s = f2_add(s, F2{y.x, y.y});
     }
     const F2 t = f2_block_sum(s, sred2, i);
@@ -271,7 +272,7 @@ __device__ __forceinline__ bool grid_reduce(const double (&v)[NV], Reduce red, d
       const bool mn = (minmask >> i) & 1u;
       double s = sred[i][0];
       for (int w = 1; w < nw; ++w) s = mn ? fmin(s, sred[i][w]) : s + sred[i][w];
-      red.partials[(size_t)i * kMaxPartials + blockIdx.x] = s;
+      red.partials[(size_t)i * red.stride + blockIdx.x] = s;
     }
     __threadfence();
     unsigned t = atomicAdd(red.ticket, 1u);
@@ -284,7 +285,7 @@ __device__ __forceinline__ bool grid_reduce(const double (&v)[NV], Reduce red, d
     const bool mn = (minmask >> i) & 1u;
     double s = mn ? INFINITY : 0.0;
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-      const double y = ((volatile double*)red.partials)[(size_t)i * kMaxPartials + b];
+      const double y = ((volatile double*)red.partials)[(size_t)i * red.stride + b];
       s = mn ? fmin(s, y) : s + y;
     }
     for (int o = 16; o > 0; o >>= 1) {

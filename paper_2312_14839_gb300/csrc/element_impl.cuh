@@ -1,0 +1,534 @@
+// Device code shared by the element kernels of one shell (element.cu) and of a batch of shells
+// (batch.cu): Hermite basis and Gauss rule (App. A), shape tables, 3-vector helpers, the
+// Gauss-point matrices of App. B and the per-patch bodies of the element kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace bhem {
+
+// ------------------------------------------------------------------------------------------
+// App. A.1 cubic Hermite basis on [0, 1] and its derivatives; App. A.2 Gauss rule.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double herm(int p, int r, double t, int d) {
+  // f = 2t^3 - 3t^2 + 1, g = t^3 - 2t^2 + t; w_{0,0} = f(t), w_{1,0} = f(1-t),
+  // w_{0,1} = g(t), w_{1,1} = -g(1-t)
+  double s = p ? 1.0 - t : t;
+  double sg = (p && (d & 1)) ? -1.0 : 1.0;   // chain rule of 1 - t
+  double v;
+  if (r == 0) v = d == 0 ? (2 * s - 3) * s * s + 1 : d == 1 ? 6 * s * s - 6 * s : 12 * s - 6;
+  else        v = d == 0 ? ((s - 2) * s + 1) * s : d == 1 ? (3 * s - 4) * s + 1 : 6 * s - 4;
+  if (r == 1 && p == 1) v = -v;
+  return sg * v;
+}
+
+__device__ __forceinline__ void gauss_unit(double th[4], double wt[4]) {
+  const double xi = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(6.0 / 5.0));
+  const double xo = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(6.0 / 5.0));
+  const double wi = (18.0 + sqrt(30.0)) / 72.0, wo = (18.0 - sqrt(30.0)) / 72.0;
+  th[0] = 0.5 * (1 - xo); th[1] = 0.5 * (1 - xi); th[2] = 0.5 * (1 + xi); th[3] = 0.5 * (1 + xo);
+  wt[0] = wo; wt[1] = wi; wt[2] = wi; wt[3] = wo;
+}
+
+// Shape table in shared memory: sphi[I * kPhiStride + k * 16 + g], k = 0..5 for
+// Phi, Phi_,1, Phi_,2, Phi_,11, Phi_,22, Phi_,12; g = g2 * 4 + g1. The odd I-stride keeps both
+// access patterns (lanes over g, lanes over I) free of bank conflicts.
+constexpr int kPhiStride = 97;
+constexpr int kPhiSize = 16 * kPhiStride;
+constexpr int kPhiTable = kPhiSize + 16;   // + the 16 Gauss weights W_g = dxi1 dxi2 w_g1 w_g2
+
+template <typename R>
+__device__ void build_shape_table(R* sphi, double d1, double d2) {
+  double th[4], wt[4];
+  gauss_unit(th, wt);
+  for (int e = threadIdx.x; e < 16 * 96; e += blockDim.x) {
+    int I = e / 96, k = (e / 16) % 6, g = e % 16;
+    int corner = I >> 2, kind = I & 3;
+    int p = corner & 1, q = corner >> 1, r = kind & 1, s = kind >> 1;
+    const int dd1[6] = {0, 1, 0, 2, 0, 1}, dd2[6] = {0, 0, 1, 0, 2, 1};
+    double t1 = th[g & 3], t2 = th[g >> 2];
+    double v = herm(p, r, t1, dd1[k]) * herm(q, s, t2, dd2[k]);
+    v *= (r ? d1 : 1.0) * (s ? d2 : 1.0);
+    for (int i = 0; i < dd1[k]; ++i) v /= d1;
+    for (int i = 0; i < dd2[k]; ++i) v /= d2;
+    sphi[I * kPhiStride + k * 16 + g] = (R)v;
+  }
+}
+
+__device__ __forceinline__ double gauss_weight(int g, double d1, double d2) {
+  double th[4], wt[4];
+  gauss_unit(th, wt);
+  return d1 * d2 * wt[g & 3] * wt[g >> 2];
+}
+
+template <typename R>
+__device__ __forceinline__ void load_shape_table(R* sphi, const R* __restrict__ table) {
+  for (int e = threadIdx.x; e < kPhiTable; e += blockDim.x) sphi[e] = table[e];
+}
+
+// ------------------------------------------------------------------------------------------
+// 3-vector helpers
+// ------------------------------------------------------------------------------------------
+template <typename R> struct V3 { R x, y, z; };
+template <typename R> __device__ __forceinline__ V3<R> mk(R a, R b, R c) { return {a, b, c}; }
+template <typename R> __device__ __forceinline__ V3<R> operator+(V3<R> a, V3<R> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename R> __device__ __forceinline__ V3<R> operator-(V3<R> a, V3<R> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename R> __device__ __forceinline__ V3<R> operator*(R s, V3<R> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <typename R> __device__ __forceinline__ R dot(V3<R> a, V3<R> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename R> __device__ __forceinline__ V3<R> cross(V3<R> a, V3<R> b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename R> __device__ __forceinline__ R comp(V3<R> a, int i) { return i == 0 ? a.x : i == 1 ? a.y : a.z; }
+
+// Interpolate the 5 derivative vectors a_1, a_2, a_{1,1}, a_{2,2}, a_{1,2} at Gauss point g from
+// 16 DOF triples (shared memory, [16][3]).
+template <typename R, typename S>
+__device__ __forceinline__ void interp5(const R* sphi, const S* qv, int g, V3<R> out[5]) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) out[k] = mk<R>(0, 0, 0);
+#pragma unroll 4
+  for (int I = 0; I < 16; ++I) {
+    V3<R> v = mk<R>((R)qv[I * 3], (R)qv[I * 3 + 1], (R)qv[I * 3 + 2]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) out[k] = out[k] + sphi[I * kPhiStride + (k + 1) * 16 + g] * v;
+  }
+}
+
+constexpr int kRestFields = 13;
+
+// ------------------------------------------------------------------------------------------
+// Light FP64 energy (and gradient) of one patch, half a warp per patch, lane = Gauss point g.
+// sq: the half warp's 48 DOFs (shared), sG: its [16][15] gradient vectors (shared). restgp is
+// SoA over S = (total patches) * 16 entries. Returns the patch energy in every lane.
+// ------------------------------------------------------------------------------------------
+constexpr int kEgPatches = 8;   // patches per CTA (128 threads)
+
+__device__ __forceinline__ double eg64_patch(const double* sphi, double* sq, double (*sG)[15],
+                                             int p, bool active, int g, const int nd[4],
+                                             const double* __restrict__ q,
+                                             const double* __restrict__ dir, double step,
+                                             const double* __restrict__ restgp, size_t S, double h,
+                                             double* __restrict__ grad, int* err) {
+  if (active) {
+    for (int l = g; l < 48; l += 16) {
+      size_t a = (size_t)nd[l / 12] * 12 + (l % 12);
+      double v = q[a];
+      if (dir) v += step * dir[a];
+      sq[l] = v;
+    }
+  }
+  __syncwarp();
+  double e = 0.0;
+  if (active) {
+    V3<double> v[5];
+    interp5<double, double>(sphi, sq, g, v);
+    const V3<double> a1 = v[0], a2 = v[1];
+    const size_t o = (size_t)p * 16 + g;
+    const double ab11 = restgp[0 * S + o], ab22 = restgp[1 * S + o], ab12 = restgp[2 * S + o];
+    const double bb11 = restgp[3 * S + o], bb22 = restgp[4 * S + o], bb12 = restgp[5 * S + o];
+    const double H00 = restgp[6 * S + o], H01 = restgp[7 * S + o], H02 = restgp[8 * S + o];
+    const double H11 = restgp[9 * S + o], H12 = restgp[10 * S + o], H22 = restgp[11 * S + o];
+    const double wgt = restgp[12 * S + o];
+    V3<double> n = cross(a1, a2);
+    double sqa = sqrt(dot(n, n));
+    if (!(sqa > 1e-300)) { atomicOr(err, ERRBIT_DEGENERATE); sqa = 1.0; }
+    V3<double> a3 = (1.0 / sqa) * n;
+    double b11 = dot(v[2], a3), b22 = dot(v[3], a3), b12 = dot(v[4], a3);
+    double al[3] = {0.5 * (dot(a1, a1) - ab11), 0.5 * (dot(a2, a2) - ab22), dot(a1, a2) - ab12};
+    double be[3] = {b11 - bb11, b22 - bb22, 2.0 * (b12 - bb12)};
+    double sg[3] = {H00 * al[0] + H01 * al[1] + H02 * al[2], H01 * al[0] + H11 * al[1] + H12 * al[2],
+                    H02 * al[0] + H12 * al[1] + H22 * al[2]};
+    double mm[3] = {H00 * be[0] + H01 * be[1] + H02 * be[2], H01 * be[0] + H11 * be[1] + H12 * be[2],
+                    H02 * be[0] + H12 * be[1] + H22 * be[2]};
+    const double h3 = h * h * h;
+    e = wgt * (0.5 * h * (al[0] * sg[0] + al[1] * sg[1] + al[2] * sg[2]) +
+               h3 / 24.0 * (be[0] * mm[0] + be[1] * mm[1] + be[2] * mm[2]));
+    if (grad) {
+      const double s = h3 / 12.0;
+      V3<double> ct = mm[0] * v[2] + mm[1] * v[3] + (2.0 * mm[2]) * v[4];
+      double bt = dot(ct, a3);
+      V3<double> t1 = cross(a2, a3), t2 = cross(a3, a1);
+      V3<double> e1 = (1.0 / sqa) * (cross(a2, ct) - bt * t1);
+      V3<double> e2 = (1.0 / sqa) * (cross(ct, a1) - bt * t2);
+      V3<double> G[5];
+      G[0] = wgt * (h * (sg[0] * a1 + sg[2] * a2) + s * e1);
+      G[1] = wgt * (h * (sg[1] * a2 + sg[2] * a1) + s * e2);
+      G[2] = (wgt * s * mm[0]) * a3;
+      G[3] = (wgt * s * mm[1]) * a3;
+      G[4] = (wgt * s * 2.0 * mm[2]) * a3;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        sG[g][k * 3 + 0] = G[k].x;
+        sG[g][k * 3 + 1] = G[k].y;
+        sG[g][k * 3 + 2] = G[k].z;
+      }
+    }
+  }
+  // energy per patch over the 16 lanes of the half warp
+  double ep = e;
+  for (int o = 8; o > 0; o >>= 1) ep += __shfl_xor_sync(0xffffffffu, ep, o);
+  __syncwarp();
+  if (active && grad) {
+    for (int l = g; l < 48; l += 16) {
+      int I = l / 3, c = l % 3;
+      double s = 0.0;
+      for (int gg = 0; gg < 16; ++gg)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) s += sphi[I * kPhiStride + (k + 1) * 16 + gg] * sG[gg][k * 3 + c];
+      atomicAdd(&grad[(size_t)nd[I >> 2] * 12 + (I & 3) * 3 + c], s);
+    }
+  }
+  __syncwarp();
+  return ep;
+}
+
+// ------------------------------------------------------------------------------------------
+// Heavy kernel: one warp per patch computes E, gradient and the 48x48 Hessian.
+// ------------------------------------------------------------------------------------------
+template <typename R> struct ElemCfg;
+template <> struct ElemCfg<float> { static constexpr int kWarps = 4, kJP = 8; };
+template <> struct ElemCfg<double> { static constexpr int kWarps = 2, kJP = 4; };
+
+template <typename R>
+struct WarpSmem {
+  R u[48];        // displacement q - rest
+  R qb[48];       // rest DOFs
+  R M[16][225];   // M_g, full 15x15 per Gauss point
+  R T[16 * 45];   // T[I][c*15 + l*3 + c'] of the current Gauss point
+  R G[16][15];    // gradient vectors per Gauss point
+  R ms[16];       // mass_scale * rho h * W sqrt(a_bar) per Gauss point
+  R en[16];       // energy per Gauss point
+};
+
+struct ElemArgs {
+  int np;
+  const void* phi;         // shape table + Gauss weights in the kernel's precision
+  const int4* pnodes;
+  const int* plist;        // optional patch list (colour order), else identity
+  int plist_n;
+  const int* pblocks;
+  const double* q;
+  const double* rest;
+  double d1, d2, lam, mu, h, rho_h, mass_scale;
+  int pseudo;
+  double* energy_p;
+  double* grad_p;
+  void* hess_p;
+  void* bsr;
+  int bsr_atomic;
+  int* err;
+};
+
+// Builds M_g (15x15) and the per-point energy, gradient vectors and mass weight for Gauss
+// point g of the warp's patch. Called by lanes 0..15, lane = g.
+template <typename R>
+__device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W, int g,
+                                                   const ElemArgs& A) {
+  V3<R> ub[5], uu[5];
+  interp5<R, R>(sphi, W.qb, g, ub);   // rest a_bar_1, a_bar_2, x_bar_{,11}, x_bar_{,22}, x_bar_{,12}
+  interp5<R, R>(sphi, W.u, g, uu);    // displacement derivatives
+  const V3<R> ab1 = ub[0], ab2 = ub[1];
+  const V3<R> a1 = ab1 + uu[0], a2 = ab2 + uu[1];
+  V3<R> c[3] = {ub[2] + uu[2], ub[3] + uu[3], ub[4] + uu[4]};
+  // rest metric, contravariant metric, Voigt H (App. B.1)
+  R ab11 = dot(ab1, ab1), ab22 = dot(ab2, ab2), ab12 = dot(ab1, ab2);
+  R det = ab11 * ab22 - ab12 * ab12;
+  if (!(det > (R)0)) { atomicOr(A.err, ERRBIT_DEGENERATE); det = (R)1; }
+  R sqab = sqrt(det);
+  V3<R> ab3 = ((R)1 / sqab) * cross(ab1, ab2);
+  R ai11 = ab22 / det, ai22 = ab11 / det, ai12 = -ab12 / det;
+  const R lam = (R)A.lam, mu = (R)A.mu, h = (R)A.h;
+  R H[3][3];
+  H[0][0] = (lam + 2 * mu) * ai11 * ai11;
+  H[0][1] = lam * ai11 * ai22 + 2 * mu * ai12 * ai12;
+  H[0][2] = (lam + 2 * mu) * ai11 * ai12;
+  H[1][1] = (lam + 2 * mu) * ai22 * ai22;
+  H[1][2] = (lam + 2 * mu) * ai12 * ai22;
+  H[2][2] = (lam + mu) * ai12 * ai12 + mu * ai11 * ai22;
+  H[1][0] = H[0][1]; H[2][0] = H[0][2]; H[2][1] = H[1][2];
+  // deformed normal
+  V3<R> n = cross(a1, a2);
+  R sqa = sqrt(dot(n, n));
+  if (!(sqa > (R)0)) { atomicOr(A.err, ERRBIT_DEGENERATE); sqa = (R)1; }
+  V3<R> a3 = ((R)1 / sqa) * n;
+  // strains from displacements (a_ab - a_bar_ab = a_bar_a.u_b + u_a.a_bar_b + u_a.u_b)
+  R al[3] = {dot(ab1, uu[0]) + (R)0.5 * dot(uu[0], uu[0]), dot(ab2, uu[1]) + (R)0.5 * dot(uu[1], uu[1]),
+             dot(ab1, uu[1]) + dot(uu[0], ab2) + dot(uu[0], uu[1])};
+  V3<R> da3 = a3 - ab3;
+  R br[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) br[m] = dot(uu[2 + m], a3) + dot(ub[2 + m], da3);   // b - b_bar
+  R be[3] = {br[0], br[1], (R)2 * br[2]};
+  R sg[3], mm[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    sg[i] = H[i][0] * al[0] + H[i][1] * al[1] + H[i][2] * al[2];
+    mm[i] = H[i][0] * be[0] + H[i][1] * be[1] + H[i][2] * be[2];
+  }
+  const R wgt = sphi[kPhiSize + g] * sqab;
+  const R s = h * h * h / (R)12;
+  W.en[g] = wgt * ((R)0.5 * h * (al[0] * sg[0] + al[1] * sg[1] + al[2] * sg[2]) +
+                   s * (R)0.5 * (be[0] * mm[0] + be[1] * mm[1] + be[2] * mm[2]));
+  W.ms[g] = (R)(A.mass_scale * A.rho_h) * wgt;
+  // first derivatives: B matrices (rows = Voigt component, columns = coordinate)
+  V3<R> t1 = cross(a2, a3), t2 = cross(a3, a1);
+  V3<R> up[3], vp[3];
+  R bdef[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    bdef[m] = dot(c[m], a3);
+    up[m] = ((R)1 / sqa) * (cross(a2, c[m]) - bdef[m] * t1);   // coefficient of Phi_,1 in d b_m
+    vp[m] = ((R)1 / sqa) * (cross(c[m], a1) - bdef[m] * t2);   // coefficient of Phi_,2 in d b_m
+  }
+  V3<R> Ba[2][3] = {{a1, mk<R>(0, 0, 0), a2}, {mk<R>(0, 0, 0), a2, a1}};
+  V3<R> Bb[5][3] = {{up[0], up[1], (R)2 * up[2]},
+                    {vp[0], vp[1], (R)2 * vp[2]},
+                    {a3, mk<R>(0, 0, 0), mk<R>(0, 0, 0)},
+                    {mk<R>(0, 0, 0), a3, mk<R>(0, 0, 0)},
+                    {mk<R>(0, 0, 0), mk<R>(0, 0, 0), (R)2 * a3}};
+  // gradient vectors G_k = W sqrt(a_bar) (h B_alpha,k^T sigma + s B_beta,k^T m)
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    V3<R> gk = mm[0] * Bb[k][0] + mm[1] * Bb[k][1] + mm[2] * Bb[k][2];
+    gk = s * gk;
+    if (k < 2) gk = gk + h * (sg[0] * Ba[k][0] + sg[1] * Ba[k][1] + sg[2] * Ba[k][2]);
+    gk = wgt * gk;
+    W.G[g][k * 3 + 0] = gk.x;
+    W.G[g][k * 3 + 1] = gk.y;
+    W.G[g][k * 3 + 2] = gk.z;
+  }
+  // Q_l = H B_l
+  V3<R> Qa[2][3], Qb[5][3];
+#pragma unroll
+  for (int l = 0; l < 5; ++l)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Qb[l][i] = H[i][0] * Bb[l][0] + H[i][1] * Bb[l][1] + H[i][2] * Bb[l][2];
+      if (l < 2) Qa[l][i] = H[i][0] * Ba[l][0] + H[i][1] * Ba[l][1] + H[i][2] * Ba[l][2];
+    }
+  // exact-Hessian extras: P_1, P_2 (d a3 = (Phi_,1 P_1 + Phi_,2 P_2) dq) and D~^{gamma delta}
+  const bool exact = !A.pseudo;
+  V3<R> ct = mm[0] * c[0] + mm[1] * c[1] + ((R)2 * mm[2]) * c[2];
+  R bt = dot(ct, a3);
+  V3<R> s1 = cross(ct, a1), s2 = cross(a2, ct);
+  const R ia = (R)1 / (sqa * sqa);
+  const R a11 = dot(a1, a1), a22 = dot(a2, a2), a12 = dot(a1, a2);
+  const R coef[3] = {mm[0], mm[1], (R)2 * mm[2]};
+  R* M = W.M[g];
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+#pragma unroll
+    for (int l = k; l < 5; ++l)
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) {
+          if (k == l && y < x) continue;
+          R v = s * (comp(Bb[k][0], x) * comp(Qb[l][0], y) + comp(Bb[k][1], x) * comp(Qb[l][1], y) +
+                     comp(Bb[k][2], x) * comp(Qb[l][2], y));
+          if (k < 2 && l < 2)
+            v += h * (comp(Ba[k][0], x) * comp(Qa[l][0], y) + comp(Ba[k][1], x) * comp(Qa[l][1], y) +
+                      comp(Ba[k][2], x) * comp(Qa[l][2], y));
+          R id = (x == y) ? (R)1 : (R)0;
+          // (H alpha)_i d^2 alpha_i
+          if (k == 0 && l == 0) v += h * sg[0] * id;
+          if (k == 1 && l == 1) v += h * sg[1] * id;
+          if (k == 0 && l == 1) v += h * sg[2] * id;
+          if (exact) {
+            // D~ blocks (App. B.2 with c = c~, beta_{ab} = c~ . a3)
+            if (k == 0 && l == 0)
+              v += s * ia * (bt * ((R)3 * comp(t1, x) * comp(t1, y) + comp(a2, x) * comp(a2, y) - a22 * id) -
+                             comp(s2, x) * comp(t1, y) - comp(t1, x) * comp(s2, y));
+            if (k == 1 && l == 1)
+              v += s * ia * (bt * ((R)3 * comp(t2, x) * comp(t2, y) + comp(a1, x) * comp(a1, y) - a11 * id) -
+                             comp(s1, x) * comp(t2, y) - comp(t2, x) * comp(s1, y));
+            if (k == 0 && l == 1) {
+              // -sqrt(a) [c~]: [v]_{xy} = eps_{x j y} v_j
+              R cx = (x == 0 && y == 1) ? -ct.z : (x == 0 && y == 2) ? ct.y : (x == 1 && y == 0) ? ct.z :
+                     (x == 1 && y == 2) ? -ct.x : (x == 2 && y == 0) ? -ct.y : (x == 2 && y == 1) ? ct.x : (R)0;
+              v += s * ia * (bt * ((R)3 * comp(t1, x) * comp(t2, y) - (R)2 * comp(a1, x) * comp(a2, y) +
+                                   comp(a2, x) * comp(a1, y) + a12 * id) -
+                             comp(s2, x) * comp(t2, y) - comp(t1, x) * comp(s1, y) - sqa * cx);
+            }
+            // Phi~^I d a3/dq_J + Phi~^J (d a3/dq_I)^T, stored in the (l in {1,2}, k' in {11,22,12})
+            // upper blocks as the transpose: entry [x][y] = coef_{k'} P_l[y][x]
+            if (k < 2 && l >= 2) {
+              // P_1 = (-[a2] - a3 (x) t1)/sqrt(a), P_2 = ([a1] - a3 (x) t2)/sqrt(a); need P_k[y][x]
+              V3<R> av = (k == 0) ? a2 : a1;
+              R sgn = (k == 0) ? (R)-1 : (R)1;
+              V3<R> tv = (k == 0) ? t1 : t2;
+              R cxm = (y == 0 && x == 1) ? -av.z : (y == 0 && x == 2) ? av.y : (y == 1 && x == 0) ? av.z :
+                      (y == 1 && x == 2) ? -av.x : (y == 2 && x == 0) ? -av.y : (y == 2 && x == 1) ? av.x : (R)0;
+              R Pyx = (sgn * cxm - comp(a3, y) * comp(tv, x)) / sqa;
+              v += s * coef[l - 2] * Pyx;
+            }
+          }
+          v *= wgt;
+          M[(k * 3 + x) * 15 + l * 3 + y] = v;
+          M[(l * 3 + y) * 15 + k * 3 + x] = v;
+        }
+}
+
+template <typename R>
+__device__ __forceinline__ void atomic_add_row12(R* dst, const R* v);
+
+template <>
+__device__ __forceinline__ void atomic_add_row12<float>(float* dst, const float* v) {
+  float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) atomicAdd(d4 + i, make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]));
+}
+template <>
+__device__ __forceinline__ void atomic_add_row12<double>(double* dst, const double* v) {
+#pragma unroll
+  for (int i = 0; i < 12; ++i) atomicAdd(dst + i, v[i]);
+}
+
+template <typename R>
+__device__ __forceinline__ void plain_add_row12(R* dst, const R* v) {
+#pragma unroll
+  for (int i = 0; i < 12; ++i) dst[i] += v[i];
+}
+
+// One patch by one warp: gather, Gauss-point matrices M_g, energy/gradient by-products, and the
+// Hessian K = sum_g phi_g^T M_g phi_g written unassembled and/or scattered into the BSR.
+template <typename R>
+__device__ __forceinline__ void element_patch(const R* sphi, WarpSmem<R>& W, int p, const ElemArgs& A,
+                                              int lane) {
+  constexpr int JP = ElemCfg<R>::kJP;          // J columns per pass (16 / 2 / JP passes)
+  const int I = lane >> 1, h = lane & 1;
+  const int4 pn = A.pnodes[p];
+  const int nd[4] = {pn.x, pn.y, pn.z, pn.w};
+  // Value DOFs enter only through derivatives, whose value-kind shape functions sum to zero
+  // (partition of unity); subtracting corner 00's value in FP64 before rounding removes the
+  // O(|x| / dxi) cancellation of the derivative interpolation from the R arithmetic.
+  for (int l = lane; l < 48; l += 32) {
+    const int kk = l % 12;
+    size_t a = (size_t)nd[l / 12] * 12 + kk;
+    double qv = A.q[a], rv = A.rest[a];
+    if (kk < 3) {
+      const size_t a0 = (size_t)nd[0] * 12 + kk;
+      const double q0 = A.q[a0], r0 = A.rest[a0];
+      W.u[l] = (R)((qv - rv) - (q0 - r0));
+      W.qb[l] = (R)(rv - r0);
+    } else {
+      W.u[l] = (R)(qv - rv);
+      W.qb[l] = (R)rv;
+    }
+  }
+  __syncwarp();
+  if (lane < 16) gauss_point_matrix<R>(sphi, W, lane, A);
+  __syncwarp();
+
+  // energy and gradient (by-products)
+  if (A.energy_p) {
+    R e = lane < 16 ? W.en[lane] : (R)0;
+    for (int o = 8; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane == 0) A.energy_p[p] = (double)e;
+  }
+  if (A.grad_p) {
+    for (int l = lane; l < 48; l += 32) {
+      int Ig = l / 3, c = l % 3;
+      R sacc = 0;
+      for (int g = 0; g < 16; ++g)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) sacc += sphi[Ig * kPhiStride + (k + 1) * 16 + g] * W.G[g][k * 3 + c];
+      A.grad_p[(size_t)p * 48 + l] = (double)sacc;
+    }
+  }
+
+  const bool want_h = A.hess_p || A.bsr;
+  if (want_h) {
+#pragma unroll 1
+    for (int pass = 0; pass < 8 / JP; ++pass) {
+      R acc[JP][9];
+#pragma unroll
+      for (int j = 0; j < JP; ++j)
+#pragma unroll
+        for (int e = 0; e < 9; ++e) acc[j][e] = (R)0;
+      const int J0 = 8 * h + pass * JP;
+#pragma unroll 1
+      for (int g = 0; g < 16; ++g) {
+        // T[I][c][l][c'] = sum_k phi_k^I M_g[(k,c),(l,c')]; lane (I, h) does (c,c') = h, h+2, ...
+        const R* Mg = W.M[g];
+        R phk[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) phk[k] = sphi[I * kPhiStride + (k + 1) * 16 + g];
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+          int pi = h + 2 * t;
+          if (pi < 9) {
+            int c = pi / 3, cp = pi % 3;
+#pragma unroll
+            for (int l = 0; l < 5; ++l) {
+              R tv = 0;
+#pragma unroll
+              for (int k = 0; k < 5; ++k) tv += phk[k] * Mg[(k * 3 + c) * 15 + l * 3 + cp];
+              W.T[I * 45 + c * 15 + l * 3 + cp] = tv;
+            }
+          }
+        }
+        __syncwarp();
+        R Tr[45];
+#pragma unroll
+        for (int e = 0; e < 45; ++e) Tr[e] = W.T[I * 45 + e];
+        const R mI = W.ms[g] * sphi[I * kPhiStride + g];
+#pragma unroll
+        for (int j = 0; j < JP; ++j) {
+          const int J = J0 + j;
+          R pj[5];
+#pragma unroll
+          for (int l = 0; l < 5; ++l) pj[l] = sphi[J * kPhiStride + (l + 1) * 16 + g];
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int cp = 0; cp < 3; ++cp) {
+              R sacc = acc[j][c * 3 + cp];
+#pragma unroll
+              for (int l = 0; l < 5; ++l) sacc += Tr[c * 15 + l * 3 + cp] * pj[l];
+              acc[j][c * 3 + cp] = sacc;
+            }
+          const R mm = mI * sphi[J * kPhiStride + g];
+          acc[j][0] += mm;
+          acc[j][4] += mm;
+          acc[j][8] += mm;
+        }
+        __syncwarp();
+      }
+      // outputs of this pass: rows (I, c), columns J0..J0+JP-1
+      if (A.hess_p) {
+        R* Hp = reinterpret_cast<R*>(A.hess_p) + (size_t)p * 2304;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int j = 0; j < JP; ++j)
+#pragma unroll
+            for (int cp = 0; cp < 3; ++cp) Hp[(I * 3 + c) * 48 + (J0 + j) * 3 + cp] = acc[j][c * 3 + cp];
+      }
+      if (A.bsr) {
+        // J0..J0+JP-1 covers whole corners (4 kinds each): row segments of 12 in the BSR block
+        R* V = reinterpret_cast<R*>(A.bsr);
+        const int a = I >> 2, r = I & 3;
+#pragma unroll
+        for (int bb = 0; bb < JP / 4; ++bb) {
+          const int b = (J0 >> 2) + bb;
+          const int kb = A.pblocks[p * 16 + a * 4 + b];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            R row[12];
+#pragma unroll
+            for (int sk = 0; sk < 4; ++sk)
+#pragma unroll
+              for (int cp = 0; cp < 3; ++cp) row[sk * 3 + cp] = acc[bb * 4 + sk][c * 3 + cp];
+            R* dst = V + (size_t)kb * 144 + (r * 3 + c) * 12;
+            if (A.bsr_atomic) atomic_add_row12<R>(dst, row);
+            else plain_add_row12<R>(dst, row);
+          }
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
+}  // namespace bhem

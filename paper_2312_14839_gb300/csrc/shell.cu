@@ -225,7 +225,10 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
   A(s->d_qn, m); A(s->d_y, m); A(s->d_g, m); A(s->d_gin, m); A(s->d_d, m); A(s->d_Md, m);
   A(s->d_rhs, m); A(s->d_Ep, np); A(s->d_qwork, m); A(s->d_vwork, m); A(s->d_qfix, m);
   A(s->d_warm, m); A(s->d_mask, m); A(s->d_ns, 1); A(s->d_err, 1); A(s->d_energy_tmp, 1);
-  A(s->red.partials, (size_t)kMaxRed * kMaxPartials);
+  // partials: one per CTA of the largest reducing launch (8 patches, 4 FP64 block rows, 16 nodes or
+  // 1024 vector CTAs per CTA) per reduced value
+  s->red.stride = std::max(1024, std::max(np / 8, n / 4) + 64);
+  A(s->red.partials, (size_t)kMaxRed * s->red.stride);
   A(s->red.ticket, 1);
 #undef A
   if (st == SHELL_OK) {

@@ -2,6 +2,8 @@
 // Jacobi preconditioner, PCG with device-resident scalars, consistent-mass products and the
 // Newton residual g = dV/dq + M (q - y)/dt^2 - F. No kernel waits on another CTA: grid
 // reductions use the last-CTA ticket of grid_reduce.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace bhem {
@@ -571,7 +573,7 @@ shell_status launch_grad_finish(Shell& s, const double* q, const double* y, doub
                                 const double grav[3], const unsigned char* mask, double* g,
                                 double* gin, double* gnorm2_out) {
   int blocks = grid_for(s.n_nodes, 16);
-  if (blocks > kMaxPartials) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
+  if (blocks > s.red.stride) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
   k_grad_finish<<<blocks, kNodeThreads, 0, s.stream>>>(s.n_nodes, s.d_row_ptr, s.d_col, s.d_mass,
                                                        s.d_fgrav, q, y, 1.0 / (dt * dt), grav[0],
                                                        grav[1], grav[2], mask, g, gin, gnorm2_out,
@@ -591,7 +593,7 @@ shell_status launch_mass_mult(Shell& s, const double* x, double* y) {
 
 shell_status launch_dots3(Shell& s, int m, const double* a0, const double* b0, const double* a1,
                           const double* b1, const double* a2, const double* b2, double* out3) {
-  int blocks = vec_blocks(m);
+  int blocks = std::min(vec_blocks(m), 1024);
   k_dots3<<<blocks, 256, 0, s.stream>>>(m, a0, b0, a1, b1, a2, b2, out3, s.red);
   BHEM_CUDA(cudaGetLastError());
   ++s.launches;
@@ -629,7 +631,7 @@ shell_status launch_diag_check(Shell& s, const unsigned char* mask, double* out1
 shell_status launch_pcg_init(Shell& s, const unsigned char* mask, const double* rhs, double rtol,
                              int fixed) {
   int blocks = grid_for(s.n_nodes, 16);
-  if (blocks > kMaxPartials) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
+  if (blocks > s.red.stride) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
   double rtol2 = fixed > 0 ? 0.0 : rtol * rtol;
   if (!s.val_fp64) {
     k_pcg32_init<<<blocks, kNodeThreads, 0, s.stream>>>(s.n_nodes, rhs, (const float*)s.d_Dinv, mask,
@@ -659,13 +661,13 @@ static shell_status launch_spmv_impl(Shell& s, const void* x, const double* xd,
   if (s.val_fp64) {
     constexpr int RPC = kSpmvThreads / 72;
     int blocks = grid_for(n, RPC);
-    if (st && blocks > kMaxPartials) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
+    if (st && blocks > s.red.stride) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
     k_spmv<double><<<blocks, kSpmvThreads, 0, s.stream>>>(n, s.d_row_ptr, s.d_col,
         (const double*)s.d_val, (const double*)x, xd, sh, mask, y, st, s.red);
   } else {
     constexpr int RPC = kSpmvThreads / 36;
     int blocks = grid_for(n, RPC);
-    if (st && blocks > kMaxPartials) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
+    if (st && blocks > s.red.stride) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
     k_spmv<float><<<blocks, kSpmvThreads, 0, s.stream>>>(n, s.d_row_ptr, s.d_col,
         (const float*)s.d_val, (const float*)x, xd, sh, mask, y, st, s.red);
   }
@@ -704,7 +706,7 @@ shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, const dou
   const int n = s.n_nodes, m = s.n_dof;
   if (!s.val_fp64) {
     const int blocks = grid_for(n, kSpmvThreads / 36);
-    if (blocks > kMaxPartials) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
+    if (blocks > s.red.stride) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
     Shift4f sh{{(float)td[0], (float)td[1], (float)td[2], (float)td[3]}};
     k_spmv32<<<blocks, kSpmvThreads, 0, s.stream>>>(n, s.d_row_ptr, s.d_col, (const float*)s.d_val,
                                                     s.d_p32, sh, mask, s.d_Ap32, s.d_pcg, s.red);
