@@ -49,7 +49,7 @@ typedef enum {
   SHELL_ERR_NONFINITE = 5,      /* a non-finite energy, gradient or residual was produced      */
   SHELL_ERR_NOT_CONVERGED = 6,  /* Newton hit newton_max; q, v hold the last iterate            */
   SHELL_ERR_LINESEARCH = 7,     /* no step satisfied the Armijo test in 20 trials               */
-  SHELL_ERR_INDEFINITE = 8,     /* negative curvature persisted up to tau = 1e4                 */
+  SHELL_ERR_INDEFINITE = 8,     /* negative curvature persisted beyond tau = 1e4                */
   SHELL_ERR_TIMEOUT = 9         /* reserved: a bounded device-side wait expired                 */
 } shell_status;
 
@@ -100,7 +100,7 @@ typedef struct {
   int newton_iters;       /* Newton updates applied                                         */
   int pcg_iters_total;    /* PCG iterations over all solves (regularised restarts included) */
   int ls_backtracks;      /* rejected line-search trials                                    */
-  int regularizations;    /* regulariser levels tried (tau D added, Sec. 6.1)               */
+  int regularizations;    /* solves with a diagonal shift tau D (Sec. 6.1 regulariser)      */
   int status;             /* shell_status of the step                                       */
   double res0;            /* |g_free| at the zero guess                                     */
   double res_final;       /* |g_free| at the returned state                                 */

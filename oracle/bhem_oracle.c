@@ -28,15 +28,15 @@
  *   - Line search: Armijo (c1 = 1e-4) from alpha = 1, then a quadratic and afterwards cubic
  *     interpolation (Nocedal-Wright Sec. 3.5), each clamped to [0.1, 0.5] of the last step, at
  *     most 20 trials; alpha = 1 is accepted without a test once |g| <= 1e-6 |g_ref|.
- *   - Regulariser (Sec. 6.1 gives no form or magnitude): PCG stops on p^T A p <= 0; the solve
- *     restarts on A + tau D with tau = 1e-8, 1e-6, ..., 1e4 (x100 per restart), then gives up.
- *     D is diagonal: for each DOF kind (x, x_,1, x_,2, x_,12) the mean of |A_ii| over the free
- *     DOFs of that kind. It is positive and scales like each kind's stiffness (the shape
- *     functions of derivative DOFs carry powers of dxi), where diag(A) itself may be negative
- *     or near zero under compression. A level whose regularised matrix has a free diagonal
- *     entry <= 0 cannot be positive definite and is skipped without running PCG. A 12x12
- *     block that is not SPD is replaced by the inverse of its diagonal in the block-Jacobi
- *     preconditioner.
+ *   - Regulariser (Sec. 6.1 adds "a diagonal regularizer" to make the matrix positive definite,
+ *     with no form or magnitude). D is diagonal: for each DOF kind (x, x_,1, x_,2, x_,12) the mean
+ *     of |A_ii| over the free DOFs of that kind (positive, and scaled like each kind's stiffness,
+ *     where diag(A) itself may be negative or near zero under compression). The first solve uses
+ *     the smallest shift that makes the free diagonal of A + tau D positive (a necessary condition
+ *     for positive definiteness): tau = 0 if it already is, else 1.01 max_k(-min_i A_ii / D_k)
+ *     (at least 1e-8). Each time PCG meets p^T A p <= 0 the solve restarts with tau = max(10 tau,
+ *     1e-8); beyond tau = 1e4 the step gives up. A 12x12 block that is not SPD is replaced by the
+ *     inverse of its diagonal in the block-Jacobi preconditioner.
  */
 #include <math.h>
 #include <stdint.h>
@@ -760,32 +760,33 @@ int og_newton_step(const og_grid* g, const og_material* mat, const double* rest,
     if (it >= P->newton_max) { status = OG_ERR_NOT_CONVERGED; break; }
     og_assemble(g, mat, rest, q, row_ptr, col, 1.0 / (P->dt * P->dt), NULL, NULL, val);
     for (int i = 0; i < m; ++i) rhs[i] = -gr[i];
-    /* tau = 0, then 1e-8, 1e-6, ..., 1e4 */
-    double tau = 0.0, dbar[4];
+    /* smallest shift that makes the free diagonal positive, then x10 per negative curvature */
+    double dbar[4], dmin[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
     og_kind_scale(n, row_ptr, col, val, mask, dbar);
-    int piters = 0, ps;
-    for (int reg = 0;; ++reg) {
-      /* a free diagonal entry <= 0 of A + tau D rules out positive definiteness */
-      int diag_ok = 1;
-      for (int i = 0; i < n && diag_ok; ++i) {
-        int k = find_block(row_ptr, col, i, i);
-        for (int a = 0; a < 12; ++a) {
-          if (mask && mask[i*12 + a]) continue;
-          double dv = val[(size_t)k*144 + a*13];
-          if (!(dv + tau * dbar[a / 3] > 0.0)) { diag_ok = 0; break; }
-        }
+    for (int i = 0; i < n; ++i) {
+      int k = find_block(row_ptr, col, i, i);
+      for (int a = 0; a < 12; ++a) {
+        if (mask && mask[i*12 + a]) continue;
+        double dv = val[(size_t)k*144 + a*13];
+        if (dv < dmin[a / 3]) dmin[a / 3] = dv;
       }
-      if (diag_ok) {
-        ps = og_pcg(n, row_ptr, col, val, mask, tau, dbar, rhs, P->pcg_rtol, P->pcg_max,
-                    P->pcg_fixed_iters, d, &piters);
-        st->pcg_iters_total += piters;
-      } else {
-        ps = OG_PCG_NEG_CURV;
-      }
-      if (ps != OG_PCG_NEG_CURV) break;
-      if (reg == 7) { status = OG_ERR_INDEFINITE; break; }
+    }
+    double tau = 0.0;
+    for (int q = 0; q < 4; ++q)
+      if (dmin[q] <= 0.0 && -dmin[q] / dbar[q] * 1.01 > tau) tau = -dmin[q] / dbar[q] * 1.01;
+    if (tau > 0.0) {
+      if (tau < 1e-8) tau = 1e-8;
       st->regularizations++;
-      tau = 1e-8 * pow(100.0, reg);
+    }
+    int piters = 0, ps;
+    for (;;) {
+      if (tau > 1e4) { status = OG_ERR_INDEFINITE; break; }
+      ps = og_pcg(n, row_ptr, col, val, mask, tau, dbar, rhs, P->pcg_rtol, P->pcg_max,
+                  P->pcg_fixed_iters, d, &piters);
+      st->pcg_iters_total += piters;
+      if (ps != OG_PCG_NEG_CURV) break;
+      st->regularizations++;
+      tau = tau * 10.0 > 1e-8 ? tau * 10.0 : 1e-8;
     }
     if (status != OG_OK) break;
 

@@ -35,6 +35,7 @@ struct ShellState {
   // PCG
   double rz, pq, rr, bb, alpha, beta, rtol2;
   int pcg_done, pcg_iters, pcg_iters_total, negcurv, restart, reg_level, regularizations, limit;
+  double tau;
   float td[4];
   double dbar[4], dmin[4], dcount[4];
   // line search
@@ -650,24 +651,6 @@ __global__ void k_ctrl_beta(int S, ShellState* st) {
   T.acc[1] = 0.0;
 }
 
-// Regulariser ladder of Sec. 6.1 (the single-shell reading): the first level whose diagonal
-// stays positive; tau = 0, 1e-8 * 100^(level-1).
-__device__ __forceinline__ bool ladder(ShellState& T) {
-  for (int lvl = 0; lvl <= 7; ++lvl) {
-    const double tau = lvl == 0 ? 0.0 : 1e-8 * pow(100.0, lvl - 1);
-    bool ok = true;
-    for (int k = 0; k < 4; ++k)
-      if (T.dcount[k] > 0 && !(T.dmin[k] + tau * T.dbar[k] > 0.0)) ok = false;
-    if (ok) {
-      T.regularizations += lvl;
-      T.reg_level = lvl;
-      for (int k = 0; k < 4; ++k) T.td[k] = (float)(tau * T.dbar[k]);
-      return true;
-    }
-  }
-  return false;
-}
-
 // After k_diag_stats: per-kind scale, first admissible regulariser level, PCG not done
 __global__ void k_ctrl_reg_init(int S, ShellState* st, const int* __restrict__ dmin_bits) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -682,42 +665,34 @@ __global__ void k_ctrl_reg_init(int S, ShellState* st, const int* __restrict__ d
   if (!T.active) return;
   T.pcg_done = 0;
   T.restart = 0;
-  T.regularizations = 0;
-  if (!ladder(T)) {
-    T.status = SHELL_ERR_INDEFINITE;
-    T.active = 0;
-    T.pcg_done = 1;
-    T.regularizations = 7;
+  // the smallest shift that keeps the free diagonal of A + tau D positive (Sec. 6.1 regulariser)
+  double tau = 0.0;
+  for (int k = 0; k < 4; ++k)
+    if (T.dcount[k] > 0 && T.dmin[k] <= 0.0) tau = fmax(tau, -T.dmin[k] / T.dbar[k] * 1.01);
+  if (tau > 0.0) {
+    tau = fmax(tau, 1e-8);
+    T.regularizations += 1;
   }
+  T.tau = tau;
+  for (int k = 0; k < 4; ++k) T.td[k] = (float)(tau * T.dbar[k]);
 }
 
-// Between PCG chunks: shells that met negative curvature move up the ladder and restart.
+// Between PCG chunks: shells that met negative curvature restart with tau x 10 (at least 1e-8);
+// beyond 1e4 the shell's step gives up.
 __global__ void k_ctrl_restart(int S, ShellState* st, Counters* cnt) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   ShellState& T = st[s];
   if (!(T.active && T.pcg_done && T.negcurv)) return;
   T.negcurv = 0;
-  const int prev = T.reg_level;
-  int lvl = prev + 1;
-  bool ok = false;
-  for (; lvl <= 7; ++lvl) {
-    const double tau = 1e-8 * pow(100.0, lvl - 1);
-    bool pos = true;
-    for (int k = 0; k < 4; ++k)
-      if (T.dcount[k] > 0 && !(T.dmin[k] + tau * T.dbar[k] > 0.0)) pos = false;
-    if (pos) { ok = true; break; }
-  }
-  if (!ok) {
-    T.regularizations += 7 - prev;
+  T.regularizations += 1;
+  T.tau = fmax(10.0 * T.tau, 1e-8);
+  if (T.tau > 1e4) {
     T.status = SHELL_ERR_INDEFINITE;
     T.active = 0;
     return;
   }
-  T.regularizations += lvl - prev;
-  T.reg_level = lvl;
-  const double tau = 1e-8 * pow(100.0, lvl - 1);
-  for (int k = 0; k < 4; ++k) T.td[k] = (float)(tau * T.dbar[k]);
+  for (int k = 0; k < 4; ++k) T.td[k] = (float)(T.tau * T.dbar[k]);
   T.pcg_done = 0;
   T.restart = 1;
   atomicAdd(&cnt->n_restart, 1);
@@ -1184,7 +1159,7 @@ shell_status solve_directions(shell_batch_s& b, const shell_step_params& P, cons
   k_ctrl_reg_init<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, b.dmin_bits);
   BL(b);
   int only_restart = 0;
-  for (int round = 0; round < 9; ++round) {
+  for (int round = 0; round < 16; ++round) {
     k_precond<<<blocks_for(b.N, 16), 192, 0, b.stream>>>(b.N, b.nshell, b.st, b.diag, b.val, mask, b.Dinv,
                                                           only_restart);
     k_pcg_init<<<blocks_for(b.N, 16), kNodeThreads, 0, b.stream>>>(b.N, b.nshell, b.st, b.rhs, b.Dinv, mask,

@@ -382,11 +382,13 @@ static shell_status kind_stats(Shell& s, const unsigned char* mask, KindStats& K
   }
   return SHELL_OK;
 }
-// A + tau D can only be positive definite if every free diagonal entry stays positive.
-static bool diag_positive(const KindStats& K, double tau) {
+// The smallest regulariser shift that keeps every free diagonal entry of A + tau D positive
+// (a necessary condition for positive definiteness): 0, or 1.01 max_k(-min A_ii / D_k) >= 1e-8.
+static double start_shift(const KindStats& K) {
+  double tau = 0.0;
   for (int q = 0; q < 4; ++q)
-    if (K.count[q] > 0 && !(K.dmin[q] + tau * K.dbar[q] > 0.0)) return false;
-  return true;
+    if (K.count[q] > 0 && K.dmin[q] <= 0.0) tau = std::max(tau, -K.dmin[q] / K.dbar[q] * 1.01);
+  return tau > 0.0 ? std::max(tau, 1e-8) : 0.0;
 }
 }  // namespace bhem
 
@@ -440,25 +442,22 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
     if (it >= P.newton_max) { status = SHELL_ERR_NOT_CONVERGED; break; }
     BHEM_TRY(assemble_hessian(s, q, inv_dt2));
     BHEM_TRY(launch_negate(s, s.d_g, s.d_rhs));
-    // Sec. 6.1 diagonal regulariser: tau = 0, then A + tau D with tau = 1e-8, 1e-6, ..., 1e4
-    // (x100 per restart) while PCG meets negative curvature; D = per-kind mean |A_ii|. A level
-    // whose diagonal has a free entry <= 0 cannot be positive definite and is skipped.
+    // Sec. 6.1 diagonal regulariser A + tau D (D = per-kind mean |A_ii|): the first solve uses the
+    // smallest shift that makes the free diagonal positive, each negative curvature met by PCG
+    // multiplies tau by 10 (at least 1e-8), beyond 1e4 the step gives up.
     KindStats K;
     BHEM_TRY(kind_stats(s, mask, K));
-    double tau = 0.0;
-    for (int reg = 0;; ++reg) {
+    double tau = start_shift(K);
+    if (tau > 0.0) st.regularizations++;
+    for (;;) {
+      if (tau > 1e4) { status = SHELL_ERR_INDEFINITE; break; }
       int pit = 0, neg = 0;
-      if (diag_positive(K, tau)) {
-        const double td[4] = {tau * K.dbar[0], tau * K.dbar[1], tau * K.dbar[2], tau * K.dbar[3]};
-        BHEM_TRY(run_pcg(s, mask, td, s.d_rhs, P.pcg_rtol, P.pcg_max, P.pcg_fixed_iters, &pit, &neg));
-        st.pcg_iters_total += pit;
-      } else {
-        neg = 1;
-      }
+      const double td[4] = {tau * K.dbar[0], tau * K.dbar[1], tau * K.dbar[2], tau * K.dbar[3]};
+      BHEM_TRY(run_pcg(s, mask, td, s.d_rhs, P.pcg_rtol, P.pcg_max, P.pcg_fixed_iters, &pit, &neg));
+      st.pcg_iters_total += pit;
       if (!neg) break;
-      if (reg == 7) { status = SHELL_ERR_INDEFINITE; break; }
       st.regularizations++;
-      tau = 1e-8 * std::pow(100.0, reg);
+      tau = std::max(10.0 * tau, 1e-8);
     }
     if (status != SHELL_OK) break;
     BHEM_CUDA(cudaMemcpyAsync(s.d_d, s.d_x, sizeof(double) * m, cudaMemcpyDeviceToDevice, s.stream));
@@ -563,7 +562,7 @@ extern "C" shell_status shell_newton_step(shell_t* shell, const shell_step_param
   if (st != SHELL_OK) {
     if (st == SHELL_ERR_NOT_CONVERGED) set_error("Newton did not reach the residual tolerance");
     else if (st == SHELL_ERR_LINESEARCH) set_error("line search failed");
-    else if (st == SHELL_ERR_INDEFINITE) set_error("negative curvature persisted up to tau = 1e4");
+    else if (st == SHELL_ERR_INDEFINITE) set_error("negative curvature persisted beyond tau = 1e4");
   }
   return st;
 }
