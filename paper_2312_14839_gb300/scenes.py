@@ -211,3 +211,47 @@ def batch_sheets(n_shells: int = 512, seed: int = 4, n_min: int = 4, n_max: int 
         g, rest = flat_sheet(n, n)
         out.append((g, mat, rest, noisy(rest, sigma, seed * 100003 + k)))
     return out
+
+
+def corner_twist_rates(seed: int, n: int = 1, max_deg: float = 2.0) -> np.ndarray:
+    """Per-trajectory twist rates of the four corners, U[-max_deg, max_deg] degrees per step;
+    shape [n, 4]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(-max_deg, max_deg, size=(n, 4))
+
+
+def corner_twist_prescription(g: Grid, rest: np.ndarray, step: int, rates) -> tuple[np.ndarray, np.ndarray]:
+    """Four corners of a sheet held in place; each corner's x_,1 and x_,2 rotated about +z by
+    rates[c] * step degrees. Returns (mask uint8 [n_dof], values float64 [n_dof])."""
+    rest = np.asarray(rest, dtype=np.float64).reshape(-1, DOF_PER_NODE)
+    corners = corner_nodes(g)
+    mask = pinned_mask(g, corners, kinds=(0, 1, 2))
+    vals = np.zeros(g.n_dof)
+    for c, rate in zip(corners, rates):
+        ang = math.radians(float(rate) * step)
+        rot = np.array([[math.cos(ang), -math.sin(ang), 0.0],
+                        [math.sin(ang), math.cos(ang), 0.0],
+                        [0.0, 0.0, 1.0]])
+        base = c * DOF_PER_NODE
+        vals[base:base + 3] = rest[c, 0:3]
+        vals[base + 3:base + 6] = rot @ rest[c, 3:6]
+        vals[base + 6:base + 9] = rot @ rest[c, 6:9]
+    return mask, vals
+
+
+# Warm-start network shape: (fan_in, fan_out) per layer, 28 node features in, 12 DOFs out.
+MLP_LAYERS = ((28, 256), (256, 256), (256, 256), (256, 12))
+
+
+def mlp_init_params(seed: int, last_scale: float = 0.1) -> np.ndarray:
+    """Seeded initial parameters of the warm-start network, packed per layer as W [fan_out,
+    fan_in] row-major then b: He-normal weights (std sqrt(2 / fan_in)), the last layer's scaled
+    by last_scale, zero biases. FP32."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for l, (fi, fo) in enumerate(MLP_LAYERS):
+        W = rng.standard_normal((fo, fi)) * math.sqrt(2.0 / fi)
+        if l == len(MLP_LAYERS) - 1:
+            W *= last_scale
+        parts += [W.reshape(-1), np.zeros(fo)]
+    return np.concatenate(parts).astype(np.float32)
