@@ -249,6 +249,73 @@ SHELL_API shell_status shell_batch_newton_step(shell_batch_t* batch, const shell
                                                double* q, double* v, const double* warm_start,
                                                shell_step_stats* stats);
 
+/* ---------------------------------------------------------------------------------------------
+   Learned Newton warm start. The paper has no learning component: this is an extension that
+   predicts the initial Newton iterate of an implicit-Euler step (Sec. 6.1) per node. The
+   network is a per-node MLP 28 -> 256 -> 256 -> 256 -> 12 with GELU after each hidden layer;
+   weights and activations are BF16, products accumulate in FP32 on the tensor cores; FP32
+   master weights are trained with an MSE loss and Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+   Node features (28 floats, written by shell_node_features): u = q - q_rest (12), v (12), the
+   mean over the node's present edge neighbours of u_nb - u for the position DOFs (3), and the
+   present fraction of its 4-neighbour stencil (1). Target and output (12 floats): the update
+   beyond the inertial predictor, q^{n+1} - q^n - dt v^n (shell_warm_targets). Inputs and
+   targets are normalised per column by shell_mlp_set_normalization (x' = (x - mean) / std;
+   a std of 0 is taken as 1); the loss is the mean of squared normalised errors.
+   The Newton step that consumes the warm start still measures convergence against the residual
+   at q^n (the zero-guess start), so the network changes the starting point, never the answer.
+   Parameters are exchanged as one packed FP32 host array: for each layer l = 1..4 the weight
+   matrix [fan_out x fan_in] row-major, then the bias [fan_out] (shell_mlp_param_count floats).
+   All GPU work runs on the stream given to shell_mlp_create, except shell_mlp_warm_start, which
+   runs on the shell's stream; a network's buffers are shared by its calls, so calls on one
+   network must not overlap.
+   --------------------------------------------------------------------------------------------- */
+typedef struct shell_mlp_s shell_mlp_t;
+
+/* Creates a network with zero parameters for batches of up to max_rows rows (1 .. 2^24) of
+   features; stream: cudaStream_t or NULL. Device memory: about 10.6 KB per row plus 2.3 MB. */
+SHELL_API shell_status shell_mlp_create(int max_rows, void* stream, shell_mlp_t** out);
+SHELL_API shell_status shell_mlp_destroy(shell_mlp_t* mlp);
+/* Number of floats of the packed parameter array (142,092). */
+SHELL_API shell_status shell_mlp_param_count(long long* count);
+/* Uploads packed FP32 parameters (host) and resets the Adam moments and step count. Synchronises. */
+SHELL_API shell_status shell_mlp_set_params(shell_mlp_t* mlp, const float* params);
+/* Downloads the packed parameters and/or the packed gradients of the last shell_mlp_gradients or
+   shell_mlp_train_step (host buffers, either may be NULL). Synchronises. */
+SHELL_API shell_status shell_mlp_get_params(shell_mlp_t* mlp, float* params, float* grads);
+/* Per-column normalisation (host arrays: in_mean, in_std [28]; out_mean, out_std [12]). */
+SHELL_API shell_status shell_mlp_set_normalization(shell_mlp_t* mlp, const float* in_mean, const float* in_std,
+                                                   const float* out_mean, const float* out_std);
+/* Mean and population standard deviation (FP64 sums) of each column of X (device [rows x cols]
+   FP32, cols <= 28); mean, std: host [cols]. Synchronises. */
+SHELL_API shell_status shell_mlp_column_stats(shell_mlp_t* mlp, const float* X, long long rows, int cols,
+                                              double* mean, double* std);
+/* Y (device [rows x 12] FP32, de-normalised) = network(X) for X device [rows x 28] FP32. */
+SHELL_API shell_status shell_mlp_forward(shell_mlp_t* mlp, const float* X, int rows, float* Y);
+/* Loss and parameter gradients on a batch of rows rows of a data set of data_rows rows (X device
+   [data_rows x 28], T device [data_rows x 12], FP32). idx: device [rows] int row indices, or NULL
+   for rows 0 .. rows-1. loss: host, may be NULL (then the call is asynchronous). An index outside
+   [0, data_rows) contributes a zero row and makes the next synchronising call of this network
+   return SHELL_ERR_ARG. */
+SHELL_API shell_status shell_mlp_gradients(shell_mlp_t* mlp, const float* X, const float* T, long long data_rows,
+                                           const int* idx, int rows, double* loss);
+/* shell_mlp_gradients followed by one Adam update with learning rate lr; loss as above (the loss
+   before the update). */
+SHELL_API shell_status shell_mlp_train_step(shell_mlp_t* mlp, const float* X, const float* T, long long data_rows,
+                                            const int* idx, int rows, float lr, double* loss);
+/* Number of CUDA kernels this network has launched (host counter). */
+SHELL_API shell_status shell_mlp_kernel_launches(const shell_mlp_t* mlp, long long* count);
+/* Node features of a shell state: q, v device [n_dof] FP64; X device [n_nodes x 28] FP32. Runs on
+   the shell's stream. */
+SHELL_API shell_status shell_node_features(shell_t* shell, const double* q, const double* v, float* X);
+/* Training targets T[k] = q_next[k] - q[k] - dt v[k] (device arrays of n_dof entries; T FP32). */
+SHELL_API shell_status shell_warm_targets(long long n_dof, const double* q_next, const double* q, const double* v,
+                                          double dt, float* T, void* stream);
+/* warm = q + dt v + network(features(q, v)) (device [n_dof] FP64), ready to pass as warm_start to
+   shell_newton_step with the same dt. The shell must have at most max_rows nodes. mlp may be NULL:
+   then warm = q + dt v, the inertial predictor alone. */
+SHELL_API shell_status shell_mlp_warm_start(shell_mlp_t* mlp, shell_t* shell, const double* q, const double* v,
+                                            double dt, double* warm);
+
 /* Number of CUDA kernels this shell has launched since shell_create (host counter; counts the
    launches of the library's own kernels, not memset/memcpy operations). */
 SHELL_API shell_status shell_kernel_launches(const shell_t* shell, long long* count);

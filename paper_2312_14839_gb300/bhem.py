@@ -82,7 +82,7 @@ def load():
             if not os.path.exists(path):
                 raise RuntimeError(f"libbhem.so not found at {path}")
             lib = C.CDLL(path)
-            p, i, d = C.c_void_p, C.c_int, C.c_double
+            p, i, d, f, ll = C.c_void_p, C.c_int, C.c_double, C.c_float, C.c_longlong
             sigs = {
                 "shell_create": [p, p, p, p, p, p],
                 "shell_destroy": [p],
@@ -101,6 +101,20 @@ def load():
                 "shell_batch_info": [p, p, p],
                 "shell_batch_autotune": [p, p, i],
                 "shell_batch_newton_step": [p, p, p, p, p, p, p, p],
+                "shell_mlp_create": [i, p, p],
+                "shell_mlp_destroy": [p],
+                "shell_mlp_param_count": [p],
+                "shell_mlp_set_params": [p, p],
+                "shell_mlp_get_params": [p, p, p],
+                "shell_mlp_set_normalization": [p, p, p, p, p],
+                "shell_mlp_column_stats": [p, p, ll, i, p, p],
+                "shell_mlp_forward": [p, p, i, p],
+                "shell_mlp_gradients": [p, p, p, ll, p, i, p],
+                "shell_mlp_train_step": [p, p, p, ll, p, i, f, p],
+                "shell_mlp_kernel_launches": [p, p],
+                "shell_node_features": [p, p, p, p],
+                "shell_warm_targets": [ll, p, p, p, d, p, p],
+                "shell_mlp_warm_start": [p, p, p, p, d, p],
             }
             for name, args in sigs.items():
                 fn = getattr(lib, name)
@@ -344,3 +358,126 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Mlp:
+    """The warm-start network (shell_mlp_*): a per-node MLP 28 -> 256 -> 256 -> 256 -> 12 whose
+    forward, backward and Adam steps run in the library's kernels. Parameters are exchanged as
+    one packed FP32 numpy array (per layer W [fan_out, fan_in] row-major, then b)."""
+
+    N_IN, N_OUT, LAYERS = 28, 12, ((28, 256), (256, 256), (256, 256), (256, 12))
+
+    def __init__(self, max_rows, stream=None):
+        lib = load()
+        self.stream, sh = _stream_handle(stream)
+        self.max_rows = int(max_rows)
+        self._h = C.c_void_p()
+        _check(lib.shell_mlp_create(self.max_rows, sh, C.byref(self._h)))
+        n = C.c_longlong()
+        _check(lib.shell_mlp_param_count(C.byref(n)))
+        self.n_params = n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().shell_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_params(self, params):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        if params.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {params.size}")
+        _check(load().shell_mlp_set_params(self._h, _ptr(params)))
+
+    def get_params(self):
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(load().shell_mlp_get_params(self._h, _ptr(out), None))
+        return out
+
+    def get_grads(self):
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(load().shell_mlp_get_params(self._h, None, _ptr(out)))
+        return out
+
+    def set_normalization(self, in_mean, in_std, out_mean, out_std):
+        a = [np.ascontiguousarray(x, dtype=np.float32) for x in (in_mean, in_std, out_mean, out_std)]
+        _check(load().shell_mlp_set_normalization(self._h, *[_ptr(x) for x in a]))
+
+    def column_stats(self, X):
+        """(mean, std) of each column of a [rows, cols] FP32 CUDA tensor."""
+        rows, cols = X.shape
+        mean, std = np.empty(cols), np.empty(cols)
+        _check(load().shell_mlp_column_stats(self._h, _ptr(X), int(rows), int(cols), _ptr(mean), _ptr(std)))
+        return mean, std
+
+    def forward(self, X, Y=None):
+        import torch
+        if Y is None:
+            Y = torch.empty(X.shape[0], self.N_OUT, dtype=torch.float32, device=X.device)
+        _check(load().shell_mlp_forward(self._h, _ptr(X), int(X.shape[0]), _ptr(Y)))
+        return Y
+
+    def gradients(self, X, T, idx=None, rows=None, want_loss=True):
+        rows = int(X.shape[0] if idx is None else idx.shape[0]) if rows is None else int(rows)
+        loss = C.c_double()
+        _check(load().shell_mlp_gradients(self._h, _ptr(X), _ptr(T), int(X.shape[0]), _ptr(idx), rows,
+                                          C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def train_step(self, X, T, idx, lr, want_loss=False):
+        loss = C.c_double()
+        _check(load().shell_mlp_train_step(self._h, _ptr(X), _ptr(T), int(X.shape[0]), _ptr(idx),
+                                           int(idx.shape[0]), float(lr), C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def kernel_launches(self) -> int:
+        n = C.c_longlong()
+        _check(load().shell_mlp_kernel_launches(self._h, C.byref(n)))
+        return n.value
+
+    def warm_start(self, shell, q, v, dt, warm=None):
+        """q + dt v + network(features) for a shell state (FP64 CUDA tensors), on the shell's stream."""
+        import torch
+        if warm is None:
+            warm = torch.empty_like(q)
+        _check(load().shell_mlp_warm_start(self._h, shell._h, _ptr(q), _ptr(v), float(dt), _ptr(warm)))
+        return warm
+
+
+def inertial_warm_start(shell, q, v, dt, warm=None):
+    """warm = q + dt v (shell_mlp_warm_start without a network), on the shell's stream."""
+    import torch
+    if warm is None:
+        warm = torch.empty_like(q)
+    _check(load().shell_mlp_warm_start(None, shell._h, _ptr(q), _ptr(v), float(dt), _ptr(warm)))
+    return warm
+
+
+def node_features(shell, q, v, X=None):
+    """Node features [n_nodes, 28] (FP32 CUDA tensor) of a shell state, on the shell's stream."""
+    import torch
+    if X is None:
+        X = torch.empty(shell.n_nodes, Mlp.N_IN, dtype=torch.float32, device=q.device)
+    _check(load().shell_node_features(shell._h, _ptr(q), _ptr(v), _ptr(X)))
+    return X
+
+
+def warm_targets(q_next, q, v, dt, T=None, stream=None):
+    """T = q_next - q - dt v as FP32 (CUDA tensors of n_dof entries)."""
+    import torch
+    if T is None:
+        T = torch.empty(q.numel(), dtype=torch.float32, device=q.device)
+    _, sh = _stream_handle(stream)
+    _check(load().shell_warm_targets(int(q.numel()), _ptr(q_next), _ptr(q), _ptr(v), float(dt), _ptr(T), sh))
+    return T
