@@ -73,7 +73,7 @@ def measured_peaks():
 def recorded_traffic(kernel_src: str, workload: str):
     """DRAM bytes per SpMV launch from the committed ncu summary, when it was taken on the
     current kernel source (sha256 recorded in the summary); else None."""
-    path = os.path.join(ROOT, "profiles", f"spmv_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"k_spmv32_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
