@@ -70,10 +70,10 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def recorded_traffic(kernel_src: str, workload: str):
+def recorded_traffic(kernel_src: str, kernel: str, workload: str):
     """DRAM bytes per SpMV launch from the committed ncu summary, when it was taken on the
     current kernel source (sha256 recorded in the summary); else None."""
-    path = os.path.join(ROOT, "profiles", f"k_spmv32_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -347,6 +347,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spmv-reps", type=int, default=50)
     ap.add_argument("--train-iters", type=int, default=4000)
+    ap.add_argument("--spmv", default="auto", choices=["auto", "plain", "tma"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -379,7 +380,7 @@ def main():
     stream = torch.cuda.current_stream()
     rest_d = torch.as_tensor(rest.reshape(-1), device=dev)
     q0_d = torch.as_tensor(q0.reshape(-1), device=dev)
-    sh = bhem.Shell(g, mat, rest_d, precision="mixed", stream=stream)
+    sh = bhem.Shell(g, mat, rest_d, precision="mixed", stream=stream, spmv=args.spmv)
     P = bhem.step_params(dt=1e-3, newton_max=1, pcg_fixed_iters=50)
     q = q0_d.clone()
     v = torch.zeros_like(q)
@@ -464,7 +465,8 @@ def main():
     spmv_bytes = nb * 144 * 4 + nb * 4 + (n + 1) * 4 + m * 4 + m * 4
     peak, peak_kind = measured_peaks()
     achieved = spmv_bytes / spmv_s / 1e9
-    traffic = recorded_traffic(os.path.join(ROOT, "paper_2312_14839_gb300", "csrc", "solver.cu"), args.workload)
+    traffic = recorded_traffic(os.path.join(ROOT, "paper_2312_14839_gb300", "csrc", "solver.cu"),
+                               "k_spmv32_tma" if args.spmv == "tma" else "k_spmv32", args.workload)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -482,7 +484,9 @@ def main():
         "last_step_stats": stats,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * m * 8,
                 "d2h_bytes_per_step": 2 * m * 8},
-        "roofline": {"kernel": "k_spmv32 (FP32 12x12 BSR SpMV of the PCG)", "bound": "hbm",
+        "roofline": {"kernel": ("k_spmv32_tma (FP32 12x12 BSR SpMV of the PCG, bulk-copy pipelined)"
+                               if args.spmv == "tma" else "k_spmv32 (FP32 12x12 BSR SpMV of the PCG)"),
+                     "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
                      "traffic": traffic, "algorithmic_bytes_per_launch": spmv_bytes,

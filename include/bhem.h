@@ -50,7 +50,7 @@ typedef enum {
   SHELL_ERR_NOT_CONVERGED = 6,  /* Newton hit newton_max; q, v hold the last iterate            */
   SHELL_ERR_LINESEARCH = 7,     /* no step satisfied the Armijo test in 20 trials               */
   SHELL_ERR_INDEFINITE = 8,     /* negative curvature persisted beyond tau = 1e4                */
-  SHELL_ERR_TIMEOUT = 9         /* reserved: a bounded device-side wait expired                 */
+  SHELL_ERR_TIMEOUT = 9         /* a bounded device-side wait expired (results of the call are void) */
 } shell_status;
 
 /* Patch grid (Sec. 4.1, Fig. regular; periodic boundary conditions of Sec. 4.2). dxi1, dxi2
@@ -70,17 +70,24 @@ typedef struct {
 enum { SHELL_PREC_FP64 = 0, SHELL_PREC_MIXED = 1 };
 enum { SHELL_HESS_EXACT = 0, SHELL_HESS_PSEUDO = 1 };
 enum { SHELL_ASM_ATOMIC = 0, SHELL_ASM_COLOR = 1 };
+enum { SHELL_SPMV_AUTO = 0, SHELL_SPMV_PLAIN = 1, SHELL_SPMV_TMA = 2 };
 
 /* precision: SHELL_PREC_FP64 = every quantity in FP64; SHELL_PREC_MIXED = element Hessian,
    BSR values, SpMV and block-Jacobi in FP32, while the energy, gradient/residual, line-search
    energy differences and PCG dot products stay FP64.
    hessian: exact (App. B.2) or the pseudo Hessian of App. B.2 without the second derivative of
-   beta. assembly: atomic scatter or 4-colour ordered scatter of the element blocks. */
+   beta. assembly: atomic scatter or 4-colour ordered scatter of the element blocks.
+   spmv (SHELL_PREC_MIXED only): the FP32 BSR SpMV of shell_spmv and of PCG. SHELL_SPMV_PLAIN:
+   one CTA per 8 block rows, blocks loaded straight into registers. SHELL_SPMV_TMA: a persistent
+   kernel that streams each CTA's row groups into a shared-memory ring with bulk asynchronous
+   copies (cp.async.bulk + mbarrier); rejected when 8 block rows of the longest row do not fit.
+   SHELL_SPMV_AUTO: plain (the faster of the two on GB300). Both give bit-identical results.
+   Batches ignore this field. */
 typedef struct {
   int precision;
   int hessian;
   int assembly;
-  int reserved;
+  int spmv;
 } shell_options;
 
 /* One implicit-Euler step (Eq. implicit, Sec. 6.1). Newton stops when |g_free| <= newton_rtol *

@@ -31,7 +31,7 @@ shell_status fail(shell_status st, const std::string& msg);
   } while (0)
 
 // Device-side error bits (OR-ed into Shell::d_err, read back at synchronising calls).
-enum : int { ERRBIT_DEGENERATE = 1, ERRBIT_NONFINITE = 2 };
+enum : int { ERRBIT_DEGENERATE = 1, ERRBIT_NONFINITE = 2, ERRBIT_TIMEOUT = 4 };
 
 // ------------------------------------------------------------------------------------------
 // Deterministic grid reductions: each CTA writes a partial, the last CTA to arrive (atomic
@@ -107,6 +107,7 @@ struct Shell {
   double *d_qn = nullptr, *d_y = nullptr, *d_g = nullptr, *d_gin = nullptr, *d_d = nullptr;
   double *d_Md = nullptr, *d_Ep = nullptr, *d_qwork = nullptr, *d_vwork = nullptr;
   double *d_qfix = nullptr, *d_warm = nullptr, *d_rhs = nullptr;
+  double *d_g2 = nullptr, *d_Ep2 = nullptr;  // elastic gradient / patch energies at the first line-search trial
   unsigned char* d_mask = nullptr;
   NewtonScalars* d_ns = nullptr;
   NewtonScalars* h_ns = nullptr;    // pinned
@@ -117,6 +118,12 @@ struct Shell {
 
   Reduce red{};
   long long launches = 0;           // kernels launched by this shell (introspection)
+
+  // FP32 SpMV variant: TMA-pipelined persistent kernel when its row-group stages fit in shared
+  // memory (max_row = most blocks in one block row)
+  int max_row = 0;
+  int spmv_tma = 0, spmv_grid = 0, spmv_stage_floats = 0;
+  size_t spmv_smem = 0;
 };
 
 // ------------------------------------------------------------------------------------------
@@ -124,6 +131,8 @@ struct Shell {
 // ------------------------------------------------------------------------------------------
 // rest per-Gauss-point data, mass, gravity factors (once per shell)
 shell_status launch_rest_setup(Shell& s);
+// chooses the FP32 SpMV variant (opt.spmv) and prepares its launch (solver.cu)
+shell_status setup_spmv(Shell& s);
 // regulariser shift tau * dbar per DOF kind, as kernel argument
 struct Shift4 { double v[4]; };
 

@@ -115,7 +115,7 @@ static void destroy_shell(shell_s* s) {
                   s->d_x, s->d_r, s->d_z, s->d_p, s->d_Ap, s->d_p32, s->d_x32, s->d_r32, s->d_z32, s->d_Ap32, s->d_Dinv, s->d_phi64, s->d_phi32,
                   s->d_pcg, s->d_qn, s->d_y, s->d_g, s->d_gin, s->d_d, s->d_Md, s->d_Ep,
                   s->d_qwork, s->d_vwork, s->d_qfix, s->d_warm, s->d_mask, s->d_ns, s->d_err,
-                  s->d_energy_tmp, s->red.partials, s->red.ticket, s->d_rhs};
+                  s->d_energy_tmp, s->red.partials, s->red.ticket, s->d_rhs, s->d_g2, s->d_Ep2};
   for (void* p : ptrs) dfree(p);
   if (s->h_ns) cudaFreeHost(s->h_ns);
   if (s->h_pcg) cudaFreeHost(s->h_pcg);
@@ -134,6 +134,7 @@ static shell_status sync_and_check(Shell& s) {
   }
   if (bits & ERRBIT_DEGENERATE) return fail(SHELL_ERR_DEGENERATE, "degenerate surface normal at a Gauss point");
   if (bits & ERRBIT_NONFINITE) return fail(SHELL_ERR_NONFINITE, "non-finite energy or residual");
+  if (bits & ERRBIT_TIMEOUT) return fail(SHELL_ERR_TIMEOUT, "a bounded wait for a bulk copy expired");
   return SHELL_OK;
 }
 
@@ -162,7 +163,8 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
   if (options) opt = *options;
   if ((opt.precision != SHELL_PREC_FP64 && opt.precision != SHELL_PREC_MIXED) ||
       (opt.hessian != SHELL_HESS_EXACT && opt.hessian != SHELL_HESS_PSEUDO) ||
-      (opt.assembly != SHELL_ASM_ATOMIC && opt.assembly != SHELL_ASM_COLOR))
+      (opt.assembly != SHELL_ASM_ATOMIC && opt.assembly != SHELL_ASM_COLOR) ||
+      (opt.spmv != SHELL_SPMV_AUTO && opt.spmv != SHELL_SPMV_PLAIN && opt.spmv != SHELL_SPMV_TMA))
     return fail(SHELL_ERR_ARG, "invalid options");
   long long np_ll = (long long)g.nu * g.nv;
   if (np_ll > (1LL << 26)) return fail(SHELL_ERR_ARG, "grid too large");
@@ -185,6 +187,7 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
   HostTopo T;
   build_topology(g, s->n1, s->n2, T);
   s->n_blocks = (int)T.col.size();
+  for (int i = 0; i < s->n1 * s->n2; ++i) s->max_row = std::max(s->max_row, T.row_ptr[i + 1] - T.row_ptr[i]);
   s->h_color_patches = new int[10];
   std::memcpy(s->h_color_patches, T.color_off, sizeof(int) * 10);
 
@@ -225,6 +228,7 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
   A(s->d_qn, m); A(s->d_y, m); A(s->d_g, m); A(s->d_gin, m); A(s->d_d, m); A(s->d_Md, m);
   A(s->d_rhs, m); A(s->d_Ep, np); A(s->d_qwork, m); A(s->d_vwork, m); A(s->d_qfix, m);
   A(s->d_warm, m); A(s->d_mask, m); A(s->d_ns, 1); A(s->d_err, 1); A(s->d_energy_tmp, 1);
+  A(s->d_g2, m); A(s->d_Ep2, np);
   // partials: one per CTA of the largest reducing launch (8 patches, 4 FP64 block rows, 16 nodes or
   // 1024 vector CTAs per CTA) per reduced value
   s->red.stride = std::max(1024, std::max(np / 8, n / 4) + 64);
@@ -260,7 +264,8 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
     destroy_shell(s);
     return fail(SHELL_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
   }
-  st = launch_rest_setup(*s);
+  st = setup_spmv(*s);
+  if (st == SHELL_OK) st = launch_rest_setup(*s);
   if (st == SHELL_OK) st = sync_and_check(*s);
   if (st != SHELL_OK) {
     destroy_shell(s);
@@ -363,6 +368,7 @@ static shell_status run_pcg(Shell& s, const unsigned char* mask, const double td
   }
   *iters = s.h_pcg->iters;
   *neg = s.h_pcg->negcurv;
+  BHEM_TRY(sync_and_check(s));
   return launch_pcg_result(s);
 }
 }  // namespace bhem
@@ -422,6 +428,17 @@ static shell_status residual(Shell& s, const double* q, const shell_step_params&
   return SHELL_OK;
 }
 
+// Residual at q when the elastic gradient and patch energies at q are already in d_g / d_Ep
+// (from the accepted first line-search trial).
+static shell_status residual_reuse(Shell& s, const double* q, const shell_step_params& P,
+                                   const unsigned char* mask, double* gnorm) {
+  BHEM_TRY(launch_grad_finish(s, q, s.d_y, P.dt, P.gravity, mask, s.d_g, s.d_gin, &s.d_ns->gnorm2));
+  BHEM_CUDA(cudaMemcpyAsync(s.h_ns, s.d_ns, sizeof(NewtonScalars), cudaMemcpyDeviceToHost, s.stream));
+  BHEM_TRY(sync_and_check(s));
+  *gnorm = std::sqrt(s.h_ns->gnorm2);
+  return SHELL_OK;
+}
+
 static shell_status newton_core(Shell& s, const shell_step_params& P, const unsigned char* mask,
                                 const double* qfix, double* q, const double* v_in,
                                 const double* warm, double* v_out, shell_step_stats& st) {
@@ -435,9 +452,15 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
   if (warm) BHEM_TRY(launch_overwrite_fixed(s, q, warm, mask, qfix));
   shell_status status = SHELL_OK;
   const double inv_dt2 = 1.0 / (P.dt * P.dt);
+  // The first line-search trial (alpha = 1) also computes the elastic gradient and patch energies
+  // at q + d; when it is accepted, q + d is the next iterate (the same FP64 sum), so the next
+  // residual reuses them instead of evaluating the elements again.
+  bool reuse = false;
   for (int it = 0;; ++it) {
-    if (it > 0 || warm) BHEM_TRY(residual(s, q, P, mask, &gn));
+    if (reuse) BHEM_TRY(residual_reuse(s, q, P, mask, &gn));
+    else if (it > 0 || warm) BHEM_TRY(residual(s, q, P, mask, &gn));
     else gn = gref;
+    reuse = false;
     if (gn <= P.newton_rtol * gref) break;
     if (it >= P.newton_max) { status = SHELL_ERR_NOT_CONVERGED; break; }
     BHEM_TRY(assemble_hessian(s, q, inv_dt2));
@@ -473,11 +496,20 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
       double a_prev = 0.0, f_prev = 0.0;
       bool ok = false;
       for (int trial = 0; trial < 20; ++trial) {
-        BHEM_TRY(launch_energy_grad64(s, q, s.d_d, alpha, nullptr, s.d_Ep, nullptr, &s.d_ns->dV));
+        if (trial == 0) {
+          BHEM_CUDA(cudaMemsetAsync(s.d_g2, 0, sizeof(double) * m, s.stream));
+          BHEM_TRY(launch_energy_grad64(s, q, s.d_d, alpha, s.d_Ep2, s.d_Ep, s.d_g2, &s.d_ns->dV));
+        } else {
+          BHEM_TRY(launch_energy_grad64(s, q, s.d_d, alpha, nullptr, s.d_Ep, nullptr, &s.d_ns->dV));
+        }
         BHEM_CUDA(cudaMemcpyAsync(&s.h_ns->dV, &s.d_ns->dV, sizeof(double), cudaMemcpyDeviceToHost, s.stream));
         BHEM_CUDA(cudaStreamSynchronize(s.stream));
         const double phi = s.h_ns->dV + alpha * dgin + 0.5 * alpha * alpha * dMd;
-        if (std::isfinite(phi) && phi <= 1e-4 * alpha * gd) { ok = true; break; }
+        if (std::isfinite(phi) && phi <= 1e-4 * alpha * gd) {
+          ok = true;
+          reuse = trial == 0;
+          break;
+        }
         st.ls_backtracks++;
         double a_new;
         if (!std::isfinite(phi)) {
@@ -503,6 +535,10 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
       if (!ok) { status = SHELL_ERR_LINESEARCH; break; }
     }
     BHEM_TRY(launch_axpy_fixed(s, q, s.d_d, alpha));
+    if (reuse) {
+      std::swap(s.d_g, s.d_g2);
+      std::swap(s.d_Ep, s.d_Ep2);
+    }
     st.newton_iters++;
   }
   st.res_final = gn;

@@ -308,6 +308,14 @@ __global__ void k_to_float(int m, const double* __restrict__ a, float* __restric
 // ------------------------------------------------------------------------------------------
 struct Shift4f { float v[4]; };
 
+// acc += a . x as an explicit FMA chain (both FP32 SpMV kernels round identically)
+__device__ __forceinline__ float dot4_acc(float acc, const float4 a, const float4 x) {
+  acc = __fmaf_rn(a.x, x.x, acc);
+  acc = __fmaf_rn(a.y, x.y, acc);
+  acc = __fmaf_rn(a.z, x.z, acc);
+  return __fmaf_rn(a.w, x.w, acc);
+}
+
 __global__ void __launch_bounds__(kSpmvThreads)
 k_spmv32(int n, const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ val,
          const float* __restrict__ x, Shift4f td, const unsigned char* __restrict__ mask,
@@ -336,12 +344,12 @@ k_spmv32(int n, const int* __restrict__ rp, const int* __restrict__ col, const f
     for (int u = 0; u < U; ++u)
       if (k0 + u < k1) {
         const float4 xv = *reinterpret_cast<const float4*>(x + (size_t)j[u] * 12 + cc * 4);
-        acc += v[u].x * xv.x + v[u].y * xv.y + v[u].z * xv.z + v[u].w * xv.w;
+        acc = dot4_acc(acc, v[u], xv);
       }
     for (int k = k0 + U; k < k1; ++k) {
       const float4 a = __ldcs(reinterpret_cast<const float4*>(val + (size_t)k * 144 + r * 12 + cc * 4));
       const float4 xv = *reinterpret_cast<const float4*>(x + (size_t)col[k] * 12 + cc * 4);
-      acc += a.x * xv.x + a.y * xv.y + a.z * xv.z + a.w * xv.w;
+      acc = dot4_acc(acc, a, xv);
     }
   }
   sacc[t] = acc;
@@ -351,7 +359,7 @@ k_spmv32(int n, const int* __restrict__ rp, const int* __restrict__ col, const f
     const size_t gi = (size_t)i * 12 + r;
     const float xi = x[gi];
     float yi = (sacc[t] + sacc[t + 1]) + sacc[t + 2];
-    yi += td.v[r / 3] * xi;
+    yi = __fmaf_rn(td.v[r / 3], xi, yi);
     if (mask && mask[gi]) yi = 0.f;
     y[gi] = yi;
     part = f2_prod(xi, yi);
@@ -372,10 +380,163 @@ k_spmv32(int n, const int* __restrict__ rp, const int* __restrict__ col, const f
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// FP32 BSR SpMV, TMA-pipelined persistent form. A CTA owns a contiguous range of row groups
+// (8 block rows each); the values of one group are contiguous in val, so one bulk asynchronous
+// copy (cp.async.bulk, completion counted on an mbarrier) moves them into one stage of a
+// shared-memory ring. kTmaStages groups are in flight while the CTA computes from the oldest
+// stage; x is gathered through L1/L2. Same arithmetic and summation order per row as k_spmv32.
+// Every mbarrier wait is bounded: on expiry the kernel raises ERRBIT_TIMEOUT, waits (bounded)
+// for the copies it issued, and leaves.
+// ------------------------------------------------------------------------------------------
+constexpr int kTmaRows = 8, kTmaThreads = kTmaRows * 36, kTmaStages = 4;
+constexpr unsigned kTmaChunk = 32768u;   // bytes per bulk copy instruction
+constexpr int kWaitPolls = 1 << 20;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (int i = 0; i < kWaitPolls; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kTmaThreads, 1)
+k_spmv32_tma(int n, const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ val,
+             const float* __restrict__ x, Shift4f td, const unsigned char* __restrict__ mask,
+             float* __restrict__ y, PcgState* st, Reduce red, int stage_floats, int* err) {
+  extern __shared__ __align__(128) float sval[];
+  __shared__ __align__(8) unsigned long long bar[kTmaStages];
+  __shared__ float sacc[kTmaThreads];
+  if (st && st->done) return;
+  const int t = threadIdx.x;
+  const int ngroups = (n + kTmaRows - 1) / kTmaRows;
+  const int per = (ngroups + gridDim.x - 1) / gridDim.x;
+  const int g0 = min(ngroups, blockIdx.x * per), g1 = min(ngroups, g0 + per);
+  if (t == 0) {
+    for (int q = 0; q < kTmaStages; ++q)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&bar[q])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  }
+  __syncthreads();
+  // thread 0 issues the copy of group g into stage q
+  auto issue = [&](int g, int q) {
+    const int i0 = g * kTmaRows, i1 = min(n, i0 + kTmaRows);
+    const long long k0 = rp[i0], k1 = rp[i1];
+    const unsigned bytes = (unsigned)((k1 - k0) * 576);
+    const unsigned b = smem_addr(&bar[q]);
+    unsigned long long state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;\n"
+                 : "=l"(state)
+                 : "r"(b), "r"(bytes)
+                 : "memory");
+    const char* src = reinterpret_cast<const char*>(val + k0 * 144);
+    const unsigned dst = smem_addr(sval + (size_t)q * stage_floats);
+    for (unsigned off = 0; off < bytes; off += kTmaChunk) {
+      const unsigned sz = min(kTmaChunk, bytes - off);
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+              dst + off),
+          "l"(src + off), "r"(sz), "r"(b)
+          : "memory");
+    }
+  };
+  if (t == 0)
+    for (int q = 0; q < kTmaStages && g0 + q < g1; ++q) issue(g0 + q, q);
+
+  const int br = t / 36, w = t % 36, r = w / 3, cc = w % 3;
+  F2 part{0.f, 0.f};
+  int it = 0;
+  bool timed_out = false;
+  for (int g = g0; g < g1; ++g, ++it) {
+    const int q = it % kTmaStages;
+    const bool ok = mbar_wait(smem_addr(&bar[q]), (unsigned)((it / kTmaStages) & 1));
+    if (__syncthreads_or(!ok)) {
+      timed_out = true;
+      break;
+    }
+    const int i0 = g * kTmaRows, i = i0 + br;
+    float acc = 0.f;
+    if (i < n) {
+      const int kbase = rp[i0], k0 = rp[i], k1 = rp[i + 1];
+      const float* sv = sval + (size_t)q * stage_floats + (size_t)(k0 - kbase) * 144 + r * 12 + cc * 4;
+      constexpr int U = 9;
+      int j[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (k0 + u < k1) j[u] = col[k0 + u];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (k0 + u < k1) {
+          const float4 a = *reinterpret_cast<const float4*>(sv + u * 144);
+          const float4 xv = *reinterpret_cast<const float4*>(x + (size_t)j[u] * 12 + cc * 4);
+          acc = dot4_acc(acc, a, xv);
+        }
+      for (int k = k0 + U; k < k1; ++k) {
+        const float4 a = *reinterpret_cast<const float4*>(sv + (k - k0) * 144);
+        const float4 xv = *reinterpret_cast<const float4*>(x + (size_t)col[k] * 12 + cc * 4);
+        acc = dot4_acc(acc, a, xv);
+      }
+    }
+    sacc[t] = acc;
+    __syncthreads();   // stage q fully read; sacc complete
+    if (t == 0 && g + kTmaStages < g1) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      issue(g + kTmaStages, q);
+    }
+    if (i < n && cc == 0) {
+      const size_t gi = (size_t)i * 12 + r;
+      const float xi = x[gi];
+      float yi = (sacc[t] + sacc[t + 1]) + sacc[t + 2];
+      yi = __fmaf_rn(td.v[r / 3], xi, yi);
+      if (mask && mask[gi]) yi = 0.f;
+      y[gi] = yi;
+      part = f2_add(part, f2_prod(xi, yi));
+    }
+    __syncthreads();   // sacc is rewritten by the next group
+  }
+  if (timed_out) {
+    // raise the error (the host voids the call's results) and drain the copies this CTA issued
+    // (local groups it .. it + stages - 1), bounded; the grid reduction below still completes
+    if (t == 0) {
+      atomicOr(err, ERRBIT_TIMEOUT);
+      for (int k = it; k < it + kTmaStages && g0 + k < g1; ++k)
+        mbar_wait(smem_addr(&bar[k % kTmaStages]), (unsigned)((k / kTmaStages) & 1));
+    }
+    __syncthreads();
+  }
+  if (st) {
+    F2 v1[1] = {part};
+    double out[1];
+    if (grid_reduce_f2<1>(v1, red, out, gridDim.x) && threadIdx.x == 0) {
+      st->pq = out[0];
+      if (!(out[0] > 0.0)) {
+        st->negcurv = 1;
+        st->done = 1;
+        st->alpha = 0.0;
+      } else {
+        st->alpha = st->rz / out[0];
+      }
+    }
+  }
+}
+
+// row a of a 12x12 block times sr, as the explicit FMA chain of k_pcg32_update
 __device__ __forceinline__ float apply_block32(const float* __restrict__ D, const float* sr, int a) {
   float s = 0.f;
 #pragma unroll
-  for (int c = 0; c < 12; ++c) s += D[a * 12 + c] * sr[c];
+  for (int c = 0; c < 12; ++c) s = __fmaf_rn(D[a * 12 + c], sr[c], s);
   return s;
 }
 
@@ -430,7 +591,14 @@ k_pcg32_update(int n, float* __restrict__ x, float* __restrict__ r, float* __res
   const size_t gi = (size_t)i * 12 + a;
   const float alpha = (float)st->alpha;
   float ri = 0.f, zi = 0.f;
+  float4 d0, d1, d2;
   if (i < n) {
+    // this thread's row of the node's 12x12 inverse: 48 contiguous bytes, streamed, issued with
+    // the vector loads so that all of them are in flight together
+    const float4* drow = reinterpret_cast<const float4*>(Dinv + (size_t)i * 144 + a * 12);
+    d0 = __ldcs(drow);
+    d1 = __ldcs(drow + 1);
+    d2 = __ldcs(drow + 2);
     x[gi] = fmaf(alpha, p[gi], x[gi]);
     ri = fmaf(-alpha, Ap[gi], r[gi]);
     r[gi] = ri;
@@ -438,7 +606,21 @@ k_pcg32_update(int n, float* __restrict__ x, float* __restrict__ r, float* __res
   }
   __syncthreads();
   if (i < n) {
-    zi = (mask && mask[gi]) ? 0.f : apply_block32(Dinv + (size_t)i * 144, sr[ln], a);
+    if (!(mask && mask[gi])) {
+      const float* q = sr[ln];
+      zi = __fmaf_rn(d0.x, q[0], 0.f);
+      zi = __fmaf_rn(d0.y, q[1], zi);
+      zi = __fmaf_rn(d0.z, q[2], zi);
+      zi = __fmaf_rn(d0.w, q[3], zi);
+      zi = __fmaf_rn(d1.x, q[4], zi);
+      zi = __fmaf_rn(d1.y, q[5], zi);
+      zi = __fmaf_rn(d1.z, q[6], zi);
+      zi = __fmaf_rn(d1.w, q[7], zi);
+      zi = __fmaf_rn(d2.x, q[8], zi);
+      zi = __fmaf_rn(d2.y, q[9], zi);
+      zi = __fmaf_rn(d2.z, q[10], zi);
+      zi = __fmaf_rn(d2.w, q[11], zi);
+    }
     z[gi] = zi;
   }
   F2 v[2] = {f2_prod(ri, zi), f2_prod(ri, ri)};
@@ -676,6 +858,9 @@ static shell_status launch_spmv_impl(Shell& s, const void* x, const double* xd,
   return SHELL_OK;
 }
 
+static shell_status launch_spmv32(Shell& s, const float* x, Shift4f sh, const unsigned char* mask, float* y,
+                                  PcgState* st);
+
 shell_status launch_spmv(Shell& s, const void* x, int x_fp32, void* y) {
   const double zero[4] = {0.0, 0.0, 0.0, 0.0};
   if (s.val_fp64) return launch_spmv_impl(s, x, nullptr, nullptr, zero, (double*)y, nullptr);
@@ -689,11 +874,7 @@ shell_status launch_spmv(Shell& s, const void* x, int x_fp32, void* y) {
     xs = s.d_z32;
     ys = s.d_Ap32;
   }
-  k_spmv32<<<grid_for(s.n_nodes, kSpmvThreads / 36), kSpmvThreads, 0, s.stream>>>(
-      s.n_nodes, s.d_row_ptr, s.d_col, (const float*)s.d_val, xs, Shift4f{{0.f, 0.f, 0.f, 0.f}},
-      nullptr, ys, nullptr, s.red);
-  BHEM_CUDA(cudaGetLastError());
-  ++s.launches;
+  BHEM_TRY(launch_spmv32(s, xs, Shift4f{{0.f, 0.f, 0.f, 0.f}}, nullptr, ys, nullptr));
   if (!x_fp32) {
     k_to_double<<<vec_blocks(s.n_dof), 256, 0, s.stream>>>(s.n_dof, s.d_Ap32, (double*)y);
     BHEM_CUDA(cudaGetLastError());
@@ -702,16 +883,55 @@ shell_status launch_spmv(Shell& s, const void* x, int x_fp32, void* y) {
   return SHELL_OK;
 }
 
+shell_status setup_spmv(Shell& s) {
+  s.spmv_tma = 0;
+  if (s.val_fp64) return SHELL_OK;
+  const size_t stage_floats = (size_t)kTmaRows * std::max(1, s.max_row) * 144;
+  const size_t smem = stage_floats * sizeof(float) * kTmaStages;
+  int dev = 0, max_optin = 0, sms = 0;
+  BHEM_CUDA(cudaGetDevice(&dev));
+  BHEM_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  BHEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const size_t static_smem = 8 * kTmaStages + sizeof(float) * kTmaThreads + 512;
+  const bool fits = smem + static_smem <= (size_t)max_optin;
+  if (s.opt.spmv == SHELL_SPMV_TMA && !fits)
+    return fail(SHELL_ERR_ARG, "SHELL_SPMV_TMA: 8 block rows of the longest row do not fit in shared memory");
+  // AUTO takes the plain kernel: on GB300 it reaches 0.87 of the measured HBM copy bandwidth at
+  // 256x256 (4 CTAs per SM keep every block load of 36 rows in flight), the bulk-copy ring 0.42
+  // (one CTA per SM computes too few groups at a time to cover the latency of the x gathers)
+  if (s.opt.spmv != SHELL_SPMV_TMA || !fits) return SHELL_OK;
+  BHEM_CUDA(cudaFuncSetAttribute(k_spmv32_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int ngroups = (s.n_nodes + kTmaRows - 1) / kTmaRows;
+  s.spmv_tma = 1;
+  s.spmv_stage_floats = (int)stage_floats;
+  s.spmv_smem = smem;
+  s.spmv_grid = std::max(1, std::min(ngroups, sms));
+  if (s.spmv_grid > s.red.stride) return fail(SHELL_ERR_ARG, "reduction workspace too small");
+  return SHELL_OK;
+}
+
+static shell_status launch_spmv32(Shell& s, const float* x, Shift4f sh, const unsigned char* mask, float* y,
+                                  PcgState* st) {
+  const int n = s.n_nodes;
+  if (s.spmv_tma) {
+    k_spmv32_tma<<<s.spmv_grid, kTmaThreads, s.spmv_smem, s.stream>>>(
+        n, s.d_row_ptr, s.d_col, (const float*)s.d_val, x, sh, mask, y, st, s.red, s.spmv_stage_floats, s.d_err);
+  } else {
+    const int blocks = grid_for(n, kSpmvThreads / 36);
+    if (st && blocks > s.red.stride) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
+    k_spmv32<<<blocks, kSpmvThreads, 0, s.stream>>>(n, s.d_row_ptr, s.d_col, (const float*)s.d_val, x, sh, mask,
+                                                    y, st, s.red);
+  }
+  BHEM_CUDA(cudaGetLastError());
+  ++s.launches;
+  return SHELL_OK;
+}
+
 shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, const double td[4]) {
   const int n = s.n_nodes, m = s.n_dof;
   if (!s.val_fp64) {
-    const int blocks = grid_for(n, kSpmvThreads / 36);
-    if (blocks > s.red.stride) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
     Shift4f sh{{(float)td[0], (float)td[1], (float)td[2], (float)td[3]}};
-    k_spmv32<<<blocks, kSpmvThreads, 0, s.stream>>>(n, s.d_row_ptr, s.d_col, (const float*)s.d_val,
-                                                    s.d_p32, sh, mask, s.d_Ap32, s.d_pcg, s.red);
-    BHEM_CUDA(cudaGetLastError());
-    ++s.launches;
+    BHEM_TRY(launch_spmv32(s, s.d_p32, sh, mask, s.d_Ap32, s.d_pcg));
     k_pcg32_update<<<grid_for(n, 16), kNodeThreads, 0, s.stream>>>(
         n, s.d_x32, s.d_r32, s.d_z32, s.d_p32, s.d_Ap32, (const float*)s.d_Dinv, mask, s.d_pcg, s.red);
     BHEM_CUDA(cudaGetLastError());

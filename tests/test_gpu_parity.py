@@ -113,6 +113,48 @@ def test_spmv_matches_dense_product(prec):
         assert rel(y32, A @ x32.astype(np.float64)) <= 1e-5
 
 
+SPMV_GRIDS = {
+    "annulus12x3": lambda: CASES["annulus12x3"](),
+    "sheet1x1": lambda: CASES["sheet1x1"](),
+    "sheet3x2": lambda: CASES["sheet3x2-rect-thick"](),
+    "sheet61x37": lambda: (lambda g, r: (g, r, S.noisy(r, 1e-2, 9), THIN))(*S.flat_sheet(61, 37)),
+    "sheet256-sinusoid": lambda: (*S.sheet_sinusoid(256, 3), THIN),
+}
+
+
+@pytest.mark.parametrize("case", list(SPMV_GRIDS))
+def test_spmv_tma_identical_to_plain(case):
+    """The TMA-pipelined FP32 SpMV computes every row with the arithmetic and order of the plain
+    kernel: outputs are bit-identical (empty tail groups, one-group grids, full size). The
+    matrices come from the colour-ordered assembly, which is deterministic."""
+    g, rest, q, mat = SPMV_GRIDS[case]()
+    ys = []
+    x32 = dev(np.random.default_rng(1).normal(size=g.n_dof), torch.float32)
+    for variant in ("plain", "tma"):
+        sh = make_shell(g, mat, rest, precision="mixed", spmv=variant, assembly="color")
+        sh.energy_grad_hess(dev(q.reshape(-1)), mass_scale=1e6, want_energy=False, want_grad=False)
+        ys.append(host(sh.spmv(x32)))
+        sh.close()
+    assert np.array_equal(ys[0], ys[1])
+
+
+def test_pcg_mixed_tma_matches_plain():
+    """PCG with the TMA SpMV: same iteration count, and the solution agrees to the solver
+    tolerance (only the order of the p.Ap partial sums differs)."""
+    g, rest, q, mat = CASES["sheet10x10-noisy"]()
+    mask = dev(S.pinned_mask(g, [0, g.n_nodes - 1]), torch.uint8)
+    res = []
+    for variant in ("plain", "tma"):
+        sh = make_shell(g, mat, rest, precision="mixed", spmv=variant)
+        _, G = sh.energy_grad_hess(dev(q.reshape(-1)), mass_scale=1e6)
+        x, it, neg = sh.pcg_solve(-G, mask=mask, rtol=1e-6, max_iter=1000)
+        res.append((host(x), it, neg))
+        sh.close()
+    assert res[0][2] == res[1][2] == 0
+    assert abs(res[0][1] - res[1][1]) <= 1
+    assert rel(res[1][0], res[0][0]) <= 1e-5
+
+
 def test_pcg_parity_fp64():
     g, rest, q, mat = CASES["sheet10x10-noisy"]()
     dt = 1e-3
