@@ -242,12 +242,13 @@ k_element(ElemBatchArgs B) {
 // mode 1: acc[3] += E_p(q + alpha_s d) - Ep[p] (shells with searching != 0)
 __global__ void __launch_bounds__(128)
 k_eg64(int n_items, const int4* __restrict__ items, int P, const ShellPar* __restrict__ par,
-       ShellState* st, const double* __restrict__ t64, const int4* __restrict__ pnodes,
+       ShellState* st, const double* __restrict__ dxi, const int4* __restrict__ pnodes,
        const double* __restrict__ q, const double* __restrict__ dir,
        const double* __restrict__ restgp, double* __restrict__ Ep, double* __restrict__ grad,
        int mode, int* err) {
-  __shared__ double sphi[kPhiTable];
+  __shared__ double w1[kHerm1D], w2[kHerm1D];
   __shared__ double sq[kEgPatches][48];
+  __shared__ double sT[kEgPatches][144];
   __shared__ double sG[kEgPatches][16][15];
   __shared__ double sbuf[32];
   const int hw = threadIdx.x >> 4, g = threadIdx.x & 15;
@@ -257,7 +258,8 @@ k_eg64(int n_items, const int4* __restrict__ items, int P, const ShellPar* __res
     const bool run = mode == 0 ? st[s].active != 0 : st[s].searching != 0;
     if (!run) continue;   // uniform over the CTA
     __syncthreads();
-    load_shape_table<double>(sphi, t64 + (size_t)s * kPhiTable);
+    build_hermite_1d(w1, dxi[2 * s], threadIdx.x, blockDim.x);
+    build_hermite_1d(w2, dxi[2 * s + 1], threadIdx.x, blockDim.x);
     __syncthreads();
     const int p = item.y + hw;
     const bool active = p < item.z;
@@ -267,7 +269,7 @@ k_eg64(int n_items, const int4* __restrict__ items, int P, const ShellPar* __res
       nd[0] = pn.x; nd[1] = pn.y; nd[2] = pn.z; nd[3] = pn.w;
     }
     const double step = mode == 1 ? st[s].ls_alpha : 0.0;
-    const double ep = eg64_patch(sphi, sq[hw], sG[hw], p, active, g, nd, q, mode == 1 ? dir : nullptr,
+    const double ep = eg64_patch(w1, w2, sq[hw], sT[hw], sG[hw], p, active, g, nd, q, mode == 1 ? dir : nullptr,
                                  step, restgp, (size_t)P * 16, par[s].h, mode == 0 ? grad : nullptr, err);
     double contrib = 0.0;
     if (active && g == 0) {
@@ -1096,7 +1098,7 @@ shell_status residual(shell_batch_s& b, const double* q, const shell_step_params
   int nsm = 0;
   BHEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b.device));
   k_eg64<<<std::min(b.n_eg_items, nsm * 16), 128, 0, b.stream>>>(b.n_eg_items, b.eg_items, b.P, b.par, b.st,
-      b.t64, b.pnodes, q, nullptr, b.restgp, b.Ep, b.g, 0, b.err);
+      b.dxi, b.pnodes, q, nullptr, b.restgp, b.Ep, b.g, 0, b.err);
   BHEM_CUDA(cudaGetLastError());
   BL(b);
   k_grad_finish<<<blocks_for(b.N, 16), kNodeThreads, 0, b.stream>>>(b.N, b.nshell, b.st, b.row_ptr, b.col,
@@ -1209,7 +1211,7 @@ shell_status line_search(shell_batch_s& b, const shell_step_params& P, const dou
   BHEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b.device));
   for (int trial = 0; trial < 20 && b.h_cnt->n_searching > 0; ++trial) {
     k_eg64<<<std::min(b.n_eg_items, nsm * 16), 128, 0, b.stream>>>(b.n_eg_items, b.eg_items, b.P, b.par, b.st,
-        b.t64, b.pnodes, q, b.d, b.restgp, b.Ep, nullptr, 1, b.err);
+        b.dxi, b.pnodes, q, b.d, b.restgp, b.Ep, nullptr, 1, b.err);
     BHEM_TRY(zero_counters(b));
     k_ctrl_ls_step<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, b.cnt);
     b.launches += 2;

@@ -133,13 +133,15 @@ shell_status launch_rest_setup(Shell& s) {
 __global__ void __launch_bounds__(128)
 k_energy_grad64(int np, const int4* __restrict__ pnodes, const double* __restrict__ q,
                 const double* __restrict__ dir, double step, const double* __restrict__ restgp,
-                const double* __restrict__ table, double h, double* __restrict__ energy_p,
+                double dxi1, double dxi2, double h, double* __restrict__ energy_p,
                 const double* __restrict__ energy_ref, double* __restrict__ grad, Reduce red,
                 double* scal_out, int* err) {
-  __shared__ double sphi[kPhiTable];
+  __shared__ double w1[kHerm1D], w2[kHerm1D];
   __shared__ double sq[kEgPatches][48];
+  __shared__ double sT[kEgPatches][144];
   __shared__ double sG[kEgPatches][16][15];
-  load_shape_table<double>(sphi, table);
+  build_hermite_1d(w1, dxi1, threadIdx.x, blockDim.x);
+  build_hermite_1d(w2, dxi2, threadIdx.x, blockDim.x);
   __syncthreads();
   const int hw = threadIdx.x >> 4, g = threadIdx.x & 15;
   const int p = blockIdx.x * kEgPatches + hw;
@@ -149,7 +151,7 @@ k_energy_grad64(int np, const int4* __restrict__ pnodes, const double* __restric
     int4 pn = pnodes[p];
     nd[0] = pn.x; nd[1] = pn.y; nd[2] = pn.z; nd[3] = pn.w;
   }
-  const double ep = eg64_patch(sphi, sq[hw], sG[hw], p, active, g, nd, q, dir, step, restgp,
+  const double ep = eg64_patch(w1, w2, sq[hw], sT[hw], sG[hw], p, active, g, nd, q, dir, step, restgp,
                                (size_t)np * 16, h, grad, err);
   double contrib = 0.0;
   if (active && g == 0) {
@@ -170,7 +172,7 @@ shell_status launch_energy_grad64(Shell& s, const double* q, const double* dir, 
   int blocks = (s.n_patches + kEgPatches - 1) / kEgPatches;
   if (blocks > s.red.stride) return fail(SHELL_ERR_ARG, "too many patches for one reduction");
   k_energy_grad64<<<blocks, 128, 0, s.stream>>>(s.n_patches, s.d_patch_nodes, q, dir, step,
-                                                s.d_restgp, s.d_phi64,
+                                                s.d_restgp, s.grid.dxi1, s.grid.dxi2,
                                                 s.mat.thickness, energy_p, energy_ref, grad, s.red,
                                                 scal_out, s.d_err);
   BHEM_CUDA(cudaGetLastError());

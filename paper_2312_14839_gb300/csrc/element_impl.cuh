@@ -94,34 +94,91 @@ __device__ __forceinline__ void interp5(const R* sphi, const S* qv, int g, V3<R>
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// 1D factors of the bicubic Hermite shape functions (Eq. hermite with the Delta-xi scaling of
+// App. A.1): a shape function of corner (p, q) and kind (r, s) is w1[a](theta^1) w2[b](theta^2)
+// with a = 2p + r, b = 2q + s, and its (d1, d2) parameter derivative is the product of the d1-th
+// and d2-th derivatives of the factors. w[(d * 4 + g) * 4 + a] holds the d-th xi-derivative of
+// factor a at Gauss abscissa g (d = 0, 1, 2): herm(p, r, theta_g, d) dxi^r / dxi^d.
+// ------------------------------------------------------------------------------------------
+constexpr int kHerm1D = 48;
+
+__device__ __forceinline__ void build_hermite_1d(double* w, double dxi, int tid, int nthreads) {
+  double th[4], wt[4];
+  gauss_unit(th, wt);
+  for (int e = tid; e < kHerm1D; e += nthreads) {
+    const int d = e / 16, gi = (e / 4) % 4, a = e % 4;
+    const int p = a >> 1, r = a & 1;
+    double v = herm(p, r, th[gi], d);
+    if (r) v *= dxi;
+    for (int i = 0; i < d; ++i) v /= dxi;
+    w[e] = v;
+  }
+}
+
 constexpr int kRestFields = 13;
 
 // ------------------------------------------------------------------------------------------
-// Light FP64 energy (and gradient) of one patch, half a warp per patch, lane = Gauss point g.
-// sq: the half warp's 48 DOFs (shared), sG: its [16][15] gradient vectors (shared). restgp is
-// SoA over S = (total patches) * 16 entries. Returns the patch energy in every lane.
+// Light FP64 energy (and gradient) of one patch, half a warp per patch, lane = Gauss point
+// g = 4 g2 + g1. The interpolation to the 4x4 Gauss points and the gradient's transpose are
+// sum-factorised over the tensor-product basis: the 48 DOFs are first contracted along theta^1
+// (T[d1][g1][b][c], 144 values), then along theta^2 per Gauss point; the gradient runs the two
+// contractions in reverse. sq: the half warp's 48 DOFs, sT: its 144-value intermediate, sG: its
+// [16][15] gradient vectors (all shared). restgp is SoA over S = (total patches) * 16 entries.
+// Returns the patch energy in every lane.
 // ------------------------------------------------------------------------------------------
 constexpr int kEgPatches = 8;   // patches per CTA (128 threads)
 
-__device__ __forceinline__ double eg64_patch(const double* sphi, double* sq, double (*sG)[15],
-                                             int p, bool active, int g, const int nd[4],
+// DOF index (corner * 12 + kind * 3 + c) of the factor pair (a, b), component c
+__device__ __forceinline__ int dof_of(int a, int b, int c) {
+  return ((a >> 1) + 2 * (b >> 1)) * 12 + ((a & 1) + 2 * (b & 1)) * 3 + c;
+}
+
+__device__ __forceinline__ double eg64_patch(const double* w1, const double* w2, double* sq, double* sT,
+                                             double (*sG)[15], int p, bool active, int g, const int nd[4],
                                              const double* __restrict__ q,
                                              const double* __restrict__ dir, double step,
                                              const double* __restrict__ restgp, size_t S, double h,
                                              double* __restrict__ grad, int* err) {
+  const int g1 = g & 3, g2 = g >> 2;
   if (active) {
     for (int l = g; l < 48; l += 16) {
       size_t a = (size_t)nd[l / 12] * 12 + (l % 12);
       double v = q[a];
-      if (dir) v += step * dir[a];
+      if (dir) v = __fma_rn(step, dir[a], v);
       sq[l] = v;
+    }
+  }
+  __syncwarp();
+  // theta^1 contraction: T[((d1 * 4 + gi) * 4 + b) * 3 + c] = sum_a w1[d1][gi][a] Q[a][b][c]
+  if (active) {
+    for (int e = g; e < 144; e += 16) {
+      const int c = e % 3, b = (e / 3) % 4, dg = e / 12;   // dg = d1 * 4 + gi
+      double t = 0.0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) t = __fma_rn(w1[dg * 4 + a], sq[dof_of(a, b, c)], t);
+      sT[e] = t;
     }
   }
   __syncwarp();
   double e = 0.0;
   if (active) {
+    // theta^2 contraction at this Gauss point: (d1, d2) = (1,0), (0,1), (2,0), (0,2), (1,1)
+    constexpr int kd1[5] = {1, 0, 2, 0, 1}, kd2[5] = {0, 1, 0, 2, 1};
     V3<double> v[5];
-    interp5<double, double>(sphi, sq, g, v);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      double x = 0.0, y = 0.0, z = 0.0;
+      const double* T = sT + (kd1[k] * 4 + g1) * 12;
+      const double* W = w2 + (kd2[k] * 4 + g2) * 4;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        x = __fma_rn(W[b], T[b * 3 + 0], x);
+        y = __fma_rn(W[b], T[b * 3 + 1], y);
+        z = __fma_rn(W[b], T[b * 3 + 2], z);
+      }
+      v[k] = mk<double>(x, y, z);
+    }
     const V3<double> a1 = v[0], a2 = v[1];
     const size_t o = (size_t)p * 16 + g;
     const double ab11 = restgp[0 * S + o], ab22 = restgp[1 * S + o], ab12 = restgp[2 * S + o];
@@ -169,13 +226,31 @@ __device__ __forceinline__ double eg64_patch(const double* sphi, double* sq, dou
   for (int o = 8; o > 0; o >>= 1) ep += __shfl_xor_sync(0xffffffffu, ep, o);
   __syncwarp();
   if (active && grad) {
-    for (int l = g; l < 48; l += 16) {
-      int I = l / 3, c = l % 3;
-      double s = 0.0;
-      for (int gg = 0; gg < 16; ++gg)
+    // transpose of the theta^2 contraction: U[d1][gi][b][c] = sum_g2 sum_{k: d1(k) = d1}
+    // w2[d2(k)][g2][b] G_k(gi, g2)[c]; kinds with d1 = 0: (0,1), (0,2); d1 = 1: (1,0), (1,1); d1 = 2: (2,0)
+    for (int e2 = g; e2 < 144; e2 += 16) {
+      const int c = e2 % 3, b = (e2 / 3) % 4, gi = (e2 / 12) % 4, d1 = e2 / 48;
+      const int ka = d1 == 0 ? 1 : d1 == 1 ? 0 : 2, da = d1 == 0 ? 1 : 0;
+      const int kb = d1 == 0 ? 3 : 4, db = d1 == 0 ? 2 : 1;
+      double u = 0.0;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) s += sphi[I * kPhiStride + (k + 1) * 16 + gg] * sG[gg][k * 3 + c];
-      atomicAdd(&grad[(size_t)nd[I >> 2] * 12 + (I & 3) * 3 + c], s);
+      for (int gj = 0; gj < 4; ++gj) {
+        u = __fma_rn(w2[(da * 4 + gj) * 4 + b], sG[gj * 4 + gi][ka * 3 + c], u);
+        if (d1 < 2) u = __fma_rn(w2[(db * 4 + gj) * 4 + b], sG[gj * 4 + gi][kb * 3 + c], u);
+      }
+      sT[e2] = u;
+    }
+  }
+  __syncwarp();
+  if (active && grad) {
+    // transpose of the theta^1 contraction: dE/dQ[a][b][c] = sum_{d1, gi} w1[d1][gi][a] U[d1][gi][b][c]
+    for (int l = g; l < 48; l += 16) {
+      const int corner = l / 12, kind = (l / 3) % 4, c = l % 3;
+      const int a = 2 * (corner & 1) + (kind & 1), b = 2 * (corner >> 1) + (kind >> 1);
+      double s = 0.0;
+#pragma unroll
+      for (int dg = 0; dg < 12; ++dg) s = __fma_rn(w1[dg * 4 + a], sT[(dg * 4 + b) * 3 + c], s);
+      atomicAdd(&grad[(size_t)nd[corner] * 12 + kind * 3 + c], s);
     }
   }
   __syncwarp();

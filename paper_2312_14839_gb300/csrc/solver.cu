@@ -719,7 +719,7 @@ __global__ void k_dots3(int m, const double* __restrict__ a0, const double* __re
 }
 
 __global__ void k_axpy(int m, double* __restrict__ q, const double* __restrict__ d, double alpha) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) q[k] += alpha * d[k];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) q[k] = __fma_rn(alpha, d[k], q[k]);
 }
 
 __global__ void k_overwrite_fixed(int m, double* __restrict__ dst, const double* __restrict__ src,
