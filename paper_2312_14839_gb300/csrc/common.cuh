@@ -51,6 +51,8 @@ struct PcgState {
   double rz, pq, alpha, beta, rr, bb;
   double rtol2;        // rtol^2 (0 disables the residual test)
   int iters, done, negcurv, fixed;
+  int limit;           // iteration cap (mixed precision: enforced on the device)
+  float td[4];         // regulariser shift tau * D_k per DOF kind (mixed precision)
 };
 
 // Scalars of one Newton step.
@@ -124,6 +126,22 @@ struct Shell {
   int max_row = 0;
   int spmv_tma = 0, spmv_grid = 0, spmv_stage_floats = 0;
   size_t spmv_smem = 0;
+
+  // CUDA graphs of mixed-precision PCG iteration chunks, keyed by (mask, iterations)
+  struct PcgGraph { const unsigned char* mask; int iters; cudaGraphExec_t exec; };
+  static constexpr int kGraphSlots = 12;
+  PcgGraph pcg_graphs[kGraphSlots] = {};
+  int pcg_graph_next = 0;
+  cudaStream_t cap_stream = nullptr;
+
+  // optional phase trace of shell_newton_step (environment BHEM_TRACE_PHASES=1): CUDA events and
+  // host times at phase boundaries, printed to stderr at the end of each step
+  int trace = 0;
+  int trace_n = 0;
+  static constexpr int kTraceMax = 256;
+  cudaEvent_t trace_ev[kTraceMax] = {};
+  const char* trace_name[kTraceMax] = {};
+  double trace_host[kTraceMax] = {};
 };
 
 // ------------------------------------------------------------------------------------------
@@ -163,9 +181,13 @@ shell_status launch_mass_mult(Shell& s, const double* x, double* y);
 shell_status launch_dots3(Shell& s, int n, const double* a0, const double* b0, const double* a1,
                           const double* b1, const double* a2, const double* b2, double* out3);
 shell_status launch_precond_setup(Shell& s, const unsigned char* mask, const double td[4]);
+// PCG start; limit caps the iterations (the mixed-precision kernels stop there on the device)
 shell_status launch_pcg_init(Shell& s, const unsigned char* mask, const double* rhs,
-                             double rtol, int fixed);
+                             double rtol, int fixed, int limit, const double td[4]);
 shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, const double td[4]);
+// `iters` mixed-precision PCG iterations replayed from a cached CUDA graph (captured on first use
+// for this mask and count); the shift comes from the PCG state
+shell_status launch_pcg_iterations_graph(Shell& s, const unsigned char* mask, int iters);
 shell_status launch_spmv(Shell& s, const void* x, int x_fp32, void* y);
 shell_status launch_pcg_result(Shell& s);
 shell_status launch_diag_check(Shell& s, const unsigned char* mask, double* out12);
@@ -239,9 +261,20 @@ __device__ __forceinline__ bool grid_reduce_f2(const F2 (&v)[NV], Reduce red, do
   if (!last2) return false;
   __threadfence();
   for (int i = 0; i < NV; ++i) {
+    // partials b = tid, tid + bd, ... summed in that order; 4 L2 loads in flight at a time
     F2 s{0.f, 0.f};
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-      const float2 y = __ldcg(part + (size_t)i * red.stride + b);   // L2: other CTAs' writes
+    const float2* pi = part + (size_t)i * red.stride;
+    const int bd = blockDim.x;
+    int b = threadIdx.x;
+    for (; b + 3 * bd < nblocks; b += 4 * bd) {
+      float2 y[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) y[u] = __ldcg(pi + b + u * bd);   // L2: other CTAs' writes
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s = f2_add(s, F2{y[u].x, y[u].y});
+    }
+    for (; b < nblocks; b += bd) {
+      const float2 y = __ldcg(pi + b);
       s = f2_add(s, F2{y.x, y.y});
     }
     const F2 t = f2_block_sum(s, sred2, i);
@@ -293,8 +326,19 @@ __device__ __forceinline__ bool grid_reduce(const double (&v)[NV], Reduce red, d
   for (int i = 0; i < NV; ++i) {
     const bool mn = (minmask >> i) & 1u;
     double s = mn ? INFINITY : 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-      const double y = ((volatile double*)red.partials)[(size_t)i * red.stride + b];
+    // partials b = tid, tid + bd, ... combined in that order; 8 L2 loads in flight at a time
+    const double* pi = red.partials + (size_t)i * red.stride;
+    const int bd = blockDim.x;
+    int b = threadIdx.x;
+    for (; b + 7 * bd < nblocks; b += 8 * bd) {
+      double y[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) y[u] = __ldcg(pi + b + u * bd);   // L2: other CTAs' writes
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s = mn ? fmin(s, y[u]) : s + y[u];
+    }
+    for (; b < nblocks; b += bd) {
+      const double y = __ldcg(pi + b);
       s = mn ? fmin(s, y) : s + y;
     }
     for (int o = 16; o > 0; o >>= 1) {

@@ -2,7 +2,10 @@
 // step (Sec. 6.1). Host code here only orchestrates; every arithmetic step of the hot path runs
 // in the kernels of element.cu and solver.cu.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -110,6 +113,11 @@ static void build_topology(const shell_grid& g, int n1, int n2, HostTopo& T) {
 
 static void destroy_shell(shell_s* s) {
   if (!s) return;
+  for (int i = 0; i < Shell::kTraceMax; ++i)
+    if (s->trace_ev[i]) cudaEventDestroy(s->trace_ev[i]);
+  for (auto& gph : s->pcg_graphs)
+    if (gph.exec) cudaGraphExecDestroy(gph.exec);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   void* ptrs[] = {s->d_patch_nodes, s->d_patch_blocks, s->d_row_ptr, s->d_col, s->d_diag_block,
                   s->d_color_list, s->d_rest, s->d_restgp, s->d_mass, s->d_fgrav, s->d_val,
                   s->d_x, s->d_r, s->d_z, s->d_p, s->d_Ap, s->d_p32, s->d_x32, s->d_r32, s->d_z32, s->d_Ap32, s->d_Dinv, s->d_phi64, s->d_phi32,
@@ -122,6 +130,30 @@ static void destroy_shell(shell_s* s) {
   if (s->h_err) cudaFreeHost(s->h_err);
   delete[] s->h_color_patches;
   delete s;
+}
+
+// Phase trace (BHEM_TRACE_PHASES=1): one CUDA event and one host time per mark.
+static void mark(Shell& s, const char* name) {
+  if (!s.trace || s.trace_n >= Shell::kTraceMax) return;
+  const int i = s.trace_n++;
+  if (!s.trace_ev[i]) cudaEventCreate(&s.trace_ev[i]);
+  cudaEventRecord(s.trace_ev[i], s.stream);
+  s.trace_name[i] = name;
+  s.trace_host[i] = std::chrono::duration<double, std::micro>(
+                        std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static void trace_report(Shell& s) {
+  if (!s.trace || s.trace_n < 2) { s.trace_n = 0; return; }
+  cudaEventSynchronize(s.trace_ev[s.trace_n - 1]);
+  std::fprintf(stderr, "[bhem trace] %d marks\n", s.trace_n);
+  for (int i = 1; i < s.trace_n; ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, s.trace_ev[i - 1], s.trace_ev[i]);
+    std::fprintf(stderr, "[bhem trace] %-22s device %9.1f us  host %9.1f us\n", s.trace_name[i], ms * 1e3,
+                 s.trace_host[i] - s.trace_host[i - 1]);
+  }
+  s.trace_n = 0;
 }
 
 static shell_status sync_and_check(Shell& s) {
@@ -264,6 +296,10 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
     destroy_shell(s);
     return fail(SHELL_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
   }
+  {
+    const char* tv = std::getenv("BHEM_TRACE_PHASES");
+    s->trace = (tv && tv[0] == '1') ? 1 : 0;
+  }
   st = setup_spmv(*s);
   if (st == SHELL_OK) st = launch_rest_setup(*s);
   if (st == SHELL_OK) st = sync_and_check(*s);
@@ -351,24 +387,35 @@ namespace bhem {
 static shell_status run_pcg(Shell& s, const unsigned char* mask, const double td[4],
                             const double* rhs, double rtol, int max_iter, int fixed, int* iters,
                             int* neg) {
-  BHEM_TRY(launch_precond_setup(s, mask, td));
-  BHEM_TRY(launch_pcg_init(s, mask, rhs, rtol, fixed));
   const int limit = fixed > 0 ? fixed : max_iter;
+  BHEM_TRY(launch_precond_setup(s, mask, td));
+  BHEM_TRY(launch_pcg_init(s, mask, rhs, rtol, fixed, limit, td));
+  mark(s, "pcg_setup_enqueued");
   int launched = 0, chunk = 4;
   *s.h_pcg = PcgState{};
   BHEM_CUDA(cudaMemcpyAsync(s.h_pcg, s.d_pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s.stream));
   BHEM_CUDA(cudaStreamSynchronize(s.stream));
+  mark(s, "pcg_setup_synced");
   while (launched < limit && !s.h_pcg->done) {
-    int c = std::min(chunk, limit - launched);
-    for (int k = 0; k < c; ++k) BHEM_TRY(launch_pcg_iteration(s, mask, td));
-    launched += c;
+    if (!s.val_fp64) {
+      // mixed precision: the kernels stop at the cap on the device, so whole power-of-two chunks
+      // replay from cached CUDA graphs
+      BHEM_TRY(launch_pcg_iterations_graph(s, mask, chunk));
+      launched += chunk;
+    } else {
+      int c = std::min(chunk, limit - launched);
+      for (int k = 0; k < c; ++k) BHEM_TRY(launch_pcg_iteration(s, mask, td));
+      launched += c;
+    }
     BHEM_CUDA(cudaMemcpyAsync(s.h_pcg, s.d_pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s.stream));
     BHEM_CUDA(cudaStreamSynchronize(s.stream));
+    mark(s, "pcg_chunk");
     chunk = std::min(chunk * 2, 64);
   }
   *iters = s.h_pcg->iters;
   *neg = s.h_pcg->negcurv;
   BHEM_TRY(sync_and_check(s));
+  mark(s, "pcg_checked");
   return launch_pcg_result(s);
 }
 }  // namespace bhem
@@ -443,11 +490,14 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
                                 const double* qfix, double* q, const double* v_in,
                                 const double* warm, double* v_out, shell_step_stats& st) {
   const int m = s.n_dof;
+  s.trace_n = 0;
+  mark(s, "start");
   BHEM_CUDA(cudaMemcpyAsync(s.d_qn, q, sizeof(double) * m, cudaMemcpyDeviceToDevice, s.stream));
   BHEM_TRY(launch_predictor(s, s.d_qn, v_in, P.dt, s.d_y));
   if (mask) BHEM_TRY(launch_overwrite_fixed(s, q, s.d_qn, mask, qfix));
   double gref = 0.0, gn = 0.0;
   BHEM_TRY(residual(s, q, P, mask, &gref));
+  mark(s, "residual0");
   st.res0 = gref;
   if (warm) BHEM_TRY(launch_overwrite_fixed(s, q, warm, mask, qfix));
   shell_status status = SHELL_OK;
@@ -460,16 +510,19 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
     if (reuse) BHEM_TRY(residual_reuse(s, q, P, mask, &gn));
     else if (it > 0 || warm) BHEM_TRY(residual(s, q, P, mask, &gn));
     else gn = gref;
+    mark(s, "residual");
     reuse = false;
     if (gn <= P.newton_rtol * gref) break;
     if (it >= P.newton_max) { status = SHELL_ERR_NOT_CONVERGED; break; }
     BHEM_TRY(assemble_hessian(s, q, inv_dt2));
+    mark(s, "assemble_enqueued");
     BHEM_TRY(launch_negate(s, s.d_g, s.d_rhs));
     // Sec. 6.1 diagonal regulariser A + tau D (D = per-kind mean |A_ii|): the first solve uses the
     // smallest shift that makes the free diagonal positive, each negative curvature met by PCG
     // multiplies tau by 10 (at least 1e-8), beyond 1e4 the step gives up.
     KindStats K;
     BHEM_TRY(kind_stats(s, mask, K));
+    mark(s, "kind_stats");
     double tau = start_shift(K);
     if (tau > 0.0) st.regularizations++;
     for (;;) {
@@ -491,6 +544,7 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
       BHEM_TRY(launch_dots3(s, m, s.d_d, s.d_Md, s.d_d, s.d_gin, s.d_g, s.d_d, s.d_ns->dots));
       BHEM_CUDA(cudaMemcpyAsync(s.h_ns, s.d_ns, sizeof(NewtonScalars), cudaMemcpyDeviceToHost, s.stream));
       BHEM_CUDA(cudaStreamSynchronize(s.stream));
+      mark(s, "ls_dots");
       const double dMd = s.h_ns->dots[0] * inv_dt2, dgin = s.h_ns->dots[1], gd = s.h_ns->dots[2];
       if (!(gd < 0.0)) { status = SHELL_ERR_LINESEARCH; break; }
       double a_prev = 0.0, f_prev = 0.0;
@@ -504,6 +558,7 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
         }
         BHEM_CUDA(cudaMemcpyAsync(&s.h_ns->dV, &s.d_ns->dV, sizeof(double), cudaMemcpyDeviceToHost, s.stream));
         BHEM_CUDA(cudaStreamSynchronize(s.stream));
+        mark(s, "ls_trial");
         const double phi = s.h_ns->dV + alpha * dgin + 0.5 * alpha * alpha * dMd;
         if (std::isfinite(phi) && phi <= 1e-4 * alpha * gd) {
           ok = true;
@@ -548,6 +603,8 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
     // leave q unchanged on failure
     BHEM_CUDA(cudaMemcpyAsync(q, s.d_qn, sizeof(double) * m, cudaMemcpyDeviceToDevice, s.stream));
   }
+  mark(s, "end");
+  trace_report(s);
   return status;
 }
 }  // namespace bhem

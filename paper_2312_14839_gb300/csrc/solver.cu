@@ -359,7 +359,7 @@ k_spmv32(int n, const int* __restrict__ rp, const int* __restrict__ col, const f
     const size_t gi = (size_t)i * 12 + r;
     const float xi = x[gi];
     float yi = (sacc[t] + sacc[t + 1]) + sacc[t + 2];
-    yi = __fmaf_rn(td.v[r / 3], xi, yi);
+    yi = __fmaf_rn(st ? st->td[r / 3] : td.v[r / 3], xi, yi);   // PCG: the solve's shift
     if (mask && mask[gi]) yi = 0.f;
     y[gi] = yi;
     part = f2_prod(xi, yi);
@@ -499,7 +499,7 @@ k_spmv32_tma(int n, const int* __restrict__ rp, const int* __restrict__ col, con
       const size_t gi = (size_t)i * 12 + r;
       const float xi = x[gi];
       float yi = (sacc[t] + sacc[t + 1]) + sacc[t + 2];
-      yi = __fmaf_rn(td.v[r / 3], xi, yi);
+      yi = __fmaf_rn(st ? st->td[r / 3] : td.v[r / 3], xi, yi);   // PCG: the solve's shift
       if (mask && mask[gi]) yi = 0.f;
       y[gi] = yi;
       part = f2_add(part, f2_prod(xi, yi));
@@ -543,8 +543,8 @@ __device__ __forceinline__ float apply_block32(const float* __restrict__ D, cons
 __global__ void __launch_bounds__(kNodeThreads)
 k_pcg32_init(int n, const double* __restrict__ rhs, const float* __restrict__ Dinv,
              const unsigned char* __restrict__ mask, float* __restrict__ x, float* __restrict__ r,
-             float* __restrict__ z, float* __restrict__ p, double rtol2, int fixed, PcgState* st,
-             Reduce red) {
+             float* __restrict__ z, float* __restrict__ p, double rtol2, int fixed, int limit, Shift4f td,
+             PcgState* st, Reduce red) {
   __shared__ float sr[16][12];
   const int ln = threadIdx.x / 12, a = threadIdx.x % 12;
   const int i = blockIdx.x * 16 + ln;
@@ -570,6 +570,8 @@ k_pcg32_init(int n, const double* __restrict__ rhs, const float* __restrict__ Di
     st->rr = out[1];
     st->rtol2 = rtol2;
     st->fixed = fixed;
+    st->limit = limit;
+    for (int k = 0; k < 4; ++k) st->td[k] = td.v[k];
     st->iters = 0;
     st->negcurv = 0;
     st->alpha = 0.0;
@@ -633,6 +635,7 @@ k_pcg32_update(int n, float* __restrict__ x, float* __restrict__ r, float* __res
     st->rz = rz_new;
     if (st->fixed == 0 && out[1] <= st->rtol2 * st->bb) st->done = 1;
     if (rz_new == 0.0) st->done = 1;
+    if (st->iters >= st->limit) st->done = 1;
   }
 }
 
@@ -811,13 +814,14 @@ shell_status launch_diag_check(Shell& s, const unsigned char* mask, double* out1
 }
 
 shell_status launch_pcg_init(Shell& s, const unsigned char* mask, const double* rhs, double rtol,
-                             int fixed) {
+                             int fixed, int limit, const double td[4]) {
   int blocks = grid_for(s.n_nodes, 16);
   if (blocks > s.red.stride) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
   double rtol2 = fixed > 0 ? 0.0 : rtol * rtol;
   if (!s.val_fp64) {
+    Shift4f sh{{(float)td[0], (float)td[1], (float)td[2], (float)td[3]}};
     k_pcg32_init<<<blocks, kNodeThreads, 0, s.stream>>>(s.n_nodes, rhs, (const float*)s.d_Dinv, mask,
-        s.d_x32, s.d_r32, s.d_z32, s.d_p32, rtol2, fixed, s.d_pcg, s.red);
+        s.d_x32, s.d_r32, s.d_z32, s.d_p32, rtol2, fixed, limit, sh, s.d_pcg, s.red);
     BHEM_CUDA(cudaGetLastError());
     ++s.launches;
     return SHELL_OK;
@@ -950,6 +954,45 @@ shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, const dou
   k_pcg_pupdate<<<vec_blocks(m), 256, 0, s.stream>>>(m, s.d_z, s.d_p, nullptr, s.d_pcg);
   BHEM_CUDA(cudaGetLastError());
   ++s.launches;
+  return SHELL_OK;
+}
+
+shell_status launch_pcg_iterations_graph(Shell& s, const unsigned char* mask, int iters) {
+  if (s.val_fp64) return fail(SHELL_ERR_ARG, "PCG graphs are for mixed precision");
+  Shell::PcgGraph* hit = nullptr;
+  for (auto& gph : s.pcg_graphs)
+    if (gph.exec && gph.mask == mask && gph.iters == iters) hit = &gph;
+  if (!hit) {
+    if (!s.cap_stream) BHEM_CUDA(cudaStreamCreateWithFlags(&s.cap_stream, cudaStreamNonBlocking));
+    // capture on a private stream (the shell's stream may be the uncapturable legacy stream);
+    // the shift argument is unused: the kernels read it from the PCG state
+    const double zero[4] = {0.0, 0.0, 0.0, 0.0};
+    cudaStream_t keep = s.stream;
+    const long long keep_launches = s.launches;
+    s.stream = s.cap_stream;
+    BHEM_CUDA(cudaStreamBeginCapture(s.cap_stream, cudaStreamCaptureModeThreadLocal));
+    shell_status st = SHELL_OK;
+    for (int k = 0; k < iters && st == SHELL_OK; ++k) st = launch_pcg_iteration(s, mask, zero);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s.cap_stream, &graph);
+    s.stream = keep;
+    s.launches = keep_launches;
+    if (st != SHELL_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return fail(SHELL_ERR_CUDA, std::string("PCG graph capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e2 = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) return fail(SHELL_ERR_CUDA, std::string("PCG graph instantiate: ") + cudaGetErrorString(e2));
+    hit = &s.pcg_graphs[s.pcg_graph_next];
+    if (hit->exec) cudaGraphExecDestroy(hit->exec);
+    *hit = Shell::PcgGraph{mask, iters, exec};
+    s.pcg_graph_next = (s.pcg_graph_next + 1) % Shell::kGraphSlots;
+  }
+  BHEM_CUDA(cudaGraphLaunch(hit->exec, s.stream));
+  s.launches += 3LL * iters;
   return SHELL_OK;
 }
 
