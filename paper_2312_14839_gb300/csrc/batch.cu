@@ -193,6 +193,7 @@ struct ElemBatchArgs {
   const ShellPar* par;
   const ShellState* st;
   const float* t32;
+  const double* dxi;           // [2 * shells] parameter extents of one patch
   const int4* pnodes;
   const int* pblocks;
   const double* q;
@@ -208,7 +209,8 @@ k_element(ElemBatchArgs B) {
   constexpr int NW = ElemCfg<float>::kWarps;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sphi = reinterpret_cast<float*>(smem_raw);
-  WarpSmem<float>* Ws = reinterpret_cast<WarpSmem<float>*>(smem_raw + sizeof(float) * ((kPhiTable + 3) & ~3));
+  float* w1d = sphi + ((kPhiTable + 3) & ~3);
+  WarpSmem<float>* Ws = reinterpret_cast<WarpSmem<float>*>(smem_raw + sizeof(float) * elem_table_elems<float>());
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int it = blockIdx.x; it < B.n_items; it += gridDim.x) {
     const int4 item = B.items[it];
@@ -216,6 +218,8 @@ k_element(ElemBatchArgs B) {
     if (!B.st[s].active) continue;   // uniform over the CTA
     __syncthreads();
     load_shape_table<float>(sphi, B.t32 + (size_t)s * kPhiTable);
+    build_hermite_1d<float>(w1d, B.dxi[2 * s], threadIdx.x, blockDim.x);
+    build_hermite_1d<float>(w1d + kHerm1D, B.dxi[2 * s + 1], threadIdx.x, blockDim.x);
     __syncthreads();
     ElemArgs A{};
     A.pnodes = B.pnodes;
@@ -232,7 +236,7 @@ k_element(ElemBatchArgs B) {
     A.err = B.err;
     for (int k = item.y + wid; k < item.z; k += NW) {
       const int p = B.plist ? B.plist[k] : k;
-      element_patch<float>(sphi, Ws[wid], p, A, lane);
+      element_patch<float>(sphi, w1d, Ws[wid], p, A, lane);
     }
   }
 }
@@ -1002,7 +1006,7 @@ shell_status zero_counters(shell_batch_s& b) {
   return SHELL_OK;
 }
 
-size_t elem_smem() { return sizeof(float) * ((kPhiTable + 3) & ~3) + sizeof(WarpSmem<float>) * ElemCfg<float>::kWarps; }
+size_t elem_smem() { return sizeof(float) * elem_table_elems<float>() + sizeof(WarpSmem<float>) * ElemCfg<float>::kWarps; }
 
 // FP32 element Hessians of active shells assembled into the BSR (+ mass_scale M)
 shell_status assemble(shell_batch_s& b, const double* q, double mass_scale) {
@@ -1018,6 +1022,7 @@ shell_status assemble(shell_batch_s& b, const double* q, double mass_scale) {
   A.par = b.par;
   A.st = b.st;
   A.t32 = b.t32;
+  A.dxi = b.dxi;
   A.pnodes = b.pnodes;
   A.pblocks = b.pblocks;
   A.q = q;

@@ -189,19 +189,22 @@ k_element_full(ElemArgs A) {
   constexpr int NW = ElemCfg<R>::kWarps;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sphi = reinterpret_cast<R*>(smem_raw);
-  WarpSmem<R>* Ws = reinterpret_cast<WarpSmem<R>*>(smem_raw + sizeof(R) * ((kPhiTable + 3) & ~3));
+  R* w1d = sphi + ((kPhiTable + 3) & ~3);
+  WarpSmem<R>* Ws = reinterpret_cast<WarpSmem<R>*>(smem_raw + sizeof(R) * elem_table_elems<R>());
   load_shape_table<R>(sphi, reinterpret_cast<const R*>(A.phi));
+  build_hermite_1d<R>(w1d, A.d1, threadIdx.x, blockDim.x);
+  build_hermite_1d<R>(w1d + kHerm1D, A.d2, threadIdx.x, blockDim.x);
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpSmem<R>& W = Ws[wid];
   const int total = A.plist ? A.plist_n : A.np;
   for (int it = blockIdx.x * NW + wid; it < total; it += gridDim.x * NW)
-    element_patch<R>(sphi, W, A.plist ? A.plist[it] : it, A, lane);
+    element_patch<R>(sphi, w1d, W, A.plist ? A.plist[it] : it, A, lane);
 }
 
 template <typename R>
 static size_t elem_smem_bytes() {
-  return sizeof(R) * ((kPhiTable + 3) & ~3) + sizeof(WarpSmem<R>) * ElemCfg<R>::kWarps;
+  return sizeof(R) * elem_table_elems<R>() + sizeof(WarpSmem<R>) * ElemCfg<R>::kWarps;
 }
 
 template <typename R>

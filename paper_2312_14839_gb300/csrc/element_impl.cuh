@@ -103,7 +103,8 @@ __device__ __forceinline__ void interp5(const R* sphi, const S* qv, int g, V3<R>
 // ------------------------------------------------------------------------------------------
 constexpr int kHerm1D = 48;
 
-__device__ __forceinline__ void build_hermite_1d(double* w, double dxi, int tid, int nthreads) {
+template <typename R>
+__device__ __forceinline__ void build_hermite_1d(R* w, double dxi, int tid, int nthreads) {
   double th[4], wt[4];
   gauss_unit(th, wt);
   for (int e = tid; e < kHerm1D; e += nthreads) {
@@ -112,9 +113,14 @@ __device__ __forceinline__ void build_hermite_1d(double* w, double dxi, int tid,
     double v = herm(p, r, th[gi], d);
     if (r) v *= dxi;
     for (int i = 0; i < d; ++i) v /= dxi;
-    w[e] = v;
+    w[e] = (R)v;
   }
 }
+
+// Elements of the element kernels' shared memory before the per-warp areas: shape table, then the
+// two 1D factor tables (theta^1, theta^2)
+template <typename R>
+constexpr int elem_table_elems() { return ((kPhiTable + 3) & ~3) + 2 * kHerm1D; }
 
 constexpr int kRestFields = 13;
 
@@ -465,11 +471,51 @@ __device__ __forceinline__ void plain_add_row12(R* dst, const R* v) {
   for (int i = 0; i < 12; ++i) dst[i] += v[i];
 }
 
+// T = Phi_g^T M_g for Gauss point g = 4 g2 + g1: T[I * 45 + c * 15 + l * 3 + c'] =
+// sum_k phi_k^I(g) M_g[(k, c), (l, c')] for the 16 DOF triples I. With the tensor-product basis,
+// phi_k^I = w1[d1(k)][g1][a] w2[d2(k)][g2][b] (I = corner (p + 2q) * 4 + kind (r + 2s),
+// a = 2p + r, b = 2q + s): each lane takes whole (c, l, c') columns, loads the 5 M values of a
+// column once, contracts along theta^2 and then theta^1 in registers, and writes 16 T values.
+template <typename R>
+__device__ __forceinline__ void t_stage(const R* w1d, const R* Mg, R* T, int g, int lane) {
+  const int g1 = g & 3, g2 = g >> 2;
+  R W1[3][4], W2[3][4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      W1[d][a] = w1d[(d * 4 + g1) * 4 + a];
+      W2[d][a] = w1d[kHerm1D + (d * 4 + g2) * 4 + a];
+    }
+  for (int col = lane; col < 45; col += 32) {
+    const int c = col / 15, l = (col / 3) % 5, cp = col % 3;
+    R m[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) m[k] = Mg[(k * 3 + c) * 15 + l * 3 + cp];
+    // kinds k = (d1, d2): 0 (1,0), 1 (0,1), 2 (2,0), 3 (0,2), 4 (1,1); V[d1][b] = sum over the
+    // kinds with that d1 of w2[d2][g2][b] M_k
+    R V[3][4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      V[0][b] = W2[1][b] * m[1] + W2[2][b] * m[3];
+      V[1][b] = W2[0][b] * m[0] + W2[1][b] * m[4];
+      V[2][b] = W2[0][b] * m[2];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int I = ((a >> 1) + 2 * (b >> 1)) * 4 + ((a & 1) + 2 * (b & 1));
+        T[I * 45 + col] = W1[0][a] * V[0][b] + W1[1][a] * V[1][b] + W1[2][a] * V[2][b];
+      }
+  }
+}
+
 // One patch by one warp: gather, Gauss-point matrices M_g, energy/gradient by-products, and the
 // Hessian K = sum_g phi_g^T M_g phi_g written unassembled and/or scattered into the BSR.
 template <typename R>
-__device__ __forceinline__ void element_patch(const R* sphi, WarpSmem<R>& W, int p, const ElemArgs& A,
-                                              int lane) {
+__device__ __forceinline__ void element_patch(const R* sphi, const R* w1d, WarpSmem<R>& W, int p,
+                                              const ElemArgs& A, int lane) {
   constexpr int JP = ElemCfg<R>::kJP;          // J columns per pass (16 / 2 / JP passes)
   const int I = lane >> 1, h = lane & 1;
   const int4 pn = A.pnodes[p];
@@ -524,25 +570,7 @@ __device__ __forceinline__ void element_patch(const R* sphi, WarpSmem<R>& W, int
       const int J0 = 8 * h + pass * JP;
 #pragma unroll 1
       for (int g = 0; g < 16; ++g) {
-        // T[I][c][l][c'] = sum_k phi_k^I M_g[(k,c),(l,c')]; lane (I, h) does (c,c') = h, h+2, ...
-        const R* Mg = W.M[g];
-        R phk[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) phk[k] = sphi[I * kPhiStride + (k + 1) * 16 + g];
-#pragma unroll
-        for (int t = 0; t < 5; ++t) {
-          int pi = h + 2 * t;
-          if (pi < 9) {
-            int c = pi / 3, cp = pi % 3;
-#pragma unroll
-            for (int l = 0; l < 5; ++l) {
-              R tv = 0;
-#pragma unroll
-              for (int k = 0; k < 5; ++k) tv += phk[k] * Mg[(k * 3 + c) * 15 + l * 3 + cp];
-              W.T[I * 45 + c * 15 + l * 3 + cp] = tv;
-            }
-          }
-        }
+        t_stage<R>(w1d, W.M[g], W.T, g, lane);
         __syncwarp();
         R Tr[45];
 #pragma unroll
