@@ -106,7 +106,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, FileNotFoundError):
@@ -146,7 +146,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(workload: str, n_steps: int = 2, n: int = 48):
+def cpu_baseline(workload: str, n_steps: int = 8, n: int = 48):
     """The oracle (plain FP64 C, single thread) on a bounded sample of the same workload: the
     same sinusoid recipe on an n x n sheet, one Newton iteration with exactly 50 PCG iterations
     per step."""
@@ -331,7 +331,8 @@ def run_learned_bench(args):
         "train": {"loss_first": losses[0][1], "loss_last": losses[-1][1], "seconds": train_sec,
                   "iters_per_s": args.train_iters / train_sec},
         "data_generation": {"steps": n_traj * gen_steps, "seconds": data.seconds,
-                            "newton_iters_mean": float(data.newton_iters.mean())},
+                            "newton_iters_mean": float(data.newton_iters.mean()),
+                            "trajectories_stopped_unconverged": data.dropped},
         "gpu_launches": l["launches"], "clocks": clk.summary(),
     }), flush=True)
     net.close()
@@ -340,7 +341,7 @@ def run_learned_bench(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="sheet256", choices=list(WORKLOADS))

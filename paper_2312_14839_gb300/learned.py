@@ -33,7 +33,7 @@ class Scene:
     newton_rtol: float = 1e-8
     pcg_rtol: float = 1e-6
     pcg_max: int = 2000
-    newton_max: int = 50
+    newton_max: int = 200       # twisted corners (up to 400 degrees) make some steps hard
     max_twist_deg: float = 2.0
 
     def params(self):
@@ -51,6 +51,7 @@ class Dataset:
     T: object          # torch float32 [rows, 12] (CUDA)
     newton_iters: np.ndarray   # [steps, n_traj] zero-guess Newton iterations of the generating runs
     seconds: float
+    dropped: int = 0           # trajectories stopped at a step the solver did not converge
 
 
 def _prescriptions(g, rest, rates, steps):
@@ -78,6 +79,8 @@ def generate(scene: Scene, n_traj: int, steps: int, seed: int) -> Dataset:
     v = torch.zeros_like(q)
     P = scene.params()
     iters = np.zeros((steps, n_traj), dtype=np.int32)
+    alive = np.ones(n_traj, dtype=bool)
+    keep = torch.ones(steps * n_traj, dtype=torch.bool, device=dev)   # per (step, trajectory) rows
     t0 = time.perf_counter()
     with bhem.Batch([(g, mat, rest)] * n_traj) as batch:
         for k in range(steps):
@@ -89,14 +92,22 @@ def generate(scene: Scene, n_traj: int, steps: int, seed: int) -> Dataset:
                 bhem.node_features(feat_shell, q[sl], v[sl], X[r0:r0 + n_nodes])
             torch.cuda.synchronize()
             stats = batch.newton_step(q, v, P, mask=mask, q_fixed=qfix_all[k])
-            bad = [st["status"] for st in stats if st["status"] != 0]
-            if bad:
-                raise bhem.ShellError(bad[0], f"generating step {k}: {len(bad)} shells failed")
+            for s, st in enumerate(stats):
+                if st["status"] != 0 and st["status"] not in (6, 7, 8):
+                    raise bhem.ShellError(st["status"], f"generating step {k}, trajectory {s}")
+                if st["status"] != 0:
+                    alive[s] = False          # a step the solver did not finish: stop recording
+                if not alive[s]:
+                    keep[k * n_traj + s] = False
             iters[k] = [st["newton_iters"] for st in stats]
             bhem.warm_targets(q, q_old, v_old, scene.dt, T[base * 12:(base + n_traj * n_nodes) * 12])
     torch.cuda.synchronize()
     feat_shell.close()
-    return Dataset(X, T.view(rows, 12), iters, time.perf_counter() - t0)
+    T = T.view(rows, 12)
+    if not bool(keep.all()):
+        rows_keep = keep.repeat_interleave(n_nodes)
+        X, T = X[rows_keep].contiguous(), T[rows_keep].contiguous()
+    return Dataset(X, T, iters, time.perf_counter() - t0, int((~alive).sum()))
 
 
 def set_normalization(net: "bhem.Mlp", data: Dataset):
