@@ -123,6 +123,7 @@ struct Shell {
 
   // FP32 SpMV variant: TMA-pipelined persistent kernel when its row-group stages fit in shared
   // memory (max_row = most blocks in one block row)
+  int num_sms = 0;                  // multiprocessors of the shell's device (grid sizes)
   int max_row = 0;
   int spmv_tma = 0, spmv_grid = 0, spmv_stage_floats = 0;
   size_t spmv_smem = 0;

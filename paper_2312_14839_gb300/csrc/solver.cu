@@ -589,43 +589,51 @@ k_pcg32_update(int n, float* __restrict__ x, float* __restrict__ r, float* __res
   if (st->done) return;
   __shared__ float sr[16][12];
   const int ln = threadIdx.x / 12, a = threadIdx.x % 12;
-  const int i = blockIdx.x * 16 + ln;
-  const size_t gi = (size_t)i * 12 + a;
   const float alpha = (float)st->alpha;
-  float ri = 0.f, zi = 0.f;
-  float4 d0, d1, d2;
-  if (i < n) {
-    // this thread's row of the node's 12x12 inverse: 48 contiguous bytes, streamed, issued with
-    // the vector loads so that all of them are in flight together
-    const float4* drow = reinterpret_cast<const float4*>(Dinv + (size_t)i * 144 + a * 12);
-    d0 = __ldcs(drow);
-    d1 = __ldcs(drow + 1);
-    d2 = __ldcs(drow + 2);
-    x[gi] = fmaf(alpha, p[gi], x[gi]);
-    ri = fmaf(-alpha, Ap[gi], r[gi]);
-    r[gi] = ri;
-    sr[ln][a] = ri;
-  }
-  __syncthreads();
-  if (i < n) {
-    if (!(mask && mask[gi])) {
-      const float* q = sr[ln];
-      zi = __fmaf_rn(d0.x, q[0], 0.f);
-      zi = __fmaf_rn(d0.y, q[1], zi);
-      zi = __fmaf_rn(d0.z, q[2], zi);
-      zi = __fmaf_rn(d0.w, q[3], zi);
-      zi = __fmaf_rn(d1.x, q[4], zi);
-      zi = __fmaf_rn(d1.y, q[5], zi);
-      zi = __fmaf_rn(d1.z, q[6], zi);
-      zi = __fmaf_rn(d1.w, q[7], zi);
-      zi = __fmaf_rn(d2.x, q[8], zi);
-      zi = __fmaf_rn(d2.y, q[9], zi);
-      zi = __fmaf_rn(d2.z, q[10], zi);
-      zi = __fmaf_rn(d2.w, q[11], zi);
+  F2 rz{0.f, 0.f}, rr{0.f, 0.f};
+  // grid-stride over groups of 16 nodes: a few CTAs per SM, so the last CTA of the grid
+  // reduction folds few partials
+  for (int base = blockIdx.x * 16; base < n; base += gridDim.x * 16) {
+    const int i = base + ln;
+    const size_t gi = (size_t)i * 12 + a;
+    float ri = 0.f, zi = 0.f;
+    float4 d0, d1, d2;
+    if (i < n) {
+      // this thread's row of the node's 12x12 inverse: 48 contiguous bytes, streamed, issued with
+      // the vector loads so that all of them are in flight together
+      const float4* drow = reinterpret_cast<const float4*>(Dinv + (size_t)i * 144 + a * 12);
+      d0 = __ldcs(drow);
+      d1 = __ldcs(drow + 1);
+      d2 = __ldcs(drow + 2);
+      x[gi] = fmaf(alpha, p[gi], x[gi]);
+      ri = fmaf(-alpha, Ap[gi], r[gi]);
+      r[gi] = ri;
+      sr[ln][a] = ri;
     }
-    z[gi] = zi;
+    __syncthreads();
+    if (i < n) {
+      if (!(mask && mask[gi])) {
+        const float* q = sr[ln];
+        zi = __fmaf_rn(d0.x, q[0], 0.f);
+        zi = __fmaf_rn(d0.y, q[1], zi);
+        zi = __fmaf_rn(d0.z, q[2], zi);
+        zi = __fmaf_rn(d0.w, q[3], zi);
+        zi = __fmaf_rn(d1.x, q[4], zi);
+        zi = __fmaf_rn(d1.y, q[5], zi);
+        zi = __fmaf_rn(d1.z, q[6], zi);
+        zi = __fmaf_rn(d1.w, q[7], zi);
+        zi = __fmaf_rn(d2.x, q[8], zi);
+        zi = __fmaf_rn(d2.y, q[9], zi);
+        zi = __fmaf_rn(d2.z, q[10], zi);
+        zi = __fmaf_rn(d2.w, q[11], zi);
+      }
+      z[gi] = zi;
+    }
+    rz = f2_add(rz, f2_prod(ri, zi));
+    rr = f2_add(rr, f2_prod(ri, ri));
+    __syncthreads();   // sr is rewritten by the next group
   }
-  F2 v[2] = {f2_prod(ri, zi), f2_prod(ri, ri)};
+  F2 v[2] = {rz, rr};
   double out[2];
   if (grid_reduce_f2<2>(v, red, out, gridDim.x) && threadIdx.x == 0) {
     const double rz_new = out[0];
@@ -889,6 +897,11 @@ shell_status launch_spmv(Shell& s, const void* x, int x_fp32, void* y) {
 
 shell_status setup_spmv(Shell& s) {
   s.spmv_tma = 0;
+  {
+    int d = 0;
+    BHEM_CUDA(cudaGetDevice(&d));
+    BHEM_CUDA(cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, d));
+  }
   if (s.val_fp64) return SHELL_OK;
   const size_t stage_floats = (size_t)kTmaRows * std::max(1, s.max_row) * 144;
   const size_t smem = stage_floats * sizeof(float) * kTmaStages;
@@ -936,7 +949,7 @@ shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, const dou
   if (!s.val_fp64) {
     Shift4f sh{{(float)td[0], (float)td[1], (float)td[2], (float)td[3]}};
     BHEM_TRY(launch_spmv32(s, s.d_p32, sh, mask, s.d_Ap32, s.d_pcg));
-    k_pcg32_update<<<grid_for(n, 16), kNodeThreads, 0, s.stream>>>(
+    k_pcg32_update<<<std::min(grid_for(n, 16), 8 * std::max(1, s.num_sms)), kNodeThreads, 0, s.stream>>>(
         n, s.d_x32, s.d_r32, s.d_z32, s.d_p32, s.d_Ap32, (const float*)s.d_Dinv, mask, s.d_pcg, s.red);
     BHEM_CUDA(cudaGetLastError());
     ++s.launches;
