@@ -270,11 +270,18 @@ template <typename R> struct ElemCfg;
 template <> struct ElemCfg<float> { static constexpr int kWarps = 4, kJP = 8; };
 template <> struct ElemCfg<double> { static constexpr int kWarps = 2, kJP = 4; };
 
+// Packed upper triangle of a symmetric 15x15 matrix (120 entries), row-major.
+constexpr int kSym15 = 120;
+__device__ __forceinline__ int sym15(int i, int j) {
+  if (i > j) { const int t = i; i = j; j = t; }
+  return i * 15 - (i * (i - 1)) / 2 + (j - i);
+}
+
 template <typename R>
 struct WarpSmem {
   R u[48];        // displacement q - rest
   R qb[48];       // rest DOFs
-  R M[16][225];   // M_g, full 15x15 per Gauss point
+  R M[16][kSym15];   // M_g per Gauss point (symmetric 15x15, packed upper triangle)
   R T[16 * 45];   // T[I][c*15 + l*3 + c'] of the current Gauss point
   R G[16][15];    // gradient vectors per Gauss point
   R ms[16];       // mass_scale * rho h * W sqrt(a_bar) per Gauss point
@@ -445,8 +452,7 @@ __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W
             }
           }
           v *= wgt;
-          M[(k * 3 + x) * 15 + l * 3 + y] = v;
-          M[(l * 3 + y) * 15 + k * 3 + x] = v;
+          M[sym15(k * 3 + x, l * 3 + y)] = v;
         }
 }
 
@@ -491,7 +497,7 @@ __device__ __forceinline__ void t_stage(const R* w1d, const R* Mg, R* T, int g, 
     const int c = col / 15, l = (col / 3) % 5, cp = col % 3;
     R m[5];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) m[k] = Mg[(k * 3 + c) * 15 + l * 3 + cp];
+    for (int k = 0; k < 5; ++k) m[k] = Mg[sym15(k * 3 + c, l * 3 + cp)];
     // kinds k = (d1, d2): 0 (1,0), 1 (0,1), 2 (2,0), 3 (0,2), 4 (1,1); V[d1][b] = sum over the
     // kinds with that d1 of w2[d2][g2][b] M_k
     R V[3][4];
