@@ -43,6 +43,9 @@ WORKLOADS = {
                  "seeded rates U[-2,2] deg/step; warm-start MLP 28-256-256-256-12 (BF16, GELU) trained "
                  "on 10,000 steps of the plain solver (50 trajectories x 200 steps); 200 implicit-Euler "
                  "steps of an unseen trajectory, Newton to 1e-8 of the zero-guess residual, PCG to 1e-6",
+    "twist30": "30x30-patch 1 m sheet, centre node held and its x_,1, x_,2 rotated 2 deg per step about +z, "
+               "no gravity, dt = 2 ms, 200 implicit-Euler steps to 1e-8 (PCG to 1e-6), mixed precision; "
+               "exact Hessian against the pseudo Hessian (App. B)",
     "annulus280x5": "280x5-patch periodic annular strip, 8-term sinusoid displacement (5 cm), "
                     "FP32 element eval + BSR assembly + 50-iteration block-Jacobi PCG, FP64 "
                     "residual/reductions",
@@ -70,20 +73,31 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_source_sha(kernel_src: str, kernel: str) -> str:
+    """sha256 (16 hex digits) of one kernel's definition in a source file: from the line that
+    starts with `kernel(` to the first closing brace at column 0."""
+    text = open(kernel_src).read()
+    start = text.find("\n" + kernel + "(")
+    if start < 0:
+        return ""
+    end = text.find("\n}\n", start)
+    return hashlib.sha256(text[start:end + 3].encode()).hexdigest()[:16]
+
+
 def recorded_traffic(kernel_src: str, kernel: str, workload: str):
     """DRAM bytes per SpMV launch from the committed ncu summary, when it was taken on the
-    current kernel source (sha256 recorded in the summary); else None."""
+    current kernel definition (sha256 of its source text recorded in the summary); else None."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    h = kernel_source_sha(kernel_src, kernel)
     vals = {}
     for line in text.splitlines():
         if ":" in line and line.strip().startswith("- `"):
             k, _, v = line.strip()[3:].partition("`:")
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("solver_cu_sha256_16") != h:
+    if not h or vals.get("kernel_source_sha256_16") != h:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -338,6 +352,124 @@ def run_learned_bench(args):
     net.close()
 
 
+# Algorithmic work per patch of the two arithmetic-bound kernels (the units are stated in DESIGN):
+#  - element Hessian: the factored Phi^T M_g Phi contraction with symmetry, 16 x 15 x 48 x 5 (T)
+#    + 1,176 x 80 (K) = 151,680 FMA;
+#  - FP64 energy + gradient: sum-factorised interpolation 1,536 + gradient transpose 1,536 +
+#    about 190 FMA of nonlinear point work at each of the 16 Gauss points = 6,112 FMA.
+ELEMENT_FLOP_PER_PATCH = 2 * (16 * 15 * 48 * 5 + 1176 * 80)
+ENERGY64_FLOP_PER_PATCH = 2 * (1536 + 1536 + 16 * 190)
+
+
+def alu_rooflines(sh, q_d, P, n_patches, stream, reps=5):
+    """Element Hessian pass and FP64 energy/gradient pass timed with CUDA events on the shell's
+    stream, against FP32 / FP64 FMA peaks measured in the same run (shell_measure_fma_peak)."""
+    import torch
+    from paper_2312_14839_gb300 import bhem
+    peak32 = bhem.measure_fma_peak(False, 4096, stream)
+    peak64 = bhem.measure_fma_peak(True, 256, stream)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    t_el = timed(lambda: sh.energy_grad_hess(q_d, mass_scale=1.0 / P.dt ** 2, want_energy=False,
+                                             want_grad=False))
+    t_eg = timed(lambda: sh.energy_grad_hess(q_d, want_hessian=False))
+    out = []
+    for kern, t, flop, pk, what in (
+            ("k_element_full<float> (FP32 exact Hessian + BSR scatter; the BSR clear is in the time)",
+             t_el, ELEMENT_FLOP_PER_PATCH, peak32, "FP32"),
+            ("k_energy_grad64 (FP64 energy + assembled gradient; the gradient clear is in the time)",
+             t_eg, ENERGY64_FLOP_PER_PATCH, peak64, "FP64")):
+        ach = flop * n_patches / t / 1e12
+        out.append({"kernel": kern, "bound": "alu", "achieved": ach, "peak": pk / 1e12, "unit": "TFLOP/s",
+                    "frac": ach * 1e12 / pk, "flop_per_patch": flop, "avg_launch_us": t * 1e6,
+                    "peak_source": f"measured {what} FMA microbenchmark (shell_measure_fma_peak)"})
+    return out
+
+
+def run_twist_bench(args):
+    """Exact against pseudo Hessian on the twist scene (one JSON line): implicit-Euler steps/s and
+    Newton iterations at 1e-8, plus the element pass time of each Hessian."""
+    import torch
+    from paper_2312_14839_gb300 import bhem
+    from paper_2312_14839_gb300 import scenes as S
+    torch.cuda.set_device(0)
+    bhem.load()
+    dev = torch.device("cuda", 0)
+    g, rest = S.flat_sheet(30, 30)
+    mat = S.SHEET_MATERIAL
+    steps = 200
+    pres = [S.twist_prescription(g, rest, k) for k in range(1, steps + 1)]
+    mask = torch.as_tensor(pres[0][0], device=dev)
+    qfix = torch.as_tensor(np.stack([v for _, v in pres]), device=dev)
+    P = bhem.step_params(dt=2e-3, gravity=(0.0, 0.0, 0.0), newton_max=100)
+    res = {}
+    clk_all = []
+    for hess in ("exact", "pseudo"):
+        sh = bhem.Shell(g, mat, torch.as_tensor(rest.reshape(-1), device=dev), precision="mixed", hessian=hess)
+        stream = sh.stream
+        rest_d = torch.as_tensor(rest.reshape(-1), device=dev)
+
+        def rollout(n):
+            q, v = rest_d.clone(), torch.zeros_like(rest_d)
+            it = []
+            for k in range(n):
+                st = sh.newton_step(q, v, P, mask=mask, q_fixed=qfix[k])
+                if st["status"] != 0:
+                    raise bhem.ShellError(st["status"], f"twist step {k} ({hess})")
+                it.append((st["newton_iters"], st["pcg_iters_total"]))
+            return it
+        rollout(args.warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = sh.kernel_launches()
+        torch.cuda.synchronize()
+        with ClockSampler(0) as clk:
+            e0.record(stream)
+            it = rollout(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        clk_all.append(clk.summary())
+        sec = e0.elapsed_time(e1) / 1e3
+        # element pass of this Hessian (BSR clear + element kernel); its cost does not depend on q
+        q_end = rest_d.clone()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(2):
+            sh.energy_grad_hess(q_end, mass_scale=1.0 / P.dt ** 2, want_energy=False, want_grad=False)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(10):
+            sh.energy_grad_hess(q_end, mass_scale=1.0 / P.dt ** 2, want_energy=False, want_grad=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        newton = np.array([a for a, _ in it])
+        res[hess] = {"steps_per_s": steps / sec, "ms_per_step": sec / steps * 1e3,
+                     "newton_iters_mean": float(newton.mean()), "newton_iters_max": int(newton.max()),
+                     "pcg_iters_per_step": float(np.mean([b for _, b in it])),
+                     "element_pass_us": ev0.elapsed_time(ev1) / 10 * 1e3,
+                     "gpu_launches": sh.kernel_launches() - l0}
+        sh.close()
+    ex, ps = res["exact"], res["pseudo"]
+    print(json.dumps({
+        "metric": METRIC, "value": ex["steps_per_s"], "unit": "implicit-Euler steps/s", "n_gpus": 1,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": ex["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (twist prescription)",
+        "config": {"workload": WORKLOADS["twist30"], "patches": g.n_patches, "dof": g.n_dof},
+        "exact_hessian": ex, "pseudo_hessian": ps,
+        "pseudo_vs_exact_steps_per_s": ps["steps_per_s"] / ex["steps_per_s"],
+        "gpu_launches": ex["gpu_launches"], "clocks": clk_all[0],
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -360,6 +492,9 @@ def main():
         return
     if args.workload == "learned64":
         run_learned_bench(args)
+        return
+    if args.workload == "twist30":
+        run_twist_bench(args)
         return
 
     import torch
@@ -472,6 +607,7 @@ def main():
     nb, n, m = sh.n_blocks, sh.n_nodes, sh.n_dof
     spmv_bytes = nb * 144 * 4 + nb * 4 + (n + 1) * 4 + m * 4 + m * 4
     peak, peak_kind = measured_peaks()
+    alu = alu_rooflines(sh, q0_d, P, g.n_patches, stream)
     achieved = spmv_bytes / spmv_s / 1e9
     traffic = recorded_traffic(os.path.join(ROOT, "paper_2312_14839_gb300", "csrc", "solver.cu"),
                                "k_spmv32_tma" if args.spmv == "tma" else "k_spmv32", args.workload)
@@ -499,6 +635,7 @@ def main():
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
                      "traffic": traffic, "algorithmic_bytes_per_launch": spmv_bytes,
                      "avg_launch_us": spmv_s * 1e6},
+        "alu_rooflines": alu,
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -323,6 +323,14 @@ SHELL_API shell_status shell_warm_targets(long long n_dof, const double* q_next,
 SHELL_API shell_status shell_mlp_warm_start(shell_mlp_t* mlp, shell_t* shell, const double* q, const double* v,
                                             double dt, double* warm);
 
+/* Measured arithmetic peak of the current device (no paper counterpart: a measurement aid for
+   the element kernel, bound by FP32 FMA, and the FP64 energy/gradient kernel, bound by the FP64
+   pipe). Times one launch of 8 independent FMA chains per thread, `iters` FMAs each, over 8 CTAs
+   of 256 threads per SM (after one warm-up launch), FP64 when fp64 != 0 else FP32; stream:
+   cudaStream_t or NULL. *flops_per_s receives 2 x FMAs / elapsed seconds. Synchronises; allocates
+   and frees a small device buffer. */
+SHELL_API shell_status shell_measure_fma_peak(int fp64, int iters, void* stream, double* flops_per_s);
+
 /* Number of CUDA kernels this shell has launched since shell_create (host counter; counts the
    launches of the library's own kernels, not memset/memcpy operations). */
 SHELL_API shell_status shell_kernel_launches(const shell_t* shell, long long* count);

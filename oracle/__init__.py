@@ -37,7 +37,7 @@ class Material(C.Structure):
 class StepParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("gravity", C.c_double * 3), ("newton_rtol", C.c_double),
                 ("newton_max", C.c_int), ("pcg_rtol", C.c_double), ("pcg_max", C.c_int),
-                ("pcg_fixed_iters", C.c_int)]
+                ("pcg_fixed_iters", C.c_int), ("pseudo_hessian", C.c_int)]
 
 
 class StepStats(C.Structure):
@@ -71,12 +71,12 @@ def _load():
         lib.og_patch_nodes.argtypes = [p, i, p]
         lib.og_element_energy.restype = d
         lib.og_element_energy.argtypes = [p, p, d, d, p]
-        lib.og_element_egh.argtypes = [p, p, d, d, p, p, p, p]
+        lib.og_element_egh.argtypes = [p, p, d, d, p, p, p, p, i]
         lib.og_element_mass.argtypes = [p, d, d, p, p, p]
-        lib.og_elements.argtypes = [p, p, p, p, i, i, p, p, p]
+        lib.og_elements.argtypes = [p, p, p, p, i, i, p, p, p, i]
         lib.og_bsr_pattern.restype = i
         lib.og_bsr_pattern.argtypes = [p, p, p]
-        lib.og_assemble.argtypes = [p, p, p, p, p, p, d, p, p, p]
+        lib.og_assemble.argtypes = [p, p, p, p, p, p, d, p, p, p, i]
         lib.og_mass.argtypes = [p, p, p, p, p, p, p]
         lib.og_pcg.restype = i
         lib.og_pcg.argtypes = [i, p, p, p, p, d, p, p, d, i, i, p, p]
@@ -145,14 +145,15 @@ def element_energy(q48, qb48, dxi1, dxi2, mat) -> float:
                                      C.byref(_mat(mat)))
 
 
-def element_egh(q48, qb48, dxi1, dxi2, mat):
-    """(E, grad[48], hess[48, 48]) of one patch; local order corner*12 + kind*3 + component."""
+def element_egh(q48, qb48, dxi1, dxi2, mat, pseudo: bool = False):
+    """(E, grad[48], hess[48, 48]) of one patch; local order corner*12 + kind*3 + component.
+    pseudo: the pseudo Hessian (App. B) instead of the exact one."""
     q48, qb48 = _f64(q48), _f64(qb48)
     E = np.zeros(1)
     g = np.zeros(48)
     H = np.zeros((48, 48))
     _load().og_element_egh(_ptr(q48), _ptr(qb48), float(dxi1), float(dxi2), C.byref(_mat(mat)),
-                           _ptr(E), _ptr(g), _ptr(H))
+                           _ptr(E), _ptr(g), _ptr(H), int(bool(pseudo)))
     return float(E[0]), g, H
 
 
@@ -163,7 +164,8 @@ def element_mass(qb48, dxi1, dxi2, mat):
     return m, f
 
 
-def elements(g, mat, rest, q, p0: int = 0, p1: int | None = None, want_hess: bool = True):
+def elements(g, mat, rest, q, p0: int = 0, p1: int | None = None, want_hess: bool = True,
+             pseudo: bool = False):
     """Per-patch (E[np], grad[np, 48], hess[np, 48, 48]) for patches p0..p1-1."""
     p1 = g.n_patches if p1 is None else p1
     rest, q = _f64(rest).reshape(-1), _f64(q).reshape(-1)
@@ -171,7 +173,7 @@ def elements(g, mat, rest, q, p0: int = 0, p1: int | None = None, want_hess: boo
     E, G = np.zeros(n), np.zeros((n, 48))
     H = np.zeros((n, 48, 48)) if want_hess else None
     _load().og_elements(C.byref(_grid(g)), C.byref(_mat(mat)), _ptr(rest), _ptr(q), p0, p1,
-                        _ptr(E), _ptr(G), _ptr(H))
+                        _ptr(E), _ptr(G), _ptr(H), int(bool(pseudo)))
     return E, G, H
 
 
@@ -188,7 +190,8 @@ def bsr_pattern(g):
     return row_ptr, col
 
 
-def assemble(g, mat, rest, q, mass_scale: float = 0.0, want_hess: bool = True, pattern=None):
+def assemble(g, mat, rest, q, mass_scale: float = 0.0, want_hess: bool = True, pattern=None,
+             pseudo: bool = False):
     """(energy, grad[n_dof], (row_ptr, col, val[nb, 12, 12]) or None): K + mass_scale * M."""
     row_ptr, col = pattern if pattern is not None else bsr_pattern(g)
     rest, q = _f64(rest).reshape(-1), _f64(q).reshape(-1)
@@ -196,7 +199,7 @@ def assemble(g, mat, rest, q, mass_scale: float = 0.0, want_hess: bool = True, p
     grad = np.zeros(g.n_dof)
     val = np.zeros((col.size, 12, 12)) if want_hess else None
     _load().og_assemble(C.byref(_grid(g)), C.byref(_mat(mat)), _ptr(rest), _ptr(q), _ptr(row_ptr),
-                        _ptr(col), float(mass_scale), _ptr(E), _ptr(grad), _ptr(val))
+                        _ptr(col), float(mass_scale), _ptr(E), _ptr(grad), _ptr(val), int(bool(pseudo)))
     return float(E[0]), grad, ((row_ptr, col, val) if want_hess else None)
 
 
@@ -247,9 +250,9 @@ def pcg(row_ptr, col, val, b, mask=None, tau=0.0, rtol=1e-6, max_iter=1000, fixe
 
 
 def step_params(dt=1e-3, gravity=(0.0, 0.0, -9.81), newton_rtol=1e-8, newton_max=50,
-                pcg_rtol=1e-6, pcg_max=1000, pcg_fixed_iters=0) -> StepParams:
+                pcg_rtol=1e-6, pcg_max=1000, pcg_fixed_iters=0, pseudo_hessian=False) -> StepParams:
     return StepParams(float(dt), (C.c_double * 3)(*gravity), float(newton_rtol), int(newton_max),
-                      float(pcg_rtol), int(pcg_max), int(pcg_fixed_iters))
+                      float(pcg_rtol), int(pcg_max), int(pcg_fixed_iters), int(bool(pseudo_hessian)))
 
 
 def newton_step(g, mat, rest, q, v, params: StepParams, mask=None, qfix=None, warm=None):

@@ -15,7 +15,8 @@
  *   - Energy density (St. Venant-Kirchhoff, thickness-integrated): Sec. 3.3 (areal density
  *     V_e = (A A h + B B h^3/3) H^{abgd}, H^{abgd} = lambda/2 a^{ab} a^{gd} + mu a^{bg} a^{ad}).
  *   - Gradient: App. B.1 (Voigt form, Eq. matrix with Eq. paabpqi and Eq. pbabpqi).
- *   - Hessian: App. B.2 (G1, G2, second derivatives of alpha and of b, D^{gamma delta}).
+ *   - Hessian: App. B.2 (G1, G2, second derivatives of alpha and of b, D^{gamma delta}); the
+ *     pseudo Hessian ("The pseudo Hessian", App. B) drops the d^2 beta / dq dq term.
  *   - Mass matrix: Eq. mass; gravity: Sec. 4.3 ("External Forces").
  *   - Time step: implicit Euler (Eq. implicit) solved by Newton with a line search (Sec. 6.1);
  *     the linear solve is block-Jacobi PCG with the diagonal regulariser of Sec. 6.1.
@@ -53,6 +54,7 @@ typedef struct {
   int newton_max;
   double pcg_rtol;
   int pcg_max, pcg_fixed_iters;
+  int pseudo_hessian;   /* 1: Newton matrix with the pseudo Hessian (App. B, "The pseudo Hessian") */
 } og_step_params;
 typedef struct {
   int newton_iters, pcg_iters_total, ls_backtracks, regularizations, status;
@@ -237,11 +239,12 @@ static void voigt_H(double lam, double mu, double ai11, double ai22, double ai12
 }
 
 /* ------------------------------------------------------------------------------------------ */
-/* Element energy, gradient (App. B.1) and exact Hessian (App. B.2).                           */
+/* Element energy, gradient (App. B.1) and exact Hessian (App. B.2), or with pseudo != 0 the     */
+/* pseudo Hessian of App. B: the same without the d^2 beta_i / dq_J dq_I term.                  */
 /* grad[I*3+c], hess[(I*3+c)*48 + (J*3+d)], local I = corner*4 + kind.                          */
 /* ------------------------------------------------------------------------------------------ */
 void og_element_egh(const double q[48], const double qb[48], double d1, double d2,
-                    const og_material* mat, double* E_out, double* grad, double* hess) {
+                    const og_material* mat, double* E_out, double* grad, double* hess, int pseudo) {
   double lam, mu, h = mat->thickness, gx[4], gw[4];
   double h3 = h * h * h;
   lame(mat, &lam, &mu);
@@ -362,8 +365,9 @@ void og_element_egh(const double q[48], const double qb[48], double d1, double d
       /* sum_i H^{ij} alpha_j d^2 alpha_i = (H alpha)_i d^2 alpha_i */
       double d2a0 = P1I * P1J, d2a1 = P2I * P2J, d2a2 = P1I * P2J + P2I * P1J;
       for (int x = 0; x < 3; ++x) G1[x][x] += Ha[0] * d2a0 + Ha[1] * d2a1 + Ha[2] * d2a2;
-      /* d^2 b_{ab} / dq_J dq_I, then d^2 beta = (d^2 b11, d^2 b22, 2 d^2 b12) */
-      for (int m = 0; m < 3; ++m) {
+      /* d^2 b_{ab} / dq_J dq_I, then d^2 beta = (d^2 b11, d^2 b22, 2 d^2 b12); the pseudo
+         Hessian leaves this term out */
+      for (int m = 0; m < 3 && !pseudo; ++m) {
         double wm = (m == 2) ? 2.0 * Hb[2] : Hb[m];
         double PabI = phi[I][3 + m], PabJ = phi[J][3 + m];
         for (int x = 0; x < 3; ++x) for (int y = 0; y < 3; ++y) {
@@ -403,14 +407,14 @@ void og_element_mass(const double qb[48], double d1, double d2, const og_materia
 
 /* Per-patch outputs over a patch range (for element-by-element comparison). */
 void og_elements(const og_grid* g, const og_material* mat, const double* rest, const double* q,
-                 int p0, int p1, double* E, double* grad, double* hess) {
+                 int p0, int p1, double* E, double* grad, double* hess, int pseudo) {
   for (int p = p0; p < p1; ++p) {
     double ql[48], qbl[48];
     gather48(g, q, p, ql);
     gather48(g, rest, p, qbl);
     og_element_egh(ql, qbl, g->dxi1, g->dxi2, mat, E ? &E[p - p0] : NULL,
                    grad ? &grad[(size_t)(p - p0) * 48] : NULL,
-                   hess ? &hess[(size_t)(p - p0) * 2304] : NULL);
+                   hess ? &hess[(size_t)(p - p0) * 2304] : NULL, pseudo);
   }
 }
 
@@ -455,10 +459,10 @@ static int find_block(const int* row_ptr, const int* col, int r, int c) {
 }
 
 /* Assembled elastic energy, gradient [n*12] and K + mass_scale * M into val[nblocks*144]
-   (any output may be NULL). */
+   (any output may be NULL); K is the pseudo Hessian when pseudo != 0. */
 void og_assemble(const og_grid* g, const og_material* mat, const double* rest, const double* q,
                  const int* row_ptr, const int* col, double mass_scale,
-                 double* energy, double* grad, double* val) {
+                 double* energy, double* grad, double* val, int pseudo) {
   int n = og_n_nodes(g), np = g->nu * g->nv;
   if (energy) *energy = 0.0;
   if (grad) memset(grad, 0, (size_t)n * 12 * sizeof(double));
@@ -470,7 +474,7 @@ void og_assemble(const og_grid* g, const og_material* mat, const double* rest, c
     og_patch_nodes(g, p, nd);
     gather48(g, q, p, ql);
     gather48(g, rest, p, qbl);
-    og_element_egh(ql, qbl, g->dxi1, g->dxi2, mat, energy ? &E : NULL, grad ? ge : NULL, H);
+    og_element_egh(ql, qbl, g->dxi1, g->dxi2, mat, energy ? &E : NULL, grad ? ge : NULL, H, pseudo);
     if (energy) *energy += E;
     if (grad) for (int c = 0; c < 4; ++c) for (int k = 0; k < 12; ++k) grad[nd[c]*12 + k] += ge[c*12 + k];
     if (!val) continue;
@@ -690,7 +694,7 @@ typedef struct {
    M (q - y)/dt^2 - F when non-NULL. */
 static double full_gradient(const og_ctx* C, const double* q, const double* y, double* gout,
                             double* ginert, double* work) {
-  og_assemble(C->g, C->mat, C->rest, q, C->row_ptr, C->col, 0.0, NULL, gout, NULL);
+  og_assemble(C->g, C->mat, C->rest, q, C->row_ptr, C->col, 0.0, NULL, gout, NULL, 0);
   for (int i = 0; i < C->m; ++i) work[i] = q[i] - y[i];
   double* Mw = (double*)malloc(C->m * sizeof(double));
   mass_mult(C->n, C->row_ptr, C->col, C->mval, work, Mw);
@@ -758,7 +762,7 @@ int og_newton_step(const og_grid* g, const og_material* mat, const double* rest,
     gn = full_gradient(&C, q, y, gr, gin, work);
     if (gn <= P->newton_rtol * gref) break;
     if (it >= P->newton_max) { status = OG_ERR_NOT_CONVERGED; break; }
-    og_assemble(g, mat, rest, q, row_ptr, col, 1.0 / (P->dt * P->dt), NULL, NULL, val);
+    og_assemble(g, mat, rest, q, row_ptr, col, 1.0 / (P->dt * P->dt), NULL, NULL, val, P->pseudo_hessian);
     for (int i = 0; i < m; ++i) rhs[i] = -gr[i];
     /* smallest shift that makes the free diagonal positive, then x10 per negative curvature */
     double dbar[4], dmin[4] = {INFINITY, INFINITY, INFINITY, INFINITY};

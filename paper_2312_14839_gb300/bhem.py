@@ -116,6 +116,7 @@ def load():
                 "shell_node_features": [p, p, p, p],
                 "shell_warm_targets": [ll, p, p, p, d, p, p],
                 "shell_mlp_warm_start": [p, p, p, p, d, p],
+                "shell_measure_fma_peak": [i, i, p, p],
             }
             for name, args in sigs.items():
                 fn = getattr(lib, name)
@@ -482,3 +483,12 @@ def warm_targets(q_next, q, v, dt, T=None, stream=None):
     _, sh = _stream_handle(stream)
     _check(load().shell_warm_targets(int(q.numel()), _ptr(q_next), _ptr(q), _ptr(v), float(dt), _ptr(T), sh))
     return T
+
+
+def measure_fma_peak(fp64: bool, iters: int, stream=None) -> float:
+    """Measured FP32 or FP64 FMA throughput of the current device in FLOP/s
+    (shell_measure_fma_peak)."""
+    _, sh = _stream_handle(stream)
+    out = C.c_double()
+    _check(load().shell_measure_fma_peak(int(bool(fp64)), int(iters), sh, C.byref(out)))
+    return out.value

@@ -124,8 +124,12 @@ def _dot(a, b):
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]
 
 
-def energy_jet(q48, qb48, d1, d2, young, poisson, h):
-    """Jet of the patch energy E(q) (value, d/dq [48], d^2/dq^2 [48, 48])."""
+def energy_jet(q48, qb48, d1, d2, young, poisson, h, pseudo=False):
+    """Jet of the patch energy E(q) (value, d/dq [48], d^2/dq^2 [48, 48]).
+
+    pseudo=True linearises the bending strain B = (b - b_bar) / 2 at q (its jet keeps the value
+    and first derivatives, with a zero Hessian): the Hessian is then the membrane Hessian plus the
+    Gauss-Newton bending term, i.e. the exact Hessian without the second derivatives of beta."""
     lam = young * poisson / (1 - poisson ** 2)
     mu = young / (2 * (1 + poisson))
     gx, gw = gauss4()
@@ -156,6 +160,8 @@ def energy_jet(q48, qb48, d1, d2, young, poisson, h):
             b = [[b11, b12], [b12, b22]]
             A = [[(a[x][y] - abar[x, y]) * 0.5 for y in range(2)] for x in range(2)]
             B = [[(b[x][y] - bbar[x, y]) * 0.5 for y in range(2)] for x in range(2)]
+            if pseudo:
+                B = [[Jet(B[x][y].v, B[x][y].g, None) for y in range(2)] for x in range(2)]
             V = Jet(0.0, np.zeros(48), None)
             for al in range(2):
                 for be in range(2):

@@ -63,6 +63,47 @@ def test_element_parity(case, prec):
         assert np.abs(H[p] - H[p].T).max() <= tol * np.abs(H0[p]).max() * 4
 
 
+@pytest.mark.parametrize("case", ["sheet3x2-rect-thick", "annulus7x2-odd-thick"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_pseudo_hessian_element_parity(case, prec):
+    """The pseudo Hessian (App. B: without the second derivatives of beta) against the oracle's."""
+    g, rest, q, mat = CASES[case]()
+    E0, G0, H0 = O.elements(g, mat, rest, q, pseudo=True)
+    _, _, Hx = O.elements(g, mat, rest, q)
+    sh = make_shell(g, mat, rest, precision=prec, hessian="pseudo")
+    E, G, H = sh.element_egh(dev(q.reshape(-1)), precision=prec)
+    torch.cuda.synchronize()
+    E, G, H = host(E), host(G), host(H)
+    tol = TOL[prec]
+    assert np.abs(E - E0).max() <= tol * np.abs(E0).sum()
+    for p in range(g.n_patches):
+        assert rel(G[p], G0[p]) <= tol, (p, rel(G[p], G0[p]))
+        assert rel(H[p], H0[p]) <= tol, (p, rel(H[p], H0[p]))
+    # the case has bending strain: the pseudo Hessian differs from the exact one beyond tolerance
+    assert max(rel(H0[p], Hx[p]) for p in range(g.n_patches)) > 100 * tol
+
+
+def test_newton_pseudo_hessian_fp64_identical_iteration_counts():
+    """Implicit-Euler steps with the pseudo Hessian: FP64 GPU against the oracle, same counts."""
+    from paper_2312_14839_gb300.bhem import step_params
+    g, rest, q0 = S.sheet_noisy(6, 2e-2, 3)
+    mat = S.Material(1e5, 0.3, 0.01, 200.0)
+    c = S.corner_nodes(g)
+    mask = S.pinned_mask(g, [c[0], c[3]])
+    qfix = q0.reshape(-1).copy()
+    sh = make_shell(g, mat, rest, precision="fp64", hessian="pseudo")
+    P = step_params(dt=1e-2)
+    Po = O.step_params(dt=1e-2, pseudo_hessian=True)
+    q, v = dev(q0.reshape(-1)), torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    qo, vo = q0.reshape(-1).copy(), np.zeros(g.n_dof)
+    for _ in range(3):
+        st = sh.newton_step(q, v, P, mask=dev(mask, torch.uint8), q_fixed=dev(qfix))
+        qo, vo, so = O.newton_step(g, mat, rest, qo, vo, Po, mask=mask, qfix=qfix)
+        assert st["status"] == 0 and so["status"] == 0
+        assert st["newton_iters"] == so["newton_iters"], (st, so)
+        assert rel(host(q), qo) <= 1e-11
+
+
 @pytest.mark.parametrize("case", ["sheet10x10-noisy", "annulus12x3", "annulus7x2-odd-thick", "sheet1x1"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("assembly", ["atomic", "color"])
@@ -218,6 +259,31 @@ def test_newton_config1_mixed_precision():
         assert st["res_final"] <= 1e-8 * st["res0"]
         assert rel(vg, v) <= 1e-5
         q, v = qg.copy(), vg.copy()   # continue the oracle from the GPU state (no drift)
+
+
+@pytest.mark.parametrize("hessian", ["exact", "pseudo"])
+def test_config2_twist_mixed_against_fp64_oracle(hessian):
+    """Config 2 (30x30 sheet, centre twist 2 deg/step, no gravity, dt = 2 ms): mixed-precision GPU
+    steps against the FP64 oracle, each step started from the GPU state. Newton counts agree to
+    within one (FP32 Hessians), every step meets 1e-8, and the states agree to the solver's
+    tolerance."""
+    from paper_2312_14839_gb300.bhem import step_params
+    g, rest = S.flat_sheet(30, 30)
+    mat = THIN
+    sh = make_shell(g, mat, rest, precision="mixed", hessian=hessian)
+    P = step_params(dt=2e-3, gravity=(0.0, 0.0, 0.0))
+    Po = O.step_params(dt=2e-3, gravity=(0.0, 0.0, 0.0), pseudo_hessian=hessian == "pseudo")
+    q, v = dev(rest.reshape(-1)), torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    for k in range(1, 5):
+        mask, vals = S.twist_prescription(g, rest, k)
+        q_prev, v_prev = host(q), host(v)
+        st = sh.newton_step(q, v, P, mask=dev(mask, torch.uint8), q_fixed=dev(vals))
+        qo, vo, so = O.newton_step(g, mat, rest, q_prev, v_prev, Po, mask=mask, qfix=vals)
+        assert st["status"] == 0 and so["status"] == 0
+        assert abs(st["newton_iters"] - so["newton_iters"]) <= 1, (k, st, so)
+        assert st["res_final"] <= 1e-8 * st["res0"]
+        dq_g, dq_o = host(q) - q_prev, qo - q_prev
+        assert rel(dq_g, dq_o) <= 1e-5, (k, rel(dq_g, dq_o))
 
 
 def test_newton_host_buffers_match_device_buffers():

@@ -233,6 +233,48 @@ def test_bending_hessian_terms_match_ad_in_isolation():
     assert np.linalg.norm(Gb - JGb) <= 1e-9 * np.linalg.norm(JGb)
 
 
+@pytest.mark.parametrize("name,build,h,sigma", CASES)
+def test_pseudo_hessian_matches_gauss_newton_ad(name, build, h, sigma):
+    """The pseudo Hessian (App. B, "The pseudo Hessian": the exact one without the second
+    derivatives of beta) against AD of the energy with the bending strain linearised at q: the
+    membrane Hessian plus the Gauss-Newton bending term. Energy and gradient are unchanged."""
+    g, rest = build()
+    mat = S.Material(1e5, 0.3, h, 200.0)
+    q = S.noisy(rest, sigma, 19)
+    for p in (0, g.n_patches - 1):
+        q48, qb48 = O.gather(g, q, p), O.gather(g, rest, p)
+        E, G, Hp = O.element_egh(q48, qb48, g.dxi1, g.dxi2, mat, pseudo=True)
+        _, _, He = O.element_egh(q48, qb48, g.dxi1, g.dxi2, mat)
+        J = energy_jet(q48, qb48, g.dxi1, g.dxi2, mat.young, mat.poisson, mat.thickness, pseudo=True)
+        assert E == pytest.approx(J.v, rel=1e-12)
+        assert np.linalg.norm(G - J.g) <= 1e-12 * np.linalg.norm(J.g)
+        assert np.linalg.norm(Hp - J.H) <= 1e-12 * np.linalg.norm(J.H)
+        # the dropped term is present in this bent state (not a vacuous comparison)
+        assert np.linalg.norm(He - Hp) > 1e-8 * np.linalg.norm(He)
+
+
+def test_pseudo_hessian_equals_exact_without_bending_strain():
+    """Where beta = 0 (H beta = 0) the dropped term vanishes: the curved rest state of the annulus
+    and a uniform in-plane stretch of a flat sheet."""
+    mat = S.Material(1e5, 0.3, 0.05, 200.0)
+    g, rest = S.annulus(10, 3)
+    for p in (0, 13):
+        qb48 = O.gather(g, rest, p)
+        _, _, He = O.element_egh(qb48, qb48, g.dxi1, g.dxi2, mat)
+        _, _, Hp = O.element_egh(qb48, qb48, g.dxi1, g.dxi2, mat, pseudo=True)
+        assert np.linalg.norm(He - Hp) <= 1e-13 * np.linalg.norm(He)
+    g, rest = S.flat_sheet(2, 2)
+    q = rest.reshape(-1, 12).copy()
+    q[:, 0] *= 1.1                                    # x -> 1.1 x, y -> 0.95 y: membrane strain only
+    q[:, 1] *= 0.95
+    q[:, 3] *= 1.1
+    q[:, 7] *= 0.95
+    q48, qb48 = O.gather(g, q, 3), O.gather(g, rest, 3)
+    _, _, He = O.element_egh(q48, qb48, g.dxi1, g.dxi2, mat)
+    _, _, Hp = O.element_egh(q48, qb48, g.dxi1, g.dxi2, mat, pseudo=True)
+    assert np.linalg.norm(He - Hp) <= 1e-13 * np.linalg.norm(He)
+
+
 def test_gradient_and_hessian_central_differences():
     g, rest = S.flat_sheet(2, 2)
     mat = S.Material(1e5, 0.3, 0.05, 200.0)
