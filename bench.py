@@ -412,7 +412,9 @@ def run_twist_bench(args):
     pres = [S.twist_prescription(g, rest, k) for k in range(1, steps + 1)]
     mask = torch.as_tensor(pres[0][0], device=dev)
     qfix = torch.as_tensor(np.stack([v for _, v in pres]), device=dev)
-    P = bhem.step_params(dt=2e-3, gravity=(0.0, 0.0, 0.0), newton_max=100)
+    # the twisted sheet buckles (negative curvature from about step 18): allow long Newton runs
+    # and count the steps that still end unconverged (q then holds the last iterate)
+    P = bhem.step_params(dt=2e-3, gravity=(0.0, 0.0, 0.0), newton_max=200)
     res = {}
     clk_all = []
     for hess in ("exact", "pseudo"):
@@ -425,9 +427,9 @@ def run_twist_bench(args):
             it = []
             for k in range(n):
                 st = sh.newton_step(q, v, P, mask=mask, q_fixed=qfix[k])
-                if st["status"] != 0:
+                if st["status"] not in (0, 6, 7, 8):
                     raise bhem.ShellError(st["status"], f"twist step {k} ({hess})")
-                it.append((st["newton_iters"], st["pcg_iters_total"]))
+                it.append((st["newton_iters"], st["pcg_iters_total"], st["status"], st["regularizations"]))
             return it
         rollout(args.warmup)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -451,10 +453,12 @@ def run_twist_bench(args):
             sh.energy_grad_hess(q_end, mass_scale=1.0 / P.dt ** 2, want_energy=False, want_grad=False)
         ev1.record(stream)
         torch.cuda.synchronize()
-        newton = np.array([a for a, _ in it])
+        newton = np.array([a for a, _, _, _ in it])
         res[hess] = {"steps_per_s": steps / sec, "ms_per_step": sec / steps * 1e3,
                      "newton_iters_mean": float(newton.mean()), "newton_iters_max": int(newton.max()),
-                     "pcg_iters_per_step": float(np.mean([b for _, b in it])),
+                     "pcg_iters_per_step": float(np.mean([b for _, b, _, _ in it])),
+                     "unconverged_steps": int(sum(1 for *_, st_, _ in it if st_ != 0)),
+                     "regularized_solves_per_step": float(np.mean([r for *_, r in it])),
                      "element_pass_us": ev0.elapsed_time(ev1) / 10 * 1e3,
                      "gpu_launches": sh.kernel_launches() - l0}
         sh.close()

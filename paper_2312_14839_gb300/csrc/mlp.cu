@@ -285,12 +285,10 @@ __global__ void k_colstats(long long rows, int cols, const float* __restrict__ X
 // ------------------------------------------------------------------------------------------
 // Shell-side kernels: node features, training targets, warm start
 // ------------------------------------------------------------------------------------------
-__global__ void k_node_features(int n1, int n2, int per_u, int per_v, const double* __restrict__ q,
-                                const double* __restrict__ rest, const double* __restrict__ v,
-                                float* __restrict__ X) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n1 * n2) return;
-  float* out = X + (size_t)i * kIn;
+// the 28 features of node i (shared by the feature kernel and the fused warm start)
+__device__ __forceinline__ void node_features_of(int i, int n1, int n2, int per_u, int per_v,
+                                                 const double* __restrict__ q, const double* __restrict__ rest,
+                                                 const double* __restrict__ v, float* out) {
   double ui[3];
   for (int k = 0; k < 12; ++k) {
     const double u = q[(size_t)i * 12 + k] - rest[(size_t)i * 12 + k];
@@ -315,6 +313,14 @@ __global__ void k_node_features(int n1, int n2, int per_u, int per_v, const doub
   out[27] = 0.25f * (float)cnt;
 }
 
+__global__ void k_node_features(int n1, int n2, int per_u, int per_v, const double* __restrict__ q,
+                                const double* __restrict__ rest, const double* __restrict__ v,
+                                float* __restrict__ X) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n1 * n2) return;
+  node_features_of(i, n1, n2, per_u, per_v, q, rest, v, X + (size_t)i * kIn);
+}
+
 __global__ void k_targets(long long n_dof, const double* __restrict__ q_next, const double* __restrict__ q,
                           const double* __restrict__ v, double dt, float* __restrict__ T) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_dof;
@@ -329,6 +335,129 @@ __global__ void k_compose(int n_nodes, const double* __restrict__ q, const doubl
     const int r = e / kOut, c = e % kOut;
     const float y = Z ? Z[(long long)r * kOutPad + c] * norm[kNormOutStd + c] + norm[kNormOutMean + c] : 0.f;
     warm[e] = q[e] + dt * v[e] + (double)y;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Fused warm start: features -> normalised BF16 input -> 4 layers -> q + dt v + output, one
+// launch. A CTA takes 32 nodes; activations stay in shared memory (BF16, as the GEMM path stores
+// them), weights are read from L2 (every CTA reads the same 280 KB). Each output element is
+// accumulated over K in the same k16 order and with the same epilogue as k_gemm, so the network
+// output equals the unfused path's.
+// ------------------------------------------------------------------------------------------
+constexpr int kFR = 32;                 // nodes per CTA
+constexpr int kLdX = kInPad + 8;        // padded row strides (bank-conflict-free fragment loads)
+constexpr int kLdA = kHid + 8;
+
+__device__ __forceinline__ unsigned lds_pair(const bf16* p) { return *reinterpret_cast<const unsigned*>(p); }
+__device__ __forceinline__ unsigned ldg_pair(const bf16* p) { return __ldg(reinterpret_cast<const unsigned*>(p)); }
+
+__global__ void __launch_bounds__(128)
+k_mlp_warm(int n_nodes, int n1, int n2, int per_u, int per_v, const double* __restrict__ q,
+           const double* __restrict__ rest, const double* __restrict__ v, double dt,
+           const bf16* __restrict__ W0, const bf16* __restrict__ W1, const bf16* __restrict__ W2,
+           const bf16* __restrict__ W3, const float* __restrict__ b0, const float* __restrict__ b1,
+           const float* __restrict__ b2, const float* __restrict__ b3, const float* __restrict__ norm,
+           double* __restrict__ warm) {
+  __shared__ __align__(16) bf16 sX[kFR * kLdX];
+  __shared__ __align__(16) bf16 sA[2][kFR * kLdA];
+  __shared__ float sY[kFR][kOutPad];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+  const int r0 = blockIdx.x * kFR;
+  // features and normalisation (the arithmetic of k_node_features and k_input)
+  if (tid < kFR) {
+    const int i = r0 + tid;
+    float f[kIn];
+    if (i < n_nodes) node_features_of(i, n1, n2, per_u, per_v, q, rest, v, f);
+    for (int c = 0; c < kInPad; ++c) {
+      float x = 0.f;
+      if (i < n_nodes && c < kIn) x = (f[c] - norm[kNormInMean + c]) * norm[kNormInIstd + c];
+      sX[tid * kLdX + c] = __float2bfloat16(x);
+    }
+  }
+  __syncthreads();
+  // hidden layers: warp w computes output columns [64 w, 64 w + 64) of all 32 rows
+  const bf16* in = sX;
+  int ldin = kLdX, K = kInPad;
+  for (int l = 0; l < kLayers - 1; ++l) {
+    const bf16* W = l == 0 ? W0 : l == 1 ? W1 : W2;
+    const float* bias = l == 0 ? b0 : l == 1 ? b1 : b2;
+    float acc[2][8][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+    for (int kk = 0; kk < K; kk += 16) {
+      unsigned a[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const bf16* ar = in + (mt * 16 + g) * ldin + kk + 2 * t;
+        a[mt][0] = lds_pair(ar);
+        a[mt][1] = lds_pair(ar + 8 * ldin);
+        a[mt][2] = lds_pair(ar + 8);
+        a[mt][3] = lds_pair(ar + 8 * ldin + 8);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const bf16* br = W + (size_t)(warp * 64 + nt * 8 + g) * K + kk + 2 * t;
+        const unsigned b[2] = {ldg_pair(br), ldg_pair(br + 8)};
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) mma_bf16(acc[mt][nt], a[mt], b);
+      }
+    }
+    bf16* out = sA[l & 1];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int m = mt * 16 + g + (e >= 2 ? 8 : 0);
+          const int n = warp * 64 + nt * 8 + 2 * t + (e & 1);
+          out[m * kLdA + n] = __float2bfloat16(gelu(acc[mt][nt][e] + bias[n]));
+        }
+    __syncthreads();
+    in = out;
+    ldin = kLdA;
+    K = kHid;
+  }
+  // output layer (16 padded columns): warps 0 and 1 take 8 columns each
+  if (warp < 2) {
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    for (int kk = 0; kk < kHid; kk += 16) {
+      unsigned a[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const bf16* ar = in + (mt * 16 + g) * kLdA + kk + 2 * t;
+        a[mt][0] = lds_pair(ar);
+        a[mt][1] = lds_pair(ar + 8 * kLdA);
+        a[mt][2] = lds_pair(ar + 8);
+        a[mt][3] = lds_pair(ar + 8 * kLdA + 8);
+      }
+      const bf16* br = W3 + (size_t)(warp * 8 + g) * kHid + kk + 2 * t;
+      const unsigned b[2] = {ldg_pair(br), ldg_pair(br + 8)};
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) mma_bf16(acc[mt], a[mt], b);
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int m = mt * 16 + g + (e >= 2 ? 8 : 0);
+        const int n = warp * 8 + 2 * t + (e & 1);
+        sY[m][n] = acc[mt][e] + b3[n];
+      }
+  }
+  __syncthreads();
+  // warm = q + dt v + out_std * y + out_mean (the arithmetic of k_compose)
+  for (int e = tid; e < kFR * kOut; e += blockDim.x) {
+    const int r = e / kOut, c = e % kOut, i = r0 + r;
+    if (i >= n_nodes) continue;
+    const size_t gi = (size_t)i * 12 + c;
+    const float y = sY[r][c] * norm[kNormOutStd + c] + norm[kNormOutMean + c];
+    warm[gi] = q[gi] + dt * v[gi] + (double)y;
   }
 }
 
@@ -740,12 +869,9 @@ extern "C" shell_status shell_mlp_warm_start(shell_mlp_t* M, shell_t* shell, con
     ++s.launches;
     return SHELL_OK;
   }
-  if (s.n_nodes > M->max_rows) return fail(SHELL_ERR_ARG, "shell has more nodes than the network's max_rows");
-  BHEM_TRY(shell_node_features(shell, q, v, M->Xraw));
-  BHEM_TRY(stage_input(*M, M->Xraw, s.n_nodes, nullptr, s.n_nodes, s.stream));
-  BHEM_TRY(forward(*M, s.n_nodes, s.stream));
-  k_compose<<<eblocks((long long)s.n_nodes * kOut), 256, 0, s.stream>>>(s.n_nodes, q, v, dt, M->Z[kLayers - 1],
-                                                                        M->norm, warm);
+  k_mlp_warm<<<(s.n_nodes + kFR - 1) / kFR, 128, 0, s.stream>>>(
+      s.n_nodes, s.n1, s.n2, s.grid.periodic_u, s.grid.periodic_v, q, s.d_rest, v, dt, M->Wb[0], M->Wb[1],
+      M->Wb[2], M->Wb[3], M->b[0], M->b[1], M->b[2], M->b[3], M->norm, warm);
   BHEM_CUDA(cudaGetLastError());
   ++M->launches;
   return SHELL_OK;

@@ -227,3 +227,25 @@ def test_learned_warm_start_gains():
     assert lrn["mean_newton"] < zero["mean_newton"], info
     assert diff <= 1e-4 * disp, info
     net.close()
+
+
+@pytest.mark.parametrize("grid", [(11, 6), (64, 64)])
+def test_fused_warm_start_matches_gemm_path(grid):
+    """shell_mlp_warm_start (one fused launch) against the unfused path: node features ->
+    shell_mlp_forward (tensor-core GEMM kernels) -> q + dt v + y. Both accumulate every output in
+    the same k16 order with the same epilogues, so the network outputs agree to the rounding of
+    the final FP64 sum."""
+    from paper_2312_14839_gb300 import bhem
+    g, rest = S.flat_sheet(*grid)
+    q = S.noisy(rest, 1e-2, 90).reshape(-1)
+    v = np.random.default_rng(91).normal(0, 0.1, g.n_dof)
+    net, _, _ = _net(g.n_nodes, 92, (np.zeros(28), np.full(28, 0.05), np.zeros(12), np.full(12, 1e-4)))
+    dt = 1e-3
+    with bhem.Shell(g, S.SHEET_MATERIAL, rest.reshape(-1)) as sh:
+        qd, vd = dev(q), dev(v)
+        w = host(net.warm_start(sh, qd, vd, dt))
+        Y = host(net.forward(bhem.node_features(sh, qd, vd))).reshape(-1)
+    y_fused = w - (q + dt * v)
+    scale = np.abs(Y).max()
+    assert np.abs(y_fused - Y).max() <= 1e-9 * scale + 8 * 2.0 ** -52 * np.abs(q).max()
+    net.close()
