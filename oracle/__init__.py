@@ -4,8 +4,8 @@ TEST INFRASTRUCTURE: only the tests, ``__graft_entry__.smoke()`` and the CPU-bas
 ``bench.py`` may import this package. The CUDA library and its Python binding never do, and the
 two share no code.
 
-The C source follows the paper's formulas step by step (Sec. 3, Sec. 4, Sec. 6.1, App. A, App. B);
-this wrapper only marshals numpy arrays.
+The C sources follow the paper's formulas step by step (``bhem_oracle.c``: Sec. 3, Sec. 4, Sec. 6.1,
+App. A, App. B; ``ray_oracle.c``: Sec. 5); this wrapper only marshals numpy arrays.
 """
 from __future__ import annotations
 
@@ -17,7 +17,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "bhem_oracle.c")
+_SRCS = [os.path.join(_HERE, "bhem_oracle.c"), os.path.join(_HERE, "ray_oracle.c")]
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
 _lock = threading.Lock()
@@ -49,10 +49,10 @@ class StepStats(C.Structure):
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, no target-specific flags) into oracle/_lib."""
     with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f) for f in _SRCS):
             os.makedirs(_LIBDIR, exist_ok=True)
             tmp = _LIB + f".{os.getpid()}.tmp"
-            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, *_SRCS, "-lm"])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -83,6 +83,12 @@ def _load():
         lib.og_kind_scale.argtypes = [i, p, p, p, p, p]
         lib.og_newton_step.restype = i
         lib.og_newton_step.argtypes = [p, p, p, p, p, p, p, p, p, p]
+        lib.og_bezier_patch.argtypes = [p, p, i, p]
+        lib.og_bezier_eval.argtypes = [p, d, d, p, p, p]
+        lib.og_bezier_sub.argtypes = [p, d, d, d, d, p]
+        lib.og_ray_box.restype = i
+        lib.og_ray_box.argtypes = [p, p, p, p, p, p, p]
+        lib.og_trace_rays.argtypes = [p, p, i, p, p, i, p, p, p, p, p]
         _lib = lib
     return _lib
 
@@ -268,3 +274,60 @@ def newton_step(g, mat, rest, q, v, params: StepParams, mask=None, qfix=None, wa
                            _ptr(m), _ptr(qf), _ptr(q), _ptr(v), _ptr(w), C.byref(st))
     stats = {f: getattr(st, f) for f, _ in StepStats._fields_}
     return q, v, stats
+
+
+# ---------------------------------------------------------------------------------------------
+# Static ray-patch intersection (Sec. 5)
+# ---------------------------------------------------------------------------------------------
+RAY_HIT, RAY_LIMIT = 1, 2
+
+
+def bezier_patch(g, q, patch: int):
+    """Bezier control points [4, 4, 3] of one patch (i along theta1, j along theta2)."""
+    q = _f64(q).reshape(-1)
+    P = np.zeros((4, 4, 3))
+    _load().og_bezier_patch(C.byref(_grid(g)), _ptr(q), int(patch), _ptr(P))
+    return P
+
+
+def bezier_eval(P, u: float, v: float):
+    """(x, x_u, x_v) of a Bezier patch at local (u, v) (derivatives with respect to theta)."""
+    P = _f64(P)
+    x, xu, xv = np.zeros(3), np.zeros(3), np.zeros(3)
+    _load().og_bezier_eval(_ptr(P), float(u), float(v), _ptr(x), _ptr(xu), _ptr(xv))
+    return x, xu, xv
+
+
+def bezier_sub(P, u0, u1, v0, v1):
+    """Control points [4, 4, 3] of the sub-patch [u0, u1] x [v0, v1] (De Casteljau)."""
+    P = _f64(P)
+    S = np.zeros((4, 4, 3))
+    _load().og_bezier_sub(_ptr(P), float(u0), float(u1), float(v0), float(v1), _ptr(S))
+    return S
+
+
+def ray_box(S, origin, direction):
+    """(hit, tau_min, tau_max, largest box side) of Eq. ineqray for control points S [4, 4, 3]."""
+    S, o, d = _f64(S), _f64(origin), _f64(direction)
+    inv = np.array([1.0 / x if x != 0.0 else 0.0 for x in d])
+    t0, t1, ext = C.c_double(), C.c_double(), C.c_double()
+    hit = _load().og_ray_box(_ptr(S), _ptr(o), _ptr(d), _ptr(inv), C.byref(t0), C.byref(t1), C.byref(ext))
+    return bool(hit), t0.value, t1.value, ext.value
+
+
+def trace_rays(g, q, origins, dirs, use_newton: bool = True, want_stats: bool = False):
+    """Nearest hits of rays o + tau d (unit d) with the shell.
+
+    Returns (tau [n] (inf on a miss), patch [n] (-1), uv [n, 2] local parameters, flags [n]
+    (RAY_HIT, RAY_LIMIT)) and, with want_stats, stats [n, 2] = (candidates split, peak heap size).
+    """
+    q = _f64(q).reshape(-1)
+    origins, dirs = _f64(origins).reshape(-1, 3), _f64(dirs).reshape(-1, 3)
+    n = origins.shape[0]
+    tau, uv = np.zeros(n), np.zeros((n, 2))
+    patch, flags = np.zeros(n, dtype=np.int32), np.zeros(n, dtype=np.int32)
+    stats = np.zeros((n, 2), dtype=np.int32) if want_stats else None
+    _load().og_trace_rays(C.byref(_grid(g)), _ptr(q), n, _ptr(origins), _ptr(dirs), int(bool(use_newton)),
+                          _ptr(tau), _ptr(patch), _ptr(uv), _ptr(flags), _ptr(stats))
+    out = (tau, patch, uv, flags)
+    return out + (stats,) if want_stats else out

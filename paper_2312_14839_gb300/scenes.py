@@ -90,6 +90,20 @@ def annulus(nu: int, nv: int, r0: float = 0.2, r1: float = 0.7):
     return g, rest
 
 
+def cylinder(nu: int, nv: int, radius: float = 0.3, length: float = 1.0):
+    """Cylinder about the z axis, periodic in u: xi^1 = angle in [0, 2 pi), xi^2 = height in
+    [0, length]. Nodal values are the exact map and its derivatives."""
+    g = Grid(nu, nv, True, False, 2.0 * math.pi / nu, length / nv)
+    j, i = np.meshgrid(np.arange(g.n2), np.arange(g.n1), indexing="ij")
+    th = (i * g.dxi1).ravel()
+    c, s = np.cos(th), np.sin(th)
+    rest = np.zeros((g.n_nodes, DOF_PER_NODE))
+    rest[:, 0], rest[:, 1], rest[:, 2] = radius * c, radius * s, (j * g.dxi2).ravel()
+    rest[:, 3], rest[:, 4] = -radius * s, radius * c
+    rest[:, 8] = 1.0
+    return g, rest
+
+
 def node_params(g: Grid, xi0=(0.0, 0.0)):
     """Parameter coordinates (xi^1, xi^2) of every node."""
     j, i = np.meshgrid(np.arange(g.n2), np.arange(g.n1), indexing="ij")
@@ -255,3 +269,37 @@ def mlp_init_params(seed: int, last_scale: float = 0.1) -> np.ndarray:
             W *= last_scale
         parts += [W.reshape(-1), np.zeros(fo)]
     return np.concatenate(parts).astype(np.float32)
+
+
+def camera_rays(width: int, height: int, eye, target, up=(0.0, 0.0, 1.0), fov_deg: float = 50.0):
+    """Pinhole camera rays through pixel centres: origins [n, 3] (all at eye) and unit
+    directions [n, 3], row-major with the first row at the top of the image."""
+    eye, target, up = (np.asarray(a, dtype=np.float64) for a in (eye, target, up))
+    fwd = target - eye
+    fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, up)
+    right /= np.linalg.norm(right)
+    upv = np.cross(right, fwd)
+    half = math.tan(math.radians(fov_deg) / 2.0)
+    aspect = width / height
+    px = ((np.arange(width) + 0.5) / width * 2.0 - 1.0) * half * aspect
+    py = (1.0 - (np.arange(height) + 0.5) / height * 2.0) * half
+    PY, PX = np.meshgrid(py, px, indexing="ij")
+    d = fwd[None, :] + PX.reshape(-1, 1) * right[None, :] + PY.reshape(-1, 1) * upv[None, :]
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    o = np.broadcast_to(eye, d.shape).copy()
+    return o, d
+
+
+def ray_scenes():
+    """Static ray-intersection scenes, name -> (grid, q [n_nodes, 12], eye, target):
+    a flat 10 x 10 sheet, a 10 x 10 cylinder (r 0.3 m, 1 m high) and a 30 x 30 sheet draped by the
+    sinusoid field (5 cm), each seen from a camera above and to the side."""
+    g1, q1 = flat_sheet(10, 10)
+    g2, q2 = cylinder(10, 10)
+    g3, _, q3 = sheet_sinusoid(30, 3, 0.05)
+    return {
+        "plane": (g1, q1, (0.3, -0.6, 0.8), (0.5, 0.5, 0.0)),
+        "cylinder": (g2, q2, (1.2, 0.4, 0.9), (0.0, 0.0, 0.5)),
+        "drape": (g3, q3, (0.5, -0.9, 0.8), (0.5, 0.5, 0.0)),
+    }
