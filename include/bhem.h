@@ -331,6 +331,45 @@ SHELL_API shell_status shell_mlp_warm_start(shell_mlp_t* mlp, shell_t* shell, co
    and frees a small device buffer. */
 SHELL_API shell_status shell_measure_fma_peak(int fp64, int iters, void* stream, double* flops_per_s);
 
+/* ------------------------------------------------------------------------------------------ */
+/* Static ray-patch intersection (Sec. 5, Eq. ray, Eq. ineqray)                                */
+/* ------------------------------------------------------------------------------------------ */
+typedef enum { SHELL_RAY_MIDPOINT = 0, SHELL_RAY_NEWTON = 1 } shell_ray_variant;
+#define SHELL_RAY_HIT 1      /* flags bit: the ray meets the shell; tau, patch, uv are written  */
+#define SHELL_RAY_LIMIT 2    /* flags bit: 65536 candidates were split and the search stopped  */
+#define SHELL_RAY_OVERFLOW 4 /* flags bit: the candidate heap was full even in the second pass
+                                (8192 entries) or more than 65536 rays of the call needed that
+                                pass; the ray is reported as a miss and its result is void    */
+#define SHELL_RAY_HEAP 256   /* candidate heap entries per ray in the first pass                */
+
+/* Nearest intersection of each ray x(tau) = o + tau d (tau >= 0, d a unit vector) with the shell
+   at configuration q, by the subdivision search of Sec. 5: every patch in Bezier form (Hermite
+   data b1 = a + a'/3, b2 = b - b'/3 per direction), ray-box tests of the control points' boxes
+   (Eq. ineqray), a min-heap of candidate sub-patches keyed by the box's entry time, and
+   De Casteljau sub-patches. variant SHELL_RAY_MIDPOINT splits every candidate at its parameter
+   midpoint (Fig. submid); SHELL_RAY_NEWTON first runs Newton's method on x(u, v) = o + tau d
+   from the candidate's centre (at most 12 iterations) and, on a root inside it, abandons the
+   root's neighbourhood (1e-3 of the candidate's parameter extent) and splits the rest into four
+   rectangles (Fig. subany). A candidate whose control-point box is at most 1e-9 on every side is
+   an intersection at the midpoint of its tau interval. All arithmetic is FP64.
+     q        device [n_dof] nodal DOFs (12 per node)
+     origins  device [n_rays][3], dirs device [n_rays][3] (unit length; a zero component is fine)
+     tau      device [n_rays]: nearest tau on a hit, +infinity on a miss
+     patch    device [n_rays]: patch id of the hit, -1 on a miss
+     uv       device [n_rays][2]: local patch parameters in [0, 1]^2 of the hit, 0 on a miss
+     flags    device [n_rays]: SHELL_RAY_* bits
+     stats    device [n_rays][2] or NULL: candidates split, largest heap size
+   A ray whose candidates outgrow the SHELL_RAY_HEAP-entry first-pass heap is traced again from
+   the start by a second kernel with an 8192-entry heap, so every result is that of an unbounded
+   heap unless SHELL_RAY_OVERFLOW is set. n_rays in [0, 2^31 - 1]; 0 does nothing. Asynchronous
+   on the shell's stream (three kernel launches and a 4-byte memset). The first call on a shell
+   allocates 448 bytes per patch plus 64.3 MB of library-owned device memory (Bezier nets and
+   boxes, the second pass's heaps), kept until shell_destroy; calls on one shell must not
+   overlap on the GPU. */
+SHELL_API shell_status shell_trace_rays(shell_t* shell, const double* q, long long n_rays, const double* origins,
+                                        const double* dirs, int variant, double* tau, int* patch, double* uv,
+                                        int* flags, int* stats);
+
 /* Number of CUDA kernels this shell has launched since shell_create (host counter; counts the
    launches of the library's own kernels, not memset/memcpy operations). */
 SHELL_API shell_status shell_kernel_launches(const shell_t* shell, long long* count);

@@ -117,6 +117,7 @@ def load():
                 "shell_warm_targets": [ll, p, p, p, d, p, p],
                 "shell_mlp_warm_start": [p, p, p, p, d, p],
                 "shell_measure_fma_peak": [i, i, p, p],
+                "shell_trace_rays": [p, p, ll, p, p, i, p, p, p, p, p],
             }
             for name, args in sigs.items():
                 fn = getattr(lib, name)
@@ -155,6 +156,10 @@ def _stream_handle(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return stream, C.c_void_p(stream.cuda_stream)
+
+
+RAY_VARIANT = {"midpoint": 0, "newton": 1}
+RAY_HIT, RAY_LIMIT, RAY_OVERFLOW, RAY_HEAP = 1, 2, 4, 256
 
 
 def step_params(dt=1e-3, gravity=(0.0, 0.0, -9.81), newton_rtol=1e-8, newton_max=50,
@@ -287,6 +292,27 @@ class Shell:
             y = torch.empty(x.shape, dtype=x.dtype, device=x.device)
         _check(load().shell_spmv(self._h, _ptr(x), int(x.dtype == torch.float32), _ptr(y)))
         return y
+
+    def trace_rays(self, q, origins, dirs, variant="newton", out=None, want_stats=False):
+        """Nearest hits of rays o + tau d (unit d) with the shell at q (Sec. 5), on the shell's
+        stream. q [n_dof], origins / dirs [n, 3]: FP64 CUDA tensors. Returns a dict of CUDA tensors
+        tau [n] (inf on a miss), patch [n] (-1), uv [n, 2], flags [n] (RAY_HIT, RAY_LIMIT,
+        RAY_OVERFLOW bits) and, with want_stats, stats [n, 2] (candidates split, peak heap size).
+        out: a dict of the same tensors to fill instead of allocating."""
+        import torch
+        n = origins.shape[0]
+        dev = origins.device
+        if out is None:
+            out = {"tau": torch.empty(n, dtype=torch.float64, device=dev),
+                   "patch": torch.empty(n, dtype=torch.int32, device=dev),
+                   "uv": torch.empty((n, 2), dtype=torch.float64, device=dev),
+                   "flags": torch.empty(n, dtype=torch.int32, device=dev)}
+            if want_stats:
+                out["stats"] = torch.empty((n, 2), dtype=torch.int32, device=dev)
+        _check(load().shell_trace_rays(self._h, _ptr(q), int(n), _ptr(origins), _ptr(dirs), RAY_VARIANT[variant],
+                                       _ptr(out["tau"]), _ptr(out["patch"]), _ptr(out["uv"]), _ptr(out["flags"]),
+                                       _ptr(out.get("stats"))))
+        return out
 
     def newton_step(self, q, v, params: shell_step_params, mask=None, q_fixed=None, warm=None,
                     raise_on_error=False):

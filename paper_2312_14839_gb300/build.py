@@ -21,6 +21,10 @@ LIB = os.path.join(LIBDIR, "libbhem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden"]
+# Per-file flags. rays.cu: no mul-add contraction, so every FP64 product and sum is rounded on
+# its own, as in plain C; ray-patch traversal decisions (heap order, refinement, Newton
+# convergence) then depend on the same roundings as a sequential C program of the same steps.
+FILE_FLAGS = {"rays.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -53,7 +57,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(LIBDIR, "obj", os.path.basename(src) + ".o")
-        cmd = [nv, *ARCH, *FLAGS, *extra, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
+        cmd = [nv, *ARCH, *FLAGS, *FILE_FLAGS.get(os.path.basename(src), []), *extra, "-I", INCLUDE, "-I", CSRC,
+               "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

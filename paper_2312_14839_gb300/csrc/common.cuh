@@ -118,6 +118,10 @@ struct Shell {
   int* h_err = nullptr;             // pinned
   double* d_energy_tmp = nullptr;
 
+  // ray-patch intersection scratch, allocated by the first shell_trace_rays (rays.cu): the
+  // second-pass heaps, per-patch Bezier nets [np][3][4][4], root boxes [np][8], the redo list
+  void* d_ray_nets = nullptr;
+
   Reduce red{};
   long long launches = 0;           // kernels launched by this shell (introspection)
 

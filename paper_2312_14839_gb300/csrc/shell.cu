@@ -123,7 +123,8 @@ static void destroy_shell(shell_s* s) {
                   s->d_x, s->d_r, s->d_z, s->d_p, s->d_Ap, s->d_p32, s->d_x32, s->d_r32, s->d_z32, s->d_Ap32, s->d_Dinv, s->d_phi64, s->d_phi32,
                   s->d_pcg, s->d_qn, s->d_y, s->d_g, s->d_gin, s->d_d, s->d_Md, s->d_Ep,
                   s->d_qwork, s->d_vwork, s->d_qfix, s->d_warm, s->d_mask, s->d_ns, s->d_err,
-                  s->d_energy_tmp, s->red.partials, s->red.ticket, s->d_rhs, s->d_g2, s->d_Ep2};
+                  s->d_energy_tmp, s->red.partials, s->red.ticket, s->d_rhs, s->d_g2, s->d_Ep2,
+                  s->d_ray_nets};
   for (void* p : ptrs) dfree(p);
   if (s->h_ns) cudaFreeHost(s->h_ns);
   if (s->h_pcg) cudaFreeHost(s->h_pcg);

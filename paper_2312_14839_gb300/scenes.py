@@ -301,5 +301,5 @@ def ray_scenes():
     return {
         "plane": (g1, q1, (0.3, -0.6, 0.8), (0.5, 0.5, 0.0)),
         "cylinder": (g2, q2, (1.2, 0.4, 0.9), (0.0, 0.0, 0.5)),
-        "drape": (g3, q3, (0.5, -0.9, 0.8), (0.5, 0.5, 0.0)),
+        "drape": (g3, q3, (0.5, -0.35, 0.55), (0.5, 0.5, 0.0)),
     }

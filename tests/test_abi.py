@@ -37,3 +37,4 @@ def test_argument_errors_need_no_gpu():
     assert lib.shell_create(None, None, None, None, None, None) == 1   # SHELL_ERR_ARG
     assert b"NULL" in lib.shell_last_error()
     assert lib.shell_destroy(None) == 0
+    assert lib.shell_trace_rays(None, None, 0, None, None, 1, None, None, None, None, None) == 1
