@@ -46,6 +46,9 @@ WORKLOADS = {
     "twist30": "30x30-patch 1 m sheet, centre node held and its x_,1, x_,2 rotated 2 deg per step about +z, "
                "no gravity, dt = 2 ms, 200 implicit-Euler steps to 1e-8 (PCG to 1e-6), mixed precision; "
                "exact Hessian against the pseudo Hessian (App. B)",
+    "rays_drape": "static ray-patch intersection (Sec. 5): 1024x768 pinhole camera (786,432 rays) on the "
+                  "30x30-patch 1 m sheet draped by the 8-term sinusoid field (5 cm), FP64, Newton split "
+                  "(Fig. subany); midpoint split and the plane / cylinder scenes reported beside it",
     "annulus280x5": "280x5-patch periodic annular strip, 8-term sinusoid displacement (5 cm), "
                     "FP32 element eval + BSR assembly + 50-iteration block-Jacobi PCG, FP64 "
                     "residual/reductions",
@@ -397,6 +400,139 @@ def alu_rooflines(sh, q_d, P, n_patches, stream, reps=5):
     return out
 
 
+# FP64 operations per step of the ray search (adds, multiplies, compares, min/max, divisions and
+# square roots one each), counted from the kernel source: a patch's root box test, one candidate
+# box (blossoming of 8 curves per coordinate and the slab test), one Newton iteration, and the
+# fixed work of one split (Newton variant: centre evaluation, projection, acceptance, pinwheel).
+RAY_OPS_ROOT = 25
+RAY_OPS_BOX = 1324
+RAY_OPS_NEWTON_ITER = 367
+RAY_OPS_SPLIT = {"midpoint": 11, "newton": 311}
+
+
+def ray_ops(stats, n_patches: int, variant: str) -> float:
+    """Algorithmic FP64 operations of one trace from the per-ray counts (stats [n, 4])."""
+    st = stats.astype(np.int64)
+    return float(RAY_OPS_ROOT * n_patches * len(st) + RAY_OPS_BOX * (st[:, 2] - n_patches).sum()
+                 + RAY_OPS_NEWTON_ITER * st[:, 3].sum() + RAY_OPS_SPLIT[variant] * st[:, 0].sum())
+
+
+def run_rays_bench(args):
+    """Static ray-patch intersection: rays/s on the draped sheet (one JSON line)."""
+    import torch
+    import oracle as O
+    from paper_2312_14839_gb300 import bhem
+    from paper_2312_14839_gb300 import scenes as S
+    torch.cuda.set_device(0)
+    bhem.load()
+    dev = torch.device("cuda", 0)
+    W, H = 1024, 768
+    n = W * H
+    scenes = S.ray_scenes()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+
+    def trace_timing(name, variant, steps, warmup, want_e2e=False):
+        g, q, eye, tgt = scenes[name]
+        o, d = S.camera_rays(W, H, eye, tgt)
+        sh = bhem.Shell(g, S.SHEET_MATERIAL, torch.as_tensor(q.reshape(-1), device=dev), precision="fp64")
+        stream = sh.stream
+        dq = torch.as_tensor(q.reshape(-1), dtype=torch.float64, device=dev)
+        do, dd = torch.as_tensor(o, device=dev), torch.as_tensor(d, device=dev)
+        out = sh.trace_rays(dq, do, dd, variant=variant, want_stats=True)
+        for _ in range(warmup):
+            sh.trace_rays(dq, do, dd, variant=variant, out=out)
+        torch.cuda.synchronize()
+        stats = out["stats"].cpu().numpy()
+        flags = out["flags"].cpu().numpy()
+        res = {"hit_fraction": float((flags & 1).mean()), "flagged": int((flags & 6).astype(bool).sum()),
+               "splits_mean": float(stats[:, 0].mean()), "splits_max": int(stats[:, 0].max()),
+               "heap_peak_max": int(stats[:, 1].max()), "newton_iters_mean": float(stats[:, 3].mean()),
+               "fp64_ops_per_trace": ray_ops(stats, g.n_patches, variant)}
+        l0 = sh.kernel_launches()
+        ms = []
+        clk = None
+        with ClockSampler(0) as c:
+            for _ in range(steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sh.trace_rays(dq, do, dd, variant=variant, out=out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        clk = c.summary()
+        res["gpu_launches_per_trace"] = (sh.kernel_launches() - l0) / max(steps, 1)
+        res["ms_per_trace"] = float(np.mean(ms))
+        res["rays_per_s"] = n / (res["ms_per_trace"] / 1e3)
+        if want_e2e:
+            # the public call with host data: pinned host rays in, host hits out, every step
+            ho, hd = torch.as_tensor(o).pin_memory(), torch.as_tensor(d).pin_memory()
+            host = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items() if k != "stats"}
+            dev_out = {k: v for k, v in out.items() if k != "stats"}
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                for _ in range(steps):
+                    do.copy_(ho, non_blocking=True)
+                    dd.copy_(hd, non_blocking=True)
+                    sh.trace_rays(dq, do, dd, variant=variant, out=dev_out)
+                    for k in host:
+                        host[k].copy_(dev_out[k], non_blocking=True)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            res["e2e"] = {"value": n * steps / sec, "unit": "rays/s",
+                          "h2d_bytes_per_step": int(ho.numel() * 8 + hd.numel() * 8),
+                          "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in host.values()))}
+        sh.close()
+        return res, clk
+
+    main_res, clk = trace_timing("drape", "newton", args.steps, args.warmup, want_e2e=True)
+    others = {}
+    for name in ("drape", "cylinder", "plane"):
+        for variant in ("newton", "midpoint"):
+            if (name, variant) == ("drape", "newton"):
+                continue
+            r, _ = trace_timing(name, variant, 1, 1)
+            others[f"{name}_{variant}"] = {k: r[k] for k in ("rays_per_s", "ms_per_trace", "hit_fraction",
+                                                             "splits_mean", "splits_max", "flagged")}
+    peak64 = bhem.measure_fma_peak(True, 256, torch.cuda.current_stream())
+    peak_ops = peak64 / 2.0     # one FP64 pipe instruction per add, multiply or compare
+    ach = main_res["fp64_ops_per_trace"] / (main_res["ms_per_trace"] / 1e3)
+    # the oracle on a seeded sample of the same frame, one core
+    cpu = None
+    if not args.no_cpu_baseline:
+        g, q, eye, tgt = scenes["drape"]
+        o, d = S.camera_rays(W, H, eye, tgt)
+        idx = np.sort(np.random.default_rng(5).choice(n, 16384, replace=False))
+        O.build()
+        t0 = time.perf_counter()
+        O.trace_rays(g, q, o[idx], d[idx], True)
+        sec = time.perf_counter() - t0
+        cpu = {"value": len(idx) / sec, "unit": "rays/s", "cores": 1, "kind": "oracle",
+               "sample": f"16,384 seeded rays of the same 1024x768 frame, Newton split, {sec:.1f} s"}
+    print(json.dumps({
+        "metric": "rays/s, static ray-patch intersection (Sec. 5)", "value": main_res["rays_per_s"],
+        "unit": "rays/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": main_res["ms_per_trace"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (pinhole camera rays)",
+        "config": {"workload": WORKLOADS["rays_drape"], "rays": n, "patches": 900,
+                   "l2": "flushed (256 MB write) before every timed trace"},
+        "e2e": main_res["e2e"], "gpu_launches": main_res["gpu_launches_per_trace"] * args.steps,
+        "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
+                     "frac": ach / peak_ops, "traffic": None,
+                     "kernel": "k_trace_rays (+ k_ray_nets, k_trace_rays_redo in the same events)",
+                     "work": "FP64 operations counted per ray from its splits, boxes and Newton iterations",
+                     "peak_source": "measured FP64 FMA rate (shell_measure_fma_peak) as instructions/s"},
+        "cpu_baseline": cpu, "search": {k: main_res[k] for k in ("hit_fraction", "flagged", "splits_mean",
+                                                              "splits_max", "heap_peak_max", "newton_iters_mean",
+                                                              "fp64_ops_per_trace")},
+        "other_scenes": others, "clocks": clk,
+    }), flush=True)
+
+
 def run_twist_bench(args):
     """Exact against pseudo Hessian on the twist scene (one JSON line): implicit-Euler steps/s and
     Newton iterations at 1e-8, plus the element pass time of each Hessian."""
@@ -499,6 +635,9 @@ def main():
         return
     if args.workload == "twist30":
         run_twist_bench(args)
+        return
+    if args.workload == "rays_drape":
+        run_rays_bench(args)
         return
 
     import torch

@@ -358,7 +358,8 @@ typedef enum { SHELL_RAY_MIDPOINT = 0, SHELL_RAY_NEWTON = 1 } shell_ray_variant;
      patch    device [n_rays]: patch id of the hit, -1 on a miss
      uv       device [n_rays][2]: local patch parameters in [0, 1]^2 of the hit, 0 on a miss
      flags    device [n_rays]: SHELL_RAY_* bits
-     stats    device [n_rays][2] or NULL: candidates split, largest heap size
+     stats    device [n_rays][4] or NULL: candidates split, largest heap size, candidate boxes
+              formed (one per patch for the roots included), Newton iterations run
    A ray whose candidates outgrow the SHELL_RAY_HEAP-entry first-pass heap is traced again from
    the start by a second kernel with an 8192-entry heap, so every result is that of an unbounded
    heap unless SHELL_RAY_OVERFLOW is set. n_rays in [0, 2^31 - 1]; 0 does nothing. Asynchronous

@@ -319,14 +319,15 @@ def trace_rays(g, q, origins, dirs, use_newton: bool = True, want_stats: bool = 
     """Nearest hits of rays o + tau d (unit d) with the shell.
 
     Returns (tau [n] (inf on a miss), patch [n] (-1), uv [n, 2] local parameters, flags [n]
-    (RAY_HIT, RAY_LIMIT)) and, with want_stats, stats [n, 2] = (candidates split, peak heap size).
+    (RAY_HIT, RAY_LIMIT)) and, with want_stats, stats [n, 4] = (candidates split, peak heap size,
+    sub-patch boxes formed with the patch roots, Newton iterations).
     """
     q = _f64(q).reshape(-1)
     origins, dirs = _f64(origins).reshape(-1, 3), _f64(dirs).reshape(-1, 3)
     n = origins.shape[0]
     tau, uv = np.zeros(n), np.zeros((n, 2))
     patch, flags = np.zeros(n, dtype=np.int32), np.zeros(n, dtype=np.int32)
-    stats = np.zeros((n, 2), dtype=np.int32) if want_stats else None
+    stats = np.zeros((n, 4), dtype=np.int32) if want_stats else None
     _load().og_trace_rays(C.byref(_grid(g)), _ptr(q), n, _ptr(origins), _ptr(dirs), int(bool(use_newton)),
                           _ptr(tau), _ptr(patch), _ptr(uv), _ptr(flags), _ptr(stats))
     out = (tau, patch, uv, flags)

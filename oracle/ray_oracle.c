@@ -208,11 +208,12 @@ static double det3(const double M[3][3]) {
 /* Newton's method on F(u, v, tau) = x(u, v) - o - tau d from (*u, *v, *tau), Jacobian
    [x_u | x_v | -d] solved by Cramer's rule. Returns 1 with the root on convergence. */
 static int newton_root(const double P[4][4][3], const double o[3], const double d[3], double* u, double* v,
-                       double* tau) {
+                       double* tau, int* iters) {
   double uu = *u, vv = *v, tt = *tau;
   const double on = sqrt((o[0] * o[0] + o[1] * o[1]) + o[2] * o[2]);
   for (int it = 0; it < NEWTON_ITERS; ++it) {
     double x[3], xu[3], xv[3], F[3];
+    ++*iters;
     og_bezier_eval(P, uu, vv, x, xu, xv);
     for (int c = 0; c < 3; ++c) F[c] = (x[c] - o[c]) - tt * d[c];
     const double fn = sqrt((F[0] * F[0] + F[1] * F[1]) + F[2] * F[2]);
@@ -238,7 +239,7 @@ static int newton_root(const double P[4][4][3], const double o[3], const double 
 
 /* 3. Binary min-heap of candidate sub-patches keyed by tau_min. */
 typedef struct { double t0, t1, ext, u0, u1, v0, v1; int patch; } og_cand;
-typedef struct { og_cand* a; int n, cap, peak; } og_heap;
+typedef struct { og_cand* a; int n, cap, peak, boxes; } og_heap;
 
 static void heap_push(og_heap* h, og_cand c) {
   if (h->n == h->cap) {
@@ -278,6 +279,7 @@ static void push_sub(og_heap* h, const double P[4][4][3], int p, double u0, doub
                      const double o[3], const double d[3], const double inv[3], double best) {
   if (!(u1 > u0) || !(v1 > v0)) return;
   double S[4][4][3], t0, t1, ext;
+  ++h->boxes;
   og_bezier_sub(P, u0, u1, v0, v1, S);
   if (!og_ray_box(S, o, d, inv, &t0, &t1, &ext) || t0 >= best) return;
   const og_cand c = {t0, t1, ext, u0, u1, v0, v1, p};
@@ -286,14 +288,15 @@ static void push_sub(og_heap* h, const double P[4][4][3], int p, double u0, doub
 
 /* One ray o + tau d (unit d) against the control nets P[np] of all patches. Returns flags:
    bit 0 set on a hit (tau, patch, local (u, v) written), bit 1 set when MAX_EXPANSIONS was
-   reached. stats (may be NULL): [0] candidates split, [1] largest heap size. */
+   reached. stats (may be NULL): [0] candidates split, [1] largest heap size, [2] sub-patch boxes
+   formed (patch roots included), [3] Newton iterations run. */
 static int trace_one(const double (*P)[4][4][3], int np, const double o[3], const double d[3], int use_newton,
-                     double* tau_out, int* patch_out, double* u_out, double* v_out, int stats[2]) {
+                     double* tau_out, int* patch_out, double* u_out, double* v_out, int stats[4]) {
   double inv[3];
   for (int c = 0; c < 3; ++c) inv[c] = d[c] != 0.0 ? 1.0 / d[c] : 0.0;
-  og_heap h = {NULL, 0, 0, 0};
+  og_heap h = {NULL, 0, 0, 0, 0};
   double best = INFINITY, bu = 0.0, bv = 0.0;
-  int bp = -1, nexp = 0, flags = 0;
+  int bp = -1, nexp = 0, flags = 0, newton_iters = 0;
   for (int p = 0; p < np; ++p) push_sub(&h, P[p], p, 0.0, 1.0, 0.0, 1.0, o, d, inv, best);
   while (h.n > 0) {
     const og_cand c = heap_pop(&h);
@@ -313,7 +316,7 @@ static int trace_one(const double (*P)[4][4][3], int np, const double o[3], cons
       double x[3], xu[3], xv[3];
       og_bezier_eval(Pp, um, vm, x, xu, xv);
       double u = um, v = vm, t = ((x[0] - o[0]) * d[0] + (x[1] - o[1]) * d[1]) + (x[2] - o[2]) * d[2];
-      if (newton_root(Pp, o, d, &u, &v, &t) && u >= c.u0 && u <= c.u1 && v >= c.v0 && v <= c.v1 && t >= 0.0) {
+      if (newton_root(Pp, o, d, &u, &v, &t, &newton_iters) && u >= c.u0 && u <= c.u1 && v >= c.v0 && v <= c.v1 && t >= 0.0) {
         if (t < best) { best = t; bp = c.patch; bu = u; bv = v; }
         /* Fig. subany: drop [a1, a2] x [b1, b2] around the root, four rectangles remain */
         const double hu = NBHD * (c.u1 - c.u0), hv = NBHD * (c.v1 - c.v0);
@@ -333,7 +336,7 @@ static int trace_one(const double (*P)[4][4][3], int np, const double o[3], cons
     push_sub(&h, Pp, c.patch, um, c.u1, c.v0, vm, o, d, inv, best);
   }
   free(h.a);
-  if (stats) { stats[0] = nexp; stats[1] = h.peak; }
+  if (stats) { stats[0] = nexp; stats[1] = h.peak; stats[2] = h.boxes; stats[3] = newton_iters; }
   if (bp >= 0) {
     flags |= 1;
     *tau_out = best; *patch_out = bp; *u_out = bu; *v_out = bv;
@@ -342,7 +345,7 @@ static int trace_one(const double (*P)[4][4][3], int np, const double o[3], cons
 }
 
 /* Many rays: origins, dirs [n][3]. Outputs: tau [n] (INFINITY on a miss), patch [n] (-1 on a
-   miss), uv [n][2] (local parameters, 0 on a miss), flags [n] (as trace_one), stats [n][2]
+   miss), uv [n][2] (local parameters, 0 on a miss), flags [n] (as trace_one), stats [n][4]
    (may be NULL). Control nets are formed once for all rays. */
 void og_trace_rays(const og_grid* g, const double* q, int n, const double* origins, const double* dirs,
                    int use_newton, double* tau, int* patch, double* uv, int* flags, int* stats) {
@@ -353,7 +356,7 @@ void og_trace_rays(const og_grid* g, const double* q, int n, const double* origi
     double t = INFINITY, u = 0.0, v = 0.0;
     int p = -1;
     const int f = trace_one((const double(*)[4][4][3])P, np, origins + 3 * (size_t)k, dirs + 3 * (size_t)k,
-                            use_newton, &t, &p, &u, &v, stats ? stats + 2 * (size_t)k : NULL);
+                            use_newton, &t, &p, &u, &v, stats ? stats + 4 * (size_t)k : NULL);
     if (f & 1) {
       tau[k] = t; patch[k] = p; uv[2 * k] = u; uv[2 * k + 1] = v;
     } else {

@@ -297,7 +297,8 @@ class Shell:
         """Nearest hits of rays o + tau d (unit d) with the shell at q (Sec. 5), on the shell's
         stream. q [n_dof], origins / dirs [n, 3]: FP64 CUDA tensors. Returns a dict of CUDA tensors
         tau [n] (inf on a miss), patch [n] (-1), uv [n, 2], flags [n] (RAY_HIT, RAY_LIMIT,
-        RAY_OVERFLOW bits) and, with want_stats, stats [n, 2] (candidates split, peak heap size).
+        RAY_OVERFLOW bits) and, with want_stats, stats [n, 4] (candidates split, peak heap size,
+        candidate boxes formed including one root box per patch, Newton iterations).
         out: a dict of the same tensors to fill instead of allocating."""
         import torch
         n = origins.shape[0]
@@ -308,7 +309,7 @@ class Shell:
                    "uv": torch.empty((n, 2), dtype=torch.float64, device=dev),
                    "flags": torch.empty(n, dtype=torch.int32, device=dev)}
             if want_stats:
-                out["stats"] = torch.empty((n, 2), dtype=torch.int32, device=dev)
+                out["stats"] = torch.empty((n, 4), dtype=torch.int32, device=dev)
         _check(load().shell_trace_rays(self._h, _ptr(q), int(n), _ptr(origins), _ptr(dirs), RAY_VARIANT[variant],
                                        _ptr(out["tau"]), _ptr(out["patch"]), _ptr(out["uv"]), _ptr(out["flags"]),
                                        _ptr(out.get("stats"))))

@@ -203,10 +203,11 @@ __device__ __forceinline__ double det3(const double M[3][3]) {
 // Newton's method on F(u, v, tau) = x(u, v) - o - tau d, Jacobian [x_u | x_v | -d] by Cramer's
 // rule. True with the root in (u, v, tau) on convergence.
 __device__ bool newton_root(const double* __restrict__ P, const double o[3], const double d[3], double on,
-                            double& u, double& v, double& tau) {
+                            double& u, double& v, double& tau, int& iters) {
   double uu = u, vv = v, tt = tau;
   for (int it = 0; it < kNewtonIters; ++it) {
     double x[3], xu[3], xv[3], F[3];
+    ++iters;
     bezier_eval(P, uu, vv, x, xu, xv);
 #pragma unroll
     for (int c = 0; c < 3; ++c) F[c] = (x[c] - o[c]) - tt * d[c];
@@ -249,6 +250,7 @@ struct Heap {
   Cand* a;
   int cap;
   int n = 0, peak = 0;
+  int boxes = 0;       // candidate boxes formed (patch roots included)
   bool overflow = false;
 
   __device__ Heap(Cand* storage, int capacity) : a(storage), cap(capacity) {}
@@ -318,6 +320,7 @@ __device__ __forceinline__ void root_push(Heap& h, const double* B, int p, const
 __device__ void push_sub(Heap& h, const double* __restrict__ P, int p, double u0, double u1, double v0, double v1,
                          const Ray& r, double best) {
   if (!(u1 > u0) || !(v1 > v0)) return;
+  ++h.boxes;
   double lo = 0.0, hi = INFINITY, e = 0.0;
 #pragma unroll 1
   for (int c = 0; c < 3; ++c) {
@@ -332,7 +335,7 @@ __device__ void push_sub(Heap& h, const double* __restrict__ P, int p, double u0
 
 struct Hit {
   double tau = INFINITY, u = 0.0, v = 0.0;
-  int patch = -1, nexp = 0, flags = 0;
+  int patch = -1, nexp = 0, flags = 0, newton_iters = 0;
 };
 
 // The search over the candidates already in the heap; stops early once the heap overflows.
@@ -366,7 +369,7 @@ __device__ Hit search(Heap& h, const Ray& r, const double* __restrict__ nets, in
       bezier_eval(P, um, vm, x, xu, xv);
       double u = um, v = vm;
       double t = ((x[0] - r.o[0]) * r.d[0] + (x[1] - r.o[1]) * r.d[1]) + (x[2] - r.o[2]) * r.d[2];
-      if (newton_root(P, r.o, r.d, on, u, v, t) && u >= c.u0 && u <= c.u1 && v >= c.v0 && v <= c.v1 &&
+      if (newton_root(P, r.o, r.d, on, u, v, t, res.newton_iters) && u >= c.u0 && u <= c.u1 && v >= c.v0 && v <= c.v1 &&
           t >= 0.0) {
         if (t < best) {
           best = t;
@@ -412,15 +415,17 @@ struct RayOut {
   int* stats;
 };
 
-__device__ __forceinline__ void write_hit(const RayOut& out, long long k, const Hit& res, int peak) {
+__device__ __forceinline__ void write_hit(const RayOut& out, long long k, const Hit& res, const Heap& h) {
   out.tau[k] = res.tau;
   out.patch[k] = res.patch;
   out.uv[2 * k] = res.u;
   out.uv[2 * k + 1] = res.v;
   out.flags[k] = res.flags;
   if (out.stats) {
-    out.stats[2 * k] = res.nexp;
-    out.stats[2 * k + 1] = peak;
+    out.stats[4 * k] = res.nexp;
+    out.stats[4 * k + 1] = h.peak;
+    out.stats[4 * k + 2] = h.boxes;
+    out.stats[4 * k + 3] = res.newton_iters;
   }
 }
 
@@ -450,6 +455,7 @@ __global__ void __launch_bounds__(kRayBlock) k_trace_rays(long long n, const dou
     for (int j = 0; j < m; ++j) root_push(h, sbox + 8 * j, base + j, r);
   }
   if (!active) return;
+  h.boxes = np;
   const Hit res = search(h, r, nets, use_newton);
   if (h.overflow) {
     const int slot = atomicAdd(redo_count, 1);
@@ -458,7 +464,7 @@ __global__ void __launch_bounds__(kRayBlock) k_trace_rays(long long n, const dou
       return;                                                         // written by the second pass
     }
   }
-  write_hit(out, k, res, h.peak);
+  write_hit(out, k, res, h);
 }
 
 // Second pass over the rays whose first-pass heap overflowed: the same search from the start
@@ -478,8 +484,9 @@ __global__ void __launch_bounds__(kRedoThreads) k_trace_rays_redo(const double* 
     load_ray(origins, dirs, k, r);
     Heap h(heaps + (size_t)tid * kRedoHeap, kRedoHeap);
     for (int p = 0; p < np; ++p) root_push(h, boxes + 8 * (size_t)p, p, r);
+    h.boxes = np;
     const Hit res = search(h, r, nets, use_newton);
-    write_hit(out, k, res, h.peak);
+    write_hit(out, k, res, h);
   }
 }
 
