@@ -3,7 +3,7 @@
 //
 //   k_ray_nets   one thread per patch: Bezier control net (Hermite data b0 = a, b1 = a + a'/3,
 //                b2 = b - b'/3, b3 = b per direction, tensor product) and its box.
-//   k_trace_rays one thread per ray, FP64: all patch boxes are tested in patch order (staged
+//   k_trace_rays one ray per thread, FP64: all patch boxes are tested in patch order (staged
 //                through shared memory, one chunk at a time for the whole CTA), hits go into a
 //                binary min-heap in local memory keyed by the box's entry time tau_min; the top
 //                candidate is refined (box at most kEpsTau on every side: an intersection at the
@@ -11,6 +11,10 @@
 //                midpoint (Fig. submid) or, in the Newton variant, around a Newton root of
 //                x(u, v) = o + tau d that is abandoned together with its neighbourhood
 //                (Fig. subany). The search ends when the heap's top cannot beat the best tau.
+//                The children's boxes (4 children x 3 coordinates per split, most of a split's
+//                FP64 work) are pooled over the warp: lanes whose rays are done or need no split
+//                take jobs of the lanes that do, so a long search left alone in its warp runs
+//                its 12 box jobs side by side instead of one after another.
 //   k_trace_rays_redo  the rays whose local heap overflowed, traced again from the start with a
 //                larger heap in global memory (the search is deterministic, so the result is
 //                the one an unbounded heap gives).
@@ -36,7 +40,7 @@ constexpr int kMaxExpansions = 65536;
 constexpr int kHeapCap = SHELL_RAY_HEAP;
 constexpr int kNetBlock = 128;
 constexpr int kRayBlock = 128;
-constexpr int kRootChunk = 256;      // patch boxes staged in shared memory per pass
+constexpr int kRootChunk = 32;       // patch boxes staged in shared memory per pass
 constexpr int kRedoThreads = 128;    // second pass: threads, each with a kRedoHeap-entry heap
 constexpr int kRedoHeap = 8192;
 constexpr int kRedoList = 65536;     // rays the second pass can take per call
@@ -316,95 +320,142 @@ __device__ __forceinline__ void root_push(Heap& h, const double* B, int p, const
   if (in && !(lo > hi)) h.push(Cand{lo, hi, B[6], 0.0, 1.0, 0.0, 1.0, p});
 }
 
-// Pushes the sub-patch [u0, u1] x [v0, v1] of patch p when the ray enters its box before best.
-__device__ void push_sub(Heap& h, const double* __restrict__ P, int p, double u0, double u1, double v0, double v1,
-                         const Ray& r, double best) {
-  if (!(u1 > u0) || !(v1 > v0)) return;
-  ++h.boxes;
-  double lo = 0.0, hi = INFINITY, e = 0.0;
-#pragma unroll 1
-  for (int c = 0; c < 3; ++c) {
-    double mn, mx;
-    sub_range(P, c, u0, u1, v0, v1, mn, mx);
-    if (mx - mn > e) e = mx - mn;
-    if (!slab(mn, mx, r.o[c], r.d[c], r.inv[c], lo, hi)) return;
-  }
-  if (lo > hi || lo >= best) return;
-  h.push(Cand{lo, hi, e, u0, u1, v0, v1, p});
-}
-
-struct Hit {
-  double tau = INFINITY, u = 0.0, v = 0.0;
-  int patch = -1, nexp = 0, flags = 0, newton_iters = 0;
+// Per-lane state of one ray's search.
+struct Search {
+  double best = INFINITY, bu = 0.0, bv = 0.0, on = 0.0;
+  int bp = -1, nexp = 0, flags = 0, newton_iters = 0;
+  bool live = false;
 };
 
-// The search over the candidates already in the heap; stops early once the heap overflows.
-__device__ Hit search(Heap& h, const Ray& r, const double* __restrict__ nets, int use_newton) {
-  Hit res;
-  const double on = sqrt((r.o[0] * r.o[0] + r.o[1] * r.o[1]) + r.o[2] * r.o[2]);
-  double best = INFINITY, bu = 0.0, bv = 0.0;
-  int bp = -1, nexp = 0;
-  while (h.n > 0 && !h.overflow) {
-    const Cand c = h.pop();
-    if (c.t0 >= best - kEpsTau) break;                               // nothing left can be closer
-    if (c.ext <= kEpsTau || (c.u1 - c.u0 < 1e-13 && c.v1 - c.v0 < 1e-13)) {   // refined
-      const double t = 0.5 * (c.t0 + c.t1);
-      if (t < best - kEpsTau) {
-        best = t;
-        bp = c.patch;
-        bu = 0.5 * (c.u0 + c.u1);
-        bv = 0.5 * (c.v0 + c.v1);
-      }
-      continue;
-    }
-    if (nexp == kMaxExpansions) {
-      res.flags |= SHELL_RAY_LIMIT;
-      break;
-    }
-    ++nexp;
-    const double* P = nets + (size_t)c.patch * 48;
-    const double um = 0.5 * (c.u0 + c.u1), vm = 0.5 * (c.v0 + c.v1);
-    if (use_newton) {
-      double x[3], xu[3], xv[3];
-      bezier_eval(P, um, vm, x, xu, xv);
-      double u = um, v = vm;
-      double t = ((x[0] - r.o[0]) * r.d[0] + (x[1] - r.o[1]) * r.d[1]) + (x[2] - r.o[2]) * r.d[2];
-      if (newton_root(P, r.o, r.d, on, u, v, t, res.newton_iters) && u >= c.u0 && u <= c.u1 && v >= c.v0 && v <= c.v1 &&
-          t >= 0.0) {
-        if (t < best) {
-          best = t;
-          bp = c.patch;
-          bu = u;
-          bv = v;
+// Shared-memory exchange of one warp: the children each lane produced in the current split and
+// the coordinate ranges computed for them by whichever lanes took those jobs.
+struct WarpSmem {
+  double rect[32][4][4];        // child rectangles u0, u1, v0, v1 in push order
+  double range[32][12][2];      // (child * 3 + coordinate): min, max
+  int patch[32];
+  unsigned short jobs[32 * 12]; // lane * 12 + child * 3 + coordinate
+};
+
+__device__ __forceinline__ void put_rect(WarpSmem& sm, int lane, int& nch, double u0, double u1, double v0,
+                                         double v1) {
+  if (!(u1 > u0) || !(v1 > v0)) return;   // degenerate pieces of a pinwheel split
+  double* R = sm.rect[lane][nch++];
+  R[0] = u0;
+  R[1] = u1;
+  R[2] = v0;
+  R[3] = v1;
+}
+
+// The search over the candidates already in each lane's heap, all 32 lanes of the warp together
+// (lanes without a ray pass live = false). Every iteration each live lane takes its top
+// candidate and, when it splits it, lists its children; the 3 coordinate ranges of every child
+// of every lane are then computed as one pool of jobs spread over the warp's lanes, and each
+// lane finishes its own children (slab test, push) in order. A ray stops early once its heap
+// overflows.
+__device__ void search(Heap& h, const Ray& r, const double* __restrict__ nets, int use_newton, Search& S,
+                       WarpSmem& sm, int lane) {
+  S.on = sqrt((r.o[0] * r.o[0] + r.o[1] * r.o[1]) + r.o[2] * r.o[2]);
+  while (__any_sync(0xffffffffu, S.live)) {
+    int nch = 0;
+    if (S.live) {
+      if (h.n == 0 || h.overflow) {
+        S.live = false;
+      } else {
+        const Cand c = h.pop();
+        if (c.t0 >= S.best - kEpsTau) {                                    // nothing left can be closer
+          S.live = false;
+        } else if (c.ext <= kEpsTau || (c.u1 - c.u0 < 1e-13 && c.v1 - c.v0 < 1e-13)) {   // refined
+          const double t = 0.5 * (c.t0 + c.t1);
+          if (t < S.best - kEpsTau) {
+            S.best = t;
+            S.bp = c.patch;
+            S.bu = 0.5 * (c.u0 + c.u1);
+            S.bv = 0.5 * (c.v0 + c.v1);
+          }
+        } else if (S.nexp == kMaxExpansions) {
+          S.flags |= SHELL_RAY_LIMIT;
+          S.live = false;
+        } else {
+          ++S.nexp;
+          const double* P = nets + (size_t)c.patch * 48;
+          const double um = 0.5 * (c.u0 + c.u1), vm = 0.5 * (c.v0 + c.v1);
+          bool pinwheel = false;
+          if (use_newton) {
+            double x[3], xu[3], xv[3];
+            bezier_eval(P, um, vm, x, xu, xv);
+            double u = um, v = vm;
+            double t = ((x[0] - r.o[0]) * r.d[0] + (x[1] - r.o[1]) * r.d[1]) + (x[2] - r.o[2]) * r.d[2];
+            if (newton_root(P, r.o, r.d, S.on, u, v, t, S.newton_iters) && u >= c.u0 && u <= c.u1 &&
+                v >= c.v0 && v <= c.v1 && t >= 0.0) {
+              if (t < S.best) {
+                S.best = t;
+                S.bp = c.patch;
+                S.bu = u;
+                S.bv = v;
+              }
+              // Fig. subany: drop [a1, a2] x [b1, b2] around the root, four rectangles remain
+              const double hu = kNbhd * (c.u1 - c.u0), hv = kNbhd * (c.v1 - c.v0);
+              const double a1 = fmax(c.u0, u - hu), a2 = fmin(c.u1, u + hu);
+              const double b1 = fmax(c.v0, v - hv), b2 = fmin(c.v1, v + hv);
+              put_rect(sm, lane, nch, c.u0, a1, b1, c.v1);
+              put_rect(sm, lane, nch, a1, c.u1, b2, c.v1);
+              put_rect(sm, lane, nch, c.u0, a2, c.v0, b1);
+              put_rect(sm, lane, nch, a2, c.u1, c.v0, b2);
+              pinwheel = true;
+            }
+          }
+          if (!pinwheel) {   // Fig. submid: four quarters at the parameter midpoint
+            put_rect(sm, lane, nch, c.u0, um, vm, c.v1);
+            put_rect(sm, lane, nch, um, c.u1, vm, c.v1);
+            put_rect(sm, lane, nch, c.u0, um, c.v0, vm);
+            put_rect(sm, lane, nch, um, c.u1, c.v0, vm);
+          }
+          sm.patch[lane] = c.patch;
+          h.boxes += nch;
         }
-        // Fig. subany: drop [a1, a2] x [b1, b2] around the root, four rectangles remain
-        const double hu = kNbhd * (c.u1 - c.u0), hv = kNbhd * (c.v1 - c.v0);
-        const double a1 = fmax(c.u0, u - hu), a2 = fmin(c.u1, u + hu);
-        const double b1 = fmax(c.v0, v - hv), b2 = fmin(c.v1, v + hv);
-        push_sub(h, P, c.patch, c.u0, a1, b1, c.v1, r, best);
-        push_sub(h, P, c.patch, a1, c.u1, b2, c.v1, r, best);
-        push_sub(h, P, c.patch, c.u0, a2, c.v0, b1, r, best);
-        push_sub(h, P, c.patch, a2, c.u1, c.v0, b2, r, best);
-        continue;
       }
     }
-    // Fig. submid: four quarters at the parameter midpoint
-    push_sub(h, P, c.patch, c.u0, um, vm, c.v1, r, best);
-    push_sub(h, P, c.patch, um, c.u1, vm, c.v1, r, best);
-    push_sub(h, P, c.patch, c.u0, um, c.v0, vm, r, best);
-    push_sub(h, P, c.patch, um, c.u1, c.v0, vm, r, best);
+    // the warp's pool of (lane, child, coordinate) range jobs
+    const int nj = 3 * nch;
+    int pre = nj;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, pre, off);
+      if (lane >= off) pre += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, 31);
+    pre -= nj;
+    for (int k = 0; k < nj; ++k) sm.jobs[pre + k] = (unsigned short)(lane * 12 + k);
+    __syncwarp();
+    for (int j = lane; j < total; j += 32) {
+      const int code = sm.jobs[j], owner = code / 12, k = code - 12 * owner;
+      const double* R = sm.rect[owner][k / 3];
+      double mn, mx;
+      sub_range(nets + (size_t)sm.patch[owner] * 48, k % 3, R[0], R[1], R[2], R[3], mn, mx);
+      sm.range[owner][k][0] = mn;
+      sm.range[owner][k][1] = mx;
+    }
+    __syncwarp();
+    for (int ch = 0; ch < nch; ++ch) {
+      double lo = 0.0, hi = INFINITY, e = 0.0;
+      bool in = true;
+      for (int cc = 0; cc < 3 && in; ++cc) {
+        const double mn = sm.range[lane][3 * ch + cc][0], mx = sm.range[lane][3 * ch + cc][1];
+        if (mx - mn > e) e = mx - mn;
+        in = slab(mn, mx, r.o[cc], r.d[cc], r.inv[cc], lo, hi);
+      }
+      if (in && !(lo > hi) && !(lo >= S.best)) {
+        const double* R = sm.rect[lane][ch];
+        h.push(Cand{lo, hi, e, R[0], R[1], R[2], R[3], sm.patch[lane]});
+      }
+    }
+    __syncwarp();
   }
-  res.nexp = nexp;
   if (h.overflow) {
-    res.flags |= SHELL_RAY_OVERFLOW;   // void: reported as a miss
-  } else if (bp >= 0) {
-    res.flags |= SHELL_RAY_HIT;
-    res.tau = best;
-    res.patch = bp;
-    res.u = bu;
-    res.v = bv;
+    S.flags |= SHELL_RAY_OVERFLOW;   // void: reported as a miss
+  } else if (S.bp >= 0) {
+    S.flags |= SHELL_RAY_HIT;
   }
-  return res;
 }
 
 struct RayOut {
@@ -415,23 +466,24 @@ struct RayOut {
   int* stats;
 };
 
-__device__ __forceinline__ void write_hit(const RayOut& out, long long k, const Hit& res, const Heap& h) {
-  out.tau[k] = res.tau;
-  out.patch[k] = res.patch;
-  out.uv[2 * k] = res.u;
-  out.uv[2 * k + 1] = res.v;
-  out.flags[k] = res.flags;
+__device__ __forceinline__ void write_hit(const RayOut& out, long long k, const Search& S, const Heap& h) {
+  const bool hit = (S.flags & SHELL_RAY_HIT) != 0;
+  out.tau[k] = hit ? S.best : INFINITY;
+  out.patch[k] = hit ? S.bp : -1;
+  out.uv[2 * k] = hit ? S.bu : 0.0;
+  out.uv[2 * k + 1] = hit ? S.bv : 0.0;
+  out.flags[k] = S.flags;
   if (out.stats) {
-    out.stats[4 * k] = res.nexp;
+    out.stats[4 * k] = S.nexp;
     out.stats[4 * k + 1] = h.peak;
     out.stats[4 * k + 2] = h.boxes;
-    out.stats[4 * k + 3] = res.newton_iters;
+    out.stats[4 * k + 3] = S.newton_iters;
   }
 }
 
-// First pass: one ray per thread, a kHeapCap-entry heap in local memory. A ray whose heap
-// overflows stops and is appended to redo_list for the second pass (or, when the list is full,
-// reported with SHELL_RAY_OVERFLOW).
+// First pass: one ray per thread, a kHeapCap-entry heap in local memory, the search shared by the
+// warp. A ray whose heap overflows stops and is appended to redo_list for the second pass (or,
+// when the list is full, reported with SHELL_RAY_OVERFLOW).
 __global__ void __launch_bounds__(kRayBlock) k_trace_rays(long long n, const double* __restrict__ origins,
                                                           const double* __restrict__ dirs, int np,
                                                           const double* __restrict__ nets,
@@ -439,6 +491,8 @@ __global__ void __launch_bounds__(kRayBlock) k_trace_rays(long long n, const dou
                                                           RayOut out, int* __restrict__ redo_count,
                                                           int* __restrict__ redo_list) {
   __shared__ double sbox[kRootChunk * 8];
+  __shared__ WarpSmem wsm[kRayBlock / 32];
+  const int lane = threadIdx.x & 31;
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = k < n;
   Ray r;
@@ -454,9 +508,11 @@ __global__ void __launch_bounds__(kRayBlock) k_trace_rays(long long n, const dou
     if (!active) continue;
     for (int j = 0; j < m; ++j) root_push(h, sbox + 8 * j, base + j, r);
   }
-  if (!active) return;
   h.boxes = np;
-  const Hit res = search(h, r, nets, use_newton);
+  Search S;
+  S.live = active;
+  search(h, r, nets, use_newton, S, wsm[threadIdx.x >> 5], lane);
+  if (!active) return;
   if (h.overflow) {
     const int slot = atomicAdd(redo_count, 1);
     if (slot < kRedoList) {
@@ -464,7 +520,7 @@ __global__ void __launch_bounds__(kRayBlock) k_trace_rays(long long n, const dou
       return;                                                         // written by the second pass
     }
   }
-  write_hit(out, k, res, h);
+  write_hit(out, k, S, h);
 }
 
 // Second pass over the rays whose first-pass heap overflowed: the same search from the start
@@ -476,17 +532,24 @@ __global__ void __launch_bounds__(kRedoThreads) k_trace_rays_redo(const double* 
                                                                   RayOut out, const int* __restrict__ redo_count,
                                                                   const int* __restrict__ redo_list,
                                                                   Cand* __restrict__ heaps) {
-  const int tid = threadIdx.x;
+  __shared__ WarpSmem wsm[kRedoThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31;
   const int count = min(*redo_count, kRedoList);
-  for (int i = tid; i < count; i += kRedoThreads) {
-    const long long k = redo_list[i];
+  for (int base = 0; base < count; base += kRedoThreads) {   // uniform trip count: the warp stays whole
+    const int i = base + tid;
+    const bool active = i < count;
+    const long long k = active ? redo_list[i] : 0;
     Ray r;
-    load_ray(origins, dirs, k, r);
     Heap h(heaps + (size_t)tid * kRedoHeap, kRedoHeap);
-    for (int p = 0; p < np; ++p) root_push(h, boxes + 8 * (size_t)p, p, r);
+    if (active) {
+      load_ray(origins, dirs, k, r);
+      for (int p = 0; p < np; ++p) root_push(h, boxes + 8 * (size_t)p, p, r);
+    }
     h.boxes = np;
-    const Hit res = search(h, r, nets, use_newton);
-    write_hit(out, k, res, h);
+    Search S;
+    S.live = active;
+    search(h, r, nets, use_newton, S, wsm[tid >> 5], lane);
+    if (active) write_hit(out, k, S, h);
   }
 }
 
