@@ -360,9 +360,10 @@ typedef enum { SHELL_RAY_MIDPOINT = 0, SHELL_RAY_NEWTON = 1 } shell_ray_variant;
      flags    device [n_rays]: SHELL_RAY_* bits
      stats    device [n_rays][4] or NULL: candidates split, largest heap size, candidate boxes
               formed (one per patch for the roots included), Newton iterations run
-   A ray whose candidates outgrow the SHELL_RAY_HEAP-entry first-pass heap is traced again from
-   the start by a second kernel with an 8192-entry heap, so every result is that of an unbounded
-   heap unless SHELL_RAY_OVERFLOW is set. n_rays in [0, 2^31 - 1]; 0 does nothing. Asynchronous
+   A ray whose candidates outgrow the SHELL_RAY_HEAP-entry first-pass heap continues in one of 128
+   library-owned 8192-entry heaps; rays beyond those 128 are traced again from the start by a
+   second kernel with such a heap, so every result is that of an unbounded heap unless
+   SHELL_RAY_OVERFLOW is set. n_rays in [0, 2^31 - 1]; 0 does nothing. Asynchronous
    on the shell's stream (three kernel launches and a 4-byte memset). The first call on a shell
    allocates 448 bytes per patch plus 64.3 MB of library-owned device memory (Bezier nets and
    boxes, the second pass's heaps), kept until shell_destroy; calls on one shell must not

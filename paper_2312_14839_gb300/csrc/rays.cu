@@ -15,9 +15,11 @@
 //                FP64 work) are pooled over the warp: lanes whose rays are done or need no split
 //                take jobs of the lanes that do, so a long search left alone in its warp runs
 //                its 12 box jobs side by side instead of one after another.
-//   k_trace_rays_redo  the rays whose local heap overflowed, traced again from the start with a
-//                larger heap in global memory (the search is deterministic, so the result is
-//                the one an unbounded heap gives).
+//                A ray whose local heap fills moves it into one of kRedoThreads larger heaps
+//                in global memory and continues.
+//   k_trace_rays_redo  the rays that found no free global heap, traced again from the start
+//                with one (the search is deterministic, so the result is the one an unbounded
+//                heap gives).
 //
 // Sub-patches are cut from the patch's net by blossoming (each restricted curve's points are
 // f(a,a,a), f(a,a,b), f(a,b,b), f(b,b,b), De Casteljau with one parameter per level) and only
@@ -249,20 +251,37 @@ struct Cand {
 };
 
 // Binary min-heap on t0 (sift rules of a textbook binary heap) over caller-given storage: a
-// local array in the first pass, a slice of library-owned global memory in the second.
+// local array in the first pass, a slice of library-owned global memory in the second. A full
+// first-pass heap moves itself into a free global slice (spill, kRedoThreads slices of kRedoHeap
+// entries, claimed through *spill_count) and carries on; only when none is left does it report
+// an overflow.
 struct Heap {
   Cand* a;
   int cap;
   int n = 0, peak = 0;
   int boxes = 0;       // candidate boxes formed (patch roots included)
   bool overflow = false;
+  Cand* spill = nullptr;
+  int* spill_count = nullptr;
 
   __device__ Heap(Cand* storage, int capacity) : a(storage), cap(capacity) {}
 
   __device__ void push(const Cand& c) {
     if (n == cap) {
-      overflow = true;
-      return;
+      if (spill) {
+        const int slot = atomicAdd(spill_count, 1);
+        if (slot < kRedoThreads) {
+          Cand* g = spill + (size_t)slot * kRedoHeap;
+          for (int i = 0; i < n; ++i) g[i] = a[i];
+          a = g;
+          cap = kRedoHeap;
+        }
+        spill = nullptr;
+      }
+      if (n == cap) {
+        overflow = true;
+        return;
+      }
     }
     int i = n++;
     if (n > peak) peak = n;
@@ -484,12 +503,12 @@ __device__ __forceinline__ void write_hit(const RayOut& out, long long k, const 
 // First pass: one ray per thread, a kHeapCap-entry heap in local memory, the search shared by the
 // warp. A ray whose heap overflows stops and is appended to redo_list for the second pass (or,
 // when the list is full, reported with SHELL_RAY_OVERFLOW).
-__global__ void __launch_bounds__(kRayBlock) k_trace_rays(long long n, const double* __restrict__ origins,
+__global__ void __launch_bounds__(kRayBlock, 4) k_trace_rays(long long n, const double* __restrict__ origins,
                                                           const double* __restrict__ dirs, int np,
                                                           const double* __restrict__ nets,
                                                           const double* __restrict__ boxes, int use_newton,
                                                           RayOut out, int* __restrict__ redo_count,
-                                                          int* __restrict__ redo_list) {
+                                                          int* __restrict__ redo_list, Cand* __restrict__ heaps) {
   __shared__ double sbox[kRootChunk * 8];
   __shared__ WarpSmem wsm[kRayBlock / 32];
   const int lane = threadIdx.x & 31;
@@ -498,6 +517,8 @@ __global__ void __launch_bounds__(kRayBlock) k_trace_rays(long long n, const dou
   Ray r;
   Cand storage[kHeapCap];
   Heap h(storage, kHeapCap);
+  h.spill = heaps;
+  h.spill_count = redo_count + 1;
   if (active) load_ray(origins, dirs, k, r);
   // every patch's box in patch order; the whole CTA stages one chunk at a time
   for (int base = 0; base < np; base += kRootChunk) {
@@ -569,7 +590,7 @@ extern "C" shell_status shell_trace_rays(shell_t* shell, const double* q, long l
   Shell& s = *shell;
   const int np = s.n_patches;
   if (!s.d_ray_nets) {
-    const size_t bytes = sizeof(double) * 56 * (size_t)np + sizeof(int) * (1 + kRedoList) +
+    const size_t bytes = sizeof(double) * 56 * (size_t)np + sizeof(int) * (2 + kRedoList) +
                          sizeof(Cand) * (size_t)kRedoThreads * kRedoHeap;
     cudaError_t e = cudaMalloc(&s.d_ray_nets, bytes);
     if (e != cudaSuccess) {
@@ -582,15 +603,15 @@ extern "C" shell_status shell_trace_rays(shell_t* shell, const double* q, long l
   Cand* heaps = (Cand*)s.d_ray_nets;
   double* nets = (double*)(heaps + (size_t)kRedoThreads * kRedoHeap);
   double* boxes = nets + 48 * (size_t)np;
-  int* redo_count = (int*)(boxes + 8 * (size_t)np);
-  int* redo_list = redo_count + 1;
+  int* redo_count = (int*)(boxes + 8 * (size_t)np);   // [0] rays for the second pass, [1] spilled heaps
+  int* redo_list = redo_count + 2;
   RayOut out{tau, patch, uv, flags, stats};
-  BHEM_CUDA(cudaMemsetAsync(redo_count, 0, sizeof(int), s.stream));
+  BHEM_CUDA(cudaMemsetAsync(redo_count, 0, 2 * sizeof(int), s.stream));
   k_ray_nets<<<grid_for(np, kNetBlock), kNetBlock, 0, s.stream>>>(np, s.d_patch_nodes, q, s.grid.dxi1,
                                                                   s.grid.dxi2, nets, boxes);
   const int use_newton = variant == SHELL_RAY_NEWTON;
   k_trace_rays<<<(unsigned)((n_rays + kRayBlock - 1) / kRayBlock), kRayBlock, 0, s.stream>>>(
-      n_rays, origins, dirs, np, nets, boxes, use_newton, out, redo_count, redo_list);
+      n_rays, origins, dirs, np, nets, boxes, use_newton, out, redo_count, redo_list, heaps);
   k_trace_rays_redo<<<1, kRedoThreads, 0, s.stream>>>(origins, dirs, np, nets, boxes, use_newton, out, redo_count,
                                                       redo_list, heaps);
   s.launches += 3;
