@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE: only the tests, ``__graft_entry__.smoke()`` and the CPU-bas
 two share no code.
 
 The C sources follow the paper's formulas step by step (``bhem_oracle.c``: Sec. 3, Sec. 4, Sec. 6.1,
-App. A, App. B; ``ray_oracle.c``: Sec. 5); this wrapper only marshals numpy arrays.
+App. A, App. B; ``ray_oracle.c``, ``ccd_oracle.c``: Sec. 5); this wrapper only marshals numpy arrays.
 """
 from __future__ import annotations
 
@@ -17,7 +17,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "bhem_oracle.c"), os.path.join(_HERE, "ray_oracle.c")]
+_SRCS = [os.path.join(_HERE, "bhem_oracle.c"), os.path.join(_HERE, "ray_oracle.c"),
+         os.path.join(_HERE, "ccd_oracle.c")]
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
 _lock = threading.Lock()
@@ -89,6 +90,9 @@ def _load():
         lib.og_ray_box.restype = i
         lib.og_ray_box.argtypes = [p, p, p, p, p, p, p]
         lib.og_trace_rays.argtypes = [p, p, i, p, p, i, p, p, p, p, p]
+        lib.og_ccd_feasible.restype = i
+        lib.og_ccd_feasible.argtypes = [p, p, p, p, p, p]
+        lib.og_ccd_points.argtypes = [p, p, p, i, p, p, i, p, p, p, p, p]
         _lib = lib
     return _lib
 
@@ -331,4 +335,35 @@ def trace_rays(g, q, origins, dirs, use_newton: bool = True, want_stats: bool = 
     _load().og_trace_rays(C.byref(_grid(g)), _ptr(q), n, _ptr(origins), _ptr(dirs), int(bool(use_newton)),
                           _ptr(tau), _ptr(patch), _ptr(uv), _ptr(flags), _ptr(stats))
     out = (tau, patch, uv, flags)
+    return out + (stats,) if want_stats else out
+
+
+# ---------------------------------------------------------------------------------------------
+# Point-patch continuous collision detection (Sec. 5, dynamic ray-patch intersection)
+# ---------------------------------------------------------------------------------------------
+def ccd_feasible(S, dS, x0, dx):
+    """Feasible normalised times of Eq. ineqccd for the moving net S + s dS ([4, 4, 3] each) and
+    the point x0 + s dx: list of closed intervals (lo, hi) in [0, 1], sorted."""
+    S, dS, x0, dx = _f64(S), _f64(dS), _f64(x0), _f64(dx)
+    lo, hi = np.zeros(8), np.zeros(8)
+    n = _load().og_ccd_feasible(_ptr(S), _ptr(dS), _ptr(x0), _ptr(dx), _ptr(lo), _ptr(hi))
+    return [(lo[i], hi[i]) for i in range(n)]
+
+
+def ccd_points(g, q, dq, x0s, dxs, use_newton: bool = True, want_stats: bool = False):
+    """Earliest contact of points x0 + s dx (s in [0, 1]) with the shell moving from q to q + dq.
+
+    Returns (s [n] (inf: no contact), patch [n] (-1), uv [n, 2], flags [n] (RAY_HIT, RAY_LIMIT))
+    and, with want_stats, stats [n, 4] = (splits, peak heap size, feasibility tests with the patch
+    roots that passed the swept-box test, Newton iterations).
+    """
+    q, dq = _f64(q).reshape(-1), _f64(dq).reshape(-1)
+    x0s, dxs = _f64(x0s).reshape(-1, 3), _f64(dxs).reshape(-1, 3)
+    n = x0s.shape[0]
+    s, uv = np.zeros(n), np.zeros((n, 2))
+    patch, flags = np.zeros(n, dtype=np.int32), np.zeros(n, dtype=np.int32)
+    stats = np.zeros((n, 4), dtype=np.int32) if want_stats else None
+    _load().og_ccd_points(C.byref(_grid(g)), _ptr(q), _ptr(dq), n, _ptr(x0s), _ptr(dxs), int(bool(use_newton)),
+                          _ptr(s), _ptr(patch), _ptr(uv), _ptr(flags), _ptr(stats))
+    out = (s, patch, uv, flags)
     return out + (stats,) if want_stats else out

@@ -303,3 +303,39 @@ def ray_scenes():
         "cylinder": (g2, q2, (1.2, 0.4, 0.9), (0.0, 0.0, 0.5)),
         "drape": (g3, q3, (0.5, -0.35, 0.55), (0.5, 0.5, 0.0)),
     }
+
+
+def ccd_scene(name: str, n_points: int = 4096, seed: int = 11):
+    """Continuous-collision scenes: (grid, q [n_nodes, 12] at the start of the step, dq [n_nodes,
+    12] displacement over the step, x0 [n, 3] point positions, dx [n, 3] point displacements).
+
+    plane: flat 10 x 10-patch 1 m sheet translated 2 cm up over the step; points in a slab
+           around it moving up or down by up to 6 cm.
+    drape: the 30 x 30-patch sinusoid sheet (5 cm, seed 3) moving to another sinusoid state
+           (5 cm, seed 7) 2 cm lower; points over the sheet within 8 cm of z = 0 moving by
+           N(0, 4 cm) vertically and N(0, 1 cm) in plane.
+    static: the drape sheet at rest (dq = 0), the same points.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if name == "plane":
+        g, q = flat_sheet(10, 10)
+        dq = np.zeros_like(q)
+        dq[:, 2] = 0.02
+        x0 = np.stack([rng.uniform(-0.05, 1.05, n_points), rng.uniform(-0.05, 1.05, n_points),
+                       rng.uniform(-0.04, 0.06, n_points)], axis=1)
+        dx = np.stack([rng.normal(0.0, 0.01, n_points), rng.normal(0.0, 0.01, n_points),
+                       rng.uniform(-0.06, 0.06, n_points)], axis=1)
+        return g, q, dq, x0, dx
+    g, _, q = sheet_sinusoid(30, 3, 0.05)
+    if name == "static":
+        dq = np.zeros_like(q)
+    else:
+        _, _, q1 = sheet_sinusoid(30, 7, 0.05)
+        q1 = q1.copy()
+        q1[:, 2] -= 0.02
+        dq = q1 - q
+    x0 = np.stack([rng.uniform(0.02, 0.98, n_points), rng.uniform(0.02, 0.98, n_points),
+                   rng.uniform(-0.08, 0.08, n_points)], axis=1)
+    dx = np.stack([rng.normal(0.0, 0.01, n_points), rng.normal(0.0, 0.01, n_points),
+                   rng.normal(0.0, 0.04, n_points)], axis=1)
+    return g, q, dq, x0, dx

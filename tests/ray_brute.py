@@ -84,3 +84,38 @@ def nearest(g, q, o, d, **kw):
     """Nearest root (tau, patch, u, v), or None."""
     roots = all_roots(g, q, o, d, **kw)
     return min(roots) if roots else None
+
+
+def all_contacts(g, q, dq, x0, dx, starts: int = 5, s_starts=(0.1, 0.5, 0.9), iters: int = 40):
+    """Every root (s, patch, u, v) in [0, 1] x patch of X(u, v) + s D(u, v) = x0 + s dx (a shell
+    moving linearly from q to q + dq, a point moving from x0 to x0 + dx) that Newton reaches from
+    a starts x starts x len(s_starts) grid in each patch."""
+    x0, dx = np.asarray(x0, dtype=np.float64), np.asarray(dx, dtype=np.float64)
+    out = []
+    g1 = (np.arange(starts) + 0.5) / starts
+    U0, V0, S0 = np.meshgrid(g1, g1, np.asarray(s_starts, dtype=np.float64), indexing="ij")
+    for p in range(g.nu * g.nv):
+        C = patch_coeffs(g, q, p)
+        Cd = patch_coeffs(g, dq, p)
+        u, v, s = U0.ravel().copy(), V0.ravel().copy(), S0.ravel().copy()
+        for _ in range(iters):
+            X, Xu, Xv = evaluate(C, u, v)
+            D, Du, Dv = evaluate(Cd, u, v)
+            F = X + s[:, None] * D - x0 - s[:, None] * dx
+            J = np.stack([Xu + s[:, None] * Du, Xv + s[:, None] * Dv, D - dx], axis=2)
+            ok = np.abs(np.linalg.det(J)) > 1e-300
+            step = np.zeros_like(F)
+            step[ok] = np.linalg.solve(J[ok], -F[ok][..., None])[..., 0]
+            u, v, s = u + step[:, 0], v + step[:, 1], s + step[:, 2]
+            u, v, s = np.clip(u, -0.5, 1.5), np.clip(v, -0.5, 1.5), np.clip(s, -1.0, 2.0)
+        X, _, _ = evaluate(C, u, v)
+        D, _, _ = evaluate(Cd, u, v)
+        r = np.linalg.norm(X + s[:, None] * D - x0 - s[:, None] * dx, axis=1)
+        good = (r < 1e-12) & (u >= 0) & (u <= 1) & (v >= 0) & (v <= 1) & (s >= 0) & (s <= 1)
+        out += [(s[i], p, u[i], v[i]) for i in np.flatnonzero(good)]
+    return out
+
+
+def earliest_contact(g, q, dq, x0, dx, **kw):
+    roots = all_contacts(g, q, dq, x0, dx, **kw)
+    return min(roots) if roots else None
