@@ -372,6 +372,32 @@ SHELL_API shell_status shell_trace_rays(shell_t* shell, const double* q, long lo
                                         const double* dirs, int variant, double* tau, int* patch, double* uv,
                                         int* flags, int* stats);
 
+/* Earliest contact of each moving point with the moving shell over one time step (Sec. 5, dynamic
+   ray-patch intersection, Eq. ineqccd). The shell moves linearly from q to q + dq (its Bezier
+   control points p_ij + s dp_ij, s = t / dt in [0, 1]); point k moves from x0[k] to
+   x0[k] + dx[k]. Patches whose swept box misses the point's segment box are skipped; the others
+   enter the subdivision search of shell_trace_rays with time in place of distance: feasible
+   times of a (sub)net are [0, 1] minus, per axis and box face, the open interval outside the
+   union of the control points' half-lines; candidates are keyed by their earliest feasible time;
+   a candidate whose start-box side plus displacement-box side is at most 1e-9 on every axis is a
+   contact at that time; variant SHELL_RAY_NEWTON splits around Newton roots in (u, v, s)
+   (Fig. subany), SHELL_RAY_MIDPOINT at the midpoint (Fig. submid). All arithmetic is FP64.
+     q, dq    device [n_dof]: DOFs at the start of the step and their change over the step
+     x0, dx   device [n_points][3]: point positions at the start, displacements over the step
+     s        device [n_points]: earliest contact time in [0, 1], +infinity when none
+     patch    device [n_points]: patch id, -1 when none; uv device [n_points][2]: local (u, v)
+     flags    device [n_points]: SHELL_RAY_HIT (contact), SHELL_RAY_LIMIT, SHELL_RAY_OVERFLOW
+     stats    device [n_points][4] or NULL: splits, largest heap size, feasibility tests (patches
+              that passed the swept-box test included), Newton iterations
+   Heaps, second pass and flags as in shell_trace_rays. n_points in [0, 2^31 - 1]; 0 does
+   nothing. Asynchronous on the shell's stream (three kernel launches and an 8-byte memset). The
+   first call allocates 832 bytes per patch (nets and swept boxes), and the first of this call
+   and shell_trace_rays the 64.3 MB search scratch they share, kept until shell_destroy; calls on
+   one shell must not overlap on the GPU. */
+SHELL_API shell_status shell_ccd_points(shell_t* shell, const double* q, const double* dq, long long n_points,
+                                        const double* x0, const double* dx, int variant, double* s, int* patch,
+                                        double* uv, int* flags, int* stats);
+
 /* Number of CUDA kernels this shell has launched since shell_create (host counter; counts the
    launches of the library's own kernels, not memset/memcpy operations). */
 SHELL_API shell_status shell_kernel_launches(const shell_t* shell, long long* count);

@@ -118,6 +118,7 @@ def load():
                 "shell_mlp_warm_start": [p, p, p, p, d, p],
                 "shell_measure_fma_peak": [i, i, p, p],
                 "shell_trace_rays": [p, p, ll, p, p, i, p, p, p, p, p],
+                "shell_ccd_points": [p, p, p, ll, p, p, i, p, p, p, p, p],
             }
             for name, args in sigs.items():
                 fn = getattr(lib, name)
@@ -312,6 +313,27 @@ class Shell:
                 out["stats"] = torch.empty((n, 4), dtype=torch.int32, device=dev)
         _check(load().shell_trace_rays(self._h, _ptr(q), int(n), _ptr(origins), _ptr(dirs), RAY_VARIANT[variant],
                                        _ptr(out["tau"]), _ptr(out["patch"]), _ptr(out["uv"]), _ptr(out["flags"]),
+                                       _ptr(out.get("stats"))))
+        return out
+
+    def ccd_points(self, q, dq, x0, dx, variant="newton", out=None, want_stats=False):
+        """Earliest contact of points moving from x0 to x0 + dx with the shell moving from q to
+        q + dq over one step (Sec. 5, Eq. ineqccd), on the shell's stream. FP64 CUDA tensors:
+        q, dq [n_dof], x0, dx [n, 3]. Returns a dict of CUDA tensors s [n] (normalised contact
+        time in [0, 1], inf when none), patch [n] (-1), uv [n, 2], flags [n] and, with
+        want_stats, stats [n, 4]. out: a dict of the same tensors to fill instead."""
+        import torch
+        n = x0.shape[0]
+        dev = x0.device
+        if out is None:
+            out = {"s": torch.empty(n, dtype=torch.float64, device=dev),
+                   "patch": torch.empty(n, dtype=torch.int32, device=dev),
+                   "uv": torch.empty((n, 2), dtype=torch.float64, device=dev),
+                   "flags": torch.empty(n, dtype=torch.int32, device=dev)}
+            if want_stats:
+                out["stats"] = torch.empty((n, 4), dtype=torch.int32, device=dev)
+        _check(load().shell_ccd_points(self._h, _ptr(q), _ptr(dq), int(n), _ptr(x0), _ptr(dx), RAY_VARIANT[variant],
+                                       _ptr(out["s"]), _ptr(out["patch"]), _ptr(out["uv"]), _ptr(out["flags"]),
                                        _ptr(out.get("stats"))))
         return out
 

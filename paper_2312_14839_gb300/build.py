@@ -21,10 +21,10 @@ LIB = os.path.join(LIBDIR, "libbhem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden"]
-# Per-file flags. rays.cu: no mul-add contraction, so every FP64 product and sum is rounded on
-# its own, as in plain C; ray-patch traversal decisions (heap order, refinement, Newton
-# convergence) then depend on the same roundings as a sequential C program of the same steps.
-FILE_FLAGS = {"rays.cu": ["-fmad=false"]}
+# Per-file flags. rays.cu, ccd.cu: no mul-add contraction, so every FP64 product and sum is
+# rounded on its own, as in plain C; the subdivision searches' decisions (heap order, refinement,
+# Newton convergence) then depend on the same roundings as a sequential C program of the same steps.
+FILE_FLAGS = {"rays.cu": ["-fmad=false"], "ccd.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:

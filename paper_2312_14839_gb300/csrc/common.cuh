@@ -118,9 +118,13 @@ struct Shell {
   int* h_err = nullptr;             // pinned
   double* d_energy_tmp = nullptr;
 
-  // ray-patch intersection scratch, allocated by the first shell_trace_rays (rays.cu): the
-  // second-pass heaps, per-patch Bezier nets [np][3][4][4], root boxes [np][8], the redo list
-  void* d_ray_nets = nullptr;
+  // Sec. 5 searches (rays.cu, ccd.cu), allocated by their first call: d_search holds the 128
+  // global candidate heaps, two counters and the redo list (shared: calls on one shell do not
+  // overlap); d_ray_nets the ray search's Bezier nets [np][3][4][4] and boxes [np][8];
+  // d_ccd_nets the collision search's start and displacement nets and swept boxes [np][104]
+  void* d_search = nullptr;
+  double* d_ray_nets = nullptr;
+  double* d_ccd_nets = nullptr;
 
   Reduce red{};
   long long launches = 0;           // kernels launched by this shell (introspection)
@@ -156,6 +160,8 @@ struct Shell {
 shell_status launch_rest_setup(Shell& s);
 // chooses the FP32 SpMV variant (opt.spmv) and prepares its launch (solver.cu)
 shell_status setup_spmv(Shell& s);
+// the shared search scratch of the Sec. 5 searches (allocated on first use; rays.cu)
+shell_status search_scratch(Shell& s, void** heaps, int** counters, int** redo_list);
 // regulariser shift tau * dbar per DOF kind, as kernel argument
 struct Shift4 { double v[4]; };
 

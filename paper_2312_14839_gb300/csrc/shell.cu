@@ -124,7 +124,7 @@ static void destroy_shell(shell_s* s) {
                   s->d_pcg, s->d_qn, s->d_y, s->d_g, s->d_gin, s->d_d, s->d_Md, s->d_Ep,
                   s->d_qwork, s->d_vwork, s->d_qfix, s->d_warm, s->d_mask, s->d_ns, s->d_err,
                   s->d_energy_tmp, s->red.partials, s->red.ticket, s->d_rhs, s->d_g2, s->d_Ep2,
-                  s->d_ray_nets};
+                  s->d_search, s->d_ray_nets, s->d_ccd_nets};
   for (void* p : ptrs) dfree(p);
   if (s->h_ns) cudaFreeHost(s->h_ns);
   if (s->h_pcg) cudaFreeHost(s->h_pcg);

@@ -38,3 +38,4 @@ def test_argument_errors_need_no_gpu():
     assert b"NULL" in lib.shell_last_error()
     assert lib.shell_destroy(None) == 0
     assert lib.shell_trace_rays(None, None, 0, None, None, 1, None, None, None, None, None) == 1
+    assert lib.shell_ccd_points(None, None, None, 0, None, None, 1, None, None, None, None, None) == 1
