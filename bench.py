@@ -49,6 +49,10 @@ WORKLOADS = {
     "rays_drape": "static ray-patch intersection (Sec. 5): 1024x768 pinhole camera (786,432 rays) on the "
                   "30x30-patch 1 m sheet draped by the 8-term sinusoid field (5 cm), FP64, Newton split "
                   "(Fig. subany); midpoint split and the plane / cylinder scenes reported beside it",
+    "ccd_drape": "point-patch continuous collision detection (Sec. 5, Eq. ineqccd): 1,048,576 points "
+                 "moving over one step against the 30x30-patch sheet deforming from one 5 cm sinusoid "
+                 "state to another 2 cm lower, FP64, Newton split; midpoint split and the translating "
+                 "plane reported beside it",
     "annulus280x5": "280x5-patch periodic annular strip, 8-term sinusoid displacement (5 cm), "
                     "FP32 element eval + BSR assembly + 50-iteration block-Jacobi PCG, FP64 "
                     "residual/reductions",
@@ -533,6 +537,126 @@ def run_rays_bench(args):
     }), flush=True)
 
 
+# FP64 operations per step of the collision search, counted from the kernel source like the ray
+# search's: a patch's swept-box test, one feasibility test (two nets cut per axis, half-line
+# classification, extents, interval subtraction), one Newton iteration in (u, v, s), and the fixed
+# work of one split.
+CCD_OPS_ROOT = 6
+CCD_OPS_FEASIBLE = 2950
+CCD_OPS_NEWTON_ITER = 660
+CCD_OPS_SPLIT = {"midpoint": 11, "newton": 30}
+
+
+def ccd_ops(stats, n_patches: int, variant: str) -> float:
+    st = stats.astype(np.int64)
+    return float(CCD_OPS_ROOT * n_patches * len(st) + CCD_OPS_FEASIBLE * st[:, 2].sum()
+                 + CCD_OPS_NEWTON_ITER * st[:, 3].sum() + CCD_OPS_SPLIT[variant] * st[:, 0].sum())
+
+
+def run_ccd_bench(args):
+    """Point-patch continuous collision detection: contact queries/s (one JSON line)."""
+    import torch
+    import oracle as O
+    from paper_2312_14839_gb300 import bhem
+    from paper_2312_14839_gb300 import scenes as S
+    torch.cuda.set_device(0)
+    bhem.load()
+    dev = torch.device("cuda", 0)
+    n = args.points
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+
+    def timing(scene, variant, steps, warmup, want_e2e=False):
+        g, q, dq, x0, dx = S.ccd_scene(scene, n)
+        sh = bhem.Shell(g, S.SHEET_MATERIAL, torch.as_tensor(q.reshape(-1), device=dev), precision="fp64")
+        stream = sh.stream
+        dq_, ddq = (torch.as_tensor(a.reshape(-1), dtype=torch.float64, device=dev) for a in (q, dq))
+        dx0, ddx = torch.as_tensor(x0, device=dev), torch.as_tensor(dx, device=dev)
+        out = sh.ccd_points(dq_, ddq, dx0, ddx, variant=variant, want_stats=True)
+        for _ in range(warmup):
+            sh.ccd_points(dq_, ddq, dx0, ddx, variant=variant, out=out)
+        torch.cuda.synchronize()
+        stats, flags = out["stats"].cpu().numpy(), out["flags"].cpu().numpy()
+        res = {"contact_fraction": float((flags & 1).mean()), "flagged": int((flags & 6).astype(bool).sum()),
+               "splits_mean": float(stats[:, 0].mean()), "splits_max": int(stats[:, 0].max()),
+               "heap_peak_max": int(stats[:, 1].max()), "feasibility_tests_mean": float(stats[:, 2].mean()),
+               "newton_iters_mean": float(stats[:, 3].mean()), "fp64_ops_per_call": ccd_ops(stats, g.n_patches, variant)}
+        l0 = sh.kernel_launches()
+        ms = []
+        with ClockSampler(0) as c:
+            for _ in range(steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sh.ccd_points(dq_, ddq, dx0, ddx, variant=variant, out=out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        clk = c.summary()
+        res["gpu_launches_per_call"] = (sh.kernel_launches() - l0) / max(steps, 1)
+        res["ms_per_call"] = float(np.mean(ms))
+        res["queries_per_s"] = n / (res["ms_per_call"] / 1e3)
+        if want_e2e:
+            hx0, hdx = torch.as_tensor(x0).pin_memory(), torch.as_tensor(dx).pin_memory()
+            host = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items() if k != "stats"}
+            dev_out = {k: v for k, v in out.items() if k != "stats"}
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                for _ in range(steps):
+                    dx0.copy_(hx0, non_blocking=True)
+                    ddx.copy_(hdx, non_blocking=True)
+                    sh.ccd_points(dq_, ddq, dx0, ddx, variant=variant, out=dev_out)
+                    for k in host:
+                        host[k].copy_(dev_out[k], non_blocking=True)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            res["e2e"] = {"value": n * steps / sec, "unit": "contact queries/s",
+                          "h2d_bytes_per_step": int((hx0.numel() + hdx.numel()) * 8),
+                          "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in host.values()))}
+        sh.close()
+        return res, clk
+
+    main_res, clk = timing("drape", "newton", args.steps, args.warmup, want_e2e=True)
+    others = {}
+    for scene, variant in (("drape", "midpoint"), ("plane", "newton"), ("plane", "midpoint")):
+        r, _ = timing(scene, variant, 1, 1)
+        others[f"{scene}_{variant}"] = {k: r[k] for k in ("queries_per_s", "ms_per_call", "contact_fraction",
+                                                          "splits_mean", "splits_max", "flagged")}
+    peak_ops = bhem.measure_fma_peak(True, 256, torch.cuda.current_stream()) / 2.0
+    ach = main_res["fp64_ops_per_call"] / (main_res["ms_per_call"] / 1e3)
+    cpu = None
+    if not args.no_cpu_baseline:
+        g, q, dq, x0, dx = S.ccd_scene("drape", n)
+        idx = np.sort(np.random.default_rng(5).choice(n, min(n, 262144), replace=False))
+        O.build()
+        t0 = time.perf_counter()
+        O.ccd_points(g, q, dq, x0[idx], dx[idx], True)
+        sec = time.perf_counter() - t0
+        cpu = {"value": len(idx) / sec, "unit": "contact queries/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(idx):,} seeded points of the same batch, Newton split, {sec:.1f} s"}
+    print(json.dumps({
+        "metric": "contact queries/s, point-patch continuous collision detection (Sec. 5)",
+        "value": main_res["queries_per_s"], "unit": "contact queries/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main_res["ms_per_call"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded moving points)",
+        "config": {"workload": WORKLOADS["ccd_drape"], "points": n, "patches": 900,
+                   "l2": "flushed (256 MB write) before every timed call"},
+        "e2e": main_res["e2e"], "gpu_launches": main_res["gpu_launches_per_call"] * args.steps,
+        "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
+                     "frac": ach / peak_ops, "traffic": None,
+                     "kernel": "k_ccd_points (+ k_ccd_nets, k_ccd_points_redo in the same events)",
+                     "work": "FP64 operations counted per point from its splits, feasibility tests and Newton iterations",
+                     "peak_source": "measured FP64 FMA rate (shell_measure_fma_peak) as instructions/s"},
+        "cpu_baseline": cpu, "search": {k: main_res[k] for k in ("contact_fraction", "flagged", "splits_mean",
+                                                              "splits_max", "heap_peak_max", "feasibility_tests_mean",
+                                                              "newton_iters_mean", "fp64_ops_per_call")},
+        "other_scenes": others, "clocks": clk,
+    }), flush=True)
+
+
 def run_twist_bench(args):
     """Exact against pseudo Hessian on the twist scene (one JSON line): implicit-Euler steps/s and
     Newton iterations at 1e-8, plus the element pass time of each Hessian."""
@@ -622,6 +746,7 @@ def main():
     ap.add_argument("--train-iters", type=int, default=4000)
     ap.add_argument("--spmv", default="auto", choices=["auto", "plain", "tma"])
     ap.add_argument("--frame", default="1024x768", help="rays_drape: camera frame WxH")
+    ap.add_argument("--points", type=int, default=1 << 20, help="ccd_drape: query points")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -639,6 +764,9 @@ def main():
         return
     if args.workload == "rays_drape":
         run_rays_bench(args)
+        return
+    if args.workload == "ccd_drape":
+        run_ccd_bench(args)
         return
 
     import torch
