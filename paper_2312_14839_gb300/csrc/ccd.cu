@@ -16,9 +16,10 @@
 //                s_min); otherwise it is split at its parameter midpoint (Fig. submid) or, in the
 //                Newton variant, around a root of x(u, v, s) = x0 + s dx found by Newton's
 //                method in (u, v, s), whose neighbourhood is abandoned (Fig. subany). The search
-//                ends when the heap's top cannot beat the best s. The children's feasibility
-//                tests are pooled over the warp, one job per child. Full local heaps move into
-//                global ones as in the ray search.
+//                ends when the heap's top cannot beat the best s. Feasibility tests, of the
+//                patch roots (up to four per lane per round, in patch order) and of the children
+//                of every split, are pooled over the warp, one job per (sub)patch. Full local
+//                heaps move into global ones as in the ray search.
 //   k_ccd_points_redo  points that found no free global heap, searched again from the start.
 //
 // Compiled without mul-add contraction, like rays.cu: every decision is that of the same IEEE FP64
@@ -37,7 +38,6 @@ constexpr double kEpsX = 1e-9;       // refinement size (positions' units)
 constexpr double kEpsS = 1e-9;       // stopping test on the normalised time
 constexpr int kNetBlock = 128;
 constexpr int kCcdBlock = 128;
-constexpr int kRootChunk = 32;       // swept boxes staged in shared memory per pass
 constexpr int kMaxPieces = 8;        // [0, 1] minus six open intervals has at most 7 pieces
 constexpr int kNetStride = 104;      // doubles per patch: P (48), dP (48), swept box (6), unused (2)
 
@@ -229,18 +229,6 @@ __device__ __forceinline__ void load_query(const double* __restrict__ x0s, const
             sqrt((Q.dx[0] * Q.dx[0] + Q.dx[1] * Q.dx[1]) + Q.dx[2] * Q.dx[2]);
 }
 
-// Patch p as a root candidate when its swept box (sw: min xyz, max xyz) meets the segment box.
-__device__ void root_push(Heap& h, const double* __restrict__ nets, const double* sw, int p, const Query& Q) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-    if (Q.seg_hi[c] < sw[c] || Q.seg_lo[c] > sw[3 + c]) return;
-  ++h.boxes;
-  const double* P = nets + (size_t)p * kNetStride;
-  double t0, t1, e;
-  if (sub_feasible(P, P + 48, 0.0, 1.0, 0.0, 1.0, Q.x0, Q.dx, t0, t1, e))
-    h.push(Cand{t0, t1, e, 0.0, 1.0, 0.0, 1.0, p});
-}
-
 struct Search {
   double best = INFINITY, bu = 0.0, bv = 0.0;
   int bp = -1, nexp = 0, flags = 0, newton_iters = 0;
@@ -254,13 +242,14 @@ struct WarpSmem {
   double res[32][4][3];         // t0, t1, ext
   double pt[32][6];             // the owner's x0, dx
   int ok[32][4];
-  int patch[32];
+  int patch[32][4];
   unsigned short jobs[32 * 4];  // lane * 4 + child
 };
 
-__device__ __forceinline__ void put_rect(WarpSmem& sm, int lane, int& nch, double u0, double u1, double v0,
-                                         double v1) {
+__device__ __forceinline__ void put_rect(WarpSmem& sm, int lane, int& nch, int patch, double u0, double u1,
+                                         double v0, double v1) {
   if (!(u1 > u0) || !(v1 > v0)) return;
+  sm.patch[lane][nch] = patch;
   double* R = sm.rect[lane][nch++];
   R[0] = u0;
   R[1] = u1;
@@ -268,15 +257,79 @@ __device__ __forceinline__ void put_rect(WarpSmem& sm, int lane, int& nch, doubl
   R[3] = v1;
 }
 
+// The warp's pool of (lane, child) feasibility jobs: every lane lists nch children in
+// sm.rect / sm.patch; the jobs are spread over the 32 lanes, then each lane pushes its own
+// feasible children in order. All 32 lanes call it together.
+__device__ void pool_and_push(Heap& h, const Query& Q, const double* __restrict__ nets, const Search& S,
+                              WarpSmem& sm, int lane, int nch) {
+  int pre = nch;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, pre, off);
+    if (lane >= off) pre += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, pre, 31);
+  pre -= nch;
+  for (int k = 0; k < nch; ++k) sm.jobs[pre + k] = (unsigned short)(lane * 4 + k);
+  __syncwarp();
+  for (int j = lane; j < total; j += 32) {
+    const int code = sm.jobs[j], owner = code >> 2, ch = code & 3;
+    const double* R = sm.rect[owner][ch];
+    const double* P = nets + (size_t)sm.patch[owner][ch] * kNetStride;
+    const double x0[3] = {sm.pt[owner][0], sm.pt[owner][1], sm.pt[owner][2]};
+    const double dx[3] = {sm.pt[owner][3], sm.pt[owner][4], sm.pt[owner][5]};
+    double t0 = 0.0, t1 = 0.0, e = 0.0;
+    sm.ok[owner][ch] = sub_feasible(P, P + 48, R[0], R[1], R[2], R[3], x0, dx, t0, t1, e) ? 1 : 0;
+    sm.res[owner][ch][0] = t0;
+    sm.res[owner][ch][1] = t1;
+    sm.res[owner][ch][2] = e;
+  }
+  __syncwarp();
+  for (int ch = 0; ch < nch; ++ch) {
+    const double t0 = sm.res[lane][ch][0];
+    if (sm.ok[lane][ch] && !(t0 >= S.best)) {
+      const double* R = sm.rect[lane][ch];
+      h.push(Cand{t0, sm.res[lane][ch][1], sm.res[lane][ch][2], R[0], R[1], R[2], R[3], sm.patch[lane][ch]});
+    }
+  }
+  __syncwarp();
+}
+
+// Root phase, all 32 lanes together: each lane scans the patches in order and lists those whose
+// swept box (nets[p * kNetStride + 96 ..]: min xyz, max xyz) meets its segment box, up to four
+// per round; the pooled feasibility tests push them in patch order.
+__device__ void push_roots(Heap& h, const Query& Q, const double* __restrict__ nets, int np, Search& S,
+                           WarpSmem& sm, int lane) {
+  int next = 0;
+  bool more = S.live;
+  while (__any_sync(0xffffffffu, more)) {
+    int nch = 0;
+    if (more) {
+      for (; next < np && nch < 4; ++next) {
+        const double* sw = nets + (size_t)next * kNetStride + 96;
+        bool miss = false;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (Q.seg_hi[c] < sw[c] || Q.seg_lo[c] > sw[3 + c]) miss = true;
+        if (!miss) put_rect(sm, lane, nch, next, 0.0, 1.0, 0.0, 1.0);
+      }
+      h.boxes += nch;
+      if (next >= np) more = false;
+    }
+    pool_and_push(h, Q, nets, S, sm, lane, nch);
+  }
+}
+
 // The search over the candidates in each lane's heap, all 32 lanes of the warp together (lanes
 // without a query pass live = false).
-__device__ void search(Heap& h, const Query& Q, const double* __restrict__ nets, int use_newton, Search& S,
-                       WarpSmem& sm, int lane) {
+__device__ void search(Heap& h, const Query& Q, const double* __restrict__ nets, int np, int use_newton,
+                       Search& S, WarpSmem& sm, int lane) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     sm.pt[lane][c] = Q.x0[c];
     sm.pt[lane][3 + c] = Q.dx[c];
   }
+  push_roots(h, Q, nets, np, S, sm, lane);
   while (__any_sync(0xffffffffu, S.live)) {
     int nch = 0;
     if (S.live) {
@@ -314,56 +367,24 @@ __device__ void search(Heap& h, const Query& Q, const double* __restrict__ nets,
               const double hu = kNbhd * (c.u1 - c.u0), hv = kNbhd * (c.v1 - c.v0);
               const double a1 = fmax(c.u0, u - hu), a2 = fmin(c.u1, u + hu);
               const double b1 = fmax(c.v0, v - hv), b2 = fmin(c.v1, v + hv);
-              put_rect(sm, lane, nch, c.u0, a1, b1, c.v1);
-              put_rect(sm, lane, nch, a1, c.u1, b2, c.v1);
-              put_rect(sm, lane, nch, c.u0, a2, c.v0, b1);
-              put_rect(sm, lane, nch, a2, c.u1, c.v0, b2);
+              put_rect(sm, lane, nch, c.patch, c.u0, a1, b1, c.v1);
+              put_rect(sm, lane, nch, c.patch, a1, c.u1, b2, c.v1);
+              put_rect(sm, lane, nch, c.patch, c.u0, a2, c.v0, b1);
+              put_rect(sm, lane, nch, c.patch, a2, c.u1, c.v0, b2);
               pinwheel = true;
             }
           }
           if (!pinwheel) {
-            put_rect(sm, lane, nch, c.u0, um, vm, c.v1);
-            put_rect(sm, lane, nch, um, c.u1, vm, c.v1);
-            put_rect(sm, lane, nch, c.u0, um, c.v0, vm);
-            put_rect(sm, lane, nch, um, c.u1, c.v0, vm);
+            put_rect(sm, lane, nch, c.patch, c.u0, um, vm, c.v1);
+            put_rect(sm, lane, nch, c.patch, um, c.u1, vm, c.v1);
+            put_rect(sm, lane, nch, c.patch, c.u0, um, c.v0, vm);
+            put_rect(sm, lane, nch, c.patch, um, c.u1, c.v0, vm);
           }
-          sm.patch[lane] = c.patch;
           h.boxes += nch;
         }
       }
     }
-    // the warp's pool of (lane, child) feasibility jobs
-    int pre = nch;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, pre, off);
-      if (lane >= off) pre += y;
-    }
-    const int total = __shfl_sync(0xffffffffu, pre, 31);
-    pre -= nch;
-    for (int k = 0; k < nch; ++k) sm.jobs[pre + k] = (unsigned short)(lane * 4 + k);
-    __syncwarp();
-    for (int j = lane; j < total; j += 32) {
-      const int code = sm.jobs[j], owner = code >> 2, ch = code & 3;
-      const double* R = sm.rect[owner][ch];
-      const double* P = nets + (size_t)sm.patch[owner] * kNetStride;
-      const double x0[3] = {sm.pt[owner][0], sm.pt[owner][1], sm.pt[owner][2]};
-      const double dx[3] = {sm.pt[owner][3], sm.pt[owner][4], sm.pt[owner][5]};
-      double t0 = 0.0, t1 = 0.0, e = 0.0;
-      sm.ok[owner][ch] = sub_feasible(P, P + 48, R[0], R[1], R[2], R[3], x0, dx, t0, t1, e) ? 1 : 0;
-      sm.res[owner][ch][0] = t0;
-      sm.res[owner][ch][1] = t1;
-      sm.res[owner][ch][2] = e;
-    }
-    __syncwarp();
-    for (int ch = 0; ch < nch; ++ch) {
-      const double t0 = sm.res[lane][ch][0];
-      if (sm.ok[lane][ch] && !(t0 >= S.best)) {
-        const double* R = sm.rect[lane][ch];
-        h.push(Cand{t0, sm.res[lane][ch][1], sm.res[lane][ch][2], R[0], R[1], R[2], R[3], sm.patch[lane]});
-      }
-    }
-    __syncwarp();
+    pool_and_push(h, Q, nets, S, sm, lane, nch);
   }
   if (h.overflow) {
     S.flags |= SHELL_RAY_OVERFLOW;
@@ -400,7 +421,6 @@ __global__ void __launch_bounds__(kCcdBlock, 4) k_ccd_points(long long n, const 
                                                              const double* __restrict__ nets, int use_newton,
                                                              CcdOut out, int* __restrict__ counters,
                                                              int* __restrict__ redo_list, Cand* __restrict__ heaps) {
-  __shared__ double ssw[kRootChunk * 6];
   __shared__ WarpSmem wsm[kCcdBlock / 32];
   const int lane = threadIdx.x & 31;
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -411,18 +431,9 @@ __global__ void __launch_bounds__(kCcdBlock, 4) k_ccd_points(long long n, const 
   h.spill = heaps;
   h.spill_count = counters + 1;
   if (active) load_query(x0s, dxs, k, Q);
-  for (int base = 0; base < np; base += kRootChunk) {
-    const int m = min(kRootChunk, np - base);
-    __syncthreads();
-    for (int i = threadIdx.x; i < m * 6; i += blockDim.x)
-      ssw[i] = nets[(size_t)(base + i / 6) * kNetStride + 96 + i % 6];
-    __syncthreads();
-    if (!active) continue;
-    for (int j = 0; j < m; ++j) root_push(h, nets, ssw + 6 * j, base + j, Q);
-  }
   Search S;
   S.live = active;
-  search(h, Q, nets, use_newton, S, wsm[threadIdx.x >> 5], lane);
+  search(h, Q, nets, np, use_newton, S, wsm[threadIdx.x >> 5], lane);
   if (!active) return;
   if (h.overflow) {
     const int slot = atomicAdd(counters, 1);
@@ -449,13 +460,10 @@ __global__ void __launch_bounds__(kRedoThreads) k_ccd_points_redo(const double* 
     const long long k = active ? redo_list[i] : 0;
     Query Q;
     Heap h(heaps + (size_t)tid * kRedoHeap, kRedoHeap);
-    if (active) {
-      load_query(x0s, dxs, k, Q);
-      for (int p = 0; p < np; ++p) root_push(h, nets, nets + (size_t)p * kNetStride + 96, p, Q);
-    }
+    if (active) load_query(x0s, dxs, k, Q);
     Search S;
     S.live = active;
-    search(h, Q, nets, use_newton, S, wsm[tid >> 5], lane);
+    search(h, Q, nets, np, use_newton, S, wsm[tid >> 5], lane);
     if (active) write_result(out, k, S, h);
   }
 }
