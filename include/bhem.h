@@ -71,6 +71,7 @@ enum { SHELL_PREC_FP64 = 0, SHELL_PREC_MIXED = 1 };
 enum { SHELL_HESS_EXACT = 0, SHELL_HESS_PSEUDO = 1 };
 enum { SHELL_ASM_ATOMIC = 0, SHELL_ASM_COLOR = 1 };
 enum { SHELL_SPMV_AUTO = 0, SHELL_SPMV_PLAIN = 1, SHELL_SPMV_TMA = 2 };
+enum { SHELL_SOLVER_PCG = 0, SHELL_SOLVER_DIRECT = 1 };
 
 /* precision: SHELL_PREC_FP64 = every quantity in FP64; SHELL_PREC_MIXED = element Hessian,
    BSR values, SpMV and block-Jacobi in FP32, while the energy, gradient/residual, line-search
@@ -82,12 +83,20 @@ enum { SHELL_SPMV_AUTO = 0, SHELL_SPMV_PLAIN = 1, SHELL_SPMV_TMA = 2 };
    kernel that streams each CTA's row groups into a shared-memory ring with bulk asynchronous
    copies (cp.async.bulk + mbarrier); rejected when 8 block rows of the longest row do not fit.
    SHELL_SPMV_AUTO: plain (the faster of the two on GB300). Both give bit-identical results.
-   Batches ignore this field. */
+   Batches ignore this field.
+   solver: the linear solver of shell_newton_step. SHELL_SOLVER_PCG: block-Jacobi PCG (the
+   default). SHELL_SOLVER_DIRECT: a comparator for the paper's direct LDL^T solve (Sec. 6.1): the
+   assembled matrix plus the regulariser, prescribed DOFs as identity rows, is expanded to a dense
+   FP64 matrix and factorised by Cholesky with cuSOLVER (potrf/potrs); a failed factorisation (not
+   positive definite) multiplies the regulariser by 10 as negative curvature does for PCG. Shells
+   of at most 65,536 DOF; the first direct step allocates 8 n_dof^2 bytes plus cuSOLVER's
+   workspace. The pcg_* fields of shell_step_params are ignored. Batches ignore this field. */
 typedef struct {
   int precision;
   int hessian;
   int assembly;
   int spmv;
+  int solver;
 } shell_options;
 
 /* One implicit-Euler step (Eq. implicit, Sec. 6.1). Newton stops when |g_free| <= newton_rtol *

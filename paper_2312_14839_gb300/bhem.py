@@ -21,6 +21,7 @@ PREC = {"fp64": 0, "mixed": 1}
 HESS = {"exact": 0, "pseudo": 1}
 ASM = {"atomic": 0, "color": 1}
 SPMV = {"auto": 0, "plain": 1, "tma": 2}
+SOLVER = {"pcg": 0, "direct": 1}
 STATUS = {0: "SHELL_OK", 1: "SHELL_ERR_ARG", 2: "SHELL_ERR_CUDA", 3: "SHELL_ERR_OOM",
           4: "SHELL_ERR_DEGENERATE", 5: "SHELL_ERR_NONFINITE", 6: "SHELL_ERR_NOT_CONVERGED",
           7: "SHELL_ERR_LINESEARCH", 8: "SHELL_ERR_INDEFINITE", 9: "SHELL_ERR_TIMEOUT"}
@@ -44,7 +45,7 @@ class shell_material(C.Structure):
 
 class shell_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("hessian", C.c_int), ("assembly", C.c_int),
-                ("spmv", C.c_int)]
+                ("spmv", C.c_int), ("solver", C.c_int)]
 
 
 class shell_step_params(C.Structure):
@@ -185,7 +186,7 @@ class Shell:
     """One BHEM shell on the current CUDA device (wraps shell_create ... shell_destroy)."""
 
     def __init__(self, grid, material, rest, precision="mixed", hessian="exact",
-                 assembly="atomic", stream=None, spmv="auto"):
+                 assembly="atomic", stream=None, spmv="auto", solver="pcg"):
         import torch
         lib = load()
         self.grid = grid
@@ -196,7 +197,7 @@ class Shell:
                        int(bool(grid.periodic_v)), float(grid.dxi1), float(grid.dxi2))
         m = shell_material(float(material.young), float(material.poisson),
                            float(material.thickness), float(material.density))
-        o = shell_options(PREC[precision], HESS[hessian], ASM[assembly], SPMV[spmv])
+        o = shell_options(PREC[precision], HESS[hessian], ASM[assembly], SPMV[spmv], SOLVER[solver])
         if isinstance(rest, np.ndarray):
             rest = np.ascontiguousarray(rest, dtype=np.float64)
         else:
@@ -367,7 +368,7 @@ class Batch:
         stream_obj, sh = (None, C.c_void_p(None)) if stream is None else _stream_handle(stream)
         self.stream = stream_obj
         self._h = C.c_void_p()
-        opts = shell_options(PREC["mixed"], HESS["exact"], ASM["atomic"], 0)
+        opts = shell_options(PREC["mixed"], HESS["exact"], ASM["atomic"], 0, 0)
         _check(lib.shell_batch_create(S, self.grids, self.mats, _ptr(rest), C.byref(opts), sh, C.byref(self._h)))
         self.n_shells = S
         self.node_offsets = np.zeros(S + 1, dtype=np.int32)

@@ -123,6 +123,11 @@ struct Shell {
   // overlap); d_ray_nets the ray search's Bezier nets [np][3][4][4] and boxes [np][8];
   // d_ccd_nets the collision search's start and displacement nets and swept boxes [np][104]
   void* d_search = nullptr;
+  // direct solver (direct.cu): cuSOLVER handle, dense matrix [n_dof^2] + 2 info ints, workspace
+  void* cusolver = nullptr;
+  double* d_dense = nullptr;
+  double* d_dense_work = nullptr;
+  int dense_lwork = 0;
   double* d_ray_nets = nullptr;
   double* d_ccd_nets = nullptr;
 
@@ -160,6 +165,9 @@ struct Shell {
 shell_status launch_rest_setup(Shell& s);
 // chooses the FP32 SpMV variant (opt.spmv) and prepares its launch (solver.cu)
 shell_status setup_spmv(Shell& s);
+// dense Cholesky solve of the regularised Newton system into s.d_x (direct.cu)
+shell_status run_direct(Shell& s, const unsigned char* mask, const double td[4], const double* rhs, int* not_pd);
+void destroy_direct(Shell& s);
 // the shared search scratch of the Sec. 5 searches (allocated on first use; rays.cu)
 shell_status search_scratch(Shell& s, void** heaps, int** counters, int** redo_list);
 // regulariser shift tau * dbar per DOF kind, as kernel argument

@@ -118,6 +118,7 @@ static void destroy_shell(shell_s* s) {
   for (auto& gph : s->pcg_graphs)
     if (gph.exec) cudaGraphExecDestroy(gph.exec);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  destroy_direct(*s);
   void* ptrs[] = {s->d_patch_nodes, s->d_patch_blocks, s->d_row_ptr, s->d_col, s->d_diag_block,
                   s->d_color_list, s->d_rest, s->d_restgp, s->d_mass, s->d_fgrav, s->d_val,
                   s->d_x, s->d_r, s->d_z, s->d_p, s->d_Ap, s->d_p32, s->d_x32, s->d_r32, s->d_z32, s->d_Ap32, s->d_Dinv, s->d_phi64, s->d_phi32,
@@ -192,12 +193,13 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
   if (!(material->thickness > 0) || !(material->young > 0) || !(material->density >= 0) ||
       !(material->poisson > -1.0 && material->poisson < 1.0))
     return fail(SHELL_ERR_ARG, "invalid material");
-  shell_options opt{SHELL_PREC_MIXED, SHELL_HESS_EXACT, SHELL_ASM_ATOMIC, 0};
+  shell_options opt{SHELL_PREC_MIXED, SHELL_HESS_EXACT, SHELL_ASM_ATOMIC, 0, SHELL_SOLVER_PCG};
   if (options) opt = *options;
   if ((opt.precision != SHELL_PREC_FP64 && opt.precision != SHELL_PREC_MIXED) ||
       (opt.hessian != SHELL_HESS_EXACT && opt.hessian != SHELL_HESS_PSEUDO) ||
       (opt.assembly != SHELL_ASM_ATOMIC && opt.assembly != SHELL_ASM_COLOR) ||
-      (opt.spmv != SHELL_SPMV_AUTO && opt.spmv != SHELL_SPMV_PLAIN && opt.spmv != SHELL_SPMV_TMA))
+      (opt.spmv != SHELL_SPMV_AUTO && opt.spmv != SHELL_SPMV_PLAIN && opt.spmv != SHELL_SPMV_TMA) ||
+      (opt.solver != SHELL_SOLVER_PCG && opt.solver != SHELL_SOLVER_DIRECT))
     return fail(SHELL_ERR_ARG, "invalid options");
   long long np_ll = (long long)g.nu * g.nv;
   if (np_ll > (1LL << 26)) return fail(SHELL_ERR_ARG, "grid too large");
@@ -530,7 +532,10 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
       if (tau > 1e4) { status = SHELL_ERR_INDEFINITE; break; }
       int pit = 0, neg = 0;
       const double td[4] = {tau * K.dbar[0], tau * K.dbar[1], tau * K.dbar[2], tau * K.dbar[3]};
-      BHEM_TRY(run_pcg(s, mask, td, s.d_rhs, P.pcg_rtol, P.pcg_max, P.pcg_fixed_iters, &pit, &neg));
+      if (s.opt.solver == SHELL_SOLVER_DIRECT)
+        BHEM_TRY(run_direct(s, mask, td, s.d_rhs, &neg));
+      else
+        BHEM_TRY(run_pcg(s, mask, td, s.d_rhs, P.pcg_rtol, P.pcg_max, P.pcg_fixed_iters, &pit, &neg));
       st.pcg_iters_total += pit;
       if (!neg) break;
       st.regularizations++;
