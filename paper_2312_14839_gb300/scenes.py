@@ -315,6 +315,8 @@ def ccd_scene(name: str, n_points: int = 4096, seed: int = 11):
            (5 cm, seed 7) 2 cm lower; points over the sheet within 8 cm of z = 0 moving by
            N(0, 4 cm) vertically and N(0, 1 cm) in plane.
     static: the drape sheet at rest (dq = 0), the same points.
+    cylinder: the periodic 10 x 10-patch cylinder (r 0.3 m) expanding radially by 10%; points at
+           radius U[0, 0.5] m moving radially by U[-0.3, 0.3] m.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     if name == "plane":
@@ -325,6 +327,17 @@ def ccd_scene(name: str, n_points: int = 4096, seed: int = 11):
                        rng.uniform(-0.04, 0.06, n_points)], axis=1)
         dx = np.stack([rng.normal(0.0, 0.01, n_points), rng.normal(0.0, 0.01, n_points),
                        rng.uniform(-0.06, 0.06, n_points)], axis=1)
+        return g, q, dq, x0, dx
+    if name == "cylinder":
+        g, q = cylinder(10, 10)
+        dq = 0.1 * q                      # radial breathing by 10% (the axis coordinate too)
+        dq[:, 2] = 0.0
+        dq[:, 8] = 0.0
+        th = rng.uniform(0.0, 2.0 * math.pi, n_points)
+        r0 = rng.uniform(0.0, 0.5, n_points)
+        x0 = np.stack([r0 * np.cos(th), r0 * np.sin(th), rng.uniform(0.05, 0.95, n_points)], axis=1)
+        dr = rng.uniform(-0.3, 0.3, n_points)
+        dx = np.stack([dr * np.cos(th), dr * np.sin(th), rng.normal(0.0, 0.02, n_points)], axis=1)
         return g, q, dq, x0, dx
     g, _, q = sheet_sinusoid(30, 3, 0.05)
     if name == "static":

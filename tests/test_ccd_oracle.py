@@ -133,3 +133,18 @@ def test_newton_split_needs_fewer_splits():
     b = O.ccd_points(g, q, dq, x0, dx, False, want_stats=True)
     assert np.array_equal(a[3] & 1, b[3] & 1)
     assert a[4][:, 0].sum() < 0.7 * b[4][:, 0].sum()
+
+
+def test_breathing_cylinder_against_multistart_newton():
+    """A periodic cylinder expanding radially (patches across the u seam included): contact or
+    not, earliest s and patch against the independent multi-start Newton search."""
+    g, q, dq, x0, dx = S.ccd_scene("cylinder", 40, seed=5)
+    s, patch, uv, flags = O.ccd_points(g, q, dq, x0, dx, True)
+    n_hit = 0
+    for k in range(len(x0)):
+        ref = RB.earliest_contact(g, q, dq, x0[k], dx[k], starts=4, s_starts=(0.2, 0.8))
+        assert bool(flags[k] & 1) == (ref is not None), k
+        if ref is not None:
+            n_hit += 1
+            assert abs(s[k] - ref[0]) <= 1e-9 and patch[k] == ref[1]
+    assert 5 < n_hit < len(x0)

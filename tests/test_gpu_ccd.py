@@ -33,10 +33,11 @@ def _assert_identical(gpu, ref, what):
     np.testing.assert_array_equal(gpu["stats"], stats, err_msg=what)
 
 
-@pytest.mark.parametrize("scene", ["plane", "drape", "static"])
+@pytest.mark.parametrize("scene", ["plane", "drape", "static", "cylinder"])
 @pytest.mark.parametrize("variant", ["newton", "midpoint"])
 def test_scenes_bit_identical(scene, variant):
-    """1,500 points (several CTAs and a ragged last one) per scene and split."""
+    """1,500 points (several CTAs and a ragged last one) per scene and split; the cylinder is
+    periodic in u, so its patches wrap around the seam."""
     g, q, dq, x0, dx = S.ccd_scene(scene, 1500)
     ref = O.ccd_points(g, q, dq, x0, dx, variant == "newton", want_stats=True)
     gpu = _gpu_ccd(g, q, dq, x0, dx, variant)
