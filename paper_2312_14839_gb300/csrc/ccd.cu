@@ -111,19 +111,17 @@ __device__ bool sub_feasible(const double* __restrict__ P, const double* __restr
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
+        // the same updates as a three-way branch on the sign of b, as selects, so that the lanes
+        // of a warp do not diverge (r is only used when b != 0)
         const double a = S[i][j] - x0[k], b = dS[i][j] - dx[k];
-        if (b > 0.0) {
-          const double r = -a / b;
-          if (r > Ll) Ll = r;
-          if (r < Ru) Ru = r;
-        } else if (b < 0.0) {
-          const double r = -a / b;
-          if (r < Rl) Rl = r;
-          if (r > Lu) Lu = r;
-        } else {
-          if (a <= 0.0) all_l = true;
-          if (a >= 0.0) all_u = true;
-        }
+        const double r = -a / b;
+        const bool pos = b > 0.0, neg = b < 0.0;
+        Ll = (pos && r > Ll) ? r : Ll;
+        Ru = (pos && r < Ru) ? r : Ru;
+        Rl = (neg && r < Rl) ? r : Rl;
+        Lu = (neg && r > Lu) ? r : Lu;
+        all_l = all_l || (!pos && !neg && a <= 0.0);
+        all_u = all_u || (!pos && !neg && a >= 0.0);
         const double sv = S[i][j], dv = dS[i][j];
         if (sv < mn) mn = sv;
         if (sv > mx) mx = sv;
