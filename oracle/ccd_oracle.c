@@ -33,7 +33,8 @@
  * Readings where the paper gives no numbers or leaves a choice:
  *   - Time is normalised to the step (s in [0, 1]); EPS_X = 1e-9 (position units), EPS_S =
  *     1e-9 for the stopping test, NBHD = 1e-3, at most 12 Newton iterations, converged when
- *     |F| <= 1e-12 (1 + |x0| + |dx|).
+ *     |F| <= 1e-12 (1 + |x0| + |dx|); as in the static search, Newton gives up once (u, v)
+ *     leaves the candidate's rectangle widened by its own extent on each side.
  *   - The refinement box is bounded over the whole step by the start box plus the displacement
  *     box per axis, so a refined candidate is small at every time, not only at s_min. A
  *     candidate below 1e-13 in both parameter extents also counts as refined.
@@ -140,7 +141,7 @@ static double det3(const double M[3][3]) {
 /* Newton on F(u, v, s) = X(u, v) + s D(u, v) - x0 - s dx, Jacobian [X_u + s D_u | X_v + s D_v |
    D - dx] by Cramer's rule, from (*u, *v, *s). Returns 1 with the root on convergence. */
 static int newton_root(const double P[4][4][3], const double dP[4][4][3], const double x0[3], const double dx[3],
-                       double scale, double* u, double* v, double* s, int* iters) {
+                       double scale, const double win[4], double* u, double* v, double* s, int* iters) {
   double uu = *u, vv = *v, ss = *s;
   for (int it = 0; it < NEWTON_ITERS; ++it) {
     double X[3], Xu[3], Xv[3], D[3], Du[3], Dv[3], F[3], J[3][3];
@@ -169,6 +170,7 @@ static int newton_root(const double P[4][4][3], const double dP[4][4][3], const 
     }
     uu += delta[0]; vv += delta[1]; ss += delta[2];
     if (!isfinite(uu) || !isfinite(vv) || !isfinite(ss)) return 0;
+    if (uu < win[0] || uu > win[1] || vv < win[2] || vv > win[3]) return 0;   /* left the window */
   }
   return 0;
 }
@@ -263,7 +265,9 @@ static int query_one(const double (*P)[4][4][3], const double (*dP)[4][4][3], co
     const double um = 0.5 * (c.u0 + c.u1), vm = 0.5 * (c.v0 + c.v1);
     if (use_newton) {
       double u = um, v = vm, s = c.t0;
-      if (newton_root(Pp, dPp, x0, dx, scale, &u, &v, &s, &newton_iters) && u >= c.u0 && u <= c.u1 &&
+      const double wu = c.u1 - c.u0, wv = c.v1 - c.v0;
+      const double win[4] = {c.u0 - wu, c.u1 + wu, c.v0 - wv, c.v1 + wv};
+      if (newton_root(Pp, dPp, x0, dx, scale, win, &u, &v, &s, &newton_iters) && u >= c.u0 && u <= c.u1 &&
           v >= c.v0 && v <= c.v1 && s >= 0.0 && s <= 1.0) {
         if (s < best) { best = s; bp = c.patch; bu = u; bv = v; }
         const double hu = NBHD * (c.u1 - c.u0), hv = NBHD * (c.v1 - c.v0);

@@ -26,6 +26,9 @@
  *   - EPS_TAU = 1e-9 (absolute, in the units of the positions; directions are unit vectors),
  *     NBHD = 1e-3, at most 12 Newton iterations, Newton converged when
  *     |F| <= 1e-12 (1 + |o| + |tau|), Newton starts with tau = (x(centre) - o) . d.
+ *   - Newton gives up as soon as an iterate leaves the candidate's parameter rectangle widened by
+ *     its own extent on each side: only a root inside the candidate is used, and Newton is an
+ *     accelerator; a region where it gives up is subdivided as usual.
  *   - "Refined" means the box is small, not only the ray's tau interval through it: a ray that
  *     clips the corner of a large box gets a tiny tau interval although the surface need not
  *     cross the ray there. A box no larger than EPS_TAU in every axis also gives a tau interval
@@ -206,9 +209,10 @@ static double det3(const double M[3][3]) {
 }
 
 /* Newton's method on F(u, v, tau) = x(u, v) - o - tau d from (*u, *v, *tau), Jacobian
-   [x_u | x_v | -d] solved by Cramer's rule. Returns 1 with the root on convergence. */
-static int newton_root(const double P[4][4][3], const double o[3], const double d[3], double* u, double* v,
-                       double* tau, int* iters) {
+   [x_u | x_v | -d] solved by Cramer's rule. Returns 1 with the root on convergence; gives up when
+   an iterate leaves the window win (u_min, u_max, v_min, v_max). */
+static int newton_root(const double P[4][4][3], const double o[3], const double d[3], const double win[4],
+                       double* u, double* v, double* tau, int* iters) {
   double uu = *u, vv = *v, tt = *tau;
   const double on = sqrt((o[0] * o[0] + o[1] * o[1]) + o[2] * o[2]);
   for (int it = 0; it < NEWTON_ITERS; ++it) {
@@ -233,6 +237,7 @@ static int newton_root(const double P[4][4][3], const double o[3], const double 
     }
     uu += delta[0]; vv += delta[1]; tt += delta[2];
     if (!isfinite(uu) || !isfinite(vv) || !isfinite(tt)) return 0;
+    if (uu < win[0] || uu > win[1] || vv < win[2] || vv > win[3]) return 0;   /* left the window */
   }
   return 0;
 }
@@ -316,7 +321,9 @@ static int trace_one(const double (*P)[4][4][3], int np, const double o[3], cons
       double x[3], xu[3], xv[3];
       og_bezier_eval(Pp, um, vm, x, xu, xv);
       double u = um, v = vm, t = ((x[0] - o[0]) * d[0] + (x[1] - o[1]) * d[1]) + (x[2] - o[2]) * d[2];
-      if (newton_root(Pp, o, d, &u, &v, &t, &newton_iters) && u >= c.u0 && u <= c.u1 && v >= c.v0 && v <= c.v1 && t >= 0.0) {
+      const double wu = c.u1 - c.u0, wv = c.v1 - c.v0;
+      const double win[4] = {c.u0 - wu, c.u1 + wu, c.v0 - wv, c.v1 + wv};
+      if (newton_root(Pp, o, d, win, &u, &v, &t, &newton_iters) && u >= c.u0 && u <= c.u1 && v >= c.v0 && v <= c.v1 && t >= 0.0) {
         if (t < best) { best = t; bp = c.patch; bu = u; bv = v; }
         /* Fig. subany: drop [a1, a2] x [b1, b2] around the root, four rectangles remain */
         const double hu = NBHD * (c.u1 - c.u0), hv = NBHD * (c.v1 - c.v0);

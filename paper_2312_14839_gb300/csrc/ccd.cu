@@ -166,9 +166,11 @@ __device__ bool sub_feasible(const double* __restrict__ P, const double* __restr
 }
 
 // Newton on F(u, v, s) = X(u, v) + s D(u, v) - x0 - s dx, Jacobian [X_u + s D_u | X_v + s D_v |
-// D - dx] by Cramer's rule. True with the root in (u, v, s) on convergence.
+// D - dx] by Cramer's rule. True with the root in (u, v, s) on convergence; gives up when (u, v)
+// leaves the window win (the candidate's rectangle widened by its extent on each side).
 __device__ bool newton_ccd(const double* __restrict__ P, const double* __restrict__ dP, const double x0[3],
-                           const double dx[3], double scale, double& u, double& v, double& s, int& iters) {
+                           const double dx[3], double scale, const double win[4], double& u, double& v, double& s,
+                           int& iters) {
   double uu = u, vv = v, ss = s;
   for (int it = 0; it < kNewtonIters; ++it) {
     double X[3], Xu[3], Xv[3], D[3], Du[3], Dv[3], F[3], J[3][3];
@@ -205,6 +207,7 @@ __device__ bool newton_ccd(const double* __restrict__ P, const double* __restric
     vv += delta[1];
     ss += delta[2];
     if (!isfinite(uu) || !isfinite(vv) || !isfinite(ss)) return false;
+    if (uu < win[0] || uu > win[1] || vv < win[2] || vv > win[3]) return false;   // left the window
   }
   return false;
 }
@@ -354,7 +357,10 @@ __device__ void search(Heap& h, const Query& Q, const double* __restrict__ nets,
           bool pinwheel = false;
           if (use_newton) {
             double u = um, v = vm, s = c.t0;
-            if (newton_ccd(P, P + 48, Q.x0, Q.dx, Q.scale, u, v, s, S.newton_iters) && u >= c.u0 && u <= c.u1 &&
+            const double wu = c.u1 - c.u0, wv = c.v1 - c.v0;
+            const double win[4] = {c.u0 - wu, c.u1 + wu, c.v0 - wv, c.v1 + wv};
+            if (newton_ccd(P, P + 48, Q.x0, Q.dx, Q.scale, win, u, v, s, S.newton_iters) && u >= c.u0 &&
+                u <= c.u1 &&
                 v >= c.v0 && v <= c.v1 && s >= 0.0 && s <= 1.0) {
               if (s < S.best) {
                 S.best = s;

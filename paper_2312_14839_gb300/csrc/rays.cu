@@ -112,9 +112,10 @@ __global__ void __launch_bounds__(kNetBlock) k_ray_nets(int np, const int4* __re
 }
 
 // Newton's method on F(u, v, tau) = x(u, v) - o - tau d, Jacobian [x_u | x_v | -d] by Cramer's
-// rule. True with the root in (u, v, tau) on convergence.
+// rule. True with the root in (u, v, tau) on convergence; gives up when an iterate leaves the
+// window win (the candidate's rectangle widened by its extent on each side).
 __device__ bool newton_root(const double* __restrict__ P, const double o[3], const double d[3], double on,
-                            double& u, double& v, double& tau, int& iters) {
+                            const double win[4], double& u, double& v, double& tau, int& iters) {
   double uu = u, vv = v, tt = tau;
   for (int it = 0; it < kNewtonIters; ++it) {
     double x[3], xu[3], xv[3], F[3];
@@ -146,6 +147,7 @@ __device__ bool newton_root(const double* __restrict__ P, const double o[3], con
     vv += delta[1];
     tt += delta[2];
     if (!isfinite(uu) || !isfinite(vv) || !isfinite(tt)) return false;
+    if (uu < win[0] || uu > win[1] || vv < win[2] || vv > win[3]) return false;   // left the window
   }
   return false;
 }
@@ -239,7 +241,9 @@ __device__ void search(Heap& h, const Ray& r, const double* __restrict__ nets, i
             bezier_eval(P, um, vm, x, xu, xv);
             double u = um, v = vm;
             double t = ((x[0] - r.o[0]) * r.d[0] + (x[1] - r.o[1]) * r.d[1]) + (x[2] - r.o[2]) * r.d[2];
-            if (newton_root(P, r.o, r.d, S.on, u, v, t, S.newton_iters) && u >= c.u0 && u <= c.u1 &&
+            const double wu = c.u1 - c.u0, wv = c.v1 - c.v0;
+            const double win[4] = {c.u0 - wu, c.u1 + wu, c.v0 - wv, c.v1 + wv};
+            if (newton_root(P, r.o, r.d, S.on, win, u, v, t, S.newton_iters) && u >= c.u0 && u <= c.u1 &&
                 v >= c.v0 && v <= c.v1 && t >= 0.0) {
               if (t < S.best) {
                 S.best = t;
