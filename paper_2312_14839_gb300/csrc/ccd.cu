@@ -18,8 +18,9 @@
 //                method in (u, v, s), whose neighbourhood is abandoned (Fig. subany). The search
 //                ends when the heap's top cannot beat the best s. Feasibility tests, of the
 //                patch roots (up to four per lane per round, in patch order) and of the children
-//                of every split, are pooled over the warp, one job per (sub)patch. Full local
-//                heaps move into global ones as in the ray search.
+//                of every split, are pooled over the warp, one job per (sub)patch and axis; the
+//                owner lane then removes the intervals in order. Full local heaps move into
+//                global ones as in the ray search.
 //   k_ccd_points_redo  points that found no free global heap, searched again from the start.
 //
 // Compiled without mul-add contraction, like rays.cu: every decision is that of the same IEEE FP64
@@ -37,7 +38,7 @@ using namespace bz;
 constexpr double kEpsX = 1e-9;       // refinement size (positions' units)
 constexpr double kEpsS = 1e-9;       // stopping test on the normalised time
 constexpr int kNetBlock = 128;
-constexpr int kCcdBlock = 128;
+constexpr int kCcdBlock = 64;         // 2 warps: the per-warp exchange is 22.7 KB
 constexpr int kMaxPieces = 8;        // [0, 1] minus six open intervals has at most 7 pieces
 constexpr int kNetStride = 104;      // doubles per patch: P (48), dP (48), swept box (6), unused (2)
 
@@ -88,53 +89,65 @@ __device__ __forceinline__ void cut_coord(const double* __restrict__ P, int k, d
   for (int i = 0; i < 4; ++i) curve_restrict(T[i], v0, v1, S[i]);
 }
 
-// Feasible times (Eq. ineqccd) of the sub-net [u0, u1] x [v0, v1] of the moving net (P, dP) for
-// the point x0 + s dx: false when there is none; else the first piece [t0, t1] and the largest
-// per-axis start-box side plus displacement-box side (ext).
-__device__ bool sub_feasible(const double* __restrict__ P, const double* __restrict__ dP, double u0, double u1,
-                             double v0, double v1, const double x0[3], const double dx[3], double& t0, double& t1,
+// One axis k of the feasibility test (Eq. ineqccd) of the sub-net [u0, u1] x [v0, v1] of the
+// moving net (P, dP) for the point x0 + s dx (x0k = x0[k], dxk = dx[k]): the open intervals
+// (L, R) that the lower and upper faces remove from the times (res[0..3] = L_lower, R_lower,
+// L_upper, R_upper; *all bit 0 / bit 1 when a face removes nothing because some control point
+// has b = 0 on the right side), and the axis's start-box side plus displacement-box side (res[4]).
+__device__ void axis_job(const double* __restrict__ P, const double* __restrict__ dP, double u0, double u1,
+                         double v0, double v1, int k, double x0k, double dxk, double res[5], int* all) {
+  double S[4][4], dS[4][4];
+  cut_coord(P, k, u0, u1, v0, v1, S);
+  cut_coord(dP, k, u0, u1, v0, v1, dS);
+  double Ll = -INFINITY, Rl = INFINITY, Lu = -INFINITY, Ru = INFINITY;   // lower face, upper face
+  bool all_l = false, all_u = false;
+  double mn = S[0][0], mx = S[0][0], dmn = dS[0][0], dmx = dS[0][0];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      // the same updates as a three-way branch on the sign of b, as selects, so that the lanes
+      // of a warp do not diverge (r is only used when b != 0)
+      const double a = S[i][j] - x0k, b = dS[i][j] - dxk;
+      const double r = -a / b;
+      const bool pos = b > 0.0, neg = b < 0.0;
+      Ll = (pos && r > Ll) ? r : Ll;
+      Ru = (pos && r < Ru) ? r : Ru;
+      Rl = (neg && r < Rl) ? r : Rl;
+      Lu = (neg && r > Lu) ? r : Lu;
+      all_l = all_l || (!pos && !neg && a <= 0.0);
+      all_u = all_u || (!pos && !neg && a >= 0.0);
+      const double sv = S[i][j], dv = dS[i][j];
+      if (sv < mn) mn = sv;
+      if (sv > mx) mx = sv;
+      if (dv < dmn) dmn = dv;
+      if (dv > dmx) dmx = dv;
+    }
+  res[0] = Ll;
+  res[1] = Rl;
+  res[2] = Lu;
+  res[3] = Ru;
+  res[4] = (mx - mn) + (dmx - dmn);
+  *all = (all_l ? 1 : 0) | (all_u ? 2 : 0);
+}
+
+// The feasible times of one (sub)net from its three axis results (ax[k][0..4], all[k]): [0, 1]
+// minus the removed intervals, axes in order and the lower face first. False when none is left;
+// else the first piece [t0, t1] and the largest per-axis extent (ext).
+__device__ bool combine_axes(const double (*ax)[5], const unsigned char* all, double& t0, double& t1,
                              double& ext) {
   double lo[kMaxPieces], hi[kMaxPieces];
   int n = 1;
   lo[0] = 0.0;
   hi[0] = 1.0;
   double e = 0.0;
-#pragma unroll 1
   for (int k = 0; k < 3; ++k) {
-    double S[4][4], dS[4][4];
-    cut_coord(P, k, u0, u1, v0, v1, S);
-    cut_coord(dP, k, u0, u1, v0, v1, dS);
-    double Ll = -INFINITY, Rl = INFINITY, Lu = -INFINITY, Ru = INFINITY;   // lower face, upper face
-    bool all_l = false, all_u = false;
-    double mn = S[0][0], mx = S[0][0], dmn = dS[0][0], dmx = dS[0][0];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        // the same updates as a three-way branch on the sign of b, as selects, so that the lanes
-        // of a warp do not diverge (r is only used when b != 0)
-        const double a = S[i][j] - x0[k], b = dS[i][j] - dx[k];
-        const double r = -a / b;
-        const bool pos = b > 0.0, neg = b < 0.0;
-        Ll = (pos && r > Ll) ? r : Ll;
-        Ru = (pos && r < Ru) ? r : Ru;
-        Rl = (neg && r < Rl) ? r : Rl;
-        Lu = (neg && r > Lu) ? r : Lu;
-        all_l = all_l || (!pos && !neg && a <= 0.0);
-        all_u = all_u || (!pos && !neg && a >= 0.0);
-        const double sv = S[i][j], dv = dS[i][j];
-        if (sv < mn) mn = sv;
-        if (sv > mx) mx = sv;
-        if (dv < dmn) dmn = dv;
-        if (dv > dmx) dmx = dv;
-      }
-    const double w = (mx - mn) + (dmx - dmn);
+    const double w = ax[k][4];
     if (w > e) e = w;
-#pragma unroll
     for (int side = 0; side < 2; ++side) {
-      const double L = side ? Lu : Ll, R = side ? Ru : Rl;
-      if ((side ? all_u : all_l) || !(L < R)) continue;
-      // remove the open interval (L, R) from every piece, in place (pieces stay sorted)
+      const double L = ax[k][2 * side], R = ax[k][2 * side + 1];
+      if ((all[k] >> side & 1) || !(L < R)) continue;
+      // remove the open interval (L, R) from every piece (pieces stay sorted)
       double nlo[kMaxPieces], nhi[kMaxPieces];
       int m = 0;
       for (int p = 0; p < n; ++p) {
@@ -237,14 +250,14 @@ struct Search {
 };
 
 // Shared-memory exchange of one warp: children listed by each lane in the current split, and
-// their feasibility results computed by whichever lane took the job.
+// the axis results computed for them by whichever lanes took the (child, axis) jobs.
 struct WarpSmem {
   double rect[32][4][4];
-  double res[32][4][3];         // t0, t1, ext
+  double ax[32][4][3][5];       // child, axis: L_lower, R_lower, L_upper, R_upper, extent
   double pt[32][6];             // the owner's x0, dx
-  int ok[32][4];
   int patch[32][4];
-  unsigned short jobs[32 * 4];  // lane * 4 + child
+  unsigned char all[32][4][3];  // bit 0 / 1: lower / upper face removes nothing
+  unsigned short jobs[32 * 12]; // lane * 12 + child * 3 + axis
 };
 
 __device__ __forceinline__ void put_rect(WarpSmem& sm, int lane, int& nch, int patch, double u0, double u1,
@@ -258,39 +271,36 @@ __device__ __forceinline__ void put_rect(WarpSmem& sm, int lane, int& nch, int p
   R[3] = v1;
 }
 
-// The warp's pool of (lane, child) feasibility jobs: every lane lists nch children in
-// sm.rect / sm.patch; the jobs are spread over the 32 lanes, then each lane pushes its own
-// feasible children in order. All 32 lanes call it together.
-__device__ void pool_and_push(Heap& h, const Query& Q, const double* __restrict__ nets, const Search& S,
-                              WarpSmem& sm, int lane, int nch) {
-  int pre = nch;
+// The warp's pool of (lane, child, axis) jobs: every lane lists nch children in sm.rect /
+// sm.patch; the 3 axes of every child are spread over the 32 lanes, then each lane combines its
+// own children's axes and pushes the feasible ones in order. All 32 lanes call it together.
+__device__ void pool_and_push(Heap& h, const double* __restrict__ nets, const Search& S, WarpSmem& sm, int lane,
+                              int nch) {
+  const int nj = 3 * nch;
+  int pre = nj;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
     const int y = __shfl_up_sync(0xffffffffu, pre, off);
     if (lane >= off) pre += y;
   }
   const int total = __shfl_sync(0xffffffffu, pre, 31);
-  pre -= nch;
-  for (int k = 0; k < nch; ++k) sm.jobs[pre + k] = (unsigned short)(lane * 4 + k);
+  pre -= nj;
+  for (int k = 0; k < nj; ++k) sm.jobs[pre + k] = (unsigned short)(lane * 12 + k);
   __syncwarp();
   for (int j = lane; j < total; j += 32) {
-    const int code = sm.jobs[j], owner = code >> 2, ch = code & 3;
+    const int code = sm.jobs[j], owner = code / 12, q = code - 12 * owner, ch = q / 3, k = q % 3;
     const double* R = sm.rect[owner][ch];
     const double* P = nets + (size_t)sm.patch[owner][ch] * kNetStride;
-    const double x0[3] = {sm.pt[owner][0], sm.pt[owner][1], sm.pt[owner][2]};
-    const double dx[3] = {sm.pt[owner][3], sm.pt[owner][4], sm.pt[owner][5]};
-    double t0 = 0.0, t1 = 0.0, e = 0.0;
-    sm.ok[owner][ch] = sub_feasible(P, P + 48, R[0], R[1], R[2], R[3], x0, dx, t0, t1, e) ? 1 : 0;
-    sm.res[owner][ch][0] = t0;
-    sm.res[owner][ch][1] = t1;
-    sm.res[owner][ch][2] = e;
+    int all = 0;
+    axis_job(P, P + 48, R[0], R[1], R[2], R[3], k, sm.pt[owner][k], sm.pt[owner][3 + k], sm.ax[owner][ch][k], &all);
+    sm.all[owner][ch][k] = (unsigned char)all;
   }
   __syncwarp();
   for (int ch = 0; ch < nch; ++ch) {
-    const double t0 = sm.res[lane][ch][0];
-    if (sm.ok[lane][ch] && !(t0 >= S.best)) {
+    double t0, t1, e;
+    if (combine_axes(sm.ax[lane][ch], sm.all[lane][ch], t0, t1, e) && !(t0 >= S.best)) {
       const double* R = sm.rect[lane][ch];
-      h.push(Cand{t0, sm.res[lane][ch][1], sm.res[lane][ch][2], R[0], R[1], R[2], R[3], sm.patch[lane][ch]});
+      h.push(Cand{t0, t1, e, R[0], R[1], R[2], R[3], sm.patch[lane][ch]});
     }
   }
   __syncwarp();
@@ -317,7 +327,7 @@ __device__ void push_roots(Heap& h, const Query& Q, const double* __restrict__ n
       h.boxes += nch;
       if (next >= np) more = false;
     }
-    pool_and_push(h, Q, nets, S, sm, lane, nch);
+    pool_and_push(h, nets, S, sm, lane, nch);
   }
 }
 
@@ -388,7 +398,7 @@ __device__ void search(Heap& h, const Query& Q, const double* __restrict__ nets,
         }
       }
     }
-    pool_and_push(h, Q, nets, S, sm, lane, nch);
+    pool_and_push(h, nets, S, sm, lane, nch);
   }
   if (h.overflow) {
     S.flags |= SHELL_RAY_OVERFLOW;
@@ -420,7 +430,7 @@ __device__ __forceinline__ void write_result(const CcdOut& out, long long k, con
   }
 }
 
-__global__ void __launch_bounds__(kCcdBlock, 4) k_ccd_points(long long n, const double* __restrict__ x0s,
+__global__ void __launch_bounds__(kCcdBlock, 8) k_ccd_points(long long n, const double* __restrict__ x0s,
                                                              const double* __restrict__ dxs, int np,
                                                              const double* __restrict__ nets, int use_newton,
                                                              CcdOut out, int* __restrict__ counters,
@@ -449,14 +459,14 @@ __global__ void __launch_bounds__(kCcdBlock, 4) k_ccd_points(long long n, const 
   write_result(out, k, S, h);
 }
 
-__global__ void __launch_bounds__(kRedoThreads) k_ccd_points_redo(const double* __restrict__ x0s,
+__global__ void __launch_bounds__(kCcdBlock) k_ccd_points_redo(const double* __restrict__ x0s,
                                                                   const double* __restrict__ dxs, int np,
                                                                   const double* __restrict__ nets, int use_newton,
                                                                   CcdOut out, const int* __restrict__ counters,
                                                                   const int* __restrict__ redo_list,
                                                                   Cand* __restrict__ heaps) {
-  __shared__ WarpSmem wsm[kRedoThreads / 32];
-  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ WarpSmem wsm[kCcdBlock / 32];
+  const int tid = blockIdx.x * kCcdBlock + threadIdx.x, lane = threadIdx.x & 31;
   const int count = min(counters[0], kRedoList);
   for (int base = 0; base < count; base += kRedoThreads) {   // uniform trip count: the warp stays whole
     const int i = base + tid;
@@ -467,7 +477,7 @@ __global__ void __launch_bounds__(kRedoThreads) k_ccd_points_redo(const double* 
     if (active) load_query(x0s, dxs, k, Q);
     Search S;
     S.live = active;
-    search(h, Q, nets, np, use_newton, S, wsm[tid >> 5], lane);
+    search(h, Q, nets, np, use_newton, S, wsm[threadIdx.x >> 5], lane);
     if (active) write_result(out, k, S, h);
   }
 }
@@ -506,7 +516,7 @@ extern "C" shell_status shell_ccd_points(shell_t* shell, const double* q, const 
   const int use_newton = variant == SHELL_RAY_NEWTON;
   k_ccd_points<<<(unsigned)((n_points + kCcdBlock - 1) / kCcdBlock), kCcdBlock, 0, sh.stream>>>(
       n_points, x0, dx, np, sh.d_ccd_nets, use_newton, out, counters, redo_list, heaps);
-  k_ccd_points_redo<<<1, kRedoThreads, 0, sh.stream>>>(x0, dx, np, sh.d_ccd_nets, use_newton, out, counters,
+  k_ccd_points_redo<<<kRedoThreads / kCcdBlock, kCcdBlock, 0, sh.stream>>>(x0, dx, np, sh.d_ccd_nets, use_newton, out, counters,
                                                        redo_list, heaps);
   sh.launches += 3;
   BHEM_CUDA(cudaGetLastError());
