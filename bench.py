@@ -424,6 +424,19 @@ def ray_ops(stats, n_patches: int, variant: str) -> float:
                  + RAY_OPS_NEWTON_ITER * st[:, 3].sum() + RAY_OPS_SPLIT[variant] * st[:, 0].sum())
 
 
+def write_depth_pgm(path: str, tau, flags, W: int, H: int):
+    """The frame's hit distances as a 16-bit binary PGM (nearest = brightest, misses black)."""
+    hit = (flags & 1) == 1
+    img = np.zeros(W * H, dtype=np.uint16)
+    if hit.any():
+        t = tau[hit]
+        lo, hi = float(t.min()), float(t.max())
+        img[hit] = (65535.0 * (1.0 - (t - lo) / max(hi - lo, 1e-30)) * 0.9 + 6553.5).astype(np.uint16)
+    with open(path, "wb") as f:
+        f.write(f"P5\n{W} {H}\n65535\n".encode())
+        f.write(img.reshape(H, W).astype(">u2").tobytes())
+
+
 def run_rays_bench(args):
     """Static ray-patch intersection: rays/s on the draped sheet (one JSON line)."""
     import torch
@@ -451,6 +464,8 @@ def run_rays_bench(args):
         torch.cuda.synchronize()
         stats = out["stats"].cpu().numpy()
         flags = out["flags"].cpu().numpy()
+        if args.image and name == "drape" and variant == "newton":
+            write_depth_pgm(args.image, out["tau"].cpu().numpy(), flags, W, H)
         res = {"hit_fraction": float((flags & 1).mean()), "flagged": int((flags & 6).astype(bool).sum()),
                "splits_mean": float(stats[:, 0].mean()), "splits_max": int(stats[:, 0].max()),
                "heap_peak_max": int(stats[:, 1].max()), "newton_iters_mean": float(stats[:, 3].mean()),
@@ -802,6 +817,7 @@ def main():
     ap.add_argument("--spmv", default="auto", choices=["auto", "plain", "tma"])
     ap.add_argument("--frame", default="1024x768", help="rays_drape: camera frame WxH")
     ap.add_argument("--points", type=int, default=1 << 20, help="ccd_drape: query points")
+    ap.add_argument("--image", default="", help="rays_drape: write the drape frame's depth buffer (PGM) here")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
