@@ -373,8 +373,8 @@ typedef enum { SHELL_RAY_MIDPOINT = 0, SHELL_RAY_NEWTON = 1 } shell_ray_variant;
    library-owned 8192-entry heaps; rays beyond those 128 are traced again from the start by a
    second kernel with such a heap, so every result is that of an unbounded heap unless
    SHELL_RAY_OVERFLOW is set. n_rays in [0, 2^31 - 1]; 0 does nothing. Asynchronous
-   on the shell's stream (three kernel launches and a 4-byte memset). The first call on a shell
-   allocates 448 bytes per patch plus 64.3 MB of library-owned device memory (Bezier nets and
+   on the shell's stream (four kernel launches and an 8-byte memset). The first call on a shell
+   allocates 450 bytes per patch plus 64.3 MB of library-owned device memory (Bezier nets and
    boxes, the second pass's heaps), kept until shell_destroy; calls on one shell must not
    overlap on the GPU. */
 SHELL_API shell_status shell_trace_rays(shell_t* shell, const double* q, long long n_rays, const double* origins,

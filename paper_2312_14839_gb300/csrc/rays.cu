@@ -3,6 +3,7 @@
 //
 //   k_ray_nets   one thread per patch: Bezier control net (Hermite data b0 = a, b1 = a + a'/3,
 //                b2 = b - b'/3, b3 = b per direction, tensor product) and its box.
+//   k_ray_groups the box of every kGroup consecutive patches, to skip groups a ray misses.
 //   k_trace_rays one ray per thread, FP64: all patch boxes are tested in patch order (staged
 //                through shared memory, one chunk at a time for the whole CTA), hits go into a
 //                binary min-heap in local memory keyed by the box's entry time tau_min; the top
@@ -41,7 +42,8 @@ using namespace bz;
 constexpr double kEpsTau = 1e-9;     // refinement size (positions' units; unit directions)
 constexpr int kNetBlock = 128;
 constexpr int kRayBlock = 128;
-constexpr int kRootChunk = 32;       // patch boxes staged in shared memory per pass
+constexpr int kRootChunk = 32;       // group boxes staged in shared memory per pass
+constexpr int kGroup = 32;           // consecutive patches per group box
 
 // Min and max of coordinate c of the sub-patch [u0, u1] x [v0, v1] of the net P ([c][i][j]).
 __device__ __forceinline__ void sub_range(const double* __restrict__ P, int c, double u0, double u1, double v0,
@@ -86,6 +88,34 @@ __device__ __forceinline__ bool slab(double mn, double mx, double o, double d, d
   if (a > lo) lo = a;
   if (b < hi) hi = b;
   return true;
+}
+
+// Box of each group of kGroup consecutive patches (min xyz, max xyz of its patches' boxes). A ray
+// that misses a group's box misses every member's: FP64 subtraction and multiplication by the
+// same 1/d are monotone, so the group's slab interval contains each member's.
+__global__ void k_ray_groups(int np, const double* __restrict__ boxes, double* __restrict__ gboxes) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p0 = gi * kGroup;
+  if (p0 >= np) return;
+  const int p1 = min(np, p0 + kGroup);
+  double mn[3], mx[3];
+  for (int c = 0; c < 3; ++c) {
+    mn[c] = boxes[(size_t)p0 * 8 + c];
+    mx[c] = boxes[(size_t)p0 * 8 + 3 + c];
+  }
+  for (int p = p0 + 1; p < p1; ++p)
+    for (int c = 0; c < 3; ++c) {
+      const double a = boxes[(size_t)p * 8 + c], b = boxes[(size_t)p * 8 + 3 + c];
+      if (a < mn[c]) mn[c] = a;
+      if (b > mx[c]) mx[c] = b;
+    }
+  double* G = gboxes + (size_t)gi * 8;
+  for (int c = 0; c < 3; ++c) {
+    G[c] = mn[c];
+    G[3 + c] = mx[c];
+  }
+  G[6] = 0.0;
+  G[7] = 0.0;
 }
 
 __global__ void __launch_bounds__(kNetBlock) k_ray_nets(int np, const int4* __restrict__ pnodes,
@@ -345,7 +375,8 @@ __device__ __forceinline__ void write_hit(const RayOut& out, long long k, const 
 __global__ void __launch_bounds__(kRayBlock, 4) k_trace_rays(long long n, const double* __restrict__ origins,
                                                           const double* __restrict__ dirs, int np,
                                                           const double* __restrict__ nets,
-                                                          const double* __restrict__ boxes, int use_newton,
+                                                          const double* __restrict__ boxes,
+                                                          const double* __restrict__ gboxes, int use_newton,
                                                           RayOut out, int* __restrict__ redo_count,
                                                           int* __restrict__ redo_list, Cand* __restrict__ heaps) {
   __shared__ double sbox[kRootChunk * 8];
@@ -359,14 +390,26 @@ __global__ void __launch_bounds__(kRayBlock, 4) k_trace_rays(long long n, const 
   h.spill = heaps;
   h.spill_count = redo_count + 1;
   if (active) load_ray(origins, dirs, k, r);
-  // every patch's box in patch order; the whole CTA stages one chunk at a time
-  for (int base = 0; base < np; base += kRootChunk) {
-    const int m = min(kRootChunk, np - base);
+  // every patch's box in patch order, skipping the groups whose box the ray misses (their members
+  // would all be missed); the whole CTA stages one chunk of group boxes at a time
+  const int ngroups = (np + kGroup - 1) / kGroup;
+  for (int base = 0; base < ngroups; base += kRootChunk) {
+    const int m = min(kRootChunk, ngroups - base);
     __syncthreads();
-    for (int i = threadIdx.x; i < m * 8; i += blockDim.x) sbox[i] = boxes[(size_t)base * 8 + i];
+    for (int i = threadIdx.x; i < m * 8; i += blockDim.x) sbox[i] = gboxes[(size_t)base * 8 + i];
     __syncthreads();
     if (!active) continue;
-    for (int j = 0; j < m; ++j) root_push(h, sbox + 8 * j, base + j, r);
+    for (int j = 0; j < m; ++j) {
+      const double* G = sbox + 8 * j;
+      double lo = 0.0, hi = INFINITY;
+      bool in = true;
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (in) in = slab(G[c], G[3 + c], r.o[c], r.d[c], r.inv[c], lo, hi);
+      if (!in || lo > hi) continue;
+      const int p0 = (base + j) * kGroup, p1 = min(np, p0 + kGroup);
+      for (int p = p0; p < p1; ++p) root_push(h, boxes + 8 * (size_t)p, p, r);
+    }
   }
   h.boxes = np;
   Search S;
@@ -451,7 +494,8 @@ extern "C" shell_status shell_trace_rays(shell_t* shell, const double* q, long l
   int *redo_count = nullptr, *redo_list = nullptr;
   BHEM_TRY(search_scratch(s, &heaps_v, &redo_count, &redo_list));
   if (!s.d_ray_nets) {
-    const cudaError_t e = cudaMalloc((void**)&s.d_ray_nets, sizeof(double) * 56 * (size_t)np);
+    const size_t ngroups = ((size_t)np + kGroup - 1) / kGroup;
+    const cudaError_t e = cudaMalloc((void**)&s.d_ray_nets, sizeof(double) * (56 * (size_t)np + 8 * ngroups));
     if (e != cudaSuccess) {
       cudaGetLastError();
       s.d_ray_nets = nullptr;
@@ -461,16 +505,19 @@ extern "C" shell_status shell_trace_rays(shell_t* shell, const double* q, long l
   Cand* heaps = (Cand*)heaps_v;
   double* nets = s.d_ray_nets;
   double* boxes = nets + 48 * (size_t)np;
+  double* gboxes = boxes + 8 * (size_t)np;
+  const int ngroups = (np + kGroup - 1) / kGroup;
   RayOut out{tau, patch, uv, flags, stats};
   BHEM_CUDA(cudaMemsetAsync(redo_count, 0, 2 * sizeof(int), s.stream));
   k_ray_nets<<<grid_for(np, kNetBlock), kNetBlock, 0, s.stream>>>(np, s.d_patch_nodes, q, s.grid.dxi1,
                                                                   s.grid.dxi2, nets, boxes);
+  k_ray_groups<<<grid_for(ngroups, kNetBlock), kNetBlock, 0, s.stream>>>(np, boxes, gboxes);
   const int use_newton = variant == SHELL_RAY_NEWTON;
   k_trace_rays<<<(unsigned)((n_rays + kRayBlock - 1) / kRayBlock), kRayBlock, 0, s.stream>>>(
-      n_rays, origins, dirs, np, nets, boxes, use_newton, out, redo_count, redo_list, heaps);
+      n_rays, origins, dirs, np, nets, boxes, gboxes, use_newton, out, redo_count, redo_list, heaps);
   k_trace_rays_redo<<<1, kRedoThreads, 0, s.stream>>>(origins, dirs, np, nets, boxes, use_newton, out, redo_count,
                                                       redo_list, heaps);
-  s.launches += 3;
+  s.launches += 4;
   BHEM_CUDA(cudaGetLastError());
   return SHELL_OK;
 }
