@@ -399,8 +399,8 @@ SHELL_API shell_status shell_trace_rays(shell_t* shell, const double* q, long lo
      stats    device [n_points][4] or NULL: splits, largest heap size, feasibility tests (patches
               that passed the swept-box test included), Newton iterations
    Heaps, second pass and flags as in shell_trace_rays. n_points in [0, 2^31 - 1]; 0 does
-   nothing. Asynchronous on the shell's stream (three kernel launches and an 8-byte memset). The
-   first call allocates 832 bytes per patch (nets and swept boxes), and the first of this call
+   nothing. Asynchronous on the shell's stream (four kernel launches and an 8-byte memset). The
+   first call allocates 834 bytes per patch (nets and swept boxes), and the first of this call
    and shell_trace_rays the 64.3 MB search scratch they share, kept until shell_destroy; calls on
    one shell must not overlap on the GPU. */
 SHELL_API shell_status shell_ccd_points(shell_t* shell, const double* q, const double* dq, long long n_points,

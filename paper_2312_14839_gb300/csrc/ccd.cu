@@ -6,6 +6,7 @@
 //
 //   k_ccd_nets   one thread per patch: start net P, displacement net dP and the swept box (the
 //                box of p_ij and p_ij + dp_ij).
+//   k_ccd_groups the swept box of every kGroup consecutive patches, to skip groups whole.
 //   k_ccd_points one point per thread, FP64. Patches whose swept box misses the point's segment
 //                box are skipped; the others enter a binary min-heap keyed by their earliest
 //                feasible time s_min. Feasible times of a (sub)net: for each axis and each face
@@ -41,6 +42,7 @@ constexpr int kNetBlock = 128;
 constexpr int kCcdBlock = 64;         // 2 warps: the per-warp exchange is 22.7 KB
 constexpr int kMaxPieces = 8;        // [0, 1] minus six open intervals has at most 7 pieces
 constexpr int kNetStride = 104;      // doubles per patch: P (48), dP (48), swept box (6), unused (2)
+constexpr int kGroup = 32;           // consecutive patches per group swept box
 
 __global__ void __launch_bounds__(kNetBlock) k_ccd_nets(int np, const int4* __restrict__ pnodes,
                                                         const double* __restrict__ q, const double* __restrict__ dq,
@@ -69,6 +71,34 @@ __global__ void __launch_bounds__(kNetBlock) k_ccd_nets(int np, const int4* __re
   }
   box[6] = 0.0;
   box[7] = 0.0;
+}
+
+// Swept box of every kGroup consecutive patches (min xyz, max xyz of its members' swept boxes,
+// 8 doubles per group after the per-patch data). A segment box that misses it misses every
+// member's (comparisons only).
+__global__ void k_ccd_groups(int np, const double* __restrict__ nets, double* __restrict__ gboxes) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p0 = gi * kGroup;
+  if (p0 >= np) return;
+  const int p1 = min(np, p0 + kGroup);
+  double mn[3], mx[3];
+  for (int c = 0; c < 3; ++c) {
+    mn[c] = nets[(size_t)p0 * kNetStride + 96 + c];
+    mx[c] = nets[(size_t)p0 * kNetStride + 99 + c];
+  }
+  for (int p = p0 + 1; p < p1; ++p)
+    for (int c = 0; c < 3; ++c) {
+      const double a = nets[(size_t)p * kNetStride + 96 + c], b = nets[(size_t)p * kNetStride + 99 + c];
+      if (a < mn[c]) mn[c] = a;
+      if (b > mx[c]) mx[c] = b;
+    }
+  double* G = gboxes + (size_t)gi * 8;
+  for (int c = 0; c < 3; ++c) {
+    G[c] = mn[c];
+    G[3 + c] = mx[c];
+  }
+  G[6] = 0.0;
+  G[7] = 0.0;
 }
 
 // Coordinate k of the sub-net [u0, u1] x [v0, v1] of P ([c][i][j]): S[i][j], theta1-curves cut
@@ -316,13 +346,25 @@ __device__ void push_roots(Heap& h, const Query& Q, const double* __restrict__ n
   while (__any_sync(0xffffffffu, more)) {
     int nch = 0;
     if (more) {
-      for (; next < np && nch < 4; ++next) {
+      while (next < np && nch < 4) {
+        if (next % kGroup == 0) {   // a group that the segment box misses is skipped whole
+          const double* G = nets + (size_t)np * kNetStride + (size_t)(next / kGroup) * 8;
+          bool gmiss = false;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            if (Q.seg_hi[c] < G[c] || Q.seg_lo[c] > G[3 + c]) gmiss = true;
+          if (gmiss) {
+            next += kGroup;
+            continue;
+          }
+        }
         const double* sw = nets + (size_t)next * kNetStride + 96;
         bool miss = false;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
           if (Q.seg_hi[c] < sw[c] || Q.seg_lo[c] > sw[3 + c]) miss = true;
         if (!miss) put_rect(sm, lane, nch, next, 0.0, 1.0, 0.0, 1.0);
+        ++next;
       }
       h.boxes += nch;
       if (next >= np) more = false;
@@ -501,7 +543,8 @@ extern "C" shell_status shell_ccd_points(shell_t* shell, const double* q, const 
   int *counters = nullptr, *redo_list = nullptr;
   BHEM_TRY(search_scratch(sh, &heaps_v, &counters, &redo_list));
   if (!sh.d_ccd_nets) {
-    const cudaError_t e = cudaMalloc((void**)&sh.d_ccd_nets, sizeof(double) * kNetStride * (size_t)np);
+    const size_t ngroups = ((size_t)np + kGroup - 1) / kGroup;
+    const cudaError_t e = cudaMalloc((void**)&sh.d_ccd_nets, sizeof(double) * (kNetStride * (size_t)np + 8 * ngroups));
     if (e != cudaSuccess) {
       cudaGetLastError();
       sh.d_ccd_nets = nullptr;
@@ -513,12 +556,14 @@ extern "C" shell_status shell_ccd_points(shell_t* shell, const double* q, const 
   BHEM_CUDA(cudaMemsetAsync(counters, 0, 2 * sizeof(int), sh.stream));
   k_ccd_nets<<<grid_for(np, kNetBlock), kNetBlock, 0, sh.stream>>>(np, sh.d_patch_nodes, q, dq, sh.grid.dxi1,
                                                                    sh.grid.dxi2, sh.d_ccd_nets);
+  k_ccd_groups<<<grid_for((np + kGroup - 1) / kGroup, kNetBlock), kNetBlock, 0, sh.stream>>>(
+      np, sh.d_ccd_nets, sh.d_ccd_nets + (size_t)kNetStride * np);
   const int use_newton = variant == SHELL_RAY_NEWTON;
   k_ccd_points<<<(unsigned)((n_points + kCcdBlock - 1) / kCcdBlock), kCcdBlock, 0, sh.stream>>>(
       n_points, x0, dx, np, sh.d_ccd_nets, use_newton, out, counters, redo_list, heaps);
   k_ccd_points_redo<<<kRedoThreads / kCcdBlock, kCcdBlock, 0, sh.stream>>>(x0, dx, np, sh.d_ccd_nets, use_newton, out, counters,
                                                        redo_list, heaps);
-  sh.launches += 3;
+  sh.launches += 4;
   BHEM_CUDA(cudaGetLastError());
   return SHELL_OK;
 }
