@@ -82,3 +82,21 @@ def test_full_size_batch_sampled():
         assert not (gpu["flags"] & 6).any()
         ref = O.ccd_points(g, q, dq, x0[idx], dx[idx], variant == "newton", want_stats=True)
         _assert_identical({k: v[idx] for k, v in gpu.items()}, ref, variant)
+
+
+def test_heap_spill_and_second_pass():
+    """Points sliding inside a flat, static 110 x 110 sheet keep up to 267 candidates (the oracle's
+    unbounded heap): 184 of the 300 outgrow the first pass's 256 entries, more than the 128 global
+    heaps, so both the in-place spill and the second pass run. Every point is bit-identical to
+    the oracle and none is flagged."""
+    from paper_2312_14839_gb300.bhem import RAY_HEAP
+    g, q = S.flat_sheet(110, 110)
+    dq = np.zeros_like(q)
+    angs = np.concatenate([np.array([0.3, 0.5]), np.linspace(0.70, 0.87, 298)])
+    x0 = np.stack([-0.05 * np.ones_like(angs), -0.05 * np.tan(angs), np.zeros_like(angs)], axis=1)
+    dx = 2.0 * np.stack([np.cos(angs), np.sin(angs), np.zeros_like(angs)], axis=1)
+    for variant in ("newton", "midpoint"):
+        ref = O.ccd_points(g, q, dq, x0, dx, variant == "newton", want_stats=True)
+        assert 128 < int((ref[4][:, 1] > RAY_HEAP).sum()) < len(x0)
+        gpu = _gpu_ccd(g, q, dq, x0, dx, variant)
+        _assert_identical(gpu, ref, variant)
