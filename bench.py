@@ -528,13 +528,13 @@ def run_rays_bench(args):
     if not args.no_cpu_baseline:
         g, q, eye, tgt = scenes["drape"]
         o, d = S.camera_rays(W, H, eye, tgt)
-        idx = np.sort(np.random.default_rng(5).choice(n, min(n, 16384), replace=False))
+        idx = np.sort(np.random.default_rng(5).choice(n, min(n, 65536), replace=False))
         O.build()
         t0 = time.perf_counter()
         O.trace_rays(g, q, o[idx], d[idx], True)
         sec = time.perf_counter() - t0
         cpu = {"value": len(idx) / sec, "unit": "rays/s", "cores": 1, "kind": "oracle",
-               "sample": f"16,384 seeded rays of the same {W}x{H} frame, Newton split, {sec:.1f} s"}
+               "sample": f"{len(idx):,} seeded rays of the same {W}x{H} frame, Newton split, {sec:.1f} s"}
     print(json.dumps({
         "metric": "rays/s, static ray-patch intersection (Sec. 5)", "value": main_res["rays_per_s"],
         "unit": "rays/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -648,7 +648,7 @@ def run_ccd_bench(args):
     cpu = None
     if not args.no_cpu_baseline:
         g, q, dq, x0, dx = S.ccd_scene("drape", n)
-        idx = np.sort(np.random.default_rng(5).choice(n, min(n, 262144), replace=False))
+        idx = np.sort(np.random.default_rng(5).choice(n, min(n, 1048576), replace=False))
         O.build()
         t0 = time.perf_counter()
         O.ccd_points(g, q, dq, x0[idx], dx[idx], True)
