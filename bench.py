@@ -192,6 +192,21 @@ def cpu_baseline(workload: str, n_steps: int = 8, n: int = 48):
                       f"{dt:.2f} s each"}
 
 
+def reduce_over_ranks(dist, seconds, units, device=None):
+    """Whole-job aggregate of a weak-scaling run: the slowest rank's timed region (max over ranks)
+    and the units of work of all ranks (sum). Every rank calls it with its own figures; with no
+    process group (dist None) the figures come back unchanged. The tensors live on `device` (the
+    rank's GPU under NCCL, the CPU under gloo)."""
+    if dist is None:
+        return float(seconds), float(units)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -891,16 +906,7 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
     launches = sh.kernel_launches() - launches0
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        it = torch.tensor([newton_iters], device=dev, dtype=torch.float64)
-        dist.all_reduce(it)
-        total_iters = float(it.item())
-    else:
-        total_iters = float(newton_iters)
+    ms, total_iters = reduce_over_ranks(dist, ev0.elapsed_time(ev1), newton_iters, dev)
     sec = ms / 1e3
     value = g.n_patches * total_iters / sec
 
@@ -927,11 +933,8 @@ def main():
         it, dt_ = e2e_step()
         e2e_iters += it
         e2e_sec += dt_
-    if dist:
-        t = torch.tensor([e2e_sec], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_sec = float(t.item())
-    e2e_value = g.n_patches * e2e_iters * world / e2e_sec
+    e2e_sec, e2e_iters = reduce_over_ranks(dist, e2e_sec, e2e_iters, dev)
+    e2e_value = g.n_patches * e2e_iters / e2e_sec
 
     # roofline of the dominant kernel (the FP32 BSR SpMV: 50 launches per step), timed live with
     # CUDA events on the shell's stream over back-to-back launches on the assembled matrix
