@@ -179,7 +179,8 @@ SHELL_API shell_status shell_pcg_solve(shell_t* shell, const unsigned char* fixe
 
 /* y = A x with the currently assembled BSR A (the product inside every PCG iteration of
    Sec. 6.1's linear solve; FP32 arithmetic with FP32 accumulation per row chunk when the shell
-   is SHELL_PREC_MIXED, FP64 otherwise). x, y: device [n_dof], x 16-byte and y 8-byte aligned.
+   is SHELL_PREC_MIXED, FP64 otherwise). x, y: device [n_dof], x 16-byte (SHELL_ERR_ARG
+   otherwise) and y 8-byte aligned.
    x_is_fp32 != 0 (SHELL_PREC_MIXED shells only): x and y are FP32 and the call is one launch of
    the kernel every PCG iteration runs. Otherwise x and y are FP64 (a mixed shell converts
    through its own FP32 vectors: three launches). No mask, no regulariser. Asynchronous. */

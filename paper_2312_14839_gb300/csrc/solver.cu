@@ -874,6 +874,8 @@ static shell_status launch_spmv32(Shell& s, const float* x, Shift4f sh, const un
                                   PcgState* st);
 
 shell_status launch_spmv(Shell& s, const void* x, int x_fp32, void* y) {
+  // every SpMV kernel reads x in 16-byte vector loads
+  if (reinterpret_cast<uintptr_t>(x) & 15) return fail(SHELL_ERR_ARG, "x must be 16-byte aligned");
   const double zero[4] = {0.0, 0.0, 0.0, 0.0};
   if (s.val_fp64) return launch_spmv_impl(s, x, nullptr, nullptr, zero, (double*)y, nullptr);
   const float* xs = (const float*)x;

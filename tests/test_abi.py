@@ -39,3 +39,21 @@ def test_argument_errors_need_no_gpu():
     assert lib.shell_destroy(None) == 0
     assert lib.shell_trace_rays(None, None, 0, None, None, 1, None, None, None, None, None) == 1
     assert lib.shell_ccd_points(None, None, None, 0, None, None, 1, None, None, None, None, None) == 1
+
+
+def test_invalid_options_are_rejected_before_any_device_work():
+    import ctypes as C
+    import numpy as np
+    lib = bhem.load()
+    g = bhem.shell_grid(2, 2, 0, 0, 0.5, 0.5)
+    m = bhem.shell_material(1e5, 0.3, 1e-3, 200.0)
+    rest = np.zeros(9 * 12)
+    out = C.c_void_p()
+    for spmv, solver in ((3, 0), (-1, 0), (0, 2)):
+        o = bhem.shell_options(1, 0, 0, spmv, solver)
+        rc = lib.shell_create(C.byref(g), C.byref(m), rest.ctypes.data_as(C.c_void_p), C.byref(o), None,
+                              C.byref(out))
+        assert rc == 1, (spmv, solver)
+        assert b"invalid options" in lib.shell_last_error()
+        assert not out.value
+

@@ -362,3 +362,17 @@ def test_degenerate_and_nonfinite_inputs_are_reported():
     # the shell stays usable afterwards
     st = sh.newton_step(dev(q.reshape(-1)), zero.clone(), P)
     assert st["status"] == 0
+
+
+def test_spmv_rejects_misaligned_x():
+    """Every SpMV kernel reads x in 16-byte vectors: a misaligned x is an argument error, raised
+    before any launch."""
+    from paper_2312_14839_gb300.bhem import ShellError
+    g, rest, q, mat = CASES["sheet1x1"]()
+    sh = make_shell(g, mat, rest, precision="mixed")
+    buf = torch.zeros(g.n_dof + 4, dtype=torch.float32, device="cuda")
+    with pytest.raises(ShellError, match="16-byte"):
+        sh.spmv(buf[1:1 + g.n_dof])
+    y = sh.spmv(buf[4:4 + g.n_dof])   # 16-byte offset: accepted
+    torch.cuda.synchronize()
+    assert float(y.abs().sum()) == 0.0
