@@ -321,14 +321,18 @@ k_spmv32(int n, const int* __restrict__ rp, const int* __restrict__ col, const f
          const float* __restrict__ x, Shift4f td, const unsigned char* __restrict__ mask,
          float* __restrict__ y, PcgState* st, Reduce red) {
   constexpr int NC = 3, TPR = 36, RPC = kSpmvThreads / TPR;
-  if (st && st->done) return;
+  // the solve's stop flag is read together with the row pointers, which the block loads wait
+  // for anyway, and tested before those loads: a launch after the solve stopped streams nothing
+  // (the flag is written only by the last CTA of a launch, after every CTA read it)
+  const int done = st ? st->done : 0;
   __shared__ float sacc[kSpmvThreads];
   const int t = threadIdx.x;
   const int br = t / TPR, w = t % TPR, r = w / NC, cc = w % NC;
   const int i = blockIdx.x * RPC + br;
+  const int k0 = i < n ? rp[i] : 0, k1 = i < n ? rp[i + 1] : 0;
+  if (done) return;
   float acc = 0.f;
   if (i < n) {
-    const int k0 = rp[i], k1 = rp[i + 1];
     constexpr int U = 9;
     float4 v[U];
     int j[U];
@@ -581,32 +585,46 @@ k_pcg32_init(int n, const double* __restrict__ rhs, const float* __restrict__ Di
   }
 }
 
-__global__ void __launch_bounds__(kNodeThreads)
+__global__ void __launch_bounds__(kNodeThreads, 8)
 k_pcg32_update(int n, float* __restrict__ x, float* __restrict__ r, float* __restrict__ z,
                const float* __restrict__ p, const float* __restrict__ Ap,
                const float* __restrict__ Dinv, const unsigned char* __restrict__ mask, PcgState* st,
                Reduce red) {
   if (st->done) return;
+  const double alpha_d = st->alpha;
   __shared__ float sr[16][12];
   const int ln = threadIdx.x / 12, a = threadIdx.x % 12;
-  const float alpha = (float)st->alpha;
   F2 rz{0.f, 0.f}, rr{0.f, 0.f};
-  // grid-stride over groups of 16 nodes: a few CTAs per SM, so the last CTA of the grid
-  // reduction folds few partials
-  for (int base = blockIdx.x * 16; base < n; base += gridDim.x * 16) {
+  float4 d0, d1, d2;
+  float xv = 0.f, pv = 0.f, av = 0.f, rv = 0.f;
+  // this thread's row of the node's 12x12 inverse (48 contiguous bytes, streamed) and its DOF of
+  // x, p, Ap, r: all in flight together
+  auto load = [&](int base) {
     const int i = base + ln;
-    const size_t gi = (size_t)i * 12 + a;
-    float ri = 0.f, zi = 0.f;
-    float4 d0, d1, d2;
     if (i < n) {
-      // this thread's row of the node's 12x12 inverse: 48 contiguous bytes, streamed, issued with
-      // the vector loads so that all of them are in flight together
       const float4* drow = reinterpret_cast<const float4*>(Dinv + (size_t)i * 144 + a * 12);
       d0 = __ldcs(drow);
       d1 = __ldcs(drow + 1);
       d2 = __ldcs(drow + 2);
-      x[gi] = fmaf(alpha, p[gi], x[gi]);
-      ri = fmaf(-alpha, Ap[gi], r[gi]);
+      const size_t gi = (size_t)i * 12 + a;
+      xv = x[gi];
+      pv = p[gi];
+      av = Ap[gi];
+      rv = r[gi];
+    }
+  };
+  const int stride = gridDim.x * 16;
+  if ((int)blockIdx.x * 16 < n) load(blockIdx.x * 16);
+  const float alpha = (float)alpha_d;
+  // grid-stride over groups of 16 nodes: a few CTAs per SM, so the last CTA of the grid
+  // reduction folds few partials
+  for (int base = blockIdx.x * 16; base < n; base += stride) {
+    const int i = base + ln;
+    const size_t gi = (size_t)i * 12 + a;
+    float ri = 0.f, zi = 0.f;
+    if (i < n) {
+      x[gi] = fmaf(alpha, pv, xv);
+      ri = fmaf(-alpha, av, rv);
       r[gi] = ri;
       sr[ln][a] = ri;
     }
@@ -632,6 +650,7 @@ k_pcg32_update(int n, float* __restrict__ x, float* __restrict__ r, float* __res
     rz = f2_add(rz, f2_prod(ri, zi));
     rr = f2_add(rr, f2_prod(ri, ri));
     __syncthreads();   // sr is rewritten by the next group
+    if (base + stride < n) load(base + stride);
   }
   F2 v[2] = {rz, rr};
   double out[2];
@@ -649,10 +668,15 @@ k_pcg32_update(int n, float* __restrict__ x, float* __restrict__ r, float* __res
 
 __global__ void k_pcg32_pupdate(int m, const float* __restrict__ z, float* __restrict__ p,
                                 const PcgState* st) {
-  if (st->done) return;
-  const float beta = (float)st->beta;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x)
-    p[k] = fmaf(beta, p[k], z[k]);
+  // z and p (8 bytes a thread) are loaded while the stop flag and beta are in flight; a launch
+  // after the solve stopped reads them for nothing
+  const int done = st->done;
+  const double beta_d = st->beta;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+    const float pk = p[k], zk = z[k];
+    if (done) return;
+    p[k] = fmaf((float)beta_d, pk, zk);
+  }
 }
 
 __global__ void k_to_double(int m, const float* __restrict__ a, double* __restrict__ b) {
