@@ -221,6 +221,8 @@ k_element(ElemBatchArgs B) {
     build_hermite_1d<float>(w1d, B.dxi[2 * s], threadIdx.x, blockDim.x);
     build_hermite_1d<float>(w1d + kHerm1D, B.dxi[2 * s + 1], threadIdx.x, blockDim.x);
     __syncthreads();
+    build_phi_gauss(w1d + 2 * kHerm1D, sphi, threadIdx.x, blockDim.x);
+    __syncthreads();
     ElemArgs A{};
     A.pnodes = B.pnodes;
     A.pblocks = B.pblocks;
@@ -236,7 +238,7 @@ k_element(ElemBatchArgs B) {
     A.err = B.err;
     for (int k = item.y + wid; k < item.z; k += NW) {
       const int p = B.plist ? B.plist[k] : k;
-      element_patch<float>(sphi, w1d, Ws[wid], p, A, lane);
+      element_patch<float>(sphi, w1d, w1d + 2 * kHerm1D, Ws[wid], p, A, lane);
     }
   }
 }

@@ -191,15 +191,20 @@ k_element_full(ElemArgs A) {
   R* sphi = reinterpret_cast<R*>(smem_raw);
   R* w1d = sphi + ((kPhiTable + 3) & ~3);
   WarpSmem<R>* Ws = reinterpret_cast<WarpSmem<R>*>(smem_raw + sizeof(R) * elem_table_elems<R>());
+  R* sphg = w1d + 2 * kHerm1D;
   load_shape_table<R>(sphi, reinterpret_cast<const R*>(A.phi));
   build_hermite_1d<R>(w1d, A.d1, threadIdx.x, blockDim.x);
   build_hermite_1d<R>(w1d + kHerm1D, A.d2, threadIdx.x, blockDim.x);
   __syncthreads();
+  if constexpr (sizeof(R) == 4) {
+    build_phi_gauss(sphg, sphi, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpSmem<R>& W = Ws[wid];
   const int total = A.plist ? A.plist_n : A.np;
   for (int it = blockIdx.x * NW + wid; it < total; it += gridDim.x * NW)
-    element_patch<R>(sphi, w1d, W, A.plist ? A.plist[it] : it, A, lane);
+    element_patch<R>(sphi, w1d, sphg, W, A.plist ? A.plist[it] : it, A, lane);
 }
 
 template <typename R>

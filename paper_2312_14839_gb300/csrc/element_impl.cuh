@@ -117,10 +117,25 @@ __device__ __forceinline__ void build_hermite_1d(R* w, double dxi, int tid, int 
   }
 }
 
-// Elements of the element kernels' shared memory before the per-warp areas: shape table, then the
-// two 1D factor tables (theta^1, theta^2)
+// FP32 Hessian stage: per Gauss point g and DOF triple J the five derivative values phi_,k and
+// the value phi, as sphg[(g * 16 + J) * 8 + l] (l = 0..4: phi_,1 .. phi_,12; 5: phi; 6, 7: 0),
+// so that a lane reads them with two 16-byte loads.
+constexpr int kPhiGauss = 16 * 16 * 8;
+
+// Elements of the element kernels' shared memory before the per-warp areas: shape table, the two
+// 1D factor tables (theta^1, theta^2) and, for FP32, the per-Gauss-point table sphg
 template <typename R>
-constexpr int elem_table_elems() { return ((kPhiTable + 3) & ~3) + 2 * kHerm1D; }
+__host__ __device__ constexpr int elem_table_elems() {
+  return ((kPhiTable + 3) & ~3) + 2 * kHerm1D + (sizeof(R) == 4 ? kPhiGauss : 0);
+}
+
+// Fills sphg from the shape table (FP32 kernels; all threads of the CTA, after sphi is complete).
+__device__ __forceinline__ void build_phi_gauss(float* sphg, const float* sphi, int tid, int nthreads) {
+  for (int e = tid; e < kPhiGauss; e += nthreads) {
+    const int g = e >> 7, J = (e >> 3) & 15, l = e & 7;
+    sphg[e] = l < 5 ? sphi[J * kPhiStride + (l + 1) * 16 + g] : (l == 5 ? sphi[J * kPhiStride + g] : 0.f);
+  }
+}
 
 constexpr int kRestFields = 13;
 
@@ -277,12 +292,17 @@ __device__ __forceinline__ int sym15(int i, int j) {
   return i * 15 - (i * (i - 1)) / 2 + (j - i);
 }
 
+// Row stride of T: FP32 rows are padded to 52 (16-byte aligned, and the rows that 8 lanes read
+// together with 16-byte loads fall in distinct banks).
+template <typename R> struct TStride { static constexpr int v = 45; };
+template <> struct TStride<float> { static constexpr int v = 52; };
+
 template <typename R>
 struct WarpSmem {
   R u[48];        // displacement q - rest
   R qb[48];       // rest DOFs
   R M[16][kSym15];   // M_g per Gauss point (symmetric 15x15, packed upper triangle)
-  R T[16 * 45];   // T[I][c*15 + l*3 + c'] of the current Gauss point
+  R T[16 * TStride<R>::v];   // T[I][c*15 + l*3 + c'] of the current Gauss point
   R G[16][15];    // gradient vectors per Gauss point
   R ms[16];       // mass_scale * rho h * W sqrt(a_bar) per Gauss point
   R en[16];       // energy per Gauss point
@@ -512,7 +532,7 @@ __device__ __forceinline__ void t_stage(const R* w1d, const R* Mg, R* T, int g, 
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int I = ((a >> 1) + 2 * (b >> 1)) * 4 + ((a & 1) + 2 * (b & 1));
-        T[I * 45 + col] = W1[0][a] * V[0][b] + W1[1][a] * V[1][b] + W1[2][a] * V[2][b];
+        T[I * TStride<R>::v + col] = W1[0][a] * V[0][b] + W1[1][a] * V[1][b] + W1[2][a] * V[2][b];
       }
   }
 }
@@ -520,7 +540,7 @@ __device__ __forceinline__ void t_stage(const R* w1d, const R* Mg, R* T, int g, 
 // One patch by one warp: gather, Gauss-point matrices M_g, energy/gradient by-products, and the
 // Hessian K = sum_g phi_g^T M_g phi_g written unassembled and/or scattered into the BSR.
 template <typename R>
-__device__ __forceinline__ void element_patch(const R* sphi, const R* w1d, WarpSmem<R>& W, int p,
+__device__ __forceinline__ void element_patch(const R* sphi, const R* w1d, const R* sphg, WarpSmem<R>& W, int p,
                                               const ElemArgs& A, int lane) {
   constexpr int JP = ElemCfg<R>::kJP;          // J columns per pass (16 / 2 / JP passes)
   const int I = lane >> 1, h = lane & 1;
@@ -579,15 +599,41 @@ __device__ __forceinline__ void element_patch(const R* sphi, const R* w1d, WarpS
         t_stage<R>(w1d, W.M[g], W.T, g, lane);
         __syncwarp();
         R Tr[45];
+        if constexpr (sizeof(R) == 4) {
+          // 11 16-byte loads and one 4-byte load of the padded row
+          const float4* t4 = reinterpret_cast<const float4*>(W.T + I * TStride<R>::v);
 #pragma unroll
-        for (int e = 0; e < 45; ++e) Tr[e] = W.T[I * 45 + e];
+          for (int e4 = 0; e4 < 11; ++e4) {
+            const float4 v4 = t4[e4];
+            Tr[4 * e4] = v4.x;
+            Tr[4 * e4 + 1] = v4.y;
+            Tr[4 * e4 + 2] = v4.z;
+            Tr[4 * e4 + 3] = v4.w;
+          }
+          Tr[44] = W.T[I * TStride<R>::v + 44];
+        } else {
+#pragma unroll
+          for (int e = 0; e < 45; ++e) Tr[e] = W.T[I * TStride<R>::v + e];
+        }
         const R mI = W.ms[g] * sphi[I * kPhiStride + g];
 #pragma unroll
         for (int j = 0; j < JP; ++j) {
           const int J = J0 + j;
-          R pj[5];
+          R pj[5], phJ;
+          if constexpr (sizeof(R) == 4) {
+            const float4* q4 = reinterpret_cast<const float4*>(sphg + (g * 16 + J) * 8);
+            const float4 a4 = q4[0], b4 = q4[1];
+            pj[0] = a4.x;
+            pj[1] = a4.y;
+            pj[2] = a4.z;
+            pj[3] = a4.w;
+            pj[4] = b4.x;
+            phJ = b4.y;
+          } else {
 #pragma unroll
-          for (int l = 0; l < 5; ++l) pj[l] = sphi[J * kPhiStride + (l + 1) * 16 + g];
+            for (int l = 0; l < 5; ++l) pj[l] = sphi[J * kPhiStride + (l + 1) * 16 + g];
+            phJ = sphi[J * kPhiStride + g];
+          }
 #pragma unroll
           for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -597,7 +643,7 @@ __device__ __forceinline__ void element_patch(const R* sphi, const R* w1d, WarpS
               for (int l = 0; l < 5; ++l) sacc += Tr[c * 15 + l * 3 + cp] * pj[l];
               acc[j][c * 3 + cp] = sacc;
             }
-          const R mm = mI * sphi[J * kPhiStride + g];
+          const R mm = mI * phJ;
           acc[j][0] += mm;
           acc[j][4] += mm;
           acc[j][8] += mm;
