@@ -537,6 +537,131 @@ __device__ __forceinline__ void t_stage(const R* w1d, const R* Mg, R* T, int g, 
   }
 }
 
+// FP32 Hessian K = sum_g Phi_g^T M_g Phi_g of one patch from its upper node-corner blocks. K is
+// symmetric, so a lane computes the 3x3 blocks (I, J) of one DOF triple I against the J of its
+// own corner and of the later ones only: 136 of the 256 (I, J) pairs in a lane map of at most 6
+// J per lane (rows of corner 0: 3 lanes of 6, 6, 4 J; corner 1: 2 lanes of 6; corner 2: 2 lanes
+// of 4; corner 3: 1 lane of 4). The blocks, and the transposes of those in a later corner, are
+// staged in shared memory over the Gauss-point matrices (no longer needed), from which the
+// unassembled Hessian and the BSR rows are written as before.
+constexpr int kKStride = 52;   // row stride of the staged 48 x 48 Hessian (16-byte aligned rows)
+
+__device__ __forceinline__ void hessian_sym32(const float* sphi, const float* w1d, const float* sphg,
+                                              WarpSmem<float>& W, int p, const ElemArgs& A, int lane) {
+  static_assert(sizeof(W.M) + sizeof(W.T) >= sizeof(float) * 48 * kKStride, "staging area");
+  constexpr int JS = 6;
+  int Is, Js, nJ;
+  if (lane < 12) {
+    Is = lane / 3;
+    Js = 6 * (lane % 3);
+    nJ = lane % 3 == 2 ? 4 : 6;
+  } else if (lane < 20) {
+    Is = 4 + (lane - 12) / 2;
+    Js = 4 + 6 * ((lane - 12) % 2);
+    nJ = 6;
+  } else if (lane < 28) {
+    Is = 8 + (lane - 20) / 2;
+    Js = 8 + 4 * ((lane - 20) % 2);
+    nJ = 4;
+  } else {
+    Is = 12 + (lane - 28);
+    Js = 12;
+    nJ = 4;
+  }
+  float acc[JS][9];
+#pragma unroll
+  for (int j = 0; j < JS; ++j)
+#pragma unroll
+    for (int e = 0; e < 9; ++e) acc[j][e] = 0.f;
+#pragma unroll 1
+  for (int g = 0; g < 16; ++g) {
+    t_stage<float>(w1d, W.M[g], W.T, g, lane);
+    __syncwarp();
+    // row Is of T: 11 16-byte loads and one 4-byte load of the padded row
+    float Tr[45];
+    const float4* t4 = reinterpret_cast<const float4*>(W.T + Is * TStride<float>::v);
+#pragma unroll
+    for (int e4 = 0; e4 < 11; ++e4) {
+      const float4 v4 = t4[e4];
+      Tr[4 * e4] = v4.x;
+      Tr[4 * e4 + 1] = v4.y;
+      Tr[4 * e4 + 2] = v4.z;
+      Tr[4 * e4 + 3] = v4.w;
+    }
+    Tr[44] = W.T[Is * TStride<float>::v + 44];
+    const float mI = W.ms[g] * sphi[Is * kPhiStride + g];
+#pragma unroll
+    for (int j = 0; j < JS; ++j) {
+      if (j >= nJ) break;
+      const float4* q4 = reinterpret_cast<const float4*>(sphg + (g * 16 + Js + j) * 8);
+      const float4 a4 = q4[0], b4 = q4[1];
+      const float pj[5] = {a4.x, a4.y, a4.z, a4.w, b4.x};
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int cp = 0; cp < 3; ++cp) {
+          float sacc = acc[j][c * 3 + cp];
+#pragma unroll
+          for (int l = 0; l < 5; ++l) sacc += Tr[c * 15 + l * 3 + cp] * pj[l];
+          acc[j][c * 3 + cp] = sacc;
+        }
+      const float mm = mI * b4.y;
+      acc[j][0] += mm;
+      acc[j][4] += mm;
+      acc[j][8] += mm;
+    }
+    __syncwarp();
+  }
+  // stage: K[(I, c)][(J, c')], row stride kKStride, over M and T
+  float* K = &W.M[0][0];
+#pragma unroll
+  for (int j = 0; j < JS; ++j) {
+    if (j >= nJ) break;
+    const int J = Js + j;
+    const bool mirror = (J >> 2) != (Is >> 2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int cp = 0; cp < 3; ++cp) {
+        const float v = acc[j][c * 3 + cp];
+        K[(Is * 3 + c) * kKStride + J * 3 + cp] = v;
+        if (mirror) K[(J * 3 + cp) * kKStride + Is * 3 + c] = v;
+      }
+  }
+  __syncwarp();
+  if (A.hess_p) {
+    float* Hp = reinterpret_cast<float*>(A.hess_p) + (size_t)p * 2304;
+    for (int e = lane; e < 2304; e += 32) Hp[e] = K[(e / 48) * kKStride + e % 48];
+  }
+  if (A.bsr) {
+    // lane (I, h): rows (I, c) of the node blocks (I >> 2, b), b = 2h, 2h + 1, 12 entries each
+    float* V = reinterpret_cast<float*>(A.bsr);
+    const int I = lane >> 1, h = lane & 1, a = I >> 2, r = I & 3;
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb) {
+      const int b = 2 * h + bb;
+      const int kb = A.pblocks[p * 16 + a * 4 + b];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float4* src = reinterpret_cast<const float4*>(K + (I * 3 + c) * kKStride + b * 12);
+        float row[12];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const float4 v4 = src[q];
+          row[4 * q] = v4.x;
+          row[4 * q + 1] = v4.y;
+          row[4 * q + 2] = v4.z;
+          row[4 * q + 3] = v4.w;
+        }
+        float* dst = V + (size_t)kb * 144 + (r * 3 + c) * 12;
+        if (A.bsr_atomic) atomic_add_row12<float>(dst, row);
+        else plain_add_row12<float>(dst, row);
+      }
+    }
+  }
+  __syncwarp();
+}
+
 // One patch by one warp: gather, Gauss-point matrices M_g, energy/gradient by-products, and the
 // Hessian K = sum_g phi_g^T M_g phi_g written unassembled and/or scattered into the BSR.
 template <typename R>
@@ -585,7 +710,9 @@ __device__ __forceinline__ void element_patch(const R* sphi, const R* w1d, const
   }
 
   const bool want_h = A.hess_p || A.bsr;
-  if (want_h) {
+  if constexpr (sizeof(R) == 4) {
+    if (want_h) hessian_sym32(sphi, w1d, sphg, reinterpret_cast<WarpSmem<float>&>(W), p, A, lane);
+  } else if (want_h) {
 #pragma unroll 1
     for (int pass = 0; pass < 8 / JP; ++pass) {
       R acc[JP][9];
