@@ -53,6 +53,7 @@ struct PcgState {
   int iters, done, negcurv, fixed;
   int limit;           // iteration cap (mixed precision: enforced on the device)
   float td[4];         // regulariser shift tau * D_k per DOF kind (mixed precision)
+  int bodies;          // loop bodies run by the device-side PCG loop (mixed precision)
 };
 
 // Scalars of one Newton step.
@@ -141,7 +142,7 @@ struct Shell {
   int spmv_tma = 0, spmv_grid = 0, spmv_stage_floats = 0;
   size_t spmv_smem = 0;
 
-  // CUDA graphs of mixed-precision PCG iteration chunks, keyed by (mask, iterations)
+  // CUDA graphs of the mixed-precision PCG loop, keyed by mask (iters = -1)
   struct PcgGraph { const unsigned char* mask; int iters; cudaGraphExec_t exec; };
   static constexpr int kGraphSlots = 12;
   PcgGraph pcg_graphs[kGraphSlots] = {};
@@ -206,7 +207,9 @@ shell_status launch_pcg_init(Shell& s, const unsigned char* mask, const double* 
 shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, const double td[4]);
 // `iters` mixed-precision PCG iterations replayed from a cached CUDA graph (captured on first use
 // for this mask and count); the shift comes from the PCG state
-shell_status launch_pcg_iterations_graph(Shell& s, const unsigned char* mask, int iters);
+// the whole mixed-precision solve as one graph: a conditional WHILE node around one iteration
+shell_status launch_pcg_loop_graph(Shell& s, const unsigned char* mask);
+int pcg_loop_unroll();   // PCG iterations per loop body
 shell_status launch_spmv(Shell& s, const void* x, int x_fp32, void* y);
 shell_status launch_pcg_result(Shell& s);
 shell_status launch_diag_check(Shell& s, const unsigned char* mask, double* out12);

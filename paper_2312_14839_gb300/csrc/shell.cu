@@ -396,20 +396,25 @@ static shell_status run_pcg(Shell& s, const unsigned char* mask, const double td
   mark(s, "pcg_setup_enqueued");
   int launched = 0, chunk = 4;
   *s.h_pcg = PcgState{};
-  BHEM_CUDA(cudaMemcpyAsync(s.h_pcg, s.d_pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s.stream));
-  BHEM_CUDA(cudaStreamSynchronize(s.stream));
-  mark(s, "pcg_setup_synced");
-  while (launched < limit && !s.h_pcg->done) {
-    if (!s.val_fp64) {
-      // mixed precision: the kernels stop at the cap on the device, so whole power-of-two chunks
-      // replay from cached CUDA graphs
-      BHEM_TRY(launch_pcg_iterations_graph(s, mask, chunk));
-      launched += chunk;
-    } else {
-      int c = std::min(chunk, limit - launched);
-      for (int k = 0; k < c; ++k) BHEM_TRY(launch_pcg_iteration(s, mask, td));
-      launched += c;
-    }
+  if (!s.val_fp64) {
+    // mixed precision: the whole solve loops on the device (one graph with a conditional WHILE
+    // node around a few iterations; the kernels stop it, at the latest after `limit` iterations)
+    if (limit > 0) BHEM_TRY(launch_pcg_loop_graph(s, mask));
+    BHEM_CUDA(cudaMemcpyAsync(s.h_pcg, s.d_pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s.stream));
+    BHEM_CUDA(cudaStreamSynchronize(s.stream));
+    // per body: SpMV, update and p-update per iteration, and the loop condition
+    s.launches += (3LL * pcg_loop_unroll() + 1) * s.h_pcg->bodies;
+    mark(s, "pcg_loop");
+    launched = limit;
+  } else {
+    BHEM_CUDA(cudaMemcpyAsync(s.h_pcg, s.d_pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s.stream));
+    BHEM_CUDA(cudaStreamSynchronize(s.stream));
+    mark(s, "pcg_setup_synced");
+  }
+  while (launched < limit && !s.h_pcg->done) {   // FP64: chunks of iterations from the host
+    const int c = std::min(chunk, limit - launched);
+    for (int k = 0; k < c; ++k) BHEM_TRY(launch_pcg_iteration(s, mask, td));
+    launched += c;
     BHEM_CUDA(cudaMemcpyAsync(s.h_pcg, s.d_pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s.stream));
     BHEM_CUDA(cudaStreamSynchronize(s.stream));
     mark(s, "pcg_chunk");
