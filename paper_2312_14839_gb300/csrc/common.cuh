@@ -138,6 +138,9 @@ struct Shell {
   // FP32 SpMV variant: TMA-pipelined persistent kernel when its row-group stages fit in shared
   // memory (max_row = most blocks in one block row)
   int num_sms = 0;                  // multiprocessors of the shell's device (grid sizes)
+  // BHEM_PCG_HOST_LOOP set: mixed-precision PCG iterations are launched from the host in chunks
+  // (as in FP64) instead of the device-side graph loop, whose kernels a profiler cannot list
+  int pcg_host_loop = 0;
   int max_row = 0;
   int spmv_tma = 0, spmv_grid = 0, spmv_stage_floats = 0;
   size_t spmv_smem = 0;

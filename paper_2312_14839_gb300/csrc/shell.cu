@@ -218,6 +218,7 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
   s->lam = material->young * material->poisson / (1.0 - material->poisson * material->poisson);
   s->mu = material->young / (2.0 * (1.0 + material->poisson));
   s->val_fp64 = opt.precision == SHELL_PREC_FP64;
+  s->pcg_host_loop = getenv("BHEM_PCG_HOST_LOOP") != nullptr;
 
   HostTopo T;
   build_topology(g, s->n1, s->n2, T);
@@ -396,7 +397,7 @@ static shell_status run_pcg(Shell& s, const unsigned char* mask, const double td
   mark(s, "pcg_setup_enqueued");
   int launched = 0, chunk = 4;
   *s.h_pcg = PcgState{};
-  if (!s.val_fp64) {
+  if (!s.val_fp64 && !s.pcg_host_loop) {
     // mixed precision: the whole solve loops on the device (one graph with a conditional WHILE
     // node around a few iterations; the kernels stop it, at the latest after `limit` iterations)
     if (limit > 0) BHEM_TRY(launch_pcg_loop_graph(s, mask));
@@ -411,7 +412,7 @@ static shell_status run_pcg(Shell& s, const unsigned char* mask, const double td
     BHEM_CUDA(cudaStreamSynchronize(s.stream));
     mark(s, "pcg_setup_synced");
   }
-  while (launched < limit && !s.h_pcg->done) {   // FP64: chunks of iterations from the host
+  while (launched < limit && !s.h_pcg->done) {   // FP64 (or BHEM_PCG_HOST_LOOP): host chunks
     const int c = std::min(chunk, limit - launched);
     for (int k = 0; k < c; ++k) BHEM_TRY(launch_pcg_iteration(s, mask, td));
     launched += c;

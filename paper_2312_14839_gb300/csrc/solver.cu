@@ -185,13 +185,28 @@ __global__ void k_diag_check(int n, const int* __restrict__ diag_block, const Rm
   double v[12];
 #pragma unroll
   for (int q = 0; q < 4; ++q) { v[3 * q] = 0.0; v[3 * q + 1] = 0.0; v[3 * q + 2] = INFINITY; }
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n * 12; k += gridDim.x * blockDim.x) {
-    if (mask && mask[k]) continue;
-    const int i = k / 12, a = k % 12, q = a / 3;
-    const double d = (double)val[(size_t)diag_block[i] * 144 + a * 13];
+  // grid-stride over the DOFs, the loads of U strides issued before their use (a few CTAs per SM:
+  // the FP64 block reductions below are the expensive part on this GPU)
+  constexpr int U = 4;
+  const int m = n * 12, stride = gridDim.x * blockDim.x;
+  for (int k0 = blockIdx.x * blockDim.x + threadIdx.x; k0 < m; k0 += U * stride) {
+    Rm d[U];
+    bool use[U];
 #pragma unroll
-    for (int qq = 0; qq < 4; ++qq)
-      if (qq == q) { v[3 * qq] += fabs(d); v[3 * qq + 1] += 1.0; v[3 * qq + 2] = fmin(v[3 * qq + 2], d); }
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u * stride;
+      use[u] = k < m && !(mask && mask[k]);
+      if (use[u]) d[u] = val[(size_t)diag_block[k / 12] * 144 + (k % 12) * 13];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (use[u]) {
+        const int q = ((k0 + u * stride) % 12) / 3;
+        const double dd = (double)d[u];
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq)
+          if (qq == q) { v[3 * qq] += fabs(dd); v[3 * qq + 1] += 1.0; v[3 * qq + 2] = fmin(v[3 * qq + 2], dd); }
+      }
   }
   grid_reduce<12>(v, red, out12, gridDim.x, 0x924u);   // the min entries: 2, 5, 8, 11
 }
@@ -833,8 +848,8 @@ shell_status launch_precond_setup(Shell& s, const unsigned char* mask, const dou
 }
 
 shell_status launch_diag_check(Shell& s, const unsigned char* mask, double* out12) {
-  int blocks = vec_blocks(s.n_dof);
-  if (blocks > 1024) blocks = 1024;
+  int blocks = grid_for(s.n_dof, 256 * 4);
+  if (blocks > 2 * std::max(1, s.num_sms)) blocks = 2 * std::max(1, s.num_sms);
   if (s.val_fp64)
     k_diag_check<double><<<blocks, 256, 0, s.stream>>>(s.n_nodes, s.d_diag_block,
         (const double*)s.d_val, mask, out12, s.red);

@@ -376,3 +376,37 @@ def test_spmv_rejects_misaligned_x():
     y = sh.spmv(buf[4:4 + g.n_dof])   # 16-byte offset: accepted
     torch.cuda.synchronize()
     assert float(y.abs().sum()) == 0.0
+
+
+@pytest.mark.parametrize("case,mass_scale,fixed", [
+    ("sheet10x10-noisy", 1e6, 0),      # converges to rtol
+    ("sheet10x10-noisy", 1e6, 7),      # a cap that ends inside a 4-iteration loop body
+    ("sinusoid16", 1.0, 0),            # indefinite: stops on negative curvature
+])
+def test_pcg_device_loop_matches_host_loop(monkeypatch, case, mass_scale, fixed):
+    """The mixed-precision solve loops on the device (a conditional graph node around 4
+    iterations); BHEM_PCG_HOST_LOOP launches the same iterations from the host. Same kernels in
+    the same order: iteration count, curvature flag and solution are identical."""
+    if case == "sinusoid16":
+        g, rest, q = S.sheet_sinusoid(16, 3)
+        mat = THIN
+    else:
+        g, rest, q, mat = CASES[case]()
+    mask = dev(S.pinned_mask(g, [0, g.n_nodes - 1]), torch.uint8)
+    res = []
+    for host_loop in (False, True):
+        if host_loop:
+            monkeypatch.setenv("BHEM_PCG_HOST_LOOP", "1")
+        else:
+            monkeypatch.delenv("BHEM_PCG_HOST_LOOP", raising=False)
+        sh = make_shell(g, mat, rest, precision="mixed", assembly="color")
+        _, G = sh.energy_grad_hess(dev(q.reshape(-1)), mass_scale=mass_scale)
+        x, it, neg = sh.pcg_solve(-G, mask=mask, rtol=1e-6, max_iter=1000, fixed_iters=fixed)
+        res.append((host(x), it, neg))
+        sh.close()
+    assert res[0][1] == res[1][1] and res[0][2] == res[1][2], (res[0][1:], res[1][1:])
+    if fixed:
+        assert res[0][1] == fixed
+    if case == "sinusoid16":
+        assert res[0][2] == 1
+    assert np.array_equal(res[0][0], res[1][0])
