@@ -93,6 +93,7 @@ struct Shell {
   double* d_phi64 = nullptr;        // shape table + Gauss weights (kPhiTable doubles)
   float* d_phi32 = nullptr;         // the same in FP32
   double* d_mass = nullptr;         // [n_blocks * 16] consistent mass, 4x4 scalar blocks
+  double* d_qmy = nullptr;          // [n_dof] q - y of the residual's inertial term
   double* d_fgrav = nullptr;        // [n_nodes * 4] gravity load factors
 
   // assembled matrix

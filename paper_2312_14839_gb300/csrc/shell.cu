@@ -123,7 +123,7 @@ static void destroy_shell(shell_s* s) {
                   s->d_color_list, s->d_rest, s->d_restgp, s->d_mass, s->d_fgrav, s->d_val,
                   s->d_x, s->d_r, s->d_z, s->d_p, s->d_Ap, s->d_p32, s->d_x32, s->d_r32, s->d_z32, s->d_Ap32, s->d_Dinv, s->d_phi64, s->d_phi32,
                   s->d_pcg, s->d_qn, s->d_y, s->d_g, s->d_gin, s->d_d, s->d_Md, s->d_Ep,
-                  s->d_qwork, s->d_vwork, s->d_qfix, s->d_warm, s->d_mask, s->d_ns, s->d_err,
+                  s->d_qwork, s->d_vwork, s->d_qfix, s->d_warm, s->d_mask, s->d_ns, s->d_err, s->d_qmy,
                   s->d_energy_tmp, s->red.partials, s->red.ticket, s->d_rhs, s->d_g2, s->d_Ep2,
                   s->d_search, s->d_ray_nets, s->d_ccd_nets};
   for (void* p : ptrs) dfree(p);
@@ -262,7 +262,7 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
   A(s->d_pcg, 1); A(s->d_p32, m); A(s->d_x32, m); A(s->d_r32, m); A(s->d_z32, m); A(s->d_Ap32, m);
   A(s->d_phi64, 1568); A(s->d_phi32, 1568);
   A(s->d_qn, m); A(s->d_y, m); A(s->d_g, m); A(s->d_gin, m); A(s->d_d, m); A(s->d_Md, m);
-  A(s->d_rhs, m); A(s->d_Ep, np); A(s->d_qwork, m); A(s->d_vwork, m); A(s->d_qfix, m);
+  A(s->d_rhs, m); A(s->d_Ep, np); A(s->d_qwork, m); A(s->d_vwork, m); A(s->d_qfix, m); A(s->d_qmy, m);
   A(s->d_warm, m); A(s->d_mask, m); A(s->d_ns, 1); A(s->d_err, 1); A(s->d_energy_tmp, 1);
   A(s->d_g2, m); A(s->d_Ep2, np);
   // partials: one per CTA of the largest reducing launch (8 patches, 4 FP64 block rows, 16 nodes or

@@ -853,6 +853,10 @@ __global__ void k_dots3(int m, const double* __restrict__ a0, const double* __re
   grid_reduce<3>(v, red, out, gridDim.x);
 }
 
+__global__ void k_diff(int m, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ c) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) c[k] = a[k] - b[k];
+}
+
 __global__ void k_axpy(int m, double* __restrict__ q, const double* __restrict__ d, double alpha) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) q[k] = __fma_rn(alpha, d[k], q[k]);
 }
@@ -891,8 +895,12 @@ shell_status launch_grad_finish(Shell& s, const double* q, const double* y, doub
                                 double* gin, double* gnorm2_out) {
   int blocks = grid_for(s.n_nodes, 16);
   if (blocks > s.red.stride) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
+  // q - y once per DOF: the mass product then takes one FP64 FMA per term instead of a
+  // subtraction and an FMA (it is bound by the FP64 pipe); same values, same sums
+  k_diff<<<vec_blocks(s.n_dof), 256, 0, s.stream>>>(s.n_dof, q, y, s.d_qmy);
+  ++s.launches;
   k_grad_finish<<<blocks, kNodeThreads, 0, s.stream>>>(s.n_nodes, s.d_row_ptr, s.d_col, s.d_mass,
-                                                       s.d_fgrav, q, y, 1.0 / (dt * dt), grav[0],
+                                                       s.d_fgrav, s.d_qmy, nullptr, 1.0 / (dt * dt), grav[0],
                                                        grav[1], grav[2], mask, g, gin, gnorm2_out,
                                                        s.red, s.d_err);
   BHEM_CUDA(cudaGetLastError());
