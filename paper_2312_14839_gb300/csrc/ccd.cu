@@ -336,40 +336,113 @@ __device__ void pool_and_push(Heap& h, const double* __restrict__ nets, const Se
   __syncwarp();
 }
 
-// Root phase, all 32 lanes together: each lane scans the patches in order and lists those whose
-// swept box (nets[p * kNetStride + 96 ..]: min xyz, max xyz) meets its segment box, up to four
-// per round; the pooled feasibility tests push them in patch order.
+// One round of a lane's root scan: the patches from `next` on, in order, whose swept box
+// (nets[p * kNetStride + 96 ..]: min xyz, max xyz) meets the query's segment box, up to four;
+// true when the scan has passed the last patch.
+__device__ __forceinline__ bool root_round(Heap& h, const Query& Q, const double* __restrict__ nets, int np,
+                                           WarpSmem& sm, int lane, int& next, int& nch) {
+  while (next < np && nch < 4) {
+    if (next % kGroup == 0) {   // a group that the segment box misses is skipped whole
+      const double* G = nets + (size_t)np * kNetStride + (size_t)(next / kGroup) * 8;
+      bool gmiss = false;
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (Q.seg_hi[c] < G[c] || Q.seg_lo[c] > G[3 + c]) gmiss = true;
+      if (gmiss) {
+        next += kGroup;
+        continue;
+      }
+    }
+    const double* sw = nets + (size_t)next * kNetStride + 96;
+    bool miss = false;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (Q.seg_hi[c] < sw[c] || Q.seg_lo[c] > sw[3 + c]) miss = true;
+    if (!miss) put_rect(sm, lane, nch, next, 0.0, 1.0, 0.0, 1.0);
+    ++next;
+  }
+  h.boxes += nch;
+  return next >= np;
+}
+
+// Root phase, all 32 lanes together: the pooled feasibility tests push each lane's roots in
+// patch order.
 __device__ void push_roots(Heap& h, const Query& Q, const double* __restrict__ nets, int np, Search& S,
                            WarpSmem& sm, int lane) {
   int next = 0;
   bool more = S.live;
   while (__any_sync(0xffffffffu, more)) {
     int nch = 0;
-    if (more) {
-      while (next < np && nch < 4) {
-        if (next % kGroup == 0) {   // a group that the segment box misses is skipped whole
-          const double* G = nets + (size_t)np * kNetStride + (size_t)(next / kGroup) * 8;
-          bool gmiss = false;
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-            if (Q.seg_hi[c] < G[c] || Q.seg_lo[c] > G[3 + c]) gmiss = true;
-          if (gmiss) {
-            next += kGroup;
-            continue;
+    if (more && root_round(h, Q, nets, np, sm, lane, next, nch)) more = false;
+    pool_and_push(h, nets, S, sm, lane, nch);
+  }
+}
+
+// One split of a lane's search: pop the earliest candidate and either finish (nothing earlier
+// can remain), record a refined contact, or list its 4 children (Newton pinwheel or midpoint
+// split) for the warp's pooled feasibility tests.
+__device__ __forceinline__ void split_step(Heap& h, const Query& Q, const double* __restrict__ nets, int use_newton,
+                                           Search& S, WarpSmem& sm, int lane, int& nch) {
+  if (h.n == 0 || h.overflow) {
+    S.live = false;
+  } else {
+    const Cand c = h.pop();
+    if (c.t0 >= S.best - kEpsS) {                                      // nothing left can be earlier
+      S.live = false;
+    } else if (c.ext <= kEpsX || (c.u1 - c.u0 < 1e-13 && c.v1 - c.v0 < 1e-13)) {   // refined
+      if (c.t0 < S.best - kEpsS) {
+        S.best = c.t0;
+        S.bp = c.patch;
+        S.bu = 0.5 * (c.u0 + c.u1);
+        S.bv = 0.5 * (c.v0 + c.v1);
+      }
+    } else if (S.nexp == kMaxExpansions) {
+      S.flags |= SHELL_RAY_LIMIT;
+      S.live = false;
+    } else {
+      ++S.nexp;
+      const double* P = nets + (size_t)c.patch * kNetStride;
+      const double um = 0.5 * (c.u0 + c.u1), vm = 0.5 * (c.v0 + c.v1);
+      bool pinwheel = false;
+      if (use_newton) {
+        double u = um, v = vm, s = c.t0;
+        const double wu = c.u1 - c.u0, wv = c.v1 - c.v0;
+        const double win[4] = {c.u0 - wu, c.u1 + wu, c.v0 - wv, c.v1 + wv};
+        if (newton_ccd(P, P + 48, Q.x0, Q.dx, Q.scale, win, u, v, s, S.newton_iters) && u >= c.u0 &&
+            u <= c.u1 &&
+            v >= c.v0 && v <= c.v1 && s >= 0.0 && s <= 1.0) {
+          if (s < S.best) {
+            S.best = s;
+            S.bp = c.patch;
+            S.bu = u;
+            S.bv = v;
           }
+          const double hu = kNbhd * (c.u1 - c.u0), hv = kNbhd * (c.v1 - c.v0);
+          const double a1 = fmax(c.u0, u - hu), a2 = fmin(c.u1, u + hu);
+          const double b1 = fmax(c.v0, v - hv), b2 = fmin(c.v1, v + hv);
+          put_rect(sm, lane, nch, c.patch, c.u0, a1, b1, c.v1);
+          put_rect(sm, lane, nch, c.patch, a1, c.u1, b2, c.v1);
+          put_rect(sm, lane, nch, c.patch, c.u0, a2, c.v0, b1);
+          put_rect(sm, lane, nch, c.patch, a2, c.u1, c.v0, b2);
+          pinwheel = true;
         }
-        const double* sw = nets + (size_t)next * kNetStride + 96;
-        bool miss = false;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          if (Q.seg_hi[c] < sw[c] || Q.seg_lo[c] > sw[3 + c]) miss = true;
-        if (!miss) put_rect(sm, lane, nch, next, 0.0, 1.0, 0.0, 1.0);
-        ++next;
+      }
+      if (!pinwheel) {
+        put_rect(sm, lane, nch, c.patch, c.u0, um, vm, c.v1);
+        put_rect(sm, lane, nch, c.patch, um, c.u1, vm, c.v1);
+        put_rect(sm, lane, nch, c.patch, c.u0, um, c.v0, vm);
+        put_rect(sm, lane, nch, c.patch, um, c.u1, c.v0, vm);
       }
       h.boxes += nch;
-      if (next >= np) more = false;
     }
-    pool_and_push(h, nets, S, sm, lane, nch);
+  }
+}
+
+__device__ __forceinline__ void finish_flags(const Heap& h, Search& S) {
+  if (h.overflow) {
+    S.flags |= SHELL_RAY_OVERFLOW;
+  } else if (S.bp >= 0) {
+    S.flags |= SHELL_RAY_HIT;
   }
 }
 
@@ -385,68 +458,10 @@ __device__ void search(Heap& h, const Query& Q, const double* __restrict__ nets,
   push_roots(h, Q, nets, np, S, sm, lane);
   while (__any_sync(0xffffffffu, S.live)) {
     int nch = 0;
-    if (S.live) {
-      if (h.n == 0 || h.overflow) {
-        S.live = false;
-      } else {
-        const Cand c = h.pop();
-        if (c.t0 >= S.best - kEpsS) {                                      // nothing left can be earlier
-          S.live = false;
-        } else if (c.ext <= kEpsX || (c.u1 - c.u0 < 1e-13 && c.v1 - c.v0 < 1e-13)) {   // refined
-          if (c.t0 < S.best - kEpsS) {
-            S.best = c.t0;
-            S.bp = c.patch;
-            S.bu = 0.5 * (c.u0 + c.u1);
-            S.bv = 0.5 * (c.v0 + c.v1);
-          }
-        } else if (S.nexp == kMaxExpansions) {
-          S.flags |= SHELL_RAY_LIMIT;
-          S.live = false;
-        } else {
-          ++S.nexp;
-          const double* P = nets + (size_t)c.patch * kNetStride;
-          const double um = 0.5 * (c.u0 + c.u1), vm = 0.5 * (c.v0 + c.v1);
-          bool pinwheel = false;
-          if (use_newton) {
-            double u = um, v = vm, s = c.t0;
-            const double wu = c.u1 - c.u0, wv = c.v1 - c.v0;
-            const double win[4] = {c.u0 - wu, c.u1 + wu, c.v0 - wv, c.v1 + wv};
-            if (newton_ccd(P, P + 48, Q.x0, Q.dx, Q.scale, win, u, v, s, S.newton_iters) && u >= c.u0 &&
-                u <= c.u1 &&
-                v >= c.v0 && v <= c.v1 && s >= 0.0 && s <= 1.0) {
-              if (s < S.best) {
-                S.best = s;
-                S.bp = c.patch;
-                S.bu = u;
-                S.bv = v;
-              }
-              const double hu = kNbhd * (c.u1 - c.u0), hv = kNbhd * (c.v1 - c.v0);
-              const double a1 = fmax(c.u0, u - hu), a2 = fmin(c.u1, u + hu);
-              const double b1 = fmax(c.v0, v - hv), b2 = fmin(c.v1, v + hv);
-              put_rect(sm, lane, nch, c.patch, c.u0, a1, b1, c.v1);
-              put_rect(sm, lane, nch, c.patch, a1, c.u1, b2, c.v1);
-              put_rect(sm, lane, nch, c.patch, c.u0, a2, c.v0, b1);
-              put_rect(sm, lane, nch, c.patch, a2, c.u1, c.v0, b2);
-              pinwheel = true;
-            }
-          }
-          if (!pinwheel) {
-            put_rect(sm, lane, nch, c.patch, c.u0, um, vm, c.v1);
-            put_rect(sm, lane, nch, c.patch, um, c.u1, vm, c.v1);
-            put_rect(sm, lane, nch, c.patch, c.u0, um, c.v0, vm);
-            put_rect(sm, lane, nch, c.patch, um, c.u1, c.v0, vm);
-          }
-          h.boxes += nch;
-        }
-      }
-    }
+    if (S.live) split_step(h, Q, nets, use_newton, S, sm, lane, nch);
     pool_and_push(h, nets, S, sm, lane, nch);
   }
-  if (h.overflow) {
-    S.flags |= SHELL_RAY_OVERFLOW;
-  } else if (S.bp >= 0) {
-    S.flags |= SHELL_RAY_HIT;
-  }
+  finish_flags(h, S);
 }
 
 struct CcdOut {
@@ -472,33 +487,73 @@ __device__ __forceinline__ void write_result(const CcdOut& out, long long k, con
   }
 }
 
+// Persistent over the queries: every lane starts on query (global lane index) and, when its
+// search ends, writes the result and takes the next query from counters[2], while the other lanes
+// of its warp go on. A lane's root scan and splits feed the same pooled feasibility tests, so a
+// warp keeps all its lanes busy until the queue is empty; each query's heap receives the same
+// pushes in the same order as in a one-query-per-lane search.
 __global__ void __launch_bounds__(kCcdBlock, 8) k_ccd_points(long long n, const double* __restrict__ x0s,
                                                              const double* __restrict__ dxs, int np,
                                                              const double* __restrict__ nets, int use_newton,
                                                              CcdOut out, int* __restrict__ counters,
                                                              int* __restrict__ redo_list, Cand* __restrict__ heaps) {
   __shared__ WarpSmem wsm[kCcdBlock / 32];
+  WarpSmem& sm = wsm[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
-  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = k < n;
-  Query Q;
+  const long long lanes = (long long)gridDim.x * blockDim.x;
   Cand storage[kHeapCap];
   Heap h(storage, kHeapCap);
-  h.spill = heaps;
-  h.spill_count = counters + 1;
-  if (active) load_query(x0s, dxs, k, Q);
+  Query Q;
   Search S;
-  S.live = active;
-  search(h, Q, nets, np, use_newton, S, wsm[threadIdx.x >> 5], lane);
-  if (!active) return;
-  if (h.overflow) {
-    const int slot = atomicAdd(counters, 1);
-    if (slot < kRedoList) {
-      redo_list[slot] = (int)k;
-      return;                                                         // written by the second pass
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int phase = 0, next = 0;   // phase 0: no query left, 1: root scan, 2: search
+  auto begin = [&]() {
+    h.a = storage;
+    h.cap = kHeapCap;
+    h.n = 0;
+    h.peak = 0;
+    h.boxes = 0;
+    h.overflow = false;
+    h.spill = heaps;
+    h.spill_count = counters + 1;
+    S = Search();
+    phase = 0;
+    if (k < n) {
+      load_query(x0s, dxs, k, Q);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        sm.pt[lane][c] = Q.x0[c];
+        sm.pt[lane][3 + c] = Q.dx[c];
+      }
+      S.live = true;
+      phase = 1;
+      next = 0;
+    }
+  };
+  begin();
+  while (__any_sync(0xffffffffu, phase != 0)) {
+    int nch = 0;
+    if (phase == 1) {
+      if (root_round(h, Q, nets, np, sm, lane, next, nch)) phase = 2;
+    } else if (phase == 2) {
+      split_step(h, Q, nets, use_newton, S, sm, lane, nch);
+    }
+    pool_and_push(h, nets, S, sm, lane, nch);   // ends with a warp barrier: sm.pt may change below
+    if (phase == 2 && !S.live) {
+      finish_flags(h, S);
+      bool deferred = false;
+      if (h.overflow) {
+        const int slot = atomicAdd(counters, 1);
+        if (slot < kRedoList) {
+          redo_list[slot] = (int)k;   // written by the second pass
+          deferred = true;
+        }
+      }
+      if (!deferred) write_result(out, k, S, h);
+      k = lanes + atomicAdd(counters + 2, 1);
+      begin();
     }
   }
-  write_result(out, k, S, h);
 }
 
 __global__ void __launch_bounds__(kCcdBlock) k_ccd_points_redo(const double* __restrict__ x0s,
@@ -553,14 +608,17 @@ extern "C" shell_status shell_ccd_points(shell_t* shell, const double* q, const 
   }
   Cand* heaps = (Cand*)heaps_v;
   CcdOut out{s, patch, uv, flags, stats};
-  BHEM_CUDA(cudaMemsetAsync(counters, 0, 2 * sizeof(int), sh.stream));
+  BHEM_CUDA(cudaMemsetAsync(counters, 0, 4 * sizeof(int), sh.stream));
   k_ccd_nets<<<grid_for(np, kNetBlock), kNetBlock, 0, sh.stream>>>(np, sh.d_patch_nodes, q, dq, sh.grid.dxi1,
                                                                    sh.grid.dxi2, sh.d_ccd_nets);
   k_ccd_groups<<<grid_for((np + kGroup - 1) / kGroup, kNetBlock), kNetBlock, 0, sh.stream>>>(
       np, sh.d_ccd_nets, sh.d_ccd_nets + (size_t)kNetStride * np);
   const int use_newton = variant == SHELL_RAY_NEWTON;
-  k_ccd_points<<<(unsigned)((n_points + kCcdBlock - 1) / kCcdBlock), kCcdBlock, 0, sh.stream>>>(
-      n_points, x0, dx, np, sh.d_ccd_nets, use_newton, out, counters, redo_list, heaps);
+  // persistent: 8 CTAs of 2 warps per SM (the resident limit), lanes refill from the query counter
+  if (sh.num_sms <= 0) BHEM_CUDA(cudaDeviceGetAttribute(&sh.num_sms, cudaDevAttrMultiProcessorCount, sh.device));
+  const long long ctas = std::min<long long>((n_points + kCcdBlock - 1) / kCcdBlock, 8LL * sh.num_sms);
+  k_ccd_points<<<(unsigned)ctas, kCcdBlock, 0, sh.stream>>>(n_points, x0, dx, np, sh.d_ccd_nets, use_newton, out,
+                                                          counters, redo_list, heaps);
   k_ccd_points_redo<<<kRedoThreads / kCcdBlock, kCcdBlock, 0, sh.stream>>>(x0, dx, np, sh.d_ccd_nets, use_newton, out, counters,
                                                        redo_list, heaps);
   sh.launches += 4;

@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(kRedoThreads) k_trace_rays_redo(const double* 
 // then two counters (queries sent to the second pass, global heaps claimed) and the redo list.
 shell_status search_scratch(Shell& s, void** heaps, int** counters, int** redo_list) {
   if (!s.d_search) {
-    const size_t bytes = sizeof(bz::Cand) * (size_t)bz::kRedoThreads * bz::kRedoHeap + sizeof(int) * (2 + bz::kRedoList);
+    const size_t bytes = sizeof(bz::Cand) * (size_t)bz::kRedoThreads * bz::kRedoHeap + sizeof(int) * (4 + bz::kRedoList);
     const cudaError_t e = cudaMalloc(&s.d_search, bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -472,7 +472,7 @@ shell_status search_scratch(Shell& s, void** heaps, int** counters, int** redo_l
   }
   *heaps = s.d_search;
   *counters = (int*)((bz::Cand*)s.d_search + (size_t)bz::kRedoThreads * bz::kRedoHeap);
-  *redo_list = *counters + 2;
+  *redo_list = *counters + 4;   // counters: redo count, spill count, query counter, pad
   return SHELL_OK;
 }
 
