@@ -614,9 +614,13 @@ extern "C" shell_status shell_ccd_points(shell_t* shell, const double* q, const 
   k_ccd_groups<<<grid_for((np + kGroup - 1) / kGroup, kNetBlock), kNetBlock, 0, sh.stream>>>(
       np, sh.d_ccd_nets, sh.d_ccd_nets + (size_t)kNetStride * np);
   const int use_newton = variant == SHELL_RAY_NEWTON;
-  // persistent: 8 CTAs of 2 warps per SM (the resident limit), lanes refill from the query counter
+  // persistent: exactly the CTAs that can be resident at once (a CTA that waits for a free SM would
+  // start only after the queue is empty), lanes refill from the query counter
   if (sh.num_sms <= 0) BHEM_CUDA(cudaDeviceGetAttribute(&sh.num_sms, cudaDevAttrMultiProcessorCount, sh.device));
-  const long long ctas = std::min<long long>((n_points + kCcdBlock - 1) / kCcdBlock, 8LL * sh.num_sms);
+  int occ = 0;
+  BHEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ccd_points, kCcdBlock, 0));
+  const long long ctas = std::min<long long>((n_points + kCcdBlock - 1) / kCcdBlock,
+                                             (long long)std::max(1, occ) * sh.num_sms);
   k_ccd_points<<<(unsigned)ctas, kCcdBlock, 0, sh.stream>>>(n_points, x0, dx, np, sh.d_ccd_nets, use_newton, out,
                                                           counters, redo_list, heaps);
   k_ccd_points_redo<<<kRedoThreads / kCcdBlock, kCcdBlock, 0, sh.stream>>>(x0, dx, np, sh.d_ccd_nets, use_newton, out, counters,
