@@ -422,6 +422,33 @@ def alu_rooflines(sh, q_d, P, n_patches, stream, reps=5):
     return out
 
 
+def element_kernel_only(sh, q_d, n_patches, stream, reps=5):
+    """The element kernel without assembly: E-, gradient- and exact-Hessian evaluation of every
+    patch with the 48x48 FP32 Hessians written unassembled (no BSR clear or scatter), CUDA events
+    on the shell's stream."""
+    import torch
+    H = torch.empty(n_patches, 48, 48, dtype=torch.float32, device=q_d.device)
+    from paper_2312_14839_gb300 import bhem
+    lib = bhem.load()
+
+    def run():
+        bhem._check(lib.shell_element_egh(sh._h, bhem._ptr(q_d), 1, None, None, bhem._ptr(H)))
+
+    for _ in range(2):
+        run()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    del H
+    return {"patch_hessians_per_s": n_patches / t, "avg_launch_us": t * 1e6,
+            "what": "k_element_full<float> writing the 48x48 FP32 Hessians unassembled (no BSR clear or scatter)"}
+
+
 # FP64 operations per step of the ray search (adds, multiplies, compares, min/max, divisions and
 # square roots one each), counted from the kernel source: a patch's root box test, one candidate
 # box (blossoming of 8 curves per coordinate and the slab test), one Newton iteration, and the
@@ -957,6 +984,7 @@ def main():
     spmv_bytes = nb * 144 * 4 + nb * 4 + (n + 1) * 4 + m * 4 + m * 4
     peak, peak_kind = measured_peaks()
     alu = alu_rooflines(sh, q0_d, P, g.n_patches, stream)
+    elem_only = element_kernel_only(sh, q0_d, g.n_patches, stream)
     achieved = spmv_bytes / spmv_s / 1e9
     traffic = recorded_traffic(os.path.join(ROOT, "paper_2312_14839_gb300", "csrc", "solver.cu"),
                                "k_spmv32_tma" if args.spmv == "tma" else "k_spmv32", args.workload)
@@ -985,6 +1013,7 @@ def main():
                      "traffic": traffic, "algorithmic_bytes_per_launch": spmv_bytes,
                      "avg_launch_us": spmv_s * 1e6},
         "alu_rooflines": alu,
+        "element_kernel_only": elem_only,
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
