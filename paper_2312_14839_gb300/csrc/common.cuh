@@ -139,6 +139,7 @@ struct Shell {
   // FP32 SpMV variant: TMA-pipelined persistent kernel when its row-group stages fit in shared
   // memory (max_row = most blocks in one block row)
   int num_sms = 0;                  // multiprocessors of the shell's device (grid sizes)
+  int update_grid = 0;              // CTAs of the mixed-precision PCG update (resident at once)
   // BHEM_PCG_HOST_LOOP set: mixed-precision PCG iterations are launched from the host in chunks
   // (as in FP64) instead of the device-side graph loop, whose kernels a profiler cannot list
   int pcg_host_loop = 0;

@@ -685,7 +685,7 @@ k_pcg32_init(int n, const double* __restrict__ rhs, const float* __restrict__ Di
   }
 }
 
-__global__ void __launch_bounds__(kNodeThreads, 8)
+__global__ void __launch_bounds__(kNodeThreads)
 k_pcg32_update(int n, float* __restrict__ x, float* __restrict__ r, float* __restrict__ z,
                const float* __restrict__ p, const float* __restrict__ Ap,
                const float* __restrict__ Dinv, const unsigned char* __restrict__ mask, PcgState* st,
@@ -695,36 +695,40 @@ k_pcg32_update(int n, float* __restrict__ x, float* __restrict__ r, float* __res
   __shared__ float sr[16][12];
   const int ln = threadIdx.x / 12, a = threadIdx.x % 12;
   F2 rz{0.f, 0.f}, rr{0.f, 0.f};
-  float4 d0, d1, d2;
-  float xv = 0.f, pv = 0.f, av = 0.f, rv = 0.f;
   // this thread's row of the node's 12x12 inverse (48 contiguous bytes, streamed) and its DOF of
-  // x, p, Ap, r: all in flight together
-  auto load = [&](int base) {
+  // x, p, Ap, r; the next group's are loaded before this group's work, so their latency overlaps it
+  struct GroupLoads {
+    float4 d0, d1, d2;
+    float xv, pv, av, rv;
+  };
+  GroupLoads cur{}, nxt{};
+  auto load = [&](int base, GroupLoads& g) {
     const int i = base + ln;
     if (i < n) {
       const float4* drow = reinterpret_cast<const float4*>(Dinv + (size_t)i * 144 + a * 12);
-      d0 = __ldcs(drow);
-      d1 = __ldcs(drow + 1);
-      d2 = __ldcs(drow + 2);
+      g.d0 = __ldcs(drow);
+      g.d1 = __ldcs(drow + 1);
+      g.d2 = __ldcs(drow + 2);
       const size_t gi = (size_t)i * 12 + a;
-      xv = x[gi];
-      pv = p[gi];
-      av = Ap[gi];
-      rv = r[gi];
+      g.xv = x[gi];
+      g.pv = p[gi];
+      g.av = Ap[gi];
+      g.rv = r[gi];
     }
   };
   const int stride = gridDim.x * 16;
-  if ((int)blockIdx.x * 16 < n) load(blockIdx.x * 16);
+  if ((int)blockIdx.x * 16 < n) load(blockIdx.x * 16, cur);
   const float alpha = (float)alpha_d;
   // grid-stride over groups of 16 nodes: a few CTAs per SM, so the last CTA of the grid
   // reduction folds few partials
   for (int base = blockIdx.x * 16; base < n; base += stride) {
+    if (base + stride < n) load(base + stride, nxt);
     const int i = base + ln;
     const size_t gi = (size_t)i * 12 + a;
     float ri = 0.f, zi = 0.f;
     if (i < n) {
-      x[gi] = fmaf(alpha, pv, xv);
-      ri = fmaf(-alpha, av, rv);
+      x[gi] = fmaf(alpha, cur.pv, cur.xv);
+      ri = fmaf(-alpha, cur.av, cur.rv);
       r[gi] = ri;
       sr[ln][a] = ri;
     }
@@ -732,25 +736,25 @@ k_pcg32_update(int n, float* __restrict__ x, float* __restrict__ r, float* __res
     if (i < n) {
       if (!(mask && mask[gi])) {
         const float* q = sr[ln];
-        zi = __fmaf_rn(d0.x, q[0], 0.f);
-        zi = __fmaf_rn(d0.y, q[1], zi);
-        zi = __fmaf_rn(d0.z, q[2], zi);
-        zi = __fmaf_rn(d0.w, q[3], zi);
-        zi = __fmaf_rn(d1.x, q[4], zi);
-        zi = __fmaf_rn(d1.y, q[5], zi);
-        zi = __fmaf_rn(d1.z, q[6], zi);
-        zi = __fmaf_rn(d1.w, q[7], zi);
-        zi = __fmaf_rn(d2.x, q[8], zi);
-        zi = __fmaf_rn(d2.y, q[9], zi);
-        zi = __fmaf_rn(d2.z, q[10], zi);
-        zi = __fmaf_rn(d2.w, q[11], zi);
+        zi = __fmaf_rn(cur.d0.x, q[0], 0.f);
+        zi = __fmaf_rn(cur.d0.y, q[1], zi);
+        zi = __fmaf_rn(cur.d0.z, q[2], zi);
+        zi = __fmaf_rn(cur.d0.w, q[3], zi);
+        zi = __fmaf_rn(cur.d1.x, q[4], zi);
+        zi = __fmaf_rn(cur.d1.y, q[5], zi);
+        zi = __fmaf_rn(cur.d1.z, q[6], zi);
+        zi = __fmaf_rn(cur.d1.w, q[7], zi);
+        zi = __fmaf_rn(cur.d2.x, q[8], zi);
+        zi = __fmaf_rn(cur.d2.y, q[9], zi);
+        zi = __fmaf_rn(cur.d2.z, q[10], zi);
+        zi = __fmaf_rn(cur.d2.w, q[11], zi);
       }
       z[gi] = zi;
     }
     rz = f2_add(rz, f2_prod(ri, zi));
     rr = f2_add(rr, f2_prod(ri, ri));
     __syncthreads();   // sr is rewritten by the next group
-    if (base + stride < n) load(base + stride);
+    cur = nxt;
   }
   F2 v[2] = {rz, rr};
   double out[2];
@@ -1083,7 +1087,12 @@ shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, const dou
   if (!s.val_fp64) {
     Shift4f sh{{(float)td[0], (float)td[1], (float)td[2], (float)td[3]}};
     BHEM_TRY(launch_spmv32(s, s.d_p32, sh, mask, s.d_Ap32, s.d_pcg));
-    k_pcg32_update<<<std::min(grid_for(n, 16), 8 * std::max(1, s.num_sms)), kNodeThreads, 0, s.stream>>>(
+    if (s.update_grid <= 0) {   // the resident CTAs: a CTA waiting for a free SM would run its groups last
+      int occ = 0;
+      BHEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg32_update, kNodeThreads, 0));
+      s.update_grid = std::max(1, std::min(grid_for(n, 16), std::max(1, occ) * std::max(1, s.num_sms)));
+    }
+    k_pcg32_update<<<s.update_grid, kNodeThreads, 0, s.stream>>>(
         n, s.d_x32, s.d_r32, s.d_z32, s.d_p32, s.d_Ap32, (const float*)s.d_Dinv, mask, s.d_pcg, s.red);
     BHEM_CUDA(cudaGetLastError());
     ++s.launches;
