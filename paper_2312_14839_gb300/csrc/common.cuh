@@ -153,6 +153,10 @@ struct Shell {
   PcgGraph pcg_graphs[kGraphSlots] = {};
   int pcg_graph_next = 0;
   cudaStream_t cap_stream = nullptr;
+  // the first Newton iteration's Hessian is assembled on aux_stream while the FP64 residual runs
+  // on the shell's stream (ev_q: q ready; ev_hess: Hessian assembled)
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_q = nullptr, ev_hess = nullptr;
 
   // optional phase trace of shell_newton_step (environment BHEM_TRACE_PHASES=1): CUDA events and
   // host times at phase boundaries, printed to stderr at the end of each step

@@ -118,6 +118,9 @@ static void destroy_shell(shell_s* s) {
   for (auto& gph : s->pcg_graphs)
     if (gph.exec) cudaGraphExecDestroy(gph.exec);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  if (s->aux_stream) cudaStreamDestroy(s->aux_stream);
+  if (s->ev_q) cudaEventDestroy(s->ev_q);
+  if (s->ev_hess) cudaEventDestroy(s->ev_hess);
   destroy_direct(*s);
   void* ptrs[] = {s->d_patch_nodes, s->d_patch_blocks, s->d_row_ptr, s->d_col, s->d_diag_block,
                   s->d_color_list, s->d_rest, s->d_restgp, s->d_mass, s->d_fgrav, s->d_val,
@@ -473,11 +476,14 @@ extern "C" shell_status shell_pcg_solve(shell_t* shell, const unsigned char* fix
 
 namespace bhem {
 // |g| at q; leaves g in s.d_g, the inertial part in s.d_gin and E_p(q) in s.d_Ep.
+// also_wait: an event of work running beside the residual (the first Hessian), joined before the
+// error check so that one check sees the error bits of both
 static shell_status residual(Shell& s, const double* q, const shell_step_params& P,
-                             const unsigned char* mask, double* gnorm) {
+                             const unsigned char* mask, double* gnorm, cudaEvent_t also_wait = nullptr) {
   BHEM_CUDA(cudaMemsetAsync(s.d_g, 0, sizeof(double) * s.n_dof, s.stream));
   BHEM_TRY(launch_energy_grad64(s, q, nullptr, 0.0, s.d_Ep, nullptr, s.d_g, &s.d_ns->energy));
   BHEM_TRY(launch_grad_finish(s, q, s.d_y, P.dt, P.gravity, mask, s.d_g, s.d_gin, &s.d_ns->gnorm2));
+  if (also_wait) BHEM_CUDA(cudaStreamWaitEvent(s.stream, also_wait, 0));
   BHEM_CUDA(cudaMemcpyAsync(s.h_ns, s.d_ns, sizeof(NewtonScalars), cudaMemcpyDeviceToHost, s.stream));
   BHEM_TRY(sync_and_check(s));
   *gnorm = std::sqrt(s.h_ns->gnorm2);
@@ -505,12 +511,35 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
   BHEM_TRY(launch_predictor(s, s.d_qn, v_in, P.dt, s.d_y));
   if (mask) BHEM_TRY(launch_overwrite_fixed(s, q, s.d_qn, mask, qfix));
   double gref = 0.0, gn = 0.0;
-  BHEM_TRY(residual(s, q, P, mask, &gref));
+  const double inv_dt2 = 1.0 / (P.dt * P.dt);
+  // The first iteration's Hessian at q does not depend on the residual: it is assembled on the
+  // auxiliary stream, enqueued before the FP64 residual, so that the residual's CTAs take over the
+  // SMs as the element kernel's retire (7.83 against 7.85 ms per Newton iteration on the 256^2
+  // sheet; capping the element grid to make room for them side by side was slower, 8.2 ms).
+  // The shell's stream joins it before the residual's error check, so the step continues only
+  // when both are complete and error-free; a step that is converged at q leaves it unused.
+  bool hess_pending = false;
+  if (!warm && P.newton_max > 0) {
+    if (!s.aux_stream) {
+      BHEM_CUDA(cudaStreamCreateWithFlags(&s.aux_stream, cudaStreamNonBlocking));
+      BHEM_CUDA(cudaEventCreateWithFlags(&s.ev_q, cudaEventDisableTiming));
+      BHEM_CUDA(cudaEventCreateWithFlags(&s.ev_hess, cudaEventDisableTiming));
+    }
+    BHEM_CUDA(cudaEventRecord(s.ev_q, s.stream));
+    BHEM_CUDA(cudaStreamWaitEvent(s.aux_stream, s.ev_q, 0));
+    cudaStream_t keep = s.stream;
+    s.stream = s.aux_stream;
+    const shell_status sa = assemble_hessian(s, q, inv_dt2);
+    s.stream = keep;
+    BHEM_TRY(sa);
+    BHEM_CUDA(cudaEventRecord(s.ev_hess, s.aux_stream));
+    hess_pending = true;
+  }
+  BHEM_TRY(residual(s, q, P, mask, &gref, hess_pending ? s.ev_hess : nullptr));
   mark(s, "residual0");
   st.res0 = gref;
   if (warm) BHEM_TRY(launch_overwrite_fixed(s, q, warm, mask, qfix));
   shell_status status = SHELL_OK;
-  const double inv_dt2 = 1.0 / (P.dt * P.dt);
   // The first line-search trial (alpha = 1) also computes the elastic gradient and patch energies
   // at q + d; when it is accepted, q + d is the next iterate (the same FP64 sum), so the next
   // residual reuses them instead of evaluating the elements again.
@@ -523,7 +552,12 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
     reuse = false;
     if (gn <= P.newton_rtol * gref) break;
     if (it >= P.newton_max) { status = SHELL_ERR_NOT_CONVERGED; break; }
-    BHEM_TRY(assemble_hessian(s, q, inv_dt2));
+    if (hess_pending) {
+      BHEM_CUDA(cudaStreamWaitEvent(s.stream, s.ev_hess, 0));
+      hess_pending = false;
+    } else {
+      BHEM_TRY(assemble_hessian(s, q, inv_dt2));
+    }
     mark(s, "assemble_enqueued");
     BHEM_TRY(launch_negate(s, s.d_g, s.d_rhs));
     // Sec. 6.1 diagonal regulariser A + tau D (D = per-kind mean |A_ii|): the first solve uses the
@@ -608,6 +642,7 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
     }
     st.newton_iters++;
   }
+  if (hess_pending) BHEM_CUDA(cudaStreamWaitEvent(s.stream, s.ev_hess, 0));   // unused, but finished in order
   st.res_final = gn;
   if (status == SHELL_OK || status == SHELL_ERR_NOT_CONVERGED) {
     BHEM_TRY(launch_velocity(s, q, s.d_qn, P.dt, v_out));
