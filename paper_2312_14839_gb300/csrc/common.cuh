@@ -134,6 +134,7 @@ struct Shell {
   double* d_ccd_nets = nullptr;
 
   Reduce red{};
+  Reduce red_aux{};                 // grid reductions of work on aux_stream (diagonal statistics)
   long long launches = 0;           // kernels launched by this shell (introspection)
 
   // FP32 SpMV variant: TMA-pipelined persistent kernel when its row-group stages fit in shared
@@ -221,7 +222,7 @@ shell_status launch_pcg_loop_graph(Shell& s, const unsigned char* mask);
 int pcg_loop_unroll();   // PCG iterations per loop body
 shell_status launch_spmv(Shell& s, const void* x, int x_fp32, void* y);
 shell_status launch_pcg_result(Shell& s);
-shell_status launch_diag_check(Shell& s, const unsigned char* mask, double* out12);
+shell_status launch_diag_check(Shell& s, const unsigned char* mask, double* out12, bool aux = false);
 shell_status launch_axpy_fixed(Shell& s, double* q, const double* d, double alpha);
 shell_status launch_overwrite_fixed(Shell& s, double* dst, const double* src,
                                     const unsigned char* mask, const double* fixed_vals);

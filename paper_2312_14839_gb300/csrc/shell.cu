@@ -127,7 +127,7 @@ static void destroy_shell(shell_s* s) {
                   s->d_x, s->d_r, s->d_z, s->d_p, s->d_Ap, s->d_p32, s->d_x32, s->d_r32, s->d_z32, s->d_Ap32, s->d_Dinv, s->d_phi64, s->d_phi32,
                   s->d_pcg, s->d_qn, s->d_y, s->d_g, s->d_gin, s->d_d, s->d_Md, s->d_Ep,
                   s->d_qwork, s->d_vwork, s->d_qfix, s->d_warm, s->d_mask, s->d_ns, s->d_err, s->d_qmy,
-                  s->d_energy_tmp, s->red.partials, s->red.ticket, s->d_rhs, s->d_g2, s->d_Ep2,
+                  s->d_energy_tmp, s->red.partials, s->red.ticket, s->red_aux.partials, s->red_aux.ticket, s->d_rhs, s->d_g2, s->d_Ep2,
                   s->d_search, s->d_ray_nets, s->d_ccd_nets};
   for (void* p : ptrs) dfree(p);
   if (s->h_ns) cudaFreeHost(s->h_ns);
@@ -273,6 +273,9 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
   s->red.stride = std::max(1024, std::max(np / 8, n / 4) + 64);
   A(s->red.partials, (size_t)kMaxRed * s->red.stride);
   A(s->red.ticket, 1);
+  s->red_aux.stride = 1024;
+  A(s->red_aux.partials, (size_t)kMaxRed * s->red_aux.stride);
+  A(s->red_aux.ticket, 1);
 #undef A
   if (st == SHELL_OK) {
     cudaError_t e1 = cudaMallocHost((void**)&s->h_ns, sizeof(NewtonScalars));
@@ -298,6 +301,7 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
     e = cudaMemcpyAsync(s->d_rest, rest_dofs, sizeof(double) * m, cudaMemcpyDefault, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->red.ticket, 0, sizeof(unsigned), s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->red_aux.ticket, 0, sizeof(unsigned), s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_pcg, 0, sizeof(PcgState), s->stream);
   if (e != cudaSuccess) {
     destroy_shell(s);
@@ -436,15 +440,19 @@ namespace bhem {
 // Per-kind regulariser scale dbar[k] = mean |A_ii| over free DOFs of kind k (1 if none) and the
 // per-kind minimum of A_ii, from the assembled matrix.
 struct KindStats { double dbar[4], dmin[4], count[4]; };
-static shell_status kind_stats(Shell& s, const unsigned char* mask, KindStats& K) {
-  BHEM_TRY(launch_diag_check(s, mask, s.d_ns->diag_stats));
-  BHEM_CUDA(cudaMemcpyAsync(s.h_ns, s.d_ns, sizeof(NewtonScalars), cudaMemcpyDeviceToHost, s.stream));
-  BHEM_CUDA(cudaStreamSynchronize(s.stream));
+static void kind_stats_from_host(const Shell& s, KindStats& K) {
   for (int q = 0; q < 4; ++q) {
     K.count[q] = s.h_ns->diag_stats[3 * q + 1];
     K.dbar[q] = K.count[q] > 0 ? s.h_ns->diag_stats[3 * q] / K.count[q] : 1.0;
     K.dmin[q] = s.h_ns->diag_stats[3 * q + 2];
   }
+}
+
+static shell_status kind_stats(Shell& s, const unsigned char* mask, KindStats& K) {
+  BHEM_TRY(launch_diag_check(s, mask, s.d_ns->diag_stats));
+  BHEM_CUDA(cudaMemcpyAsync(s.h_ns, s.d_ns, sizeof(NewtonScalars), cudaMemcpyDeviceToHost, s.stream));
+  BHEM_CUDA(cudaStreamSynchronize(s.stream));
+  kind_stats_from_host(s, K);
   return SHELL_OK;
 }
 // The smallest regulariser shift that keeps every free diagonal entry of A + tau D positive
@@ -529,7 +537,9 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
     BHEM_CUDA(cudaStreamWaitEvent(s.aux_stream, s.ev_q, 0));
     cudaStream_t keep = s.stream;
     s.stream = s.aux_stream;
-    const shell_status sa = assemble_hessian(s, q, inv_dt2);
+    shell_status sa = assemble_hessian(s, q, inv_dt2);
+    // its diagonal statistics too: the residual's host copy of the Newton scalars carries them
+    if (sa == SHELL_OK) sa = launch_diag_check(s, mask, s.d_ns->diag_stats, true);
     s.stream = keep;
     BHEM_TRY(sa);
     BHEM_CUDA(cudaEventRecord(s.ev_hess, s.aux_stream));
@@ -552,7 +562,12 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
     reuse = false;
     if (gn <= P.newton_rtol * gref) break;
     if (it >= P.newton_max) { status = SHELL_ERR_NOT_CONVERGED; break; }
-    if (hess_pending) {
+    // Sec. 6.1 diagonal regulariser A + tau D (D = per-kind mean |A_ii|): the first solve uses the
+    // smallest shift that makes the free diagonal positive, each negative curvature met by PCG
+    // multiplies tau by 10 (at least 1e-8), beyond 1e4 the step gives up.
+    KindStats K;
+    const bool from_pending = hess_pending;
+    if (hess_pending) {   // assembled and its statistics read with the residual (joined there)
       BHEM_CUDA(cudaStreamWaitEvent(s.stream, s.ev_hess, 0));
       hess_pending = false;
     } else {
@@ -560,11 +575,8 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
     }
     mark(s, "assemble_enqueued");
     BHEM_TRY(launch_negate(s, s.d_g, s.d_rhs));
-    // Sec. 6.1 diagonal regulariser A + tau D (D = per-kind mean |A_ii|): the first solve uses the
-    // smallest shift that makes the free diagonal positive, each negative curvature met by PCG
-    // multiplies tau by 10 (at least 1e-8), beyond 1e4 the step gives up.
-    KindStats K;
-    BHEM_TRY(kind_stats(s, mask, K));
+    if (from_pending) kind_stats_from_host(s, K);
+    else BHEM_TRY(kind_stats(s, mask, K));
     mark(s, "kind_stats");
     double tau = start_shift(K);
     if (tau > 0.0) st.regularizations++;

@@ -943,15 +943,18 @@ shell_status launch_precond_setup(Shell& s, const unsigned char* mask, const dou
   return SHELL_OK;
 }
 
-shell_status launch_diag_check(Shell& s, const unsigned char* mask, double* out12) {
+shell_status launch_diag_check(Shell& s, const unsigned char* mask, double* out12, bool aux) {
+  // aux: beside other reducing kernels, on the shell's second workspace
+  const Reduce& red = aux ? s.red_aux : s.red;
   int blocks = grid_for(s.n_dof, 256 * 4);
   if (blocks > 2 * std::max(1, s.num_sms)) blocks = 2 * std::max(1, s.num_sms);
+  if (blocks > red.stride) return fail(SHELL_ERR_ARG, "reduction workspace too small");
   if (s.val_fp64)
     k_diag_check<double><<<blocks, 256, 0, s.stream>>>(s.n_nodes, s.d_diag_block,
-        (const double*)s.d_val, mask, out12, s.red);
+        (const double*)s.d_val, mask, out12, red);
   else
     k_diag_check<float><<<blocks, 256, 0, s.stream>>>(s.n_nodes, s.d_diag_block,
-        (const float*)s.d_val, mask, out12, s.red);
+        (const float*)s.d_val, mask, out12, red);
   BHEM_CUDA(cudaGetLastError());
   ++s.launches;
   return SHELL_OK;
