@@ -526,8 +526,11 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
   // sheet; capping the element grid to make room for them side by side was slower, 8.2 ms).
   // The shell's stream joins it before the residual's error check, so the step continues only
   // when both are complete and error-free; a step that is converged at q leaves it unused.
+  // Only for large shells: on small ones every kernel is short, the step is launch- and sync-bound,
+  // and the second stream's fixed costs outweigh the overlap (30 x 30 patches: 3% slower).
+  constexpr int kOverlapMinPatches = 16384;
   bool hess_pending = false;
-  if (!warm && P.newton_max > 0) {
+  if (!warm && P.newton_max > 0 && s.n_patches >= kOverlapMinPatches) {
     if (!s.aux_stream) {
       BHEM_CUDA(cudaStreamCreateWithFlags(&s.aux_stream, cudaStreamNonBlocking));
       BHEM_CUDA(cudaEventCreateWithFlags(&s.ev_q, cudaEventDisableTiming));
