@@ -414,25 +414,30 @@ def test_pcg_device_loop_matches_host_loop(monkeypatch, case, mass_scale, fixed)
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_step_converged_at_start_then_step_again(prec):
-    """A step that is converged at q (here: newton_rtol = 1, met by the residual at q itself)
-    takes no Newton iteration: the first Hessian, assembled beside the residual on the second
-    stream, is left unused and joined; the shell then steps as a fresh shell does."""
-    from paper_2312_14839_gb300.bhem import step_params
-    g, rest, q, mat = CASES["sheet10x10-noisy"]()
+    """On a shell large enough for the second stream (128 x 128 patches), a step that is converged
+    at q (here: newton_rtol = 1, met by the residual at q itself) takes no Newton iteration: the
+    first Hessian, assembled beside the residual, is left unused and joined. A degenerate input
+    on that path is reported, and the shell then steps as a fresh shell does."""
+    from paper_2312_14839_gb300.bhem import ShellError, step_params
+    g, rest, q = S.sheet_noisy(128, 1e-3, 1)
+    mat = THIN
     c = S.corner_nodes(g)
     mask = dev(S.pinned_mask(g, [c[0], c[3]]), torch.uint8)
-    P = step_params(dt=1e-3, gravity=(0.0, 0.0, 0.0))
+    P = step_params(dt=1e-3, gravity=(0.0, 0.0, 0.0), newton_max=3, pcg_fixed_iters=30)
     P0 = step_params(dt=1e-3, gravity=(0.0, 0.0, 0.0), newton_rtol=1.0)
     sh = make_shell(g, mat, rest, precision=prec)
     zero = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
     q0 = dev(q.reshape(-1))
     st = sh.newton_step(q0.clone(), zero.clone(), P0, mask=mask, q_fixed=q0)
     assert st["status"] == 0 and st["newton_iters"] == 0, st
-    qa, va = dev(q.reshape(-1)), zero.clone()
-    st_a = sh.newton_step(qa, va, P, mask=mask, q_fixed=dev(q.reshape(-1)))
+    with pytest.raises(ShellError) as e:
+        sh.newton_step(zero.clone(), zero.clone(), P0)
+    assert e.value.status == 4
+    qa, va = q0.clone(), zero.clone()
+    st_a = sh.newton_step(qa, va, P, mask=mask, q_fixed=q0)
     fresh = make_shell(g, mat, rest, precision=prec)
-    qb, vb = dev(q.reshape(-1)), zero.clone()
-    st_b = fresh.newton_step(qb, vb, P, mask=mask, q_fixed=dev(q.reshape(-1)))
-    assert st_a["status"] == st_b["status"] == 0
+    qb, vb = q0.clone(), zero.clone()
+    st_b = fresh.newton_step(qb, vb, P, mask=mask, q_fixed=q0)
+    assert st_a["status"] in (0, 6) and st_a["status"] == st_b["status"]
     assert st_a["newton_iters"] == st_b["newton_iters"]
-    assert rel(host(qa), host(qb)) <= (1e-12 if prec == "fp64" else 1e-6)
+    assert rel(host(qa) - host(q0), host(qb) - host(q0)) <= (1e-9 if prec == "fp64" else 1e-4)
