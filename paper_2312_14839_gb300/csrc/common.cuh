@@ -158,6 +158,9 @@ struct Shell {
   // on the shell's stream (ev_q: q ready; ev_hess: Hessian assembled)
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t ev_q = nullptr, ev_hess = nullptr;
+  // work was enqueued on aux_stream and no error-free check of the shell's stream has joined it
+  // since (a step that failed in between): the next step and shell_destroy synchronise it first
+  bool aux_unjoined = false;
 
   // optional phase trace of shell_newton_step (environment BHEM_TRACE_PHASES=1): CUDA events and
   // host times at phase boundaries, printed to stderr at the end of each step

@@ -325,6 +325,7 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
 extern "C" shell_status shell_destroy(shell_t* shell) {
   if (!shell) return SHELL_OK;
   cudaStreamSynchronize(shell->stream);
+  if (shell->aux_unjoined) cudaStreamSynchronize(shell->aux_stream);
   destroy_shell(shell);
   return SHELL_OK;
 }
@@ -513,6 +514,10 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
                                 const double* qfix, double* q, const double* v_in,
                                 const double* warm, double* v_out, shell_step_stats& st) {
   const int m = s.n_dof;
+  if (s.aux_unjoined) {   // the previous step failed while its first Hessian was in flight
+    BHEM_CUDA(cudaStreamSynchronize(s.aux_stream));
+    s.aux_unjoined = false;
+  }
   s.trace_n = 0;
   mark(s, "start");
   BHEM_CUDA(cudaMemcpyAsync(s.d_qn, q, sizeof(double) * m, cudaMemcpyDeviceToDevice, s.stream));
@@ -538,6 +543,7 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
     }
     BHEM_CUDA(cudaEventRecord(s.ev_q, s.stream));
     BHEM_CUDA(cudaStreamWaitEvent(s.aux_stream, s.ev_q, 0));
+    s.aux_unjoined = true;
     cudaStream_t keep = s.stream;
     s.stream = s.aux_stream;
     shell_status sa = assemble_hessian(s, q, inv_dt2);
@@ -549,6 +555,7 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
     hess_pending = true;
   }
   BHEM_TRY(residual(s, q, P, mask, &gref, hess_pending ? s.ev_hess : nullptr));
+  s.aux_unjoined = false;   // the residual's synchronised check waited for ev_hess
   mark(s, "residual0");
   st.res0 = gref;
   if (warm) BHEM_TRY(launch_overwrite_fixed(s, q, warm, mask, qfix));
