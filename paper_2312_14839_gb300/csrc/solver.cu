@@ -695,7 +695,7 @@ k_pcg32_update(int n, float* __restrict__ x, float* __restrict__ r, float* __res
   __shared__ float sr[16][12];
   const int ln = threadIdx.x / 12, a = threadIdx.x % 12;
   F2 rz{0.f, 0.f}, rr{0.f, 0.f};
-  // this thread's row of the node's 12x12 inverse (48 contiguous bytes, streamed) and its DOF of
+  // this thread's row of the node's 12x12 inverse (48 contiguous bytes) and its DOF of
   // x, p, Ap, r; the next group's are loaded before this group's work, so their latency overlaps it
   struct GroupLoads {
     float4 d0, d1, d2;
@@ -706,9 +706,9 @@ k_pcg32_update(int n, float* __restrict__ x, float* __restrict__ r, float* __res
     const int i = base + ln;
     if (i < n) {
       const float4* drow = reinterpret_cast<const float4*>(Dinv + (size_t)i * 144 + a * 12);
-      g.d0 = __ldcs(drow);
-      g.d1 = __ldcs(drow + 1);
-      g.d2 = __ldcs(drow + 2);
+      g.d0 = __ldg(drow);
+      g.d1 = __ldg(drow + 1);
+      g.d2 = __ldg(drow + 2);
       const size_t gi = (size_t)i * 12 + a;
       g.xv = x[gi];
       g.pv = p[gi];
