@@ -208,9 +208,12 @@ __device__ __forceinline__ double eg64_patch(const double* w1, const double* w2,
     const double H11 = restgp[9 * S + o], H12 = restgp[10 * S + o], H22 = restgp[11 * S + o];
     const double wgt = restgp[12 * S + o];
     V3<double> n = cross(a1, a2);
-    double sqa = sqrt(dot(n, n));
-    if (!(sqa > 1e-300)) { atomicOr(err, ERRBIT_DEGENERATE); sqa = 1.0; }
-    V3<double> a3 = (1.0 / sqa) * n;
+    // 1 / sqrt(a) by one reciprocal square root: no FP64 square root or divide on this path
+    const double nn = dot(n, n);
+    double isqa = 1.0;
+    if (!(nn > 0.0)) atomicOr(err, ERRBIT_DEGENERATE);
+    else isqa = rsqrt(nn);
+    V3<double> a3 = isqa * n;
     double b11 = dot(v[2], a3), b22 = dot(v[3], a3), b12 = dot(v[4], a3);
     double al[3] = {0.5 * (dot(a1, a1) - ab11), 0.5 * (dot(a2, a2) - ab22), dot(a1, a2) - ab12};
     double be[3] = {b11 - bb11, b22 - bb22, 2.0 * (b12 - bb12)};
@@ -220,14 +223,14 @@ __device__ __forceinline__ double eg64_patch(const double* w1, const double* w2,
                     H02 * be[0] + H12 * be[1] + H22 * be[2]};
     const double h3 = h * h * h;
     e = wgt * (0.5 * h * (al[0] * sg[0] + al[1] * sg[1] + al[2] * sg[2]) +
-               h3 / 24.0 * (be[0] * mm[0] + be[1] * mm[1] + be[2] * mm[2]));
+               h3 * (1.0 / 24.0) * (be[0] * mm[0] + be[1] * mm[1] + be[2] * mm[2]));
     if (grad) {
-      const double s = h3 / 12.0;
+      const double s = h3 * (1.0 / 12.0);
       V3<double> ct = mm[0] * v[2] + mm[1] * v[3] + (2.0 * mm[2]) * v[4];
       double bt = dot(ct, a3);
       V3<double> t1 = cross(a2, a3), t2 = cross(a3, a1);
-      V3<double> e1 = (1.0 / sqa) * (cross(a2, ct) - bt * t1);
-      V3<double> e2 = (1.0 / sqa) * (cross(ct, a1) - bt * t2);
+      V3<double> e1 = isqa * (cross(a2, ct) - bt * t1);
+      V3<double> e2 = isqa * (cross(ct, a1) - bt * t2);
       V3<double> G[5];
       G[0] = wgt * (h * (sg[0] * a1 + sg[2] * a2) + s * e1);
       G[1] = wgt * (h * (sg[1] * a2 + sg[2] * a1) + s * e2);
@@ -344,7 +347,10 @@ __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W
   if (!(det > (R)0)) { atomicOr(A.err, ERRBIT_DEGENERATE); det = (R)1; }
   R sqab = sqrt(det);
   V3<R> ab3 = ((R)1 / sqab) * cross(ab1, ab2);
-  R ai11 = ab22 / det, ai22 = ab11 / det, ai12 = -ab12 / det;
+  // one reciprocal each for det and sqrt(a), then products (the M_g loop below would otherwise
+  // divide by sqrt(a) 54 times)
+  const R idet = (R)1 / det;
+  R ai11 = ab22 * idet, ai22 = ab11 * idet, ai12 = -ab12 * idet;
   const R lam = (R)A.lam, mu = (R)A.mu, h = (R)A.h;
   R H[3][3];
   H[0][0] = (lam + 2 * mu) * ai11 * ai11;
@@ -358,7 +364,8 @@ __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W
   V3<R> n = cross(a1, a2);
   R sqa = sqrt(dot(n, n));
   if (!(sqa > (R)0)) { atomicOr(A.err, ERRBIT_DEGENERATE); sqa = (R)1; }
-  V3<R> a3 = ((R)1 / sqa) * n;
+  const R isqa = (R)1 / sqa;
+  V3<R> a3 = isqa * n;
   // strains from displacements (a_ab - a_bar_ab = a_bar_a.u_b + u_a.a_bar_b + u_a.u_b)
   R al[3] = {dot(ab1, uu[0]) + (R)0.5 * dot(uu[0], uu[0]), dot(ab2, uu[1]) + (R)0.5 * dot(uu[1], uu[1]),
              dot(ab1, uu[1]) + dot(uu[0], ab2) + dot(uu[0], uu[1])};
@@ -374,7 +381,7 @@ __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W
     mm[i] = H[i][0] * be[0] + H[i][1] * be[1] + H[i][2] * be[2];
   }
   const R wgt = sphi[kPhiSize + g] * sqab;
-  const R s = h * h * h / (R)12;
+  const R s = h * h * h * ((R)1 / (R)12);
   W.en[g] = wgt * ((R)0.5 * h * (al[0] * sg[0] + al[1] * sg[1] + al[2] * sg[2]) +
                    s * (R)0.5 * (be[0] * mm[0] + be[1] * mm[1] + be[2] * mm[2]));
   W.ms[g] = (R)(A.mass_scale * A.rho_h) * wgt;
@@ -385,8 +392,8 @@ __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     bdef[m] = dot(c[m], a3);
-    up[m] = ((R)1 / sqa) * (cross(a2, c[m]) - bdef[m] * t1);   // coefficient of Phi_,1 in d b_m
-    vp[m] = ((R)1 / sqa) * (cross(c[m], a1) - bdef[m] * t2);   // coefficient of Phi_,2 in d b_m
+    up[m] = isqa * (cross(a2, c[m]) - bdef[m] * t1);   // coefficient of Phi_,1 in d b_m
+    vp[m] = isqa * (cross(c[m], a1) - bdef[m] * t2);   // coefficient of Phi_,2 in d b_m
   }
   V3<R> Ba[2][3] = {{a1, mk<R>(0, 0, 0), a2}, {mk<R>(0, 0, 0), a2, a1}};
   V3<R> Bb[5][3] = {{up[0], up[1], (R)2 * up[2]},
@@ -419,7 +426,7 @@ __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W
   V3<R> ct = mm[0] * c[0] + mm[1] * c[1] + ((R)2 * mm[2]) * c[2];
   R bt = dot(ct, a3);
   V3<R> s1 = cross(ct, a1), s2 = cross(a2, ct);
-  const R ia = (R)1 / (sqa * sqa);
+  const R ia = isqa * isqa;
   const R a11 = dot(a1, a1), a22 = dot(a2, a2), a12 = dot(a1, a2);
   const R coef[3] = {mm[0], mm[1], (R)2 * mm[2]};
   R* M = W.M[g];
@@ -467,7 +474,7 @@ __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W
               V3<R> tv = (k == 0) ? t1 : t2;
               R cxm = (y == 0 && x == 1) ? -av.z : (y == 0 && x == 2) ? av.y : (y == 1 && x == 0) ? av.z :
                       (y == 1 && x == 2) ? -av.x : (y == 2 && x == 0) ? -av.y : (y == 2 && x == 1) ? av.x : (R)0;
-              R Pyx = (sgn * cxm - comp(a3, y) * comp(tv, x)) / sqa;
+              R Pyx = (sgn * cxm - comp(a3, y) * comp(tv, x)) * isqa;
               v += s * coef[l - 2] * Pyx;
             }
           }
