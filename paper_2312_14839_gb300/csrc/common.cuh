@@ -211,6 +211,8 @@ shell_status launch_grad_finish(Shell& s, const double* q, const double* y, doub
                                 const double grav[3], const unsigned char* mask, double* g,
                                 double* gin, double* gnorm2_out);
 shell_status launch_mass_mult(Shell& s, const double* x, double* y);
+shell_status launch_grad_linear(Shell& s, const double* Md, double alpha, double dt,
+                                const unsigned char* mask, double* g, double* gin, double* gnorm2_out);
 shell_status launch_dots3(Shell& s, int n, const double* a0, const double* b0, const double* a1,
                           const double* b1, const double* a2, const double* b2, double* out3);
 shell_status launch_precond_setup(Shell& s, const unsigned char* mask, const double td[4]);

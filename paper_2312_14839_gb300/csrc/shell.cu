@@ -499,11 +499,12 @@ static shell_status residual(Shell& s, const double* q, const shell_step_params&
   return SHELL_OK;
 }
 
-// Residual at q when the elastic gradient and patch energies at q are already in d_g / d_Ep
-// (from the accepted first line-search trial).
-static shell_status residual_reuse(Shell& s, const double* q, const shell_step_params& P,
-                                   const unsigned char* mask, double* gnorm) {
-  BHEM_TRY(launch_grad_finish(s, q, s.d_y, P.dt, P.gravity, mask, s.d_g, s.d_gin, &s.d_ns->gnorm2));
+// Residual at q = q_prev + d when the elastic gradient and patch energies at q are already in
+// d_g / d_Ep (from the accepted first line-search trial, alpha = 1): the inertial part follows from
+// the previous one and M d (d_Md, formed for the line search), without a second mass product.
+static shell_status residual_reuse(Shell& s, const shell_step_params& P, const unsigned char* mask,
+                                   double* gnorm) {
+  BHEM_TRY(launch_grad_linear(s, s.d_Md, 1.0, P.dt, mask, s.d_g, s.d_gin, &s.d_ns->gnorm2));
   BHEM_CUDA(cudaMemcpyAsync(s.h_ns, s.d_ns, sizeof(NewtonScalars), cudaMemcpyDeviceToHost, s.stream));
   BHEM_TRY(sync_and_check(s));
   *gnorm = std::sqrt(s.h_ns->gnorm2);
@@ -565,7 +566,7 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
   // residual reuses them instead of evaluating the elements again.
   bool reuse = false;
   for (int it = 0;; ++it) {
-    if (reuse) BHEM_TRY(residual_reuse(s, q, P, mask, &gn));
+    if (reuse) BHEM_TRY(residual_reuse(s, P, mask, &gn));
     else if (it > 0 || warm) BHEM_TRY(residual(s, q, P, mask, &gn));
     else gn = gref;
     mark(s, "residual");

@@ -844,6 +844,26 @@ k_grad_finish(int n, const int* __restrict__ rp, const int* __restrict__ col,
   grid_reduce<1>(v, red, gn2, gridDim.x);
 }
 
+// Residual after a step q' = q + alpha d when the elastic gradient at q' is already in g: the
+// inertial part is linear in q, M (q' - y) / dt^2 - F = gin + alpha M d / dt^2 with M d from the
+// line search, so no second mass product is formed. c = alpha / dt^2; fixed DOFs get zero.
+__global__ void k_grad_linear(int m, const double* __restrict__ Md, double c,
+                              const unsigned char* __restrict__ mask, double* __restrict__ g,
+                              double* __restrict__ gin, double* gn2, Reduce red, int* err) {
+  double part = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+    double gi_in = __fma_rn(c, Md[k], gin[k]);
+    double gv = g[k] + gi_in;
+    if (mask && mask[k]) { gv = 0.0; gi_in = 0.0; }
+    if (!isfinite(gv)) atomicOr(err, ERRBIT_NONFINITE);
+    g[k] = gv;
+    gin[k] = gi_in;
+    part += gv * gv;
+  }
+  double v[1] = {part};
+  grid_reduce<1>(v, red, gn2, gridDim.x);
+}
+
 __global__ void k_dots3(int m, const double* __restrict__ a0, const double* __restrict__ b0,
                         const double* __restrict__ a1, const double* __restrict__ b1,
                         const double* __restrict__ a2, const double* __restrict__ b2, double* out,
@@ -907,6 +927,16 @@ shell_status launch_grad_finish(Shell& s, const double* q, const double* y, doub
                                                        s.d_fgrav, s.d_qmy, nullptr, 1.0 / (dt * dt), grav[0],
                                                        grav[1], grav[2], mask, g, gin, gnorm2_out,
                                                        s.red, s.d_err);
+  BHEM_CUDA(cudaGetLastError());
+  ++s.launches;
+  return SHELL_OK;
+}
+
+shell_status launch_grad_linear(Shell& s, const double* Md, double alpha, double dt,
+                                const unsigned char* mask, double* g, double* gin, double* gnorm2_out) {
+  const int blocks = std::min(vec_blocks(s.n_dof), 1024);
+  k_grad_linear<<<blocks, 256, 0, s.stream>>>(s.n_dof, Md, alpha / (dt * dt), mask, g, gin, gnorm2_out,
+                                              s.red, s.d_err);
   BHEM_CUDA(cudaGetLastError());
   ++s.launches;
   return SHELL_OK;
