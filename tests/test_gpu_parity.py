@@ -286,6 +286,42 @@ def test_config2_twist_mixed_against_fp64_oracle(hessian):
         assert rel(dq_g, dq_o) <= 1e-5, (k, rel(dq_g, dq_o))
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_accepted_step_residual_matches_direct_residual(prec):
+    """After an accepted full Newton step (alpha = 1 at the first trial), the step forms the
+    residual's inertial part from the line search's M d instead of a second mass product. It must
+    equal the residual g = M (q' - y) / dt^2 + grad V(q') - F_g of the implicit-Euler equations
+    (Sec. 6.1), formed here directly at the returned q' from the oracle's gradient, mass and load,
+    within the FP64 tolerance relative to the step's reference residual."""
+    from paper_2312_14839_gb300.bhem import step_params
+    g, rest, q0 = S.sheet_noisy(10, 1e-3, 1)
+    mat = THIN
+    c = S.corner_nodes(g)
+    mask = S.pinned_mask(g, [c[0], c[3]])
+    qfix = q0.reshape(-1).copy()
+    dt, grav = 1e-3, np.array([0.0, 0.0, -9.81])
+    sh = make_shell(g, mat, rest, precision=prec)
+    q, v = dev(q0.reshape(-1)), torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    st = sh.newton_step(q, v, step_params(dt=dt, newton_max=1), mask=dev(mask, torch.uint8),
+                        q_fixed=dev(qfix))
+    assert st["newton_iters"] == 1 and st["ls_backtracks"] == 0
+    assert st["res_final"] < st["res0"]
+    q1 = host(q)
+    y = q0.reshape(-1)   # q^n + dt v^n with v^n = 0
+    _, grad, _ = O.assemble(g, mat, rest, q1, want_hess=False)
+    mval, fs = O.mass(g, mat, rest)
+    rp, col = O.bsr_pattern(g)
+    x = (q1 - y).reshape(g.n_nodes, 4, 3)
+    Mx = np.zeros_like(x)
+    for i in range(g.n_nodes):
+        for k in range(rp[i], rp[i + 1]):
+            Mx[i] += mval[k] @ x[col[k]]
+    res = Mx / dt ** 2 + grad.reshape(g.n_nodes, 4, 3) - fs[:, :, None] * grav[None, None, :]
+    res = res.reshape(-1)
+    res[mask.astype(bool)] = 0.0
+    assert abs(st["res_final"] - np.linalg.norm(res)) <= 1e-11 * st["res0"]
+
+
 def test_newton_host_buffers_match_device_buffers():
     *_, out_d = _config1_run("fp64", steps=3)
     *_, out_h = _config1_run("fp64", steps=3, host_buffers=True)
