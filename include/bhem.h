@@ -77,7 +77,7 @@ enum { SHELL_SOLVER_PCG = 0, SHELL_SOLVER_DIRECT = 1 };
    BSR values, SpMV and block-Jacobi in FP32, while the energy, gradient/residual, line-search
    energy differences and PCG dot products stay FP64.
    hessian: exact (App. B.2) or the pseudo Hessian of App. B.2 without the second derivative of
-   beta. assembly: atomic scatter or 4-colour ordered scatter of the element blocks.
+   beta. assembly: atomic scatter or colour-ordered scatter of the element blocks (shell_grid_colours).
    spmv (SHELL_PREC_MIXED only): the FP32 BSR SpMV of shell_spmv and of PCG. SHELL_SPMV_PLAIN:
    one CTA per 8 block rows, blocks loaded straight into registers. SHELL_SPMV_TMA: a persistent
    kernel that streams each CTA's row groups into a shared-memory ring with bulk asynchronous
@@ -140,6 +140,15 @@ SHELL_API shell_status shell_destroy(shell_t* shell);
 
 /* Sizes of the shell (host output). */
 SHELL_API shell_status shell_info(const shell_t* shell, shell_info_t* info);
+
+/* Colour classes of the colour-ordered assembly (SHELL_ASM_COLOR, Sec. 4.3 "Properties of the
+   mass matrix": two patches add into the same block iff they share a node). colour: host
+   [nu * nv], receives colour[pv * nu + pu] in [0, 9): pu % 2 + 3 (pv % 2), except that along a
+   periodic direction with an odd patch count the seam patch (index n - 1) takes colour 2 there,
+   so that it does not share the colour of patch 0 across the wrap. Patches of one colour share
+   no node, and their element blocks are added with plain (non-atomic) writes, one launch per
+   colour. Host computation only: needs no GPU. */
+SHELL_API shell_status shell_grid_colours(const shell_grid* grid, int* colour);
 
 /* Element-by-element evaluation, unassembled (App. B): for every patch p, energy_p[p] (FP64),
    grad_p[p * 48 + l] (FP64) and hess_p[p * 2304 + l * 48 + m] (FP32 when precision is

@@ -89,6 +89,7 @@ def load():
                 "shell_create": [p, p, p, p, p, p],
                 "shell_destroy": [p],
                 "shell_info": [p, p],
+                "shell_grid_colours": [p, p],
                 "shell_element_egh": [p, p, i, p, p, p],
                 "shell_energy_grad_hess": [p, p, d, p, p, i],
                 "shell_get_bsr": [p, p, p, p, p],
@@ -134,6 +135,14 @@ def load():
 def _check(st: int):
     if st != 0:
         raise ShellError(st, load().shell_last_error().decode())
+
+
+def grid_colours(nu: int, nv: int, periodic_u: int = 0, periodic_v: int = 0):
+    """Colour of every patch of the colour-ordered assembly (``shell_grid_colours``), [nv, nu]."""
+    g = shell_grid(nu, nv, periodic_u, periodic_v, 1.0, 1.0)
+    out = np.zeros(nu * nv, dtype=np.int32)
+    _check(load().shell_grid_colours(C.byref(g), out.ctypes.data_as(C.c_void_p)))
+    return out.reshape(nv, nu)
 
 
 def _ptr(t):

@@ -1301,7 +1301,6 @@ extern "C" shell_status shell_batch_create(int n_shells, const shell_grid* grids
     dxi.push_back(g.dxi1);
     dxi.push_back(g.dxi2);
     std::vector<std::vector<int>> nb(n);
-    const int cu = (g.periodic_u && (g.nu % 2)) ? 3 : 2, cv = (g.periodic_v && (g.nv % 2)) ? 3 : 2;
     for (int pv = 0; pv < g.nv; ++pv)
       for (int pu = 0; pu < g.nu; ++pu) {
         const int i0 = pu % n1, i1 = (pu + 1) % n1, j0 = pv % n2, j1 = (pv + 1) % n2;
@@ -1311,7 +1310,7 @@ extern "C" shell_status shell_batch_create(int n_shells, const shell_grid* grids
         const int nd[4] = {pn.x - node0, pn.y - node0, pn.z - node0, pn.w - node0};
         for (int a = 0; a < 4; ++a)
           for (int c = 0; c < 4; ++c) nb[nd[a]].push_back(nd[c]);
-        color_lists[((pu % cu) + cu * (pv % cv)) * n_shells + s].push_back(patch0 + pv * g.nu + pu);
+        color_lists[patch_colour(g, pu, pv) * n_shells + s].push_back(patch0 + pv * g.nu + pu);
       }
     const int blk0 = (int)col.size();
     for (int i = 0; i < n; ++i) {

@@ -30,6 +30,21 @@ shell_status fail(shell_status st, const std::string& msg);
     if (s_ != SHELL_OK) return s_;              \
   } while (0)
 
+// ------------------------------------------------------------------------------------------
+// Patch colours of the colour-ordered assembly: two patches of one colour share no node.
+// Along one direction, patches p and p +- 1 share a node column (and, when periodic, the seam
+// patch n - 1 shares one with patch 0), so a proper colouring of that path or cycle is p % 2,
+// except on an odd cycle, whose seam patch takes the third colour. A 2D colour is the pair
+// (u colour, v colour) numbered u + 3 v, so colour ids lie in [0, 9) (some may be empty).
+// ------------------------------------------------------------------------------------------
+inline int patch_colour_1d(int p, int n, int periodic) {
+  return (periodic && (n & 1) && p == n - 1) ? 2 : (p & 1);
+}
+inline int patch_colour(const shell_grid& g, int pu, int pv) {
+  return patch_colour_1d(pu, g.nu, g.periodic_u) + 3 * patch_colour_1d(pv, g.nv, g.periodic_v);
+}
+constexpr int kColours = 9;
+
 // Device-side error bits (OR-ed into Shell::d_err, read back at synchronising calls).
 enum : int { ERRBIT_DEGENERATE = 1, ERRBIT_NONFINITE = 2, ERRBIT_TIMEOUT = 4 };
 
@@ -84,7 +99,7 @@ struct Shell {
   int* d_col = nullptr;             // [n_blocks]
   int* d_diag_block = nullptr;      // [n_nodes]
   int* d_color_start = nullptr;     // unused by the atomic path
-  int* h_color_patches = nullptr;   // host copy of colour offsets (5 ints)
+  int* h_color_patches = nullptr;   // host copy of the colour offsets (kColours + 1 ints)
   int* d_color_list = nullptr;      // [np] patches ordered by colour
 
   // reference configuration

@@ -95,13 +95,11 @@ static void build_topology(const shell_grid& g, int n1, int n2, HostTopo& T) {
   }
   T.diag.resize(n);
   for (int i = 0; i < n; ++i) T.diag[i] = find(i, i);
-  // colours: patches of one colour share no node (3 colours along a periodic odd direction)
-  int cu = (g.periodic_u && (g.nu % 2)) ? 3 : 2, cv = (g.periodic_v && (g.nv % 2)) ? 3 : 2;
+  // colours: patches of one colour share no node (patch_colour)
   std::vector<int> cnt(10, 0);
   std::vector<int> colr(np);
   for (int p = 0; p < np; ++p) {
-    int pu = p % g.nu, pv = p / g.nu;
-    colr[p] = (pu % cu) + cu * (pv % cv);
+    colr[p] = patch_colour(g, p % g.nu, p / g.nu);
     cnt[colr[p] + 1]++;
   }
   for (int c = 0; c < 9; ++c) cnt[c + 1] += cnt[c];
@@ -336,6 +334,14 @@ extern "C" shell_status shell_info(const shell_t* shell, shell_info_t* info) {
   info->n_patches = shell->n_patches;
   info->n_blocks = shell->n_blocks;
   info->n_dof = shell->n_dof;
+  return SHELL_OK;
+}
+
+extern "C" shell_status shell_grid_colours(const shell_grid* grid, int* colour) {
+  if (!grid || !colour) return fail(SHELL_ERR_ARG, "NULL argument");
+  if (grid->nu < 1 || grid->nv < 1) return fail(SHELL_ERR_ARG, "empty grid");
+  for (int pv = 0; pv < grid->nv; ++pv)
+    for (int pu = 0; pu < grid->nu; ++pu) colour[pv * grid->nu + pu] = patch_colour(*grid, pu, pv);
   return SHELL_OK;
 }
 

@@ -57,3 +57,32 @@ def test_invalid_options_are_rejected_before_any_device_work():
         assert b"invalid options" in lib.shell_last_error()
         assert not out.value
 
+
+
+def _patch_nodes(nu, nv, pu_per, pv_per):
+    """Corner node ids of every patch, written from the header's node and patch numbering."""
+    n1 = nu if pu_per else nu + 1
+    n2 = nv if pv_per else nv + 1
+    out = []
+    for pv in range(nv):
+        for pu in range(nu):
+            out.append({((pv + b) % n2) * n1 + (pu + a) % n1 for a in (0, 1) for b in (0, 1)})
+    return out
+
+
+def test_colour_classes_share_no_node():
+    """Colour-ordered assembly adds element blocks without atomics, one launch per colour: two
+    patches of one colour must never touch the same node, also across a periodic seam with an odd
+    patch count (nu = 7, 13, ... put patch nu - 1 and patch 0 on one colour before)."""
+    for per_u in (0, 1):
+        for per_v in (0, 1):
+            for nu in range(1, 21):
+                for nv in range(1, 21):
+                    col = bhem.grid_colours(nu, nv, per_u, per_v).reshape(-1)
+                    assert col.min() >= 0 and col.max() < 9
+                    nodes = _patch_nodes(nu, nv, per_u, per_v)
+                    for c in set(col.tolist()):
+                        seen = set()
+                        for p in (col == c).nonzero()[0]:
+                            assert not (nodes[p] & seen), (nu, nv, per_u, per_v, c, int(p))
+                            seen |= nodes[p]
