@@ -44,7 +44,11 @@ class StepParams(C.Structure):
 class StepStats(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("pcg_iters_total", C.c_int),
                 ("ls_backtracks", C.c_int), ("regularizations", C.c_int), ("status", C.c_int),
-                ("res0", C.c_double), ("res_final", C.c_double)]
+                ("diag_fixes", C.c_int), ("res0", C.c_double), ("res_final", C.c_double)]
+
+
+# phi(alpha, ctx) callback of og_line_search
+PHI_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
 
 
 def build(force: bool = False) -> str:
@@ -83,6 +87,14 @@ def _load():
         lib.og_pcg.argtypes = [i, p, p, p, p, d, p, p, d, i, i, p, p]
         lib.og_kind_scale.argtypes = [i, p, p, p, p, p]
         lib.og_newton_step.restype = i
+        lib.og_fix_diagonal.restype = i
+        lib.og_fix_diagonal.argtypes = [i, p, p, p, p, p]
+        lib.og_newton_direction.restype = i
+        lib.og_newton_direction.argtypes = [i, p, p, p, p, p, d, i, i, p, p, p, p, p]
+        lib.og_ls_next_alpha.restype = d
+        lib.og_ls_next_alpha.argtypes = [i, d, d, d, d, d]
+        lib.og_line_search.restype = i
+        lib.og_line_search.argtypes = [d, PHI_FN, p, p, p]
         lib.og_newton_step.argtypes = [p, p, p, p, p, p, p, p, p, p]
         lib.og_bezier_patch.argtypes = [p, p, i, p]
         lib.og_bezier_eval.argtypes = [p, d, d, p, p, p]
@@ -257,6 +269,52 @@ def pcg(row_ptr, col, val, b, mask=None, tau=0.0, rtol=1e-6, max_iter=1000, fixe
     st = _load().og_pcg(n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(m), float(tau), _ptr(dbar),
                         _ptr(b), float(rtol), int(max_iter), int(fixed_iters), _ptr(x), C.byref(it))
     return x, it.value, st
+
+
+def fix_diagonal(row_ptr, col, val, mask=None, dbar=None):
+    """Local part of the regulariser on a copy of val: (fixed val, entries replaced)."""
+    n = row_ptr.size - 1
+    v = _f64(val).copy()
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    dbar = kind_scale(row_ptr, col, val, m) if dbar is None else _f64(dbar)
+    cnt = _load().og_fix_diagonal(n, _ptr(row_ptr), _ptr(col), _ptr(v), _ptr(m), _ptr(dbar))
+    return v, cnt
+
+
+def newton_direction(row_ptr, col, val, rhs, mask=None, tau_carry=0.0, rtol=1e-6, max_iter=1000,
+                     fixed_iters=0):
+    """Regularised Newton direction (og_newton_direction). Returns (d, status, tau, pcg iterations,
+    solves with tau > 0, diagonal entries replaced)."""
+    n = row_ptr.size - 1
+    val = _f64(val)
+    rhs = _f64(rhs).reshape(-1)
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    d = np.zeros(n * 12)
+    tau = C.c_double(tau_carry)
+    it, regs, fixes = C.c_int(0), C.c_int(0), C.c_int(0)
+    st = _load().og_newton_direction(n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(m), _ptr(rhs), float(rtol),
+                                     int(max_iter), int(fixed_iters), C.byref(tau), _ptr(d), C.byref(it),
+                                     C.byref(regs), C.byref(fixes))
+    return d, st, tau.value, it.value, regs.value, fixes.value
+
+
+def ls_next_alpha(trial, alpha, phi, gd, a_prev=0.0, f_prev=0.0) -> float:
+    return float(_load().og_ls_next_alpha(int(trial), float(alpha), float(phi), float(gd), float(a_prev),
+                                          float(f_prev)))
+
+
+def line_search(gd, phi):
+    """Armijo backtracking on a Python function phi(alpha). Returns (alpha or None, backtracks,
+    the alphas tried)."""
+    tried = []
+
+    def cb(a, _ctx):
+        tried.append(a)
+        return float(phi(a))
+    fn = PHI_FN(cb)
+    alpha, bt = C.c_double(0.0), C.c_int(0)
+    st = _load().og_line_search(float(gd), fn, None, C.byref(alpha), C.byref(bt))
+    return (alpha.value if st == 0 else None), bt.value, tried
 
 
 def step_params(dt=1e-3, gravity=(0.0, 0.0, -9.81), newton_rtol=1e-8, newton_max=50,

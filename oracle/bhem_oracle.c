@@ -30,14 +30,15 @@
  *     interpolation (Nocedal-Wright Sec. 3.5), each clamped to [0.1, 0.5] of the last step, at
  *     most 20 trials; alpha = 1 is accepted without a test once |g| <= 1e-6 |g_ref|.
  *   - Regulariser (Sec. 6.1 adds "a diagonal regularizer" to make the matrix positive definite,
- *     with no form or magnitude). D is diagonal: for each DOF kind (x, x_,1, x_,2, x_,12) the mean
- *     of |A_ii| over the free DOFs of that kind (positive, and scaled like each kind's stiffness,
- *     where diag(A) itself may be negative or near zero under compression). The first solve uses
- *     the smallest shift that makes the free diagonal of A + tau D positive (a necessary condition
- *     for positive definiteness): tau = 0 if it already is, else 1.01 max_k(-min_i A_ii / D_k)
- *     (at least 1e-8). Each time PCG meets p^T A p <= 0 the solve restarts with tau = max(10 tau,
- *     1e-8); beyond tau = 1e4 the step gives up. A 12x12 block that is not SPD is replaced by the
- *     inverse of its diagonal in the block-Jacobi preconditioner.
+ *     with no form or magnitude), in two parts. D is diagonal: for each DOF kind (x, x_,1, x_,2,
+ *     x_,12) the mean of |A_ii| over the free DOFs of that kind (positive, and scaled like each
+ *     kind's stiffness). Local part: every free diagonal entry A_ii <= 0 is replaced by
+ *     max(-A_ii, 1e-8 D_k), its magnitude, so that the diagonal is positive without shifting the
+ *     entries that already are. Global part: PCG solves (A + tau D) d = -g; tau starts at a tenth
+ *     of the previous Newton iteration's accepted tau of the same step (0 at the first iteration,
+ *     and 0 when a tenth is below 1e-8), each time PCG meets p^T A p <= 0 the solve restarts with
+ *     tau = max(10 tau, 1e-8), and beyond tau = 1e4 the step gives up. A 12x12 block that is not
+ *     SPD is replaced by the inverse of its diagonal in the block-Jacobi preconditioner.
  */
 #include <math.h>
 #include <stdint.h>
@@ -58,6 +59,7 @@ typedef struct {
 } og_step_params;
 typedef struct {
   int newton_iters, pcg_iters_total, ls_backtracks, regularizations, status;
+  int diag_fixes;   /* free diagonal entries replaced by the local part of the regulariser */
   double res0, res_final;
 } og_step_stats;
 
@@ -680,6 +682,110 @@ done:
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* The regularised Newton direction (Sec. 6.1 "a diagonal regularizer is added").               */
+/* ------------------------------------------------------------------------------------------ */
+/* Local part of the regulariser: every free diagonal entry A_ii <= 0 (i of kind k) is replaced by
+   max(-A_ii, 1e-8 D_k). val is changed in place; returns the number of entries replaced. */
+int og_fix_diagonal(int n, const int* row_ptr, const int* col, double* val,
+                    const unsigned char* mask, const double* dbar) {
+  int fixed = 0;
+  for (int i = 0; i < n; ++i) {
+    int k = find_block(row_ptr, col, i, i);
+    for (int a = 0; a < 12; ++a) {
+      if (mask && mask[i*12 + a]) continue;
+      double* v = &val[(size_t)k*144 + a*13];
+      if (*v <= 0.0) {
+        double floor = 1e-8 * dbar[a / 3];
+        *v = -*v > floor ? -*v : floor;
+        ++fixed;
+      }
+    }
+  }
+  return fixed;
+}
+
+/* Solves (A' + tau D) d = rhs by block-Jacobi PCG, A' = A with its diagonal fixed by
+   og_fix_diagonal and D from A (og_kind_scale). tau starts at *tau_carry / 10, or at 0 when that
+   is below 1e-8; each negative curvature met by PCG restarts the solve with tau = max(10 tau,
+   1e-8); a tau beyond 1e4 ends it with OG_ERR_INDEFINITE. On success *tau_carry receives the tau of
+   the accepted solve. Counters (added to): PCG iterations, solves run with tau > 0, diagonal
+   entries replaced. */
+int og_newton_direction(int n, const int* row_ptr, const int* col, const double* val,
+                        const unsigned char* mask, const double* rhs, double rtol, int max_iter,
+                        int fixed_iters, double* tau_carry, double* d, int* pcg_iters,
+                        int* regularizations, int* diag_fixes) {
+  size_t nb = (size_t)row_ptr[n];
+  double* A = (double*)malloc(nb * 144 * sizeof(double));
+  memcpy(A, val, nb * 144 * sizeof(double));
+  double dbar[4];
+  og_kind_scale(n, row_ptr, col, val, mask, dbar);
+  *diag_fixes += og_fix_diagonal(n, row_ptr, col, A, mask, dbar);
+  double tau = *tau_carry / 10.0;
+  if (tau < 1e-8) tau = 0.0;
+  int status = OG_OK;
+  for (;;) {
+    if (tau > 1e4) { status = OG_ERR_INDEFINITE; break; }
+    int it = 0;
+    int ps = og_pcg(n, row_ptr, col, A, mask, tau, dbar, rhs, rtol, max_iter, fixed_iters, d, &it);
+    *pcg_iters += it;
+    if (tau > 0.0) *regularizations += 1;
+    if (ps != OG_PCG_NEG_CURV) break;
+    tau = 10.0 * tau > 1e-8 ? 10.0 * tau : 1e-8;
+  }
+  if (status == OG_OK) *tau_carry = tau;
+  free(A);
+  return status;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Backtracking line search on phi(alpha) = Pi(q + alpha d) - Pi(q), phi'(0) = gd < 0 (Sec. 6.1  */
+/* "quadratic and cubic line searches"; interpolation formulas of Nocedal-Wright Sec. 3.5).     */
+/* ------------------------------------------------------------------------------------------ */
+/* The trial after a failed trial number `trial` (0-based) at alpha with value phi; a_prev, f_prev
+   are the trial before it (used from the second backtrack on). */
+double og_ls_next_alpha(int trial, double alpha, double phi, double gd, double a_prev, double f_prev) {
+  double a_new;
+  if (!isfinite(phi)) {
+    a_new = 0.5 * alpha;
+  } else if (trial == 0) {
+    /* minimiser of the quadratic with phi(0) = 0, phi'(0) = gd, phi(alpha) = phi */
+    a_new = -gd * alpha * alpha / (2.0 * (phi - gd * alpha));
+  } else {
+    /* minimiser of the cubic c a^3 + b a^2 + gd a through phi(a_prev) and phi(alpha) */
+    double a0 = a_prev, a1 = alpha;
+    double r1 = phi - gd * a1, r0 = f_prev - gd * a0;
+    double den = a0 * a0 * a1 * a1 * (a1 - a0);
+    double c = (a0 * a0 * r1 - a1 * a1 * r0) / den;
+    double b = (-a0 * a0 * a0 * r1 + a1 * a1 * a1 * r0) / den;
+    double disc = b * b - 3.0 * c * gd;
+    if (c == 0.0 || disc < 0.0) a_new = 0.5 * alpha;
+    else a_new = (-b + sqrt(disc)) / (3.0 * c);
+  }
+  if (!(a_new >= 0.1 * alpha)) a_new = 0.1 * alpha;
+  if (a_new > 0.5 * alpha) a_new = 0.5 * alpha;
+  return a_new;
+}
+
+typedef double (*og_phi_fn)(double alpha, void* ctx);
+
+/* Armijo backtracking from alpha = 1: accepts the first trial with a finite phi(alpha) <= 1e-4
+   alpha gd, at most 20 trials. Returns OG_OK with *alpha, or OG_ERR_LINESEARCH; *backtracks is
+   incremented once per rejected trial. */
+int og_line_search(double gd, og_phi_fn phi_of, void* ctx, double* alpha_out, int* backtracks) {
+  double alpha = 1.0, a_prev = 0.0, f_prev = 0.0;
+  for (int trial = 0; trial < 20; ++trial) {
+    double phi = phi_of(alpha, ctx);
+    if (isfinite(phi) && phi <= 1e-4 * alpha * gd) { *alpha_out = alpha; return OG_OK; }
+    *backtracks += 1;
+    double a_new = og_ls_next_alpha(trial, alpha, phi, gd, a_prev, f_prev);
+    a_prev = alpha;
+    f_prev = phi;
+    alpha = a_new;
+  }
+  return OG_ERR_LINESEARCH;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* One implicit-Euler step (Eq. implicit) by Newton's method with a line search (Sec. 6.1).     */
 /* Incremental potential Pi(q) = 1/(2 dt^2) (q-y)^T M (q-y) + V_e(q) - F^T q, y = q^n + dt v^n; */
 /* its stationarity is Eq. implicit. Fixed DOFs take prescribed values (Sec. 4.2).             */
@@ -722,6 +828,23 @@ static void patch_energies(const og_ctx* C, const double* q, double* Ep) {
   }
 }
 
+/* phi(alpha) = Pi(q + alpha d) - Pi(q): the elastic part as a sum of per-patch energy differences,
+   the inertial and load parts exactly (alpha d.g_inert + alpha^2/2 d^T M d / dt^2). */
+typedef struct {
+  const og_ctx* C; const double* q; const double* d; double* qt; const double* Ep; double* Et;
+  double dMd, dgin;
+} og_phi_ctx;
+
+static double phi_of_alpha(double alpha, void* ctx) {
+  og_phi_ctx* L = (og_phi_ctx*)ctx;
+  int m = L->C->m, np = L->C->g->nu * L->C->g->nv;
+  for (int i = 0; i < m; ++i) L->qt[i] = L->q[i] + alpha * L->d[i];
+  patch_energies(L->C, L->qt, L->Et);
+  double dV = 0.0;
+  for (int p = 0; p < np; ++p) dV += L->Et[p] - L->Ep[p];
+  return dV + alpha * L->dgin + 0.5 * alpha * alpha * L->dMd;
+}
+
 int og_newton_step(const og_grid* g, const og_material* mat, const double* rest,
                    const og_step_params* P, const unsigned char* mask, const double* qfix,
                    double* q, double* v, const double* warm, og_step_stats* st) {
@@ -757,41 +880,16 @@ int og_newton_step(const og_grid* g, const og_material* mat, const double* rest,
   st->res0 = gref;
   if (warm) for (int i = 0; i < m; ++i) q[i] = (mask && mask[i]) ? qfix[i] : warm[i];
   int status = OG_OK;
-  double gn = 0.0;
+  double gn = 0.0, tau_carry = 0.0;
   for (int it = 0;; ++it) {
     gn = full_gradient(&C, q, y, gr, gin, work);
     if (gn <= P->newton_rtol * gref) break;
     if (it >= P->newton_max) { status = OG_ERR_NOT_CONVERGED; break; }
     og_assemble(g, mat, rest, q, row_ptr, col, 1.0 / (P->dt * P->dt), NULL, NULL, val, P->pseudo_hessian);
     for (int i = 0; i < m; ++i) rhs[i] = -gr[i];
-    /* smallest shift that makes the free diagonal positive, then x10 per negative curvature */
-    double dbar[4], dmin[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
-    og_kind_scale(n, row_ptr, col, val, mask, dbar);
-    for (int i = 0; i < n; ++i) {
-      int k = find_block(row_ptr, col, i, i);
-      for (int a = 0; a < 12; ++a) {
-        if (mask && mask[i*12 + a]) continue;
-        double dv = val[(size_t)k*144 + a*13];
-        if (dv < dmin[a / 3]) dmin[a / 3] = dv;
-      }
-    }
-    double tau = 0.0;
-    for (int q = 0; q < 4; ++q)
-      if (dmin[q] <= 0.0 && -dmin[q] / dbar[q] * 1.01 > tau) tau = -dmin[q] / dbar[q] * 1.01;
-    if (tau > 0.0) {
-      if (tau < 1e-8) tau = 1e-8;
-      st->regularizations++;
-    }
-    int piters = 0, ps;
-    for (;;) {
-      if (tau > 1e4) { status = OG_ERR_INDEFINITE; break; }
-      ps = og_pcg(n, row_ptr, col, val, mask, tau, dbar, rhs, P->pcg_rtol, P->pcg_max,
-                  P->pcg_fixed_iters, d, &piters);
-      st->pcg_iters_total += piters;
-      if (ps != OG_PCG_NEG_CURV) break;
-      st->regularizations++;
-      tau = tau * 10.0 > 1e-8 ? tau * 10.0 : 1e-8;
-    }
+    status = og_newton_direction(n, row_ptr, col, val, mask, rhs, P->pcg_rtol, P->pcg_max,
+                                 P->pcg_fixed_iters, &tau_carry, d, &st->pcg_iters_total,
+                                 &st->regularizations, &st->diag_fixes);
     if (status != OG_OK) break;
 
     /* line search on phi(alpha) = Pi(q + alpha d) - Pi(q) */
@@ -800,40 +898,13 @@ int og_newton_step(const og_grid* g, const og_material* mat, const double* rest,
     if (gn > 1e-6 * gref) {
       if (!(gd < 0.0)) { status = OG_ERR_LINESEARCH; break; }
       mass_mult(n, row_ptr, col, mval, d, Md);
-      double dMd = vdot(m, d, Md) / (P->dt * P->dt);
-      double dgin = vdot(m, d, gin);
+      og_phi_ctx L;
+      L.C = &C; L.q = q; L.d = d; L.qt = qt; L.Ep = Ep; L.Et = Et;
+      L.dMd = vdot(m, d, Md) / (P->dt * P->dt);
+      L.dgin = vdot(m, d, gin);
       patch_energies(&C, q, Ep);
-      double a_prev = 0.0, f_prev = 0.0;
-      int ok = 0;
-      for (int trial = 0; trial < 20; ++trial) {
-        for (int i = 0; i < m; ++i) qt[i] = q[i] + alpha * d[i];
-        patch_energies(&C, qt, Et);
-        double dV = 0.0;
-        for (int p = 0; p < np; ++p) dV += Et[p] - Ep[p];
-        double phi = dV + alpha * dgin + 0.5 * alpha * alpha * dMd;
-        if (isfinite(phi) && phi <= 1e-4 * alpha * gd) { ok = 1; break; }
-        st->ls_backtracks++;
-        double a_new;
-        if (!isfinite(phi)) a_new = 0.5 * alpha;
-        else if (trial == 0) {
-          a_new = -gd * alpha * alpha / (2.0 * (phi - gd * alpha));
-        } else {
-          /* cubic through phi(0), phi'(0), phi(a_prev), phi(alpha) */
-          double a0 = a_prev, a1 = alpha;
-          double r1 = phi - gd * a1, r0 = f_prev - gd * a0;
-          double den = a0 * a0 * a1 * a1 * (a1 - a0);
-          double ca = (a0 * a0 * r1 - a1 * a1 * r0) / den;
-          double cb = (-a0 * a0 * a0 * r1 + a1 * a1 * a1 * r0) / den;
-          double disc = cb * cb - 3.0 * ca * gd;
-          if (ca == 0.0 || disc < 0.0) a_new = 0.5 * alpha;
-          else a_new = (-cb + sqrt(disc)) / (3.0 * ca);
-        }
-        if (!(a_new >= 0.1 * alpha)) a_new = 0.1 * alpha;
-        if (a_new > 0.5 * alpha) a_new = 0.5 * alpha;
-        a_prev = alpha; f_prev = phi;
-        alpha = a_new;
-      }
-      if (!ok) { status = OG_ERR_LINESEARCH; break; }
+      status = og_line_search(gd, phi_of_alpha, &L, &alpha, &st->ls_backtracks);
+      if (status != OG_OK) break;
     }
     for (int i = 0; i < m; ++i) q[i] += alpha * d[i];
     st->newton_iters++;
