@@ -116,8 +116,9 @@ typedef struct {
   int newton_iters;       /* Newton updates applied                                         */
   int pcg_iters_total;    /* PCG iterations over all solves (regularised restarts included) */
   int ls_backtracks;      /* rejected line-search trials                                    */
-  int regularizations;    /* solves with a diagonal shift tau D (Sec. 6.1 regulariser)      */
+  int regularizations;    /* solves with a diagonal shift tau D > 0 (Sec. 6.1 regulariser)  */
   int status;             /* shell_status of the step                                       */
+  int diag_fixes;         /* free diagonal entries A_ii <= 0 replaced (regulariser, local)  */
   double res0;            /* |g_free| at the zero guess                                     */
   double res_final;       /* |g_free| at the returned state                                 */
 } shell_step_stats;
@@ -198,6 +199,14 @@ SHELL_API shell_status shell_spmv(shell_t* shell, const void* x, int x_is_fp32, 
 /* One implicit-Euler step (Eq. implicit) by Newton with line search (Sec. 6.1):
    minimises Pi(q) = (q - y)^T M (q - y) / (2 dt^2) + V_e(q) - F^T q, y = q^n + dt v^n, over the
    free DOFs; fixed DOFs (fixed_mask[k] != 0) take q_fixed[k] (Sec. 4.2 positional constraints).
+   Each Newton direction solves (A' + tau D) d = -g, A = M / dt^2 + K (Sec. 6.1's diagonal
+   regulariser): A' replaces every free diagonal entry A_ii <= 0 of DOF kind k by
+   max(-A_ii, 1e-8 D_k) (D_k = mean |A_ii| over the free DOFs of kind k; the assembled matrix
+   read by shell_get_bsr afterwards holds A'); tau starts at a tenth of the previous iteration's
+   tau of the same step (0 at the first, and 0 when a tenth is below 1e-8); negative curvature
+   met by the solve multiplies tau by 10 (at least 1e-8) and restarts it; beyond tau = 1e4 the
+   step returns SHELL_ERR_INDEFINITE. The line search is Armijo (c1 = 1e-4) from alpha = 1 with
+   the quadratic, then cubic, interpolant's minimiser clamped to [0.1, 0.5] of the last trial.
    q, v: [n_dof] FP64 in/out (host or device); fixed_mask [n_dof] uint8 and q_fixed [n_dof]
    (host or device, may be NULL together); warm_start [n_dof] or NULL: initial Newton iterate
    (the residual reference stays the zero guess q^n). stats: host. Returns stats->status. On

@@ -57,7 +57,7 @@ class shell_step_params(C.Structure):
 class shell_step_stats(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("pcg_iters_total", C.c_int),
                 ("ls_backtracks", C.c_int), ("regularizations", C.c_int), ("status", C.c_int),
-                ("res0", C.c_double), ("res_final", C.c_double)]
+                ("diag_fixes", C.c_int), ("res0", C.c_double), ("res_final", C.c_double)]
 
 
 class shell_batch_info_t(C.Structure):

@@ -40,7 +40,7 @@ struct ShellState {
   double dbar[4], dmin[4], dcount[4];
   // line search
   double dMd, dgin, gd, ls_alpha, ls_prev_alpha, ls_prev_phi, dV;
-  int searching, ls_trials, ls_backtracks, pad;
+  int searching, ls_trials, ls_backtracks, diag_fixes;
   // reduction accumulators, zeroed by the controllers before use
   double acc[4];
   double acc2[12];
@@ -673,16 +673,31 @@ __global__ void k_ctrl_reg_init(int S, ShellState* st, const int* __restrict__ d
   if (!T.active) return;
   T.pcg_done = 0;
   T.restart = 0;
-  // the smallest shift that keeps the free diagonal of A + tau D positive (Sec. 6.1 regulariser)
-  double tau = 0.0;
-  for (int k = 0; k < 4; ++k)
-    if (T.dcount[k] > 0 && T.dmin[k] <= 0.0) tau = fmax(tau, -T.dmin[k] / T.dbar[k] * 1.01);
-  if (tau > 0.0) {
-    tau = fmax(tau, 1e-8);
-    T.regularizations += 1;
-  }
+  // Sec. 6.1 regulariser: tau starts at a tenth of the previous Newton iteration's tau of this
+  // step (T.tau, 0 at the first; 0 when a tenth is below 1e-8)
+  double tau = T.tau / 10.0;
+  if (tau < 1e-8) tau = 0.0;
+  if (tau > 0.0) T.regularizations += 1;
   T.tau = tau;
   for (int k = 0; k < 4; ++k) T.td[k] = (float)(tau * T.dbar[k]);
+}
+
+// Local part of the regulariser, after k_ctrl_reg_init: every free diagonal entry A_ii <= 0 of an
+// active shell becomes max(-A_ii, 1e-8 D_k) of that shell (D_k from the diagonal before the fix).
+__global__ void k_fix_diag(int m, const int* __restrict__ nshell, ShellState* st, const int* __restrict__ diag_block,
+                           float* __restrict__ val, const unsigned char* __restrict__ mask) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+    if (mask && mask[k]) continue;
+    const int i = k / 12, a = k % 12;
+    float* d = &val[(size_t)diag_block[i] * 144 + a * 13];
+    const float v = *d;
+    if (v > 0.f) continue;
+    ShellState& T = st[nshell[i]];
+    if (!T.active) continue;
+    const float f = (float)(1e-8 * T.dbar[a / 3]);
+    *d = -v > f ? -v : f;
+    atomicAdd(&T.diag_fixes, 1);
+  }
 }
 
 // Between PCG chunks: shells that met negative curvature restart with tau x 10 (at least 1e-8);
@@ -693,13 +708,13 @@ __global__ void k_ctrl_restart(int S, ShellState* st, Counters* cnt) {
   ShellState& T = st[s];
   if (!(T.active && T.pcg_done && T.negcurv)) return;
   T.negcurv = 0;
-  T.regularizations += 1;
   T.tau = fmax(10.0 * T.tau, 1e-8);
   if (T.tau > 1e4) {
     T.status = SHELL_ERR_INDEFINITE;
     T.active = 0;
     return;
   }
+  T.regularizations += 1;   // the restarted solve runs with tau > 0
   for (int k = 0; k < 4; ++k) T.td[k] = (float)(T.tau * T.dbar[k]);
   T.pcg_done = 0;
   T.restart = 1;
@@ -1167,6 +1182,8 @@ shell_status solve_directions(shell_batch_s& b, const shell_step_params& P, cons
   BL(b);
   k_ctrl_reg_init<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, b.dmin_bits);
   BL(b);
+  k_fix_diag<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, b.nshell, b.st, b.diag, b.val, mask);
+  BL(b);
   int only_restart = 0;
   for (int round = 0; round < 16; ++round) {
     k_precond<<<blocks_for(b.N, 16), 192, 0, b.stream>>>(b.N, b.nshell, b.st, b.diag, b.val, mask, b.Dinv,
@@ -1550,6 +1567,7 @@ extern "C" shell_status shell_batch_newton_step(shell_batch_t* batch, const shel
     o.ls_backtracks = T.ls_backtracks;
     o.regularizations = T.regularizations;
     o.status = T.status;
+    o.diag_fixes = T.diag_fixes;
     o.res0 = T.gref;
     o.res_final = T.gn;
     if (T.status != SHELL_OK && worst == SHELL_OK) worst = (shell_status)T.status;

@@ -78,6 +78,8 @@ struct NewtonScalars {
   double dV;           // sum_p (E_p(q + a d) - E_p(q))
   double energy;       // assembled elastic energy
   double diag_stats[12];  // per DOF kind: sum |A_ii|, count, min A_ii over free DOFs
+  int diag_fixes;      // free diagonal entries changed by the regulariser's local part (per step)
+  int pad_;
 };
 
 // ------------------------------------------------------------------------------------------
@@ -243,6 +245,7 @@ int pcg_loop_unroll();   // PCG iterations per loop body
 shell_status launch_spmv(Shell& s, const void* x, int x_fp32, void* y);
 shell_status launch_pcg_result(Shell& s);
 shell_status launch_diag_check(Shell& s, const unsigned char* mask, double* out12, bool aux = false);
+shell_status launch_fix_diag(Shell& s, const unsigned char* mask, const double floor4[4], int* count);
 shell_status launch_axpy_fixed(Shell& s, double* q, const double* d, double alpha);
 shell_status launch_overwrite_fixed(Shell& s, double* dst, const double* src,
                                     const unsigned char* mask, const double* fixed_vals);

@@ -462,13 +462,14 @@ static shell_status kind_stats(Shell& s, const unsigned char* mask, KindStats& K
   kind_stats_from_host(s, K);
   return SHELL_OK;
 }
-// The smallest regulariser shift that keeps every free diagonal entry of A + tau D positive
-// (a necessary condition for positive definiteness): 0, or 1.01 max_k(-min A_ii / D_k) >= 1e-8.
-static double start_shift(const KindStats& K) {
-  double tau = 0.0;
-  for (int q = 0; q < 4; ++q)
-    if (K.count[q] > 0 && K.dmin[q] <= 0.0) tau = std::max(tau, -K.dmin[q] / K.dbar[q] * 1.01);
-  return tau > 0.0 ? std::max(tau, 1e-8) : 0.0;
+// Sec. 6.1 diagonal regulariser, local part: when some free diagonal entry is <= 0, each such
+// entry A_ii of kind k becomes max(-A_ii, 1e-8 D_k) (in place, counted in d_ns->diag_fixes).
+static shell_status fix_diagonal(Shell& s, const unsigned char* mask, const KindStats& K) {
+  bool any = false;
+  for (int q = 0; q < 4; ++q) any = any || (K.count[q] > 0 && K.dmin[q] <= 0.0);
+  if (!any) return SHELL_OK;
+  const double floor4[4] = {1e-8 * K.dbar[0], 1e-8 * K.dbar[1], 1e-8 * K.dbar[2], 1e-8 * K.dbar[3]};
+  return launch_fix_diag(s, mask, floor4, &s.d_ns->diag_fixes);
 }
 }  // namespace bhem
 
@@ -530,8 +531,9 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
   BHEM_CUDA(cudaMemcpyAsync(s.d_qn, q, sizeof(double) * m, cudaMemcpyDeviceToDevice, s.stream));
   BHEM_TRY(launch_predictor(s, s.d_qn, v_in, P.dt, s.d_y));
   if (mask) BHEM_TRY(launch_overwrite_fixed(s, q, s.d_qn, mask, qfix));
-  double gref = 0.0, gn = 0.0;
+  double gref = 0.0, gn = 0.0, tau_carry = 0.0;
   const double inv_dt2 = 1.0 / (P.dt * P.dt);
+  BHEM_CUDA(cudaMemsetAsync(&s.d_ns->diag_fixes, 0, sizeof(int), s.stream));
   // The first iteration's Hessian at q does not depend on the residual: it is assembled on the
   // auxiliary stream, enqueued before the FP64 residual, so that the residual's CTAs take over the
   // SMs as the element kernel's retire (7.83 against 7.85 ms per Newton iteration on the 256^2
@@ -579,9 +581,10 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
     reuse = false;
     if (gn <= P.newton_rtol * gref) break;
     if (it >= P.newton_max) { status = SHELL_ERR_NOT_CONVERGED; break; }
-    // Sec. 6.1 diagonal regulariser A + tau D (D = per-kind mean |A_ii|): the first solve uses the
-    // smallest shift that makes the free diagonal positive, each negative curvature met by PCG
-    // multiplies tau by 10 (at least 1e-8), beyond 1e4 the step gives up.
+    // Sec. 6.1 diagonal regulariser: the non-positive free diagonal entries fixed in place, then
+    // A + tau D (D = per-kind mean |A_ii| before the fix) with tau from a tenth of the previous
+    // iteration's tau; each negative curvature met by PCG multiplies tau by 10 (at least 1e-8),
+    // beyond 1e4 the step gives up.
     KindStats K;
     const bool from_pending = hess_pending;
     if (hess_pending) {   // assembled and its statistics read with the residual (joined there)
@@ -595,8 +598,9 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
     if (from_pending) kind_stats_from_host(s, K);
     else BHEM_TRY(kind_stats(s, mask, K));
     mark(s, "kind_stats");
-    double tau = start_shift(K);
-    if (tau > 0.0) st.regularizations++;
+    BHEM_TRY(fix_diagonal(s, mask, K));
+    double tau = tau_carry / 10.0;
+    if (tau < 1e-8) tau = 0.0;
     for (;;) {
       if (tau > 1e4) { status = SHELL_ERR_INDEFINITE; break; }
       int pit = 0, neg = 0;
@@ -606,11 +610,12 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
       else
         BHEM_TRY(run_pcg(s, mask, td, s.d_rhs, P.pcg_rtol, P.pcg_max, P.pcg_fixed_iters, &pit, &neg));
       st.pcg_iters_total += pit;
+      if (tau > 0.0) st.regularizations++;
       if (!neg) break;
-      st.regularizations++;
       tau = std::max(10.0 * tau, 1e-8);
     }
     if (status != SHELL_OK) break;
+    tau_carry = tau;
     BHEM_CUDA(cudaMemcpyAsync(s.d_d, s.d_x, sizeof(double) * m, cudaMemcpyDeviceToDevice, s.stream));
     // line search on phi(a) = Pi(q + a d) - Pi(q) = dV(a) + a d.g_in + a^2/2 d^T M d / dt^2
     double alpha = 1.0;
@@ -673,6 +678,10 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
   }
   if (hess_pending) BHEM_CUDA(cudaStreamWaitEvent(s.stream, s.ev_hess, 0));   // unused, but finished in order
   st.res_final = gn;
+  BHEM_CUDA(cudaMemcpyAsync(&s.h_ns->diag_fixes, &s.d_ns->diag_fixes, sizeof(int), cudaMemcpyDeviceToHost,
+                            s.stream));
+  BHEM_CUDA(cudaStreamSynchronize(s.stream));
+  st.diag_fixes = s.h_ns->diag_fixes;
   if (status == SHELL_OK || status == SHELL_ERR_NOT_CONVERGED) {
     BHEM_TRY(launch_velocity(s, q, s.d_qn, P.dt, v_out));
   } else {

@@ -987,6 +987,34 @@ shell_status launch_precond_setup(Shell& s, const unsigned char* mask, const dou
   return SHELL_OK;
 }
 
+// Local part of the Sec. 6.1 regulariser: every free diagonal entry A_ii <= 0 (DOF kind k) becomes
+// max(-A_ii, floor_k), floor_k = 1e-8 D_k; the number of entries changed is added to *count.
+template <typename Rm>
+__global__ void k_fix_diag(int m, const int* __restrict__ diag_block, Rm* __restrict__ val,
+                           const unsigned char* __restrict__ mask, Shift4 floor, int* count) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m || (mask && mask[k])) return;
+  Rm* a = &val[(size_t)diag_block[k / 12] * 144 + (k % 12) * 13];
+  const Rm v = *a;
+  if (v <= Rm(0)) {
+    const Rm f = (Rm)floor.v[(k % 12) / 3];
+    *a = -v > f ? -v : f;
+    atomicAdd(count, 1);
+  }
+}
+
+shell_status launch_fix_diag(Shell& s, const unsigned char* mask, const double floor4[4], int* count) {
+  Shift4 f{{floor4[0], floor4[1], floor4[2], floor4[3]}};
+  const int blocks = (s.n_dof + 255) / 256;
+  if (s.val_fp64)
+    k_fix_diag<double><<<blocks, 256, 0, s.stream>>>(s.n_dof, s.d_diag_block, (double*)s.d_val, mask, f, count);
+  else
+    k_fix_diag<float><<<blocks, 256, 0, s.stream>>>(s.n_dof, s.d_diag_block, (float*)s.d_val, mask, f, count);
+  BHEM_CUDA(cudaGetLastError());
+  ++s.launches;
+  return SHELL_OK;
+}
+
 shell_status launch_diag_check(Shell& s, const unsigned char* mask, double* out12, bool aux) {
   // aux: beside other reducing kernels, on the shell's second workspace
   const Reduce& red = aux ? s.red_aux : s.red;
