@@ -3,10 +3,14 @@
 
 One step = one Newton iteration through shell_newton_step (newton_max = 1): FP64 residual
 (energy + gradient kernels, mass product), FP32 element Hessians of every patch assembled into
-the 12x12 BSR (+ M / dt^2), block-Jacobi set-up, exactly 50 PCG iterations (FP32 SpMV, FP64
-dots), line search with FP64 per-patch energy differences, update and velocity. The metric is
-patch-Hessians/s: patches whose E, 48-gradient and exact 48x48 Hessian were evaluated and
-assembled, per second, with everything else the Newton iteration needs included in the time.
+the 12x12 BSR (+ M / dt^2), the regulariser's diagonal fix, block-Jacobi set-up, PCG solves of 50
+iterations (FP32 SpMV, FP64 dots; a solve that meets negative curvature restarts with a larger
+shift, and pcg_iterations_per_step counts every iteration), line search with FP64 per-patch
+energy differences, update and velocity. The metric is patch-Hessians/s: patches whose E,
+48-gradient and exact 48x48 Hessian were evaluated and assembled, per second, with everything
+else the Newton iteration needs included in the time. The default run adds, as extra keys, the
+280x5 annulus, the 512-sheet batch, the learned warm start and the 200-step twist, and the
+oracle on all host cores and on one thread.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload W]
 Prints one JSON line (rank 0).
@@ -33,8 +37,8 @@ METRIC = "patch-Hessians/s and Newton steps/s at 1e-8 residual; batched/learned 
 UNIT = "patch-Hessians/s"
 WORKLOADS = {
     "sheet256": "256x256-patch 1 m sheet, 8-term sinusoid displacement (5 cm), FP32 element eval "
-                "+ BSR assembly + block-Jacobi PCG of 50 iterations (fewer only when the FP32 residual "
-                "is exhausted), FP64 residual/reductions",
+                "+ BSR assembly + block-Jacobi PCG solves of 50 iterations (fewer only when the FP32 "
+                "residual is exhausted or negative curvature restarts the solve), FP64 residual/reductions",
     "sheet192": "192x192-patch 1 m sheet (profiling size: FP32 BSR 192 MB > L2), same recipe as sheet256",
     "batch512": "512 independent 1 m sheets, n x n patches with n ~ U{4..40}, log10 E ~ U[4,6], "
                 "h ~ U[0.5,2] mm, N(0,1e-3) noise, two corners pinned, gravity; one implicit-Euler "
@@ -141,6 +145,18 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout: float = 10.0):
+        """Blocks until the sampler has printed its first line (nvidia-smi's start-up, NVML
+        initialisation included, is then over), so that it does not overlap a timed region."""
+        t0 = time.perf_counter()
+        while self.proc and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.02)
+        return self
+
+    def mark(self):
+        """Start of the timed region: the summary covers the samples taken from here on."""
+        self.skip = len(self.lines)
+
     def __exit__(self, *a):
         if self.proc:
             self.proc.terminate()
@@ -152,7 +168,7 @@ class ClockSampler:
     def summary(self):
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for line in self.lines[getattr(self, "skip", 0):]:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -170,10 +186,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(workload: str, n_steps: int = 8, n: int = 48):
-    """The oracle (plain FP64 C, single thread) on a bounded sample of the same workload: the
-    same sinusoid recipe on an n x n sheet, one Newton iteration with exactly 50 PCG iterations
-    per step."""
+def cpu_baselines(workload: str, n_steps: int = 4, n: int = 48):
+    """The oracle (plain FP64 C) on a bounded sample of the same workload: the same sinusoid
+    recipe on an n x n sheet (a 70x5 annulus for the strip), one Newton iteration with 50-iteration
+    PCG solves per step, on all host cores (its OpenMP loops over patches and rows) and on one
+    thread. Returns (all cores, single thread)."""
     import oracle as O
     from paper_2312_14839_gb300 import scenes as S
     if workload == "annulus280x5":
@@ -183,13 +200,21 @@ def cpu_baseline(workload: str, n_steps: int = 8, n: int = 48):
         g, rest, q = S.sheet_sinusoid(n, 3)
         sample = f"{n}x{n}-patch sheet, same recipe"
     P = O.step_params(dt=1e-3, newton_max=1, pcg_fixed_iters=50)
-    t0 = time.perf_counter()
-    for _ in range(n_steps):
-        O.newton_step(g, S.SHEET_MATERIAL, rest, q.reshape(-1), np.zeros(g.n_dof), P)
-    dt = (time.perf_counter() - t0) / n_steps
-    return {"value": g.n_patches / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sample}, {n_steps} x one Newton iteration (50 PCG iterations), "
-                      f"{dt:.2f} s each"}
+    out = []
+    for threads in (os.cpu_count() or 1, 1):
+        used = O.set_threads(threads)
+        # warm-up; then the regulariser level is carried from step to step, as on the GPU
+        P.tau_carry = O.newton_step(g, S.SHEET_MATERIAL, rest, q.reshape(-1), np.zeros(g.n_dof), P)[2]["tau_final"]
+        t0 = time.perf_counter()
+        for _ in range(n_steps):
+            O.newton_step(g, S.SHEET_MATERIAL, rest, q.reshape(-1), np.zeros(g.n_dof), P)
+        dt = (time.perf_counter() - t0) / n_steps
+        out.append({"value": g.n_patches / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+                    "nproc": os.cpu_count(),
+                    "sample": f"{sample}, {n_steps} x one Newton iteration (50-iteration PCG solves), "
+                              f"{dt:.2f} s each, {used} thread(s)"})
+    O.set_threads(os.cpu_count() or 1)
+    return out[0], out[1]
 
 
 def reduce_over_ranks(dist, seconds, units, device=None):
@@ -214,30 +239,38 @@ def run_reference(args):
     import oracle as O
     from paper_2312_14839_gb300 import scenes as S
     O.build()
-    n = 32
+    cores = O.set_threads(os.cpu_count() or 1)
+    n = 48
     g, rest, q = S.sheet_sinusoid(n, 3) if args.workload == "sheet256" else S.annulus_sinusoid(70, 5, 3)
     P = O.step_params(dt=1e-3, newton_max=1, pcg_fixed_iters=50)
     for _ in range(args.warmup):
-        O.newton_step(g, S.SHEET_MATERIAL, rest, q.reshape(-1), np.zeros(g.n_dof), P)
+        P.tau_carry = O.newton_step(g, S.SHEET_MATERIAL, rest, q.reshape(-1), np.zeros(g.n_dof), P)[2]["tau_final"]
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        O.newton_step(g, S.SHEET_MATERIAL, rest, q.reshape(-1), np.zeros(g.n_dof), P)
+        P.tau_carry = O.newton_step(g, S.SHEET_MATERIAL, rest, q.reshape(-1), np.zeros(g.n_dof), P)[2]["tau_final"]
     el = time.perf_counter() - t0
     v = g.n_patches * args.steps / el
     sample = (f"{g.nu}x{g.nv}-patch sample of the {args.workload} recipe, one Newton iteration "
-              f"(50 PCG iterations) per step")
+              f"(50-iteration PCG solves) per step, {cores} host threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "sample": sample},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "nproc": os.cpu_count()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
 def run_batch_bench(args):
     """Batched vs plain GPU Newton on the 512-sheet workload (one JSON line)."""
+    print(json.dumps(batch_line(args, args.steps, args.warmup, max(1, min(args.steps, 2)))), flush=True)
+
+
+def batch_line(args, steps, warmup, plain_reps):
+    """Batched vs plain GPU Newton on the 512-sheet workload: `steps` timed batch steps after
+    `warmup`, and `plain_reps` timed passes over the same sheets one by one."""
     import torch
     from paper_2312_14839_gb300 import bhem
     from paper_2312_14839_gb300 import scenes as S
@@ -263,15 +296,17 @@ def run_batch_bench(args):
         v.copy_(v0)
         return B.newton_step(q, v, P, mask=mask, q_fixed=q0)
 
-    for _ in range(args.warmup):
-        st = bstep()
-    torch.cuda.synchronize()
-    l0 = B.info()["kernel_launches"]
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
+        clk.wait_first()
+        for _ in range(warmup):
+            st = bstep()
+        torch.cuda.synchronize()
+        l0 = B.info()["kernel_launches"]
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clk.mark()
         ev0.record()
         ph, iters = 0.0, []
-        for _ in range(args.steps):
+        for _ in range(steps):
             st = bstep()
             it = np.array([x["newton_iters"] for x in st])
             ph += float((patches * it).sum())
@@ -299,7 +334,7 @@ def run_batch_bench(args):
     pstep()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    preps = max(1, min(args.steps, 2))
+    preps = plain_reps
     for _ in range(preps):
         pph = pstep()
     torch.cuda.synchronize()
@@ -307,27 +342,33 @@ def run_batch_bench(args):
     for sh in shells:
         sh.close()
     it_all = np.concatenate(iters)
-    print(json.dumps({
-        "metric": METRIC, "value": ph / sec, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True,
+    B.close()
+    return {
+        "metric": METRIC, "value": ph / sec, "unit": UNIT, "n_gpus": 1, "steps": steps,
+        "warmup": warmup, "ms_per_step": sec / steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded sheets)",
         "config": {"workload": WORKLOADS["batch512"], "sheets": len(sheets), "patches": int(patches.sum()),
                    "dof": B.n_dof, "autotuned": {"patches_per_item": tune["patches_per_item"],
                                                  "assembly": ["atomic", "color"][tune["assembly"]]}},
-        "sheet_steps_per_s": len(sheets) * args.steps / sec,
+        "sheet_steps_per_s": len(sheets) * steps / sec,
         "plain_sheet_steps_per_s": len(sheets) / psec,
-        "batched_vs_plain": (len(sheets) * args.steps / sec) / (len(sheets) / psec),
+        "batched_vs_plain": (len(sheets) * steps / sec) / (len(sheets) / psec),
         "plain_value": pph / psec,
         "newton_iters_per_sheet": {"mean": float(it_all.mean()), "max": int(it_all.max())},
         "all_sheets_converged_1e-8": bool(ok), "gpu_launches": launches, "clocks": clk.summary(),
-    }), flush=True)
-    B.close()
+    }
 
 
 def run_learned_bench(args):
     """Learned warm start vs the plain zero-guess Newton (and the inertial predictor) on the
-    64x64 corner-twist sheet (one JSON line). The timed region of each arm is a 200-step
-    rollout, warm-start inference included."""
+    64x64 corner-twist sheet (one JSON line)."""
+    print(json.dumps(learned_line(args)), flush=True)
+
+
+def learned_line(args):
+    """Learned warm start vs the plain zero-guess Newton (and the inertial predictor) on the
+    64x64 corner-twist sheet. The timed region of each arm is a 200-step rollout, warm-start
+    inference included."""
     import torch
     from paper_2312_14839_gb300 import bhem
     from paper_2312_14839_gb300 import learned as L
@@ -345,6 +386,8 @@ def run_learned_bench(args):
         L.rollout(scene, rates, args.warmup, mode, net)
     res = {}
     with ClockSampler(0) as clk:
+        clk.wait_first()
+        clk.mark()
         for mode in ("zero", "inertial", "learned"):
             res[mode] = L.rollout(scene, rates, roll_steps, mode, net)
     z, i, l = res["zero"], res["inertial"], res["learned"]
@@ -356,7 +399,7 @@ def run_learned_bench(args):
         return {"steps_per_s": r["steps_per_s"], "newton_iters_mean": r["mean_newton"],
                 "pcg_iters_per_step": r["mean_pcg"], "newton_hist": np.bincount(r["newton"]).tolist(),
                 "fallbacks": r["fallbacks"], "max_final_residual_ratio": r["max_res_ratio"]}
-    print(json.dumps({
+    line = {
         "metric": METRIC, "value": l["steps_per_s"], "unit": "implicit-Euler steps/s", "n_gpus": 1,
         "steps": roll_steps, "warmup": args.warmup, "ms_per_step": l["seconds"] / roll_steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 MLP + f32/f64 solver",
@@ -373,8 +416,9 @@ def run_learned_bench(args):
                             "newton_iters_mean": float(data.newton_iters.mean()),
                             "trajectories_stopped_unconverged": data.dropped},
         "gpu_launches": l["launches"], "clocks": clk.summary(),
-    }), flush=True)
+    }
     net.close()
+    return line
 
 
 # Algorithmic work per patch of the two arithmetic-bound kernels (the units are stated in DESIGN):
@@ -770,8 +814,13 @@ def run_direct_bench(args):
 
 
 def run_twist_bench(args):
-    """Exact against pseudo Hessian on the twist scene (one JSON line): implicit-Euler steps/s and
-    Newton iterations at 1e-8, plus the element pass time of each Hessian."""
+    """Exact against pseudo Hessian on the twist scene (one JSON line)."""
+    print(json.dumps(twist_line(args)), flush=True)
+
+
+def twist_line(args):
+    """Exact against pseudo Hessian on the twist scene: implicit-Euler steps/s and Newton
+    iterations at 1e-8, plus the element pass time of each Hessian."""
     import torch
     from paper_2312_14839_gb300 import bhem
     from paper_2312_14839_gb300 import scenes as S
@@ -784,8 +833,8 @@ def run_twist_bench(args):
     pres = [S.twist_prescription(g, rest, k) for k in range(1, steps + 1)]
     mask = torch.as_tensor(pres[0][0], device=dev)
     qfix = torch.as_tensor(np.stack([v for _, v in pres]), device=dev)
-    # the twisted sheet buckles (negative curvature from about step 18): allow long Newton runs
-    # and count the steps that still end unconverged (q then holds the last iterate)
+    # the Newton cap is generous; steps that still end unconverged are counted (q then holds the
+    # last iterate)
     P = bhem.step_params(dt=2e-3, gravity=(0.0, 0.0, 0.0), newton_max=200)
     res = {}
     clk_all = []
@@ -808,6 +857,8 @@ def run_twist_bench(args):
         l0 = sh.kernel_launches()
         torch.cuda.synchronize()
         with ClockSampler(0) as clk:
+            clk.wait_first()
+            clk.mark()
             e0.record(stream)
             it = rollout(steps)
             e1.record(stream)
@@ -835,7 +886,7 @@ def run_twist_bench(args):
                      "gpu_launches": sh.kernel_launches() - l0}
         sh.close()
     ex, ps = res["exact"], res["pseudo"]
-    print(json.dumps({
+    return {
         "metric": METRIC, "value": ex["steps_per_s"], "unit": "implicit-Euler steps/s", "n_gpus": 1,
         "steps": steps, "warmup": args.warmup, "ms_per_step": ex["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (twist prescription)",
@@ -843,17 +894,19 @@ def run_twist_bench(args):
         "exact_hessian": ex, "pseudo_hessian": ps,
         "pseudo_vs_exact_steps_per_s": ps["steps_per_s"] / ex["steps_per_s"],
         "gpu_launches": ex["gpu_launches"], "clocks": clk_all[0],
-    }), flush=True)
+    }
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="sheet256", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="sheet256: leave out the annulus, batch, learned and twist measurements")
     ap.add_argument("--spmv-reps", type=int, default=50)
     ap.add_argument("--train-iters", type=int, default=4000)
     ap.add_argument("--spmv", default="auto", choices=["auto", "plain", "tma"])
@@ -899,7 +952,28 @@ def main():
     from paper_2312_14839_gb300 import bhem
     bhem.load()
 
-    g, mat, rest, q0 = make_workload(args.workload)
+    line = step_workload_line(args, args.workload, dist, world, rank, full=True)
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == "sheet256":
+        line["workloads"] = extra_workloads(args)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        line["cpu_baseline"], line["cpu_baseline_single_thread"] = cpu_baselines(args.workload)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def step_workload_line(args, workload, dist, world, rank, full=True):
+    """One Newton iteration of the implicit-Euler step per bench step (newton_max = 1, 50 PCG
+    iterations) on a sinusoid-displaced shell: device-timed steps, and with full=True the end-to-
+    end (host buffers) leg, the SpMV roofline, the arithmetic rooflines and the element-only
+    rate."""
+    import torch
+    from paper_2312_14839_gb300 import bhem
+    g, mat, rest, q0 = make_workload(workload)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     rest_d = torch.as_tensor(rest.reshape(-1), device=dev)
@@ -911,60 +985,96 @@ def main():
     v0 = torch.zeros_like(q)
 
     def step():
+        # every step restarts from the same state; the regulariser level of the previous step is
+        # carried in (tau_carry), as a simulation carries it from step to step
         q.copy_(q0_d)
         v.copy_(v0)
-        return sh.newton_step(q, v, P)
+        st = sh.newton_step(q, v, P)
+        P.tau_carry = st["tau_final"]
+        return st
 
     stats = None
-    for _ in range(args.warmup):
-        stats = step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    launches0 = sh.kernel_launches()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the clock sampler starts before the warm-up, and its start-up (NVML) is over before the
+    # timed region opens
     with ClockSampler(torch.cuda.current_device()) as clk:
+        clk.wait_first()
+        for _ in range(args.warmup):
+            stats = step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        launches0 = sh.kernel_launches()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clk.mark()
         torch.cuda.synchronize()
         ev0.record(stream)
-        newton_iters = 0
+        newton_iters, spmvs = 0, 0
         for _ in range(args.steps):
             stats = step()
             newton_iters += stats["newton_iters"]
+            spmvs += stats["pcg_iters_total"]
         ev1.record(stream)
         torch.cuda.synchronize()
-    launches = sh.kernel_launches() - launches0
-    ms, total_iters = reduce_over_ranks(dist, ev0.elapsed_time(ev1), newton_iters, dev)
-    sec = ms / 1e3
-    value = g.n_patches * total_iters / sec
+        launches = sh.kernel_launches() - launches0
+        ms, total_iters = reduce_over_ranks(dist, ev0.elapsed_time(ev1), newton_iters, dev)
+        sec = ms / 1e3
+        value = g.n_patches * total_iters / sec
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded sinusoid displacement, no external data)",
+            "config": {"workload": WORKLOADS[workload], "patches": g.n_patches, "nodes": g.n_nodes,
+                       "dof": g.n_dof, "bsr_blocks": sh.n_blocks, "newton_iterations_per_step": 1,
+                       "pcg_iterations_per_solve": 50, "precision": "mixed",
+                       "l2": "inputs larger than L2 (FP32 BSR 340 MB)" if workload == "sheet256"
+                             else "working set smaller than L2 (not flushed)",
+                       "parallelism": f"replicas{world}" if world > 1 else "single GPU"},
+            "newton_steps_per_s": total_iters / sec,
+            "pcg_iterations_per_step": spmvs / args.steps,
+            "gpu_launches": launches,
+            "last_step_stats": stats,
+        }
+        if not full:
+            line["clocks"] = clk.summary()
+            sh.close()
+            return line
 
-    # e2e: the same Newton iteration through the C ABI with pinned host buffers (H2D of q, v and
-    # D2H of q, v inside the timed region). Every step starts from the same host state as the
-    # device-timed steps; the host-side reset of the pinned buffers is outside the timed calls.
-    qh = torch.empty(g.n_dof, dtype=torch.float64, pin_memory=True)
-    vh = torch.empty(g.n_dof, dtype=torch.float64, pin_memory=True)
-    qh_np, vh_np = qh.numpy(), vh.numpy()
-    q0_flat = np.ascontiguousarray(q0.reshape(-1))
+        # e2e: the same Newton iteration through the C ABI with pinned host buffers (H2D of q, v
+        # and D2H of q, v inside the timed region). Every step starts from the same host state as
+        # the device-timed steps; the host-side reset of the pinned buffers is outside the timed
+        # calls.
+        qh = torch.empty(g.n_dof, dtype=torch.float64, pin_memory=True)
+        vh = torch.empty(g.n_dof, dtype=torch.float64, pin_memory=True)
+        qh_np, vh_np = qh.numpy(), vh.numpy()
+        q0_flat = np.ascontiguousarray(q0.reshape(-1))
 
-    def e2e_step():
-        np.copyto(qh_np, q0_flat)
-        vh_np.fill(0.0)
-        t = time.perf_counter()
-        it = sh.newton_step(qh_np, vh_np, P)["newton_iters"]   # synchronous: returns host stats
-        return it, time.perf_counter() - t
+        def e2e_step():
+            np.copyto(qh_np, q0_flat)
+            vh_np.fill(0.0)
+            t = time.perf_counter()
+            st = sh.newton_step(qh_np, vh_np, P)   # synchronous: returns host stats
+            el = time.perf_counter() - t
+            P.tau_carry = st["tau_final"]
+            return st["newton_iters"], el
 
-    for _ in range(args.warmup):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_iters, e2e_sec = 0, 0.0
-    for _ in range(args.steps):
-        it, dt_ = e2e_step()
-        e2e_iters += it
-        e2e_sec += dt_
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_iters, e2e_sec = 0, 0.0
+        for _ in range(args.steps):
+            it, dt_ = e2e_step()
+            e2e_iters += it
+            e2e_sec += dt_
+        line["clocks"] = clk.summary()
     e2e_sec, e2e_iters = reduce_over_ranks(dist, e2e_sec, e2e_iters, dev)
-    e2e_value = g.n_patches * e2e_iters / e2e_sec
+    m = g.n_dof
+    line["e2e"] = {"value": g.n_patches * e2e_iters / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": 2 * m * 8,
+                   "d2h_bytes_per_step": 2 * m * 8}
 
-    # roofline of the dominant kernel (the FP32 BSR SpMV: 50 launches per step), timed live with
-    # CUDA events on the shell's stream over back-to-back launches on the assembled matrix
+    # roofline of the dominant kernel (the FP32 BSR SpMV, one launch per PCG iteration), timed
+    # live with CUDA events on the shell's stream over back-to-back launches on the assembled
+    # matrix
     sh.energy_grad_hess(q0_d, mass_scale=1.0 / P.dt ** 2, want_energy=False, want_grad=False)
     x = torch.randn(g.n_dof, dtype=torch.float32, device=dev)
     y = torch.empty(g.n_dof, dtype=torch.float32, device=dev)
@@ -980,52 +1090,48 @@ def main():
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     spmv_s = e0.elapsed_time(e1) / 1e3 / args.spmv_reps
-    nb, n, m = sh.n_blocks, sh.n_nodes, sh.n_dof
+    nb, n = sh.n_blocks, sh.n_nodes
     spmv_bytes = nb * 144 * 4 + nb * 4 + (n + 1) * 4 + m * 4 + m * 4
     peak, peak_kind = measured_peaks()
-    alu = alu_rooflines(sh, q0_d, P, g.n_patches, stream)
-    elem_only = element_kernel_only(sh, q0_d, g.n_patches, stream)
     achieved = spmv_bytes / spmv_s / 1e9
     traffic = recorded_traffic(os.path.join(ROOT, "paper_2312_14839_gb300", "csrc", "solver.cu"),
-                               "k_spmv32_tma" if args.spmv == "tma" else "k_spmv32", args.workload)
-
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-        "data": "synthetic (seeded sinusoid displacement, no external data)",
-        "config": {"workload": WORKLOADS[args.workload], "patches": g.n_patches, "nodes": g.n_nodes,
-                   "dof": g.n_dof, "bsr_blocks": nb, "newton_iterations_per_step": 1,
-                   "pcg_iteration_cap": 50, "precision": "mixed",
-                   "l2": "inputs larger than L2 (FP32 BSR 340 MB)",
-                   "parallelism": f"replicas{world}" if world > 1 else "single GPU"},
-        "newton_steps_per_s": total_iters / sec,
-        "pcg_iterations_last_step": stats["pcg_iters_total"] if stats else None,
-        "gpu_launches": launches,
-        "last_step_stats": stats,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * m * 8,
-                "d2h_bytes_per_step": 2 * m * 8},
-        "roofline": {"kernel": ("k_spmv32_tma (FP32 12x12 BSR SpMV of the PCG, bulk-copy pipelined)"
-                               if args.spmv == "tma" else "k_spmv32 (FP32 12x12 BSR SpMV of the PCG)"),
-                     "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
-                     "traffic": traffic, "algorithmic_bytes_per_launch": spmv_bytes,
-                     "avg_launch_us": spmv_s * 1e6},
-        "alu_rooflines": alu,
-        "element_kernel_only": elem_only,
-        "clocks": clk.summary(),
-    }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        line["cpu_baseline"] = cpu_baseline(args.workload)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+                               "k_spmv32_tma" if args.spmv == "tma" else "k_spmv32", workload)
+    line["roofline"] = {
+        "kernel": ("k_spmv32_tma (FP32 12x12 BSR SpMV of the PCG, bulk-copy pipelined)"
+                   if args.spmv == "tma" else "k_spmv32 (FP32 12x12 BSR SpMV of the PCG)"),
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
+        "traffic": traffic, "algorithmic_bytes_per_launch": spmv_bytes, "avg_launch_us": spmv_s * 1e6}
+    line["alu_rooflines"] = alu_rooflines(sh, q0_d, P, g.n_patches, stream)
+    line["element_kernel_only"] = element_kernel_only(sh, q0_d, g.n_patches, stream)
     sh.close()
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+    return line
+
+
+def extra_workloads(args):
+    """The other configurations of the metric, measured in the same run: the 280x5 annulus step,
+    the 512-sheet batch (batched against plain), the learned warm start (against the zero guess
+    and the inertial predictor) and the 200-step twist (exact and pseudo Hessian)."""
+    out = {}
+    t0 = time.perf_counter()
+    ann = step_workload_line(args, "annulus280x5", None, 1, 0, full=False)
+    out["annulus280x5"] = {k: ann[k] for k in ("value", "unit", "ms_per_step", "newton_steps_per_s",
+                                               "pcg_iterations_per_step", "gpu_launches", "clocks")}
+    out["annulus280x5"]["patches"] = ann["config"]["patches"]
+    b = batch_line(args, steps=min(args.steps, 5), warmup=2, plain_reps=1)
+    out["batch512"] = {k: b[k] for k in ("sheet_steps_per_s", "plain_sheet_steps_per_s", "batched_vs_plain",
+                                         "value", "plain_value", "unit", "newton_iters_per_sheet",
+                                         "all_sheets_converged_1e-8", "steps", "clocks")}
+    out["batch512"]["autotuned"] = b["config"]["autotuned"]
+    lr = learned_line(args)
+    out["learned64"] = {k: lr[k] for k in ("learned", "plain_zero_guess", "inertial_predictor",
+                                           "learned_vs_plain", "learned_vs_inertial", "train",
+                                           "data_generation", "clocks")}
+    tw = twist_line(args)
+    out["twist30"] = {k: tw[k] for k in ("exact_hessian", "pseudo_hessian", "pseudo_vs_exact_steps_per_s",
+                                         "clocks")}
+    out["seconds"] = time.perf_counter() - t0
+    return out
 
 
 if __name__ == "__main__":

@@ -101,7 +101,10 @@ typedef struct {
 
 /* One implicit-Euler step (Eq. implicit, Sec. 6.1). Newton stops when |g_free| <= newton_rtol *
    |g_free(zero guess)|; PCG stops when |r| <= pcg_rtol |b| or after pcg_max iterations, or
-   runs exactly pcg_fixed_iters iterations when that is > 0. */
+   runs exactly pcg_fixed_iters iterations when that is > 0. tau_carry (>= 0) is the regulariser
+   level carried into the step: its first Newton iteration starts at tau_carry / 10, as later
+   iterations start at a tenth of the previous one's (pass the previous step's
+   shell_step_stats.tau_final to carry it across steps, 0 for none). */
 typedef struct {
   double dt;
   double gravity[3];
@@ -110,6 +113,7 @@ typedef struct {
   double pcg_rtol;
   int pcg_max;
   int pcg_fixed_iters;
+  double tau_carry;
 } shell_step_params;
 
 typedef struct {
@@ -121,6 +125,7 @@ typedef struct {
   int diag_fixes;         /* free diagonal entries A_ii <= 0 replaced (regulariser, local)  */
   double res0;            /* |g_free| at the zero guess                                     */
   double res_final;       /* |g_free| at the returned state                                 */
+  double tau_final;       /* regulariser level of the last accepted solve (0: none)         */
 } shell_step_stats;
 
 typedef struct {
@@ -203,7 +208,7 @@ SHELL_API shell_status shell_spmv(shell_t* shell, const void* x, int x_is_fp32, 
    regulariser): A' replaces every free diagonal entry A_ii <= 0 of DOF kind k by
    max(-A_ii, 1e-8 D_k) (D_k = mean |A_ii| over the free DOFs of kind k; the assembled matrix
    read by shell_get_bsr afterwards holds A'); tau starts at a tenth of the previous iteration's
-   tau of the same step (0 at the first, and 0 when a tenth is below 1e-8); negative curvature
+   tau (at the first iteration, of params->tau_carry; 0 when a tenth is below 1e-8); negative curvature
    met by the solve multiplies tau by 10 (at least 1e-8) and restarts it; beyond tau = 1e4 the
    step returns SHELL_ERR_INDEFINITE. The line search is Armijo (c1 = 1e-4) from alpha = 1 with
    the quadratic, then cubic, interpolant's minimiser clamped to [0.1, 0.5] of the last trial.

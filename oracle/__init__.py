@@ -38,13 +38,14 @@ class Material(C.Structure):
 class StepParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("gravity", C.c_double * 3), ("newton_rtol", C.c_double),
                 ("newton_max", C.c_int), ("pcg_rtol", C.c_double), ("pcg_max", C.c_int),
-                ("pcg_fixed_iters", C.c_int), ("pseudo_hessian", C.c_int)]
+                ("pcg_fixed_iters", C.c_int), ("pseudo_hessian", C.c_int), ("tau_carry", C.c_double)]
 
 
 class StepStats(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("pcg_iters_total", C.c_int),
                 ("ls_backtracks", C.c_int), ("regularizations", C.c_int), ("status", C.c_int),
-                ("diag_fixes", C.c_int), ("res0", C.c_double), ("res_final", C.c_double)]
+                ("diag_fixes", C.c_int), ("res0", C.c_double), ("res_final", C.c_double),
+                ("tau_final", C.c_double)]
 
 
 # phi(alpha, ctx) callback of og_line_search
@@ -52,12 +53,17 @@ PHI_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, no target-specific flags) into oracle/_lib."""
+    """Compile the oracle with gcc (-O2, -fopenmp when available, no target-specific flags) into
+    oracle/_lib."""
     with _lock:
         if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f) for f in _SRCS):
             os.makedirs(_LIBDIR, exist_ok=True)
             tmp = _LIB + f".{os.getpid()}.tmp"
-            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, *_SRCS, "-lm"])
+            base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, *_SRCS, "-lm"]
+            try:   # OpenMP over the independent per-patch and per-row loops, when the compiler has it
+                subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+            except subprocess.CalledProcessError:
+                subprocess.check_call(base)
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -87,6 +93,8 @@ def _load():
         lib.og_pcg.argtypes = [i, p, p, p, p, d, p, p, d, i, i, p, p]
         lib.og_kind_scale.argtypes = [i, p, p, p, p, p]
         lib.og_newton_step.restype = i
+        lib.og_set_threads.restype = i
+        lib.og_set_threads.argtypes = [i]
         lib.og_fix_diagonal.restype = i
         lib.og_fix_diagonal.argtypes = [i, p, p, p, p, p]
         lib.og_newton_direction.restype = i
@@ -107,6 +115,11 @@ def _load():
         lib.og_ccd_points.argtypes = [p, p, p, i, p, p, i, p, p, p, p, p]
         _lib = lib
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Host threads of the oracle's independent loops (n <= 0 leaves the count); returns it."""
+    return int(_load().og_set_threads(int(n)))
 
 
 def _ptr(a):
@@ -318,9 +331,11 @@ def line_search(gd, phi):
 
 
 def step_params(dt=1e-3, gravity=(0.0, 0.0, -9.81), newton_rtol=1e-8, newton_max=50,
-                pcg_rtol=1e-6, pcg_max=1000, pcg_fixed_iters=0, pseudo_hessian=False) -> StepParams:
+                pcg_rtol=1e-6, pcg_max=1000, pcg_fixed_iters=0, pseudo_hessian=False,
+                tau_carry=0.0) -> StepParams:
     return StepParams(float(dt), (C.c_double * 3)(*gravity), float(newton_rtol), int(newton_max),
-                      float(pcg_rtol), int(pcg_max), int(pcg_fixed_iters), int(bool(pseudo_hessian)))
+                      float(pcg_rtol), int(pcg_max), int(pcg_fixed_iters), int(bool(pseudo_hessian)),
+                      float(tau_carry))
 
 
 def newton_step(g, mat, rest, q, v, params: StepParams, mask=None, qfix=None, warm=None):

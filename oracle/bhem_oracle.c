@@ -35,8 +35,9 @@
  *     kind's stiffness). Local part: every free diagonal entry A_ii <= 0 is replaced by
  *     max(-A_ii, 1e-8 D_k), its magnitude, so that the diagonal is positive without shifting the
  *     entries that already are. Global part: PCG solves (A + tau D) d = -g; tau starts at a tenth
- *     of the previous Newton iteration's accepted tau of the same step (0 at the first iteration,
- *     and 0 when a tenth is below 1e-8), each time PCG meets p^T A p <= 0 the solve restarts with
+ *     of the previous Newton iteration's accepted tau (at the first iteration, of the level the
+ *     caller carries in, 0 by default; 0 when a tenth is below 1e-8), each time PCG meets
+ *     p^T A p <= 0 the solve restarts with
  *     tau = max(10 tau, 1e-8), and beyond tau = 1e4 the step gives up. A 12x12 block that is not
  *     SPD is replaced by the inverse of its diagonal in the block-Jacobi preconditioner.
  */
@@ -44,6 +45,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------------------------------ */
 /* Types shared with the Python wrapper (plain structs of ints and doubles).                   */
@@ -56,15 +60,29 @@ typedef struct {
   double pcg_rtol;
   int pcg_max, pcg_fixed_iters;
   int pseudo_hessian;   /* 1: Newton matrix with the pseudo Hessian (App. B, "The pseudo Hessian") */
+  double tau_carry;     /* regulariser level carried in: the first iteration starts at a tenth */
 } og_step_params;
 typedef struct {
   int newton_iters, pcg_iters_total, ls_backtracks, regularizations, status;
   int diag_fixes;   /* free diagonal entries replaced by the local part of the regulariser */
   double res0, res_final;
+  double tau_final; /* tau of the last accepted solve */
 } og_step_stats;
 
 enum { OG_OK = 0, OG_ERR_ARG = 1, OG_ERR_NOT_CONVERGED = 6, OG_ERR_LINESEARCH = 7,
        OG_ERR_INDEFINITE = 8, OG_PCG_NEG_CURV = 100 };
+
+/* Host threads of the independent per-patch and per-row loops (OpenMP builds; 1 otherwise).
+   Results do not depend on the count: sums over patches and dot products stay serial. */
+int og_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------------------------ */
 /* Small vector helpers                                                                       */
@@ -410,6 +428,7 @@ void og_element_mass(const double qb[48], double d1, double d2, const og_materia
 /* Per-patch outputs over a patch range (for element-by-element comparison). */
 void og_elements(const og_grid* g, const og_material* mat, const double* rest, const double* q,
                  int p0, int p1, double* E, double* grad, double* hess, int pseudo) {
+#pragma omp parallel for schedule(dynamic, 1)
   for (int p = p0; p < p1; ++p) {
     double ql[48], qbl[48];
     gather48(g, q, p, ql);
@@ -469,29 +488,44 @@ void og_assemble(const og_grid* g, const og_material* mat, const double* rest, c
   if (energy) *energy = 0.0;
   if (grad) memset(grad, 0, (size_t)n * 12 * sizeof(double));
   if (val) memset(val, 0, (size_t)row_ptr[n] * 144 * sizeof(double));
-  double* H = val ? (double*)malloc(2304 * sizeof(double)) : NULL;
-  for (int p = 0; p < np; ++p) {
-    double ql[48], qbl[48], ge[48], E, m[256], f[16];
-    int nd[4];
-    og_patch_nodes(g, p, nd);
-    gather48(g, q, p, ql);
-    gather48(g, rest, p, qbl);
-    og_element_egh(ql, qbl, g->dxi1, g->dxi2, mat, energy ? &E : NULL, grad ? ge : NULL, H, pseudo);
-    if (energy) *energy += E;
-    if (grad) for (int c = 0; c < 4; ++c) for (int k = 0; k < 12; ++k) grad[nd[c]*12 + k] += ge[c*12 + k];
-    if (!val) continue;
-    if (mass_scale != 0.0) {
-      og_element_mass(qbl, g->dxi1, g->dxi2, mat, m, f);
-      for (int I = 0; I < 16; ++I) for (int J = 0; J < 16; ++J)
-        for (int c = 0; c < 3; ++c) H[(I*3 + c)*48 + J*3 + c] += mass_scale * m[I*16 + J];
+  /* The patches' element terms are independent: a chunk of them is evaluated (on all host cores
+     when built with OpenMP), then added in patch order, so the sums do not depend on the threads. */
+  enum { CHUNK = 64 };
+  double* Ec = (double*)malloc(CHUNK * sizeof(double));
+  double* Gc = (double*)malloc((size_t)CHUNK * 48 * sizeof(double));
+  double* Hc = val ? (double*)malloc((size_t)CHUNK * 2304 * sizeof(double)) : NULL;
+  for (int p0 = 0; p0 < np; p0 += CHUNK) {
+    int p1 = p0 + CHUNK < np ? p0 + CHUNK : np;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int p = p0; p < p1; ++p) {
+      double ql[48], qbl[48], m[256], f[16];
+      double* H = val ? &Hc[(size_t)(p - p0) * 2304] : NULL;
+      gather48(g, q, p, ql);
+      gather48(g, rest, p, qbl);
+      og_element_egh(ql, qbl, g->dxi1, g->dxi2, mat, energy ? &Ec[p - p0] : NULL,
+                     grad ? &Gc[(size_t)(p - p0) * 48] : NULL, H, pseudo);
+      if (val && mass_scale != 0.0) {
+        og_element_mass(qbl, g->dxi1, g->dxi2, mat, m, f);
+        for (int I = 0; I < 16; ++I) for (int J = 0; J < 16; ++J)
+          for (int c = 0; c < 3; ++c) H[(I*3 + c)*48 + J*3 + c] += mass_scale * m[I*16 + J];
+      }
     }
-    for (int a = 0; a < 4; ++a) for (int b = 0; b < 4; ++b) {
-      int k = find_block(row_ptr, col, nd[a], nd[b]);
-      for (int x = 0; x < 12; ++x) for (int y = 0; y < 12; ++y)
-        val[(size_t)k*144 + x*12 + y] += H[(a*12 + x)*48 + b*12 + y];
+    for (int p = p0; p < p1; ++p) {
+      int nd[4];
+      og_patch_nodes(g, p, nd);
+      const double* ge = &Gc[(size_t)(p - p0) * 48];
+      if (energy) *energy += Ec[p - p0];
+      if (grad) for (int c = 0; c < 4; ++c) for (int k = 0; k < 12; ++k) grad[nd[c]*12 + k] += ge[c*12 + k];
+      if (!val) continue;
+      const double* H = &Hc[(size_t)(p - p0) * 2304];
+      for (int a = 0; a < 4; ++a) for (int b = 0; b < 4; ++b) {
+        int k = find_block(row_ptr, col, nd[a], nd[b]);
+        for (int x = 0; x < 12; ++x) for (int y = 0; y < 12; ++y)
+          val[(size_t)k*144 + x*12 + y] += H[(a*12 + x)*48 + b*12 + y];
+      }
     }
   }
-  free(H);
+  free(Ec); free(Gc); free(Hc);
 }
 
 /* Nodal mass in the same pattern as 4x4 scalar blocks mval[nblocks*16] (M = mval (x) I3), and
@@ -521,6 +555,7 @@ void og_mass(const og_grid* g, const og_material* mat, const double* rest,
 /* y = M x with the 4x4-block scalar mass. */
 static void mass_mult(int n, const int* row_ptr, const int* col, const double* mval,
                       const double* x, double* y) {
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) {
     double acc[12] = {0};
     for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
@@ -540,6 +575,7 @@ static void mass_mult(int n, const int* row_ptr, const int* col, const double* m
 static void bsr_mult(int n, const int* row_ptr, const int* col, const double* val,
                      const unsigned char* mask, double tau, const double* dbar,
                      const double* x, double* y) {
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) {
     for (int r = 0; r < 12; ++r) {
       int gi = i*12 + r;
@@ -592,6 +628,7 @@ static int chol_inverse12(const double* A, double* Ainv) {
 /* Block-Jacobi inverses D[n*144] of the masked, regularised diagonal blocks. */
 static void block_jacobi(int n, const int* row_ptr, const int* col, const double* val,
                          const unsigned char* mask, double tau, const double* dbar, double* D) {
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) {
     int k = find_block(row_ptr, col, i, i);
     double A[144];
@@ -647,6 +684,7 @@ int og_pcg(int n, const int* row_ptr, const int* col, const double* val,
   int status = OG_OK, it = 0;
   int limit = fixed_iters > 0 ? fixed_iters : max_iter;
   if (bnorm == 0.0) goto done;
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) for (int a = 0; a < 12; ++a) {
     double s = 0.0;
     for (int c = 0; c < 12; ++c) s += D[(size_t)i*144 + a*12 + c] * r[i*12 + c];
@@ -664,6 +702,7 @@ int og_pcg(int n, const int* row_ptr, const int* col, const double* val,
     ++it;
     double rn = sqrt(vdot(m, r, r));
     if (fixed_iters <= 0 && rn <= rtol * bnorm) break;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) for (int a = 0; a < 12; ++a) {
       double s = 0.0;
       for (int c = 0; c < 12; ++c) s += D[(size_t)i*144 + a*12 + c] * r[i*12 + c];
@@ -820,6 +859,7 @@ static double full_gradient(const og_ctx* C, const double* q, const double* y, d
 /* Per-patch elastic energies. */
 static void patch_energies(const og_ctx* C, const double* q, double* Ep) {
   int np = C->g->nu * C->g->nv;
+#pragma omp parallel for schedule(static)
   for (int p = 0; p < np; ++p) {
     double ql[48], qbl[48];
     gather48(C->g, q, p, ql);
@@ -880,7 +920,7 @@ int og_newton_step(const og_grid* g, const og_material* mat, const double* rest,
   st->res0 = gref;
   if (warm) for (int i = 0; i < m; ++i) q[i] = (mask && mask[i]) ? qfix[i] : warm[i];
   int status = OG_OK;
-  double gn = 0.0, tau_carry = 0.0;
+  double gn = 0.0, tau_carry = P->tau_carry;
   for (int it = 0;; ++it) {
     gn = full_gradient(&C, q, y, gr, gin, work);
     if (gn <= P->newton_rtol * gref) break;
@@ -910,6 +950,7 @@ int og_newton_step(const og_grid* g, const og_material* mat, const double* rest,
     st->newton_iters++;
   }
   st->res_final = gn;
+  st->tau_final = tau_carry;
   for (int i = 0; i < m; ++i) v[i] = (q[i] - qn[i]) / P->dt;
   st->status = status;
   free(row_ptr); free(col); free(mval); free(fs); free(qn); free(y); free(gr); free(gin);

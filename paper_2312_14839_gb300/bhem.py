@@ -51,13 +51,14 @@ class shell_options(C.Structure):
 class shell_step_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("gravity", C.c_double * 3), ("newton_rtol", C.c_double),
                 ("newton_max", C.c_int), ("pcg_rtol", C.c_double), ("pcg_max", C.c_int),
-                ("pcg_fixed_iters", C.c_int)]
+                ("pcg_fixed_iters", C.c_int), ("tau_carry", C.c_double)]
 
 
 class shell_step_stats(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("pcg_iters_total", C.c_int),
                 ("ls_backtracks", C.c_int), ("regularizations", C.c_int), ("status", C.c_int),
-                ("diag_fixes", C.c_int), ("res0", C.c_double), ("res_final", C.c_double)]
+                ("diag_fixes", C.c_int), ("res0", C.c_double), ("res_final", C.c_double),
+                ("tau_final", C.c_double)]
 
 
 class shell_batch_info_t(C.Structure):
@@ -174,9 +175,10 @@ RAY_HIT, RAY_LIMIT, RAY_OVERFLOW, RAY_HEAP = 1, 2, 4, 256
 
 
 def step_params(dt=1e-3, gravity=(0.0, 0.0, -9.81), newton_rtol=1e-8, newton_max=50,
-                pcg_rtol=1e-6, pcg_max=1000, pcg_fixed_iters=0) -> shell_step_params:
+                pcg_rtol=1e-6, pcg_max=1000, pcg_fixed_iters=0, tau_carry=0.0) -> shell_step_params:
     return shell_step_params(float(dt), (C.c_double * 3)(*gravity), float(newton_rtol),
-                             int(newton_max), float(pcg_rtol), int(pcg_max), int(pcg_fixed_iters))
+                             int(newton_max), float(pcg_rtol), int(pcg_max), int(pcg_fixed_iters),
+                             float(tau_carry))
 
 
 def energy_grad_noalloc(grid, material, rest, q, energy, grad=None, stream=None):

@@ -673,8 +673,8 @@ __global__ void k_ctrl_reg_init(int S, ShellState* st, const int* __restrict__ d
   if (!T.active) return;
   T.pcg_done = 0;
   T.restart = 0;
-  // Sec. 6.1 regulariser: tau starts at a tenth of the previous Newton iteration's tau of this
-  // step (T.tau, 0 at the first; 0 when a tenth is below 1e-8)
+  // Sec. 6.1 regulariser: tau starts at a tenth of the previous Newton iteration's tau (T.tau;
+  // at the first, of the level carried into the step; 0 when a tenth is below 1e-8)
   double tau = T.tau / 10.0;
   if (tau < 1e-8) tau = 0.0;
   if (tau > 0.0) T.regularizations += 1;
@@ -884,11 +884,12 @@ __global__ void k_count_newton(int S, ShellState* st) {
   if (s < S && st[s].active) st[s].newton_iters += 1;
 }
 
-__global__ void k_begin_step(int S, ShellState* st) {
+__global__ void k_begin_step(int S, ShellState* st, double tau_carry) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   st[s] = ShellState{};
   st[s].active = 1;
+  st[s].tau = tau_carry;   // the regulariser level carried in (the first solve starts at a tenth)
 }
 
 __global__ void k_predict(int m, const double* __restrict__ q, const double* __restrict__ v, double dt,
@@ -1468,7 +1469,7 @@ extern "C" shell_status shell_batch_autotune(shell_batch_t* batch, const double*
   shell_batch_s& b = *batch;
   if (repeats < 1) repeats = 3;
   // every shell active for the trial assemblies
-  k_begin_step<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st);
+  k_begin_step<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, 0.0);
   BL(b);
   const int ppis[4] = {4, 8, 16, 32};
   const int schemes[2] = {SHELL_ASM_ATOMIC, SHELL_ASM_COLOR};
@@ -1509,7 +1510,8 @@ extern "C" shell_status shell_batch_newton_step(shell_batch_t* batch, const shel
   if (!batch || !params || !q || !v || !stats) return fail(SHELL_ERR_ARG, "NULL argument");
   if ((fixed_mask == nullptr) != (q_fixed == nullptr)) return fail(SHELL_ERR_ARG, "fixed_mask and q_fixed go together");
   const shell_step_params& P = *params;
-  if (!(P.dt > 0) || P.newton_max < 0 || P.pcg_max < 0 || P.pcg_fixed_iters < 0)
+  if (!(P.dt > 0) || P.newton_max < 0 || P.pcg_max < 0 || P.pcg_fixed_iters < 0 || !(P.tau_carry >= 0) ||
+      !std::isfinite(P.tau_carry))
     return fail(SHELL_ERR_ARG, "invalid step parameters");
   shell_batch_s& b = *batch;
   const size_t bytes = sizeof(double) * b.M;
@@ -1531,7 +1533,7 @@ extern "C" shell_status shell_batch_newton_step(shell_batch_t* batch, const shel
     BHEM_CUDA(cudaMemcpyAsync(b.warm, warm_start, bytes, cudaMemcpyDefault, b.stream));
     warm = b.warm;
   }
-  k_begin_step<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st);
+  k_begin_step<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, P.tau_carry);
   k_predict<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, dq, dv, P.dt, b.qn, b.y);
   k_fix<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, dq, b.qn, mask, qfix);
   b.launches += 3;
@@ -1568,6 +1570,7 @@ extern "C" shell_status shell_batch_newton_step(shell_batch_t* batch, const shel
     o.regularizations = T.regularizations;
     o.status = T.status;
     o.diag_fixes = T.diag_fixes;
+    o.tau_final = T.tau;
     o.res0 = T.gref;
     o.res_final = T.gn;
     if (T.status != SHELL_OK && worst == SHELL_OK) worst = (shell_status)T.status;

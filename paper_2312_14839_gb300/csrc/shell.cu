@@ -531,7 +531,7 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
   BHEM_CUDA(cudaMemcpyAsync(s.d_qn, q, sizeof(double) * m, cudaMemcpyDeviceToDevice, s.stream));
   BHEM_TRY(launch_predictor(s, s.d_qn, v_in, P.dt, s.d_y));
   if (mask) BHEM_TRY(launch_overwrite_fixed(s, q, s.d_qn, mask, qfix));
-  double gref = 0.0, gn = 0.0, tau_carry = 0.0;
+  double gref = 0.0, gn = 0.0, tau_carry = P.tau_carry;
   const double inv_dt2 = 1.0 / (P.dt * P.dt);
   BHEM_CUDA(cudaMemsetAsync(&s.d_ns->diag_fixes, 0, sizeof(int), s.stream));
   // The first iteration's Hessian at q does not depend on the residual: it is assembled on the
@@ -682,6 +682,7 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
                             s.stream));
   BHEM_CUDA(cudaStreamSynchronize(s.stream));
   st.diag_fixes = s.h_ns->diag_fixes;
+  st.tau_final = tau_carry;
   if (status == SHELL_OK || status == SHELL_ERR_NOT_CONVERGED) {
     BHEM_TRY(launch_velocity(s, q, s.d_qn, P.dt, v_out));
   } else {
@@ -701,7 +702,8 @@ extern "C" shell_status shell_newton_step(shell_t* shell, const shell_step_param
   if (!shell || !params || !q || !v || !stats) return fail(SHELL_ERR_ARG, "NULL argument");
   if ((fixed_mask == nullptr) != (q_fixed == nullptr)) return fail(SHELL_ERR_ARG, "fixed_mask and q_fixed go together");
   const shell_step_params& P = *params;
-  if (!(P.dt > 0) || P.newton_max < 0 || P.pcg_max < 0 || P.pcg_fixed_iters < 0 || !(P.newton_rtol >= 0))
+  if (!(P.dt > 0) || P.newton_max < 0 || P.pcg_max < 0 || P.pcg_fixed_iters < 0 || !(P.newton_rtol >= 0) ||
+      !(P.tau_carry >= 0) || !std::isfinite(P.tau_carry))
     return fail(SHELL_ERR_ARG, "invalid step parameters");
   Shell& s = *shell;
   std::memset(stats, 0, sizeof(*stats));

@@ -316,6 +316,16 @@ def test_newton_backtracking_and_regulariser_ladder_fp64_identical():
     for key in ("status", "newton_iters", "pcg_iters_total", "ls_backtracks", "regularizations", "diag_fixes"):
         assert st[key] == so[key], (key, st, so)
     assert rel(qg, qo) <= 1e-11
+    assert so["tau_final"] > 0 and st["tau_final"] == pytest.approx(so["tau_final"], rel=1e-12)
+    # the same step with a regulariser level carried in (the first solve starts at 0.1): the same
+    # decisions on both sides
+    tau = 1.0
+    st2, so2, qg2, qo2 = _fp64_step_against_oracle(g, THIN, rest, q0, step_params(dt=1e-3, newton_max=50, tau_carry=tau),
+                                                   O.step_params(dt=1e-3, newton_max=50, tau_carry=tau))
+    assert so2["status"] == 0
+    for key in ("status", "newton_iters", "pcg_iters_total", "ls_backtracks", "regularizations", "diag_fixes"):
+        assert st2[key] == so2[key], (key, st2, so2)
+    assert rel(qg2, qo2) <= 1e-11
 
 
 def test_newton_planar_twist_diagonal_fix_fp64_identical():
