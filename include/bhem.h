@@ -86,11 +86,14 @@ enum { SHELL_SOLVER_PCG = 0, SHELL_SOLVER_DIRECT = 1 };
    Batches ignore this field.
    solver: the linear solver of shell_newton_step. SHELL_SOLVER_PCG: block-Jacobi PCG (the
    default). SHELL_SOLVER_DIRECT: a comparator for the paper's direct LDL^T solve (Sec. 6.1): the
-   assembled matrix plus the regulariser, prescribed DOFs as identity rows, is expanded to a dense
-   FP64 matrix and factorised by Cholesky with cuSOLVER (potrf/potrs); a failed factorisation (not
-   positive definite) multiplies the regulariser by 10 as negative curvature does for PCG. Shells
-   of at most 65,536 DOF; the first direct step allocates 8 n_dof^2 bytes plus cuSOLVER's
-   workspace. The pcg_* fields of shell_step_params are ignored. Batches ignore this field. */
+   assembled matrix plus the regulariser, prescribed DOFs as identity rows, is factorised in FP64
+   by a banded Cholesky over the node rows of the grid (the matrix is block tridiagonal over the
+   rows of one grid direction, so the factor has no fill-in outside those bands), with hand-
+   written kernels; a pivot that is not positive multiplies the regulariser by 10 as negative
+   curvature does for PCG. The rows run along a direction that is not periodic (shells periodic in
+   both directions are rejected) and hold at most 4096 unknowns; the first direct step allocates
+   16 rows B^2 bytes (B unknowns per row) for the factor. The pcg_* fields of shell_step_params
+   are ignored. Batches ignore this field. */
 typedef struct {
   int precision;
   int hessian;
@@ -146,6 +149,15 @@ SHELL_API shell_status shell_destroy(shell_t* shell);
 
 /* Sizes of the shell (host output). */
 SHELL_API shell_status shell_info(const shell_t* shell, shell_info_t* info);
+
+/* Budget of the library's bounded device-side waits on this shell: the mbarrier waits of the
+   bulk-copy SpMV (SHELL_SPMV_TMA) poll at most `polls` times for a stage before the kernel gives
+   up; it then raises SHELL_ERR_TIMEOUT for the call (whose results are void), still waits, with
+   the default budget, for the copies it has issued, and returns, so that the device stays usable.
+   polls < 0 restores the default (2^20 polls); 0 makes every stage wait expire at once (a test
+   of the timeout path). Synchronises the shell's stream and drops its cached PCG graphs. No paper
+   counterpart (a watchdog of this implementation). */
+SHELL_API shell_status shell_set_wait_budget(shell_t* shell, int polls);
 
 /* Colour classes of the colour-ordered assembly (SHELL_ASM_COLOR, Sec. 4.3 "Properties of the
    mass matrix": two patches add into the same block iff they share a node). colour: host

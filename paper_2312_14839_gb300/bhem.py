@@ -91,6 +91,7 @@ def load():
                 "shell_destroy": [p],
                 "shell_info": [p, p],
                 "shell_grid_colours": [p, p],
+                "shell_set_wait_budget": [p, i],
                 "shell_element_egh": [p, p, i, p, p, p],
                 "shell_energy_grad_hess": [p, p, d, p, p, i],
                 "shell_get_bsr": [p, p, p, p, p],
@@ -291,6 +292,10 @@ class Shell:
         _check(load().shell_pcg_solve(self._h, _ptr(mask), float(tau), _ptr(rhs), _ptr(x), float(rtol),
                                       int(max_iter), int(fixed_iters), C.byref(it), C.byref(neg)))
         return x, it.value, neg.value
+
+    def set_wait_budget(self, polls: int):
+        """shell_set_wait_budget: polls of each bounded device-side wait (< 0: the default)."""
+        _check(load().shell_set_wait_budget(self._h, int(polls)))
 
     def kernel_launches(self) -> int:
         n = C.c_longlong()

@@ -45,6 +45,9 @@ inline int patch_colour(const shell_grid& g, int pu, int pv) {
 }
 constexpr int kColours = 9;
 
+// Polls of a bounded device-side wait (an mbarrier of the bulk-copy SpMV) before it gives up.
+constexpr int kDefaultWaitPolls = 1 << 20;
+
 // Device-side error bits (OR-ed into Shell::d_err, read back at synchronising calls).
 enum : int { ERRBIT_DEGENERATE = 1, ERRBIT_NONFINITE = 2, ERRBIT_TIMEOUT = 4 };
 
@@ -142,11 +145,8 @@ struct Shell {
   // overlap); d_ray_nets the ray search's Bezier nets [np][3][4][4] and boxes [np][8];
   // d_ccd_nets the collision search's start and displacement nets and swept boxes [np][104]
   void* d_search = nullptr;
-  // direct solver (direct.cu): cuSOLVER handle, dense matrix [n_dof^2] + 2 info ints, workspace
-  void* cusolver = nullptr;
+  // direct solver (direct.cu): the banded Cholesky factor (row blocks), solve vectors and a flag
   double* d_dense = nullptr;
-  double* d_dense_work = nullptr;
-  int dense_lwork = 0;
   double* d_ray_nets = nullptr;
   double* d_ccd_nets = nullptr;
 
@@ -164,6 +164,7 @@ struct Shell {
   int max_row = 0;
   int spmv_tma = 0, spmv_grid = 0, spmv_stage_floats = 0;
   size_t spmv_smem = 0;
+  int wait_polls = kDefaultWaitPolls;   // budget of each bounded device-side wait (shell_set_wait_budget)
 
   // CUDA graphs of the mixed-precision PCG loop, keyed by mask (iters = -1)
   struct PcgGraph { const unsigned char* mask; int iters; cudaGraphExec_t exec; };
@@ -246,6 +247,7 @@ shell_status launch_spmv(Shell& s, const void* x, int x_fp32, void* y);
 shell_status launch_pcg_result(Shell& s);
 shell_status launch_diag_check(Shell& s, const unsigned char* mask, double* out12, bool aux = false);
 shell_status launch_fix_diag(Shell& s, const unsigned char* mask, const double floor4[4], int* count);
+void drop_pcg_graphs(Shell& s);
 shell_status launch_axpy_fixed(Shell& s, double* q, const double* d, double alpha);
 shell_status launch_overwrite_fixed(Shell& s, double* dst, const double* src,
                                     const unsigned char* mask, const double* fixed_vals);

@@ -337,6 +337,14 @@ extern "C" shell_status shell_info(const shell_t* shell, shell_info_t* info) {
   return SHELL_OK;
 }
 
+extern "C" shell_status shell_set_wait_budget(shell_t* shell, int polls) {
+  if (!shell) return fail(SHELL_ERR_ARG, "NULL argument");
+  cudaStreamSynchronize(shell->stream);   // no launch in flight uses the graphs dropped below
+  shell->wait_polls = polls < 0 ? kDefaultWaitPolls : polls;
+  drop_pcg_graphs(*shell);   // captured launches hold the previous budget
+  return SHELL_OK;
+}
+
 extern "C" shell_status shell_grid_colours(const shell_grid* grid, int* colour) {
   if (!grid || !colour) return fail(SHELL_ERR_ARG, "NULL argument");
   if (grid->nu < 1 || grid->nv < 1) return fail(SHELL_ERR_ARG, "empty grid");

@@ -494,14 +494,14 @@ k_spmv32(int n, const int* __restrict__ rp, const int* __restrict__ col, const f
 // ------------------------------------------------------------------------------------------
 constexpr int kTmaRows = 8, kTmaThreads = kTmaRows * 36, kTmaStages = 4;
 constexpr unsigned kTmaChunk = 32768u;   // bytes per bulk copy instruction
-constexpr int kWaitPolls = 1 << 20;
+constexpr int kWaitPolls = kDefaultWaitPolls;
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  for (int i = 0; i < kWaitPolls; ++i) {
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, int polls = kWaitPolls) {
+  for (int i = 0; i < polls; ++i) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -517,7 +517,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
 __global__ void __launch_bounds__(kTmaThreads, 1)
 k_spmv32_tma(int n, const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ val,
              const float* __restrict__ x, Shift4f td, const unsigned char* __restrict__ mask,
-             float* __restrict__ y, PcgState* st, Reduce red, int stage_floats, int* err) {
+             float* __restrict__ y, PcgState* st, Reduce red, int stage_floats, int* err, int polls) {
   extern __shared__ __align__(128) float sval[];
   __shared__ __align__(8) unsigned long long bar[kTmaStages];
   __shared__ float sacc[kTmaThreads];
@@ -564,7 +564,7 @@ k_spmv32_tma(int n, const int* __restrict__ rp, const int* __restrict__ col, con
   bool timed_out = false;
   for (int g = g0; g < g1; ++g, ++it) {
     const int q = it % kTmaStages;
-    const bool ok = mbar_wait(smem_addr(&bar[q]), (unsigned)((it / kTmaStages) & 1));
+    const bool ok = mbar_wait(smem_addr(&bar[q]), (unsigned)((it / kTmaStages) & 1), polls);
     if (__syncthreads_or(!ok)) {
       timed_out = true;
       break;
@@ -611,7 +611,8 @@ k_spmv32_tma(int n, const int* __restrict__ rp, const int* __restrict__ col, con
   }
   if (timed_out) {
     // raise the error (the host voids the call's results) and drain the copies this CTA issued
-    // (local groups it .. it + stages - 1), bounded; the grid reduction below still completes
+    // (local groups it .. it + stages - 1) with the full default budget, whatever the stage
+    // waits were given; the grid reduction below still completes
     if (t == 0) {
       atomicOr(err, ERRBIT_TIMEOUT);
       for (int k = it; k < it + kTmaStages && g0 + k < g1; ++k)
@@ -1145,7 +1146,8 @@ static shell_status launch_spmv32(Shell& s, const float* x, Shift4f sh, const un
   const int n = s.n_nodes;
   if (s.spmv_tma) {
     k_spmv32_tma<<<s.spmv_grid, kTmaThreads, s.spmv_smem, s.stream>>>(
-        n, s.d_row_ptr, s.d_col, (const float*)s.d_val, x, sh, mask, y, st, s.red, s.spmv_stage_floats, s.d_err);
+        n, s.d_row_ptr, s.d_col, (const float*)s.d_val, x, sh, mask, y, st, s.red, s.spmv_stage_floats, s.d_err,
+        s.wait_polls);
   } else {
     const int blocks = grid_for(n, kSpmvThreads / 36);
     if (st && blocks > s.red.stride) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
@@ -1206,6 +1208,14 @@ __global__ void k_pcg_loop_cond(PcgState* st, cudaGraphConditionalHandle loop) {
 }
 
 int pcg_loop_unroll() { return kLoopUnroll; }
+
+void drop_pcg_graphs(Shell& s) {
+  for (auto& gph : s.pcg_graphs) {
+    if (gph.exec) cudaGraphExecDestroy(gph.exec);
+    gph = Shell::PcgGraph{};
+  }
+  s.pcg_graph_next = 0;
+}
 
 shell_status launch_pcg_loop_graph(Shell& s, const unsigned char* mask) {
   if (s.val_fp64) return fail(SHELL_ERR_ARG, "PCG graphs are for mixed precision");

@@ -196,6 +196,28 @@ def test_pcg_mixed_tma_matches_plain():
     assert rel(res[1][0], res[0][0]) <= 1e-5
 
 
+def test_tma_spmv_wait_timeout_is_reported_and_the_shell_recovers():
+    """The bulk-copy SpMV's stage waits are bounded. With a zero budget every stage wait expires:
+    the solve returns SHELL_ERR_TIMEOUT (the kernel still drains the copies it issued, with the
+    default budget, so nothing is left in flight), and after the default budget is restored the
+    same shell solves the system as before."""
+    from paper_2312_14839_gb300.bhem import ShellError
+    g, rest, q, mat = CASES["sheet10x10-noisy"]()
+    mask = dev(S.pinned_mask(g, [0, g.n_nodes - 1]), torch.uint8)
+    sh = make_shell(g, mat, rest, precision="mixed", spmv="tma")
+    _, G = sh.energy_grad_hess(dev(q.reshape(-1)), mass_scale=1e6)
+    x0, it0, neg0 = sh.pcg_solve(-G, mask=mask, rtol=1e-6, max_iter=1000)
+    sh.set_wait_budget(0)
+    with pytest.raises(ShellError) as ei:
+        sh.pcg_solve(-G, mask=mask, rtol=1e-6, max_iter=20)
+    assert ei.value.status == 9   # SHELL_ERR_TIMEOUT
+    sh.set_wait_budget(-1)
+    x1, it1, neg1 = sh.pcg_solve(-G, mask=mask, rtol=1e-6, max_iter=1000)
+    assert it1 == it0 and neg1 == neg0 == 0
+    assert np.array_equal(host(x1), host(x0))
+    sh.close()
+
+
 def test_pcg_parity_fp64():
     g, rest, q, mat = CASES["sheet10x10-noisy"]()
     dt = 1e-3
