@@ -14,6 +14,7 @@
 // or colour-ordered) are chosen by shell_batch_autotune.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -47,6 +48,18 @@ struct ShellState {
 };
 
 struct Counters { int n_active, n_running, n_restart, n_searching; };
+
+// Device-side loop state of the captured Newton step (one CUDA graph per step: WHILE nodes for
+// the Newton iterations, the regulariser rounds, the PCG chunks and the line-search trials, each
+// condition set by a one-thread kernel from the counters), and the body executions of each loop
+// for the launch count.
+struct LoopState {
+  int newton_it, round, pcg_iters, trial;
+  long long n_newton, n_reg, n_pcg, n_ls;
+};
+// Per-step input written by the host before each step (a graph replays with new values)
+struct StepInput { double tau_carry; };
+constexpr int kGraphPcgChunk = 4;   // PCG iterations per body of the PCG WHILE node
 
 constexpr int kRowNodes = 8;          // block rows per SpMV CTA (36 threads each)
 constexpr int kSpmvThreads = 288;
@@ -672,7 +685,7 @@ __global__ void k_ctrl_reg_init(int S, ShellState* st, const int* __restrict__ d
   }
   if (!T.active) return;
   T.pcg_done = 0;
-  T.restart = 0;
+  T.restart = 1;   // the solve (re)starts: the PCG set-up kernels take the shells with this flag
   // Sec. 6.1 regulariser: tau starts at a tenth of the previous Newton iteration's tau (T.tau;
   // at the first, of the level carried into the step; 0 when a tenth is below 1e-8)
   double tau = T.tau / 10.0;
@@ -812,6 +825,52 @@ __global__ void k_ctrl_ls_step(int S, ShellState* st, Counters* cnt) {
 }
 
 // ------------------------------------------------------------------------------------------
+// Conditions of the captured step's WHILE nodes (one thread). Each mirrors a loop bound of the
+// host-driven step: Newton while a shell is active and it <= newton_max; regulariser rounds while
+// a shell restarts, at most 16; PCG chunks while a shell runs and the iterations are below the
+// limit; line-search trials while a shell searches, at most 20.
+// ------------------------------------------------------------------------------------------
+__global__ void k_cond_newton(const Counters* cnt, LoopState* L, int newton_max, cudaGraphConditionalHandle h,
+                              int first) {
+  if (first) *L = LoopState{};
+  const bool go = cnt->n_active > 0 && L->newton_it <= newton_max;
+  if (go) {
+    L->newton_it += 1;
+    L->n_newton += 1;
+  }
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void k_cond_reg(const Counters* cnt, LoopState* L, cudaGraphConditionalHandle h, int first) {
+  bool go;
+  if (first) {
+    L->round = 0;
+    go = true;
+  } else {
+    L->round += 1;
+    go = cnt->n_restart > 0 && L->round < 16;
+  }
+  if (go) L->n_reg += 1;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void k_cond_pcg(const Counters* cnt, LoopState* L, int limit, cudaGraphConditionalHandle h, int first) {
+  if (first) L->pcg_iters = 0;
+  else L->pcg_iters += kGraphPcgChunk;
+  const bool go = cnt->n_running > 0 && L->pcg_iters < limit;
+  if (go) L->n_pcg += 1;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void k_cond_ls(const Counters* cnt, LoopState* L, cudaGraphConditionalHandle h, int first) {
+  if (first) L->trial = 0;
+  else L->trial += 1;
+  const bool go = cnt->n_searching > 0 && L->trial < 20;
+  if (go) L->n_ls += 1;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// ------------------------------------------------------------------------------------------
 // Vector kernels over all DOFs (with per-shell coefficients)
 // ------------------------------------------------------------------------------------------
 __global__ void k_dots3(int n, const int* __restrict__ nshell, ShellState* st,
@@ -884,12 +943,12 @@ __global__ void k_count_newton(int S, ShellState* st) {
   if (s < S && st[s].active) st[s].newton_iters += 1;
 }
 
-__global__ void k_begin_step(int S, ShellState* st, double tau_carry) {
+__global__ void k_begin_step(int S, ShellState* st, const StepInput* in) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   st[s] = ShellState{};
   st[s].active = 1;
-  st[s].tau = tau_carry;   // the regulariser level carried in (the first solve starts at a tenth)
+  st[s].tau = in ? in->tau_carry : 0.0;   // the regulariser level carried in (the first solve starts at a tenth)
 }
 
 __global__ void k_predict(int m, const double* __restrict__ q, const double* __restrict__ v, double dt,
@@ -959,6 +1018,15 @@ struct shell_batch_s {
   cudaGraphExec_t pcg_graph = nullptr;
   int pcg_graph_iters = 0;
   const unsigned char* pcg_graph_mask = nullptr;
+  // the captured whole-step graph, its key, capture streams and loop state
+  cudaGraphExec_t step_graph = nullptr;
+  std::vector<unsigned char> step_key;
+  cudaStream_t cap[4] = {nullptr, nullptr, nullptr, nullptr};
+  LoopState* loop = nullptr;
+  LoopState* h_loop = nullptr;
+  StepInput* input = nullptr;      // device copy of the step's inputs (regulariser level)
+  StepInput* h_input = nullptr;    // pinned
+  long long k_fixed = 0, k_newton = 0, k_reg = 0, k_pcg = 0, k_ls = 0;   // kernels per body
 };
 
 namespace {
@@ -980,13 +1048,18 @@ void bfree_all(shell_batch_s* b) {
                   b->plist_color, b->dmin_bits, b->pnodes, b->items, b->eg_items, b->color_items, b->dxi,
                   b->t64, b->rest, b->restgp, b->mass, b->fgrav, b->t32, b->val, b->Dinv, b->x32, b->r32,
                   b->z32, b->p32, b->Ap32, b->qn, b->y, b->g, b->gin, b->d, b->Md, b->rhs, b->Ep,
-                  b->qwork, b->vwork, b->qfix, b->warm, b->mask, b->err};
+                  b->qwork, b->vwork, b->qfix, b->warm, b->mask, b->err, b->loop, b->input};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->h_cnt) cudaFreeHost(b->h_cnt);
   if (b->h_st) cudaFreeHost(b->h_st);
   if (b->h_err) cudaFreeHost(b->h_err);
   if (b->pcg_graph) cudaGraphExecDestroy(b->pcg_graph);
+  if (b->step_graph) cudaGraphExecDestroy(b->step_graph);
+  if (b->h_loop) cudaFreeHost(b->h_loop);
+  if (b->h_input) cudaFreeHost(b->h_input);
+  for (cudaStream_t c : b->cap)
+    if (c) cudaStreamDestroy(c);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -1026,14 +1099,20 @@ shell_status zero_counters(shell_batch_s& b) {
 
 size_t elem_smem() { return sizeof(float) * elem_table_elems<float>() + sizeof(WarpSmem<float>) * ElemCfg<float>::kWarps; }
 
+// The element kernel's dynamic shared memory limit, set once per device (outside any capture)
+shell_status element_attr(int device) {
+  static bool done[128] = {false};
+  if (!done[device & 127]) {
+    BHEM_CUDA(cudaFuncSetAttribute(k_element, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)elem_smem()));
+    done[device & 127] = true;
+  }
+  return SHELL_OK;
+}
+
 // FP32 element Hessians of active shells assembled into the BSR (+ mass_scale M)
 shell_status assemble(shell_batch_s& b, const double* q, double mass_scale) {
   BHEM_CUDA(cudaMemsetAsync(b.val, 0, sizeof(float) * 144 * (size_t)b.NB, b.stream));
-  static bool attr[128] = {false};
-  if (!attr[b.device & 127]) {
-    BHEM_CUDA(cudaFuncSetAttribute(k_element, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)elem_smem()));
-    attr[b.device & 127] = true;
-  }
+  BHEM_TRY(element_attr(b.device));
   int nsm = 0;
   BHEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b.device));
   ElemBatchArgs A{};
@@ -1243,6 +1322,235 @@ shell_status line_search(shell_batch_s& b, const shell_step_params& P, const dou
     BHEM_CUDA(cudaGetLastError());
     BHEM_TRY(read_counters(b));
   }
+  return SHELL_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// The whole implicit-Euler step as one CUDA graph: the same kernels as the host-driven step, in
+// the same order, with the host's loop decisions moved into WHILE conditional nodes whose
+// conditions one-thread kernels set from the device counters. One graph launch per step, no
+// host round trip between the phases.
+// ------------------------------------------------------------------------------------------
+// Creates a condition handle on the graph being captured on s.
+shell_status cap_handle(cudaStream_t s, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  BHEM_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+  if (cs != cudaStreamCaptureStatusActive || !g) return fail(SHELL_ERR_CUDA, "step graph: no active capture");
+  BHEM_CUDA(cudaGraphConditionalHandleCreate(h, g, 0, 0));
+  return SHELL_OK;
+}
+
+// Appends a WHILE node with handle h at the capture point of s; later captured work depends on
+// it. *body receives the node's body graph.
+shell_status cap_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  BHEM_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+  std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  BHEM_CUDA(cudaGraphAddNode(&node, g, dv.empty() ? nullptr : dv.data(), nullptr, dv.size(), &np));
+  BHEM_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  *body = np.conditional.phGraph_out[0];
+  return SHELL_OK;
+}
+
+// Runs fn with b.stream set to capture stream `level` capturing into graph `body`.
+template <typename F>
+shell_status cap_body(shell_batch_s& b, int level, cudaGraph_t body, F fn) {
+  cudaStream_t keep = b.stream;
+  cudaStream_t s = b.cap[level];
+  BHEM_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  b.stream = s;
+  shell_status st = fn();
+  b.stream = keep;
+  cudaGraph_t out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &out);
+  if (st != SHELL_OK) return st;
+  if (e != cudaSuccess) return fail(SHELL_ERR_CUDA, std::string("step graph capture: ") + cudaGetErrorString(e));
+  return SHELL_OK;
+}
+
+// FP64 residual without the host's error check and counter read (those follow the graph)
+shell_status enqueue_residual(shell_batch_s& b, const double* q, const shell_step_params& P,
+                              const unsigned char* mask, int set_ref, int nsm) {
+  BHEM_CUDA(cudaMemsetAsync(b.g, 0, sizeof(double) * b.M, b.stream));
+  k_eg64<<<std::min(b.n_eg_items, nsm * 16), 128, 0, b.stream>>>(b.n_eg_items, b.eg_items, b.P, b.par, b.st,
+      b.dxi, b.pnodes, q, nullptr, b.restgp, b.Ep, b.g, 0, b.err);
+  k_grad_finish<<<blocks_for(b.N, 16), kNodeThreads, 0, b.stream>>>(b.N, b.nshell, b.st, b.row_ptr, b.col,
+      b.mass, b.fgrav, q, b.y, 1.0 / (P.dt * P.dt), P.gravity[0], P.gravity[1], P.gravity[2], mask, b.g,
+      b.gin, b.err);
+  BHEM_TRY(zero_counters(b));
+  k_ctrl_newton<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, b.cnt, P.newton_rtol, P.newton_max, set_ref);
+  b.launches += 3;
+  BHEM_CUDA(cudaGetLastError());
+  return SHELL_OK;
+}
+
+// One Newton iteration's body: assembly, regularised PCG direction, line search, update and the
+// residual at the new iterate (then the Newton condition).
+shell_status enqueue_newton_body(shell_batch_s& b, const shell_step_params& P, const unsigned char* mask,
+                                 double* dq, int nsm, cudaGraphConditionalHandle h_newton) {
+  const long long l0 = b.launches;
+  BHEM_TRY(assemble(b, dq, 1.0 / (P.dt * P.dt)));
+  k_dir<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, b.nshell, b.st, b.x32, b.g, b.d, b.rhs, 0);
+  BHEM_CUDA(cudaMemsetAsync(b.dmin_bits, 0x7f, sizeof(int) * 4 * (size_t)b.S, b.stream));
+  k_diag_stats<<<blocks_for(b.N, 16), kNodeThreads, 0, b.stream>>>(b.N, b.nshell, b.st, b.diag, b.val, mask,
+                                                                     b.dmin_bits);
+  k_ctrl_reg_init<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, b.dmin_bits);
+  k_fix_diag<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, b.nshell, b.st, b.diag, b.val, mask);
+  b.launches += 4;
+  cudaGraphConditionalHandle h_reg;
+  BHEM_TRY(cap_handle(b.stream, &h_reg));
+  k_cond_reg<<<1, 1, 0, b.stream>>>(b.cnt, b.loop, h_reg, 1);
+  BL(b);
+  cudaGraph_t reg_body = nullptr;
+  BHEM_TRY(cap_while(b.stream, h_reg, &reg_body));
+  const int limit = P.pcg_fixed_iters > 0 ? P.pcg_fixed_iters : P.pcg_max;
+  BHEM_TRY(cap_body(b, 2, reg_body, [&]() -> shell_status {
+    const long long r0 = b.launches;
+    k_precond<<<blocks_for(b.N, 16), 192, 0, b.stream>>>(b.N, b.nshell, b.st, b.diag, b.val, mask, b.Dinv, 1);
+    k_pcg_init<<<blocks_for(b.N, 16), kNodeThreads, 0, b.stream>>>(b.N, b.nshell, b.st, b.rhs, b.Dinv, mask,
+                                                                    b.x32, b.r32, b.z32, b.p32, 1);
+    BHEM_TRY(zero_counters(b));
+    k_ctrl_pcg_start<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, b.cnt, 1, P.pcg_rtol, P.pcg_max,
+                                                                 P.pcg_fixed_iters);
+    b.launches += 3;
+    cudaGraphConditionalHandle h_pcg;
+    BHEM_TRY(cap_handle(b.stream, &h_pcg));
+    k_cond_pcg<<<1, 1, 0, b.stream>>>(b.cnt, b.loop, limit, h_pcg, 1);
+    BL(b);
+    cudaGraph_t pcg_body = nullptr;
+    BHEM_TRY(cap_while(b.stream, h_pcg, &pcg_body));
+    BHEM_TRY(cap_body(b, 3, pcg_body, [&]() -> shell_status {
+      const long long p0 = b.launches;
+      BHEM_TRY(pcg_chunk(b, mask, kGraphPcgChunk));
+      b.launches += 5LL * kGraphPcgChunk;
+      BHEM_TRY(zero_counters(b));
+      k_ctrl_count_running<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, b.cnt);
+      k_cond_pcg<<<1, 1, 0, b.stream>>>(b.cnt, b.loop, limit, h_pcg, 0);
+      b.launches += 2;
+      BHEM_CUDA(cudaGetLastError());
+      b.k_pcg = b.launches - p0;
+      return SHELL_OK;
+    }));
+    BHEM_TRY(zero_counters(b));
+    k_ctrl_restart<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, b.cnt);
+    k_cond_reg<<<1, 1, 0, b.stream>>>(b.cnt, b.loop, h_reg, 0);
+    b.launches += 2;
+    BHEM_CUDA(cudaGetLastError());
+    b.k_reg = (b.launches - r0) - b.k_pcg;
+    return SHELL_OK;
+  }));
+  k_dir<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, b.nshell, b.st, b.x32, b.g, b.d, b.rhs, 1);
+  // line search
+  k_mass_mult<<<blocks_for(b.N, 16), kNodeThreads, 0, b.stream>>>(b.N, b.row_ptr, b.col, b.mass, b.d, b.Md);
+  k_dots3<<<blocks_for(b.N, 16), kNodeThreads, 0, b.stream>>>(b.N, b.nshell, b.st, b.d, b.Md, b.gin, b.g);
+  BHEM_TRY(zero_counters(b));
+  k_ctrl_ls_start<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, b.cnt, 1.0 / (P.dt * P.dt));
+  b.launches += 4;
+  cudaGraphConditionalHandle h_ls;
+  BHEM_TRY(cap_handle(b.stream, &h_ls));
+  k_cond_ls<<<1, 1, 0, b.stream>>>(b.cnt, b.loop, h_ls, 1);
+  BL(b);
+  cudaGraph_t ls_body = nullptr;
+  BHEM_TRY(cap_while(b.stream, h_ls, &ls_body));
+  BHEM_TRY(cap_body(b, 2, ls_body, [&]() -> shell_status {
+    const long long s0 = b.launches;
+    k_eg64<<<std::min(b.n_eg_items, nsm * 16), 128, 0, b.stream>>>(b.n_eg_items, b.eg_items, b.P, b.par, b.st,
+        b.dxi, b.pnodes, dq, b.d, b.restgp, b.Ep, nullptr, 1, b.err);
+    BHEM_TRY(zero_counters(b));
+    k_ctrl_ls_step<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, b.cnt);
+    k_cond_ls<<<1, 1, 0, b.stream>>>(b.cnt, b.loop, h_ls, 0);
+    b.launches += 3;
+    BHEM_CUDA(cudaGetLastError());
+    b.k_ls = b.launches - s0;
+    return SHELL_OK;
+  }));
+  k_update<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, b.nshell, b.st, dq, b.d);
+  k_count_newton<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st);
+  b.launches += 2;
+  BHEM_TRY(enqueue_residual(b, dq, P, mask, 0, nsm));
+  k_cond_newton<<<1, 1, 0, b.stream>>>(b.cnt, b.loop, P.newton_max, h_newton, 0);
+  BL(b);
+  BHEM_CUDA(cudaGetLastError());
+  b.k_newton = (b.launches - l0) - b.k_reg - b.k_pcg - b.k_ls;
+  return SHELL_OK;
+}
+
+// Captures (or reuses) the graph of one whole step for these pointers and parameters.
+shell_status step_graph(shell_batch_s& b, const shell_step_params& P, const unsigned char* mask,
+                        const double* qfix, const double* warm, double* dq, double* dv) {
+  // the key: every value the captured kernels take by value (the regulariser level carried into
+  // the step is read from device memory instead, so it needs no new capture)
+  const double fp[7] = {P.dt, P.gravity[0], P.gravity[1], P.gravity[2], P.newton_rtol, P.pcg_rtol, 0.0};
+  const int ip[5] = {P.newton_max, P.pcg_max, P.pcg_fixed_iters, b.ppi, b.assembly};
+  const void* ptrs[6] = {mask, qfix, warm, dq, dv, b.items};
+  std::vector<unsigned char> key(sizeof(fp) + sizeof(ip) + sizeof(ptrs));
+  std::memcpy(key.data(), fp, sizeof(fp));
+  std::memcpy(key.data() + sizeof(fp), ip, sizeof(ip));
+  std::memcpy(key.data() + sizeof(fp) + sizeof(ip), ptrs, sizeof(ptrs));
+  if (b.step_graph && key == b.step_key) return SHELL_OK;
+  if (b.step_graph) cudaGraphExecDestroy(b.step_graph);
+  b.step_graph = nullptr;
+  for (int l = 0; l < 4; ++l)
+    if (!b.cap[l]) BHEM_CUDA(cudaStreamCreateWithFlags(&b.cap[l], cudaStreamNonBlocking));
+  if (!b.loop) {
+    BHEM_TRY(balloc(&b.loop, 1));
+    BHEM_CUDA(cudaMallocHost((void**)&b.h_loop, sizeof(LoopState)));
+  }
+  BHEM_TRY(element_attr(b.device));
+  int nsm = 0;
+  BHEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b.device));
+  cudaGraph_t graph = nullptr;
+  BHEM_CUDA(cudaGraphCreate(&graph, 0));
+  const long long keep_launches = b.launches;
+  shell_status st = cap_body(b, 0, graph, [&]() -> shell_status {
+    const long long f0 = b.launches;
+    k_begin_step<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, b.input);
+    k_predict<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, dq, dv, P.dt, b.qn, b.y);
+    k_fix<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, dq, b.qn, mask, qfix);
+    b.launches += 3;
+    BHEM_TRY(enqueue_residual(b, dq, P, mask, 1, nsm));
+    if (warm) {
+      k_fix<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, dq, warm, mask, qfix);
+      BL(b);
+      BHEM_TRY(enqueue_residual(b, dq, P, mask, 0, nsm));
+    }
+    cudaGraphConditionalHandle h_newton;
+    BHEM_TRY(cap_handle(b.stream, &h_newton));
+    k_cond_newton<<<1, 1, 0, b.stream>>>(b.cnt, b.loop, P.newton_max, h_newton, 1);
+    BL(b);
+    const long long f1 = b.launches;
+    cudaGraph_t newton_body = nullptr;
+    BHEM_TRY(cap_while(b.stream, h_newton, &newton_body));
+    BHEM_TRY(cap_body(b, 1, newton_body, [&]() { return enqueue_newton_body(b, P, mask, dq, nsm, h_newton); }));
+    const long long f2 = b.launches;
+    k_velocity<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, b.nshell, b.st, dq, b.qn, 1.0 / P.dt, dv);
+    BL(b);
+    BHEM_CUDA(cudaGetLastError());
+    b.k_fixed = (f1 - f0) + (b.launches - f2);
+    return SHELL_OK;
+  });
+  b.launches = keep_launches;
+  if (st != SHELL_OK) {
+    cudaGraphDestroy(graph);
+    return st;
+  }
+  const cudaError_t e = cudaGraphInstantiate(&b.step_graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    b.step_graph = nullptr;
+    return fail(SHELL_ERR_CUDA, std::string("step graph instantiate: ") + cudaGetErrorString(e));
+  }
+  b.step_key = key;
   return SHELL_OK;
 }
 
@@ -1469,7 +1777,7 @@ extern "C" shell_status shell_batch_autotune(shell_batch_t* batch, const double*
   shell_batch_s& b = *batch;
   if (repeats < 1) repeats = 3;
   // every shell active for the trial assemblies
-  k_begin_step<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, 0.0);
+  k_begin_step<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, nullptr);
   BL(b);
   const int ppis[4] = {4, 8, 16, 32};
   const int schemes[2] = {SHELL_ASM_ATOMIC, SHELL_ASM_COLOR};
@@ -1533,29 +1841,48 @@ extern "C" shell_status shell_batch_newton_step(shell_batch_t* batch, const shel
     BHEM_CUDA(cudaMemcpyAsync(b.warm, warm_start, bytes, cudaMemcpyDefault, b.stream));
     warm = b.warm;
   }
-  k_begin_step<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, P.tau_carry);
-  k_predict<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, dq, dv, P.dt, b.qn, b.y);
-  k_fix<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, dq, b.qn, mask, qfix);
-  b.launches += 3;
-  BHEM_CUDA(cudaGetLastError());
-  BHEM_TRY(residual(b, dq, P, mask, 1));
-  if (warm) {
-    k_fix<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, dq, warm, mask, qfix);
-    BL(b);
-    BHEM_TRY(residual(b, dq, P, mask, 0));
+  const bool host_loop = std::getenv("BHEM_BATCH_HOST_LOOP") != nullptr;
+  if (!b.input) {
+    BHEM_TRY(balloc(&b.input, 1));
+    BHEM_CUDA(cudaMallocHost((void**)&b.h_input, sizeof(StepInput)));
   }
-  for (int it = 0; it <= P.newton_max && b.h_cnt->n_active > 0; ++it) {
-    BHEM_TRY(assemble(b, dq, 1.0 / (P.dt * P.dt)));
-    BHEM_TRY(solve_directions(b, P, mask));
-    BHEM_TRY(line_search(b, P, dq));
-    k_update<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, b.nshell, b.st, dq, b.d);
-    k_count_newton<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st);
-    b.launches += 2;
+  b.h_input->tau_carry = P.tau_carry;   // the previous step has synchronised: the buffer is free
+  BHEM_CUDA(cudaMemcpyAsync(b.input, b.h_input, sizeof(StepInput), cudaMemcpyHostToDevice, b.stream));
+  if (!host_loop) {
+    // the whole step is one graph launch; its device-side loops replace the host's decisions
+    BHEM_TRY(step_graph(b, P, mask, qfix, warm, dq, dv));
+    BHEM_CUDA(cudaGraphLaunch(b.step_graph, b.stream));
+    BHEM_CUDA(cudaMemcpyAsync(b.h_loop, b.loop, sizeof(LoopState), cudaMemcpyDeviceToHost, b.stream));
+    BHEM_TRY(check_err(b));   // synchronises the stream
+    const LoopState& L = *b.h_loop;
+    b.launches += b.k_fixed + L.n_newton * b.k_newton + L.n_reg * b.k_reg + L.n_pcg * b.k_pcg + L.n_ls * b.k_ls;
+  } else {
+    // host-driven step (BHEM_BATCH_HOST_LOOP set): the same kernels, each loop decided on the
+    // host from the counters; profilers list every kernel of this form
+    k_begin_step<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, b.input);
+    k_predict<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, dq, dv, P.dt, b.qn, b.y);
+    k_fix<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, dq, b.qn, mask, qfix);
+    b.launches += 3;
     BHEM_CUDA(cudaGetLastError());
-    BHEM_TRY(residual(b, dq, P, mask, 0));
+    BHEM_TRY(residual(b, dq, P, mask, 1));
+    if (warm) {
+      k_fix<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, dq, warm, mask, qfix);
+      BL(b);
+      BHEM_TRY(residual(b, dq, P, mask, 0));
+    }
+    for (int it = 0; it <= P.newton_max && b.h_cnt->n_active > 0; ++it) {
+      BHEM_TRY(assemble(b, dq, 1.0 / (P.dt * P.dt)));
+      BHEM_TRY(solve_directions(b, P, mask));
+      BHEM_TRY(line_search(b, P, dq));
+      k_update<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, b.nshell, b.st, dq, b.d);
+      k_count_newton<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st);
+      b.launches += 2;
+      BHEM_CUDA(cudaGetLastError());
+      BHEM_TRY(residual(b, dq, P, mask, 0));
+    }
+    k_velocity<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, b.nshell, b.st, dq, b.qn, 1.0 / P.dt, dv);
+    BL(b);
   }
-  k_velocity<<<vblocks(b.M), 256, 0, b.stream>>>(b.M, b.nshell, b.st, dq, b.qn, 1.0 / P.dt, dv);
-  BL(b);
   if (!q_dev) BHEM_CUDA(cudaMemcpyAsync(q, dq, bytes, cudaMemcpyDeviceToHost, b.stream));
   if (!v_dev) BHEM_CUDA(cudaMemcpyAsync(v, dv, bytes, cudaMemcpyDeviceToHost, b.stream));
   BHEM_CUDA(cudaMemcpyAsync(b.h_st, b.st, sizeof(ShellState) * b.S, cudaMemcpyDeviceToHost, b.stream));

@@ -98,3 +98,47 @@ def test_autotune_keeps_results():
     for s in range(len(shells)):
         assert abs(base[0][0][s]["newton_iters"] - tuned[0][0][s]["newton_iters"]) <= 1
     assert rel(tuned[0][2], base[0][2]) <= 1e-5
+
+
+def test_graph_step_equals_host_driven_step(monkeypatch):
+    """A batch step is one CUDA graph launch whose WHILE nodes take the host's loop decisions
+    on the device; with BHEM_BATCH_HOST_LOOP set the same kernels run in the same order with the
+    decisions taken on the host. The per-shell dot products are summed across CTAs with FP64
+    atomics, whose order varies from run to run, so a PCG solve may stop one iteration apart:
+    the two forms agree in status and Newton counts, PCG totals within one per Newton iteration,
+    and the states to 1e-6, for two steps (the second replays the captured graph)."""
+    shells = make_shells()
+    monkeypatch.delenv("BHEM_BATCH_HOST_LOOP", raising=False)
+    graph, off = run_batch(shells, steps=2)
+    monkeypatch.setenv("BHEM_BATCH_HOST_LOOP", "1")
+    host, _ = run_batch(shells, steps=2)
+    for (sg, qg, vg), (sh_, qh, vh) in zip(graph, host):
+        for s in range(len(shells)):
+            for key in ("status", "newton_iters", "ls_backtracks", "regularizations", "diag_fixes"):
+                assert sg[s][key] == sh_[s][key], (s, key, sg[s], sh_[s])
+            assert abs(sg[s]["pcg_iters_total"] - sh_[s]["pcg_iters_total"]) <= sg[s]["newton_iters"]
+        assert rel(qg, qh) <= 1e-6 and rel(vg, vh) <= 1e-6
+
+
+def test_config4_sample_of_32_sheets_against_the_oracle():
+    """32 seeded sheets of the 512-sheet recipe (n x n patches, n ~ U{4..40}, log10 E ~ U[4, 6],
+    h ~ U[0.5, 2] mm, corners (0,0) and (1,1) pinned, gravity): one batched step (one graph
+    launch) against the FP64 oracle sheet by sheet: every sheet converges to 1e-8, Newton counts
+    agree to within one (FP32 Hessians), and the velocities agree to the solver's tolerance."""
+    sheets = S.batch_sheets(512, seed=4)[::16]
+    shells = []
+    for g, mat, rest, q in sheets:
+        c = S.corner_nodes(g)
+        shells.append((g, mat, rest, q, S.pinned_mask(g, [c[0], c[3]])))
+    assert len(shells) == 32 and len({g.nu for g, *_ in shells}) > 10
+    hist, off = run_batch(shells, steps=1)
+    st, qb, vb = hist[0]
+    Po = O.step_params(dt=1e-3)
+    for s, (g, mat, rest, q0, mask) in enumerate(shells):
+        a, b = off[s] * 12, off[s + 1] * 12
+        qo, vo, so = O.newton_step(g, mat, rest, q0.reshape(-1), np.zeros(g.n_dof), Po, mask=mask,
+                                   qfix=q0.reshape(-1))
+        assert st[s]["status"] == 0 and so["status"] == 0, (s, g.nu, st[s], so)
+        assert abs(st[s]["newton_iters"] - so["newton_iters"]) <= 1, (s, g.nu, st[s], so)
+        assert st[s]["res_final"] <= 1e-8 * st[s]["res0"]
+        assert rel(vb[a:b], vo) <= 1e-5, (s, g.nu, rel(vb[a:b], vo))
