@@ -251,7 +251,9 @@ SHELL_API shell_status shell_newton_step(shell_t* shell, const shell_step_params
    a counter), present on every GPU that loads the library until the process exits. Grids of
    more than 131072 patches are rejected with SHELL_ERR_ARG. The first call on a device looks up
    the array's device address (cudaGetSymbolAddress) with that device current; make that first
-   call before any stream capture. All calls share the array and each call resets the counter it
+   call before any stream capture. The address is kept for the life of the process: after
+   cudaDeviceReset on a device (which unloads the library's module there) this entry point must
+   not be called on that device again. All calls share the array and each call resets the counter it
    needs: calls whose work overlaps on the GPU (other streams, other host threads on the same
    device) race on it and must be serialised by the caller. A degenerate geometry gives a
    non-finite energy instead of an error code. */

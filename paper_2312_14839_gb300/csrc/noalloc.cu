@@ -194,7 +194,8 @@ k_energy_grad(int nu, int nv, int per_u, int per_v, const double* __restrict__ r
   }
 }
 
-// Device address of g_scratch, looked up once per device (with that device current).
+// Device address of g_scratch, looked up once per device (with that device current) and kept for
+// the life of the process; a cudaDeviceReset on that device invalidates it (documented in bhem.h).
 static std::mutex g_mutex;
 static Scratch* g_addr[128] = {nullptr};
 
