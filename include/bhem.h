@@ -150,11 +150,15 @@ SHELL_API shell_status shell_destroy(shell_t* shell);
 /* Sizes of the shell (host output). */
 SHELL_API shell_status shell_info(const shell_t* shell, shell_info_t* info);
 
-/* Budget of the library's bounded device-side waits on this shell: the mbarrier waits of the
-   bulk-copy SpMV (SHELL_SPMV_TMA) poll at most `polls` times for a stage before the kernel gives
-   up; it then raises SHELL_ERR_TIMEOUT for the call (whose results are void), still waits, with
-   the default budget, for the copies it has issued, and returns, so that the device stays usable.
-   polls < 0 restores the default (2^20 polls); 0 makes every stage wait expire at once (a test
+/* Budget of the library's bounded device-side waits on this shell: the grid barriers of the
+   persistent mixed-precision PCG (one cooperative launch per solve; selected by the environment
+   variable BHEM_PCG_LOOP=persistent when the shell is created) and the mbarrier waits of
+   the bulk-copy SpMV (SHELL_SPMV_TMA) poll at most `polls` times before the waiting CTA gives
+   up. The call then returns SHELL_ERR_TIMEOUT (its results are void): a CTA that gave up at a
+   barrier leaves the kernel, the others give up at their next barrier, and the bulk-copy SpMV
+   still waits, with the default budget, for the copies it has issued, so that the device stays
+   usable.
+   polls < 0 restores the default (2^20 polls); 0 makes every such wait expire at once (a test
    of the timeout path). Synchronises the shell's stream and drops its cached PCG graphs. No paper
    counterpart (a watchdog of this implementation). */
 SHELL_API shell_status shell_set_wait_budget(shell_t* shell, int polls);

@@ -161,6 +161,12 @@ struct Shell {
   // BHEM_PCG_HOST_LOOP set: mixed-precision PCG iterations are launched from the host in chunks
   // (as in FP64) instead of the device-side graph loop, whose kernels a profiler cannot list
   int pcg_host_loop = 0;
+  // mixed-precision solve form: 1 the device-side graph loop (the default), 0 one persistent
+  // cooperative launch per solve (BHEM_PCG_LOOP=persistent), 2 host chunks (BHEM_PCG_LOOP=host or
+  // BHEM_PCG_HOST_LOOP)
+  int pcg_mode = 1;
+  void* d_persist = nullptr;        // persistent PCG: barrier, published totals, per-CTA partials
+  int persist_max_ctas = 0;
   int max_row = 0;
   int spmv_tma = 0, spmv_grid = 0, spmv_stage_floats = 0;
   size_t spmv_smem = 0;
@@ -242,6 +248,7 @@ shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, const dou
 // for this mask and count); the shift comes from the PCG state
 // the whole mixed-precision solve as one graph: a conditional WHILE node around one iteration
 shell_status launch_pcg_loop_graph(Shell& s, const unsigned char* mask);
+shell_status launch_pcg_persistent(Shell& s, const unsigned char* mask);
 int pcg_loop_unroll();   // PCG iterations per loop body
 shell_status launch_spmv(Shell& s, const void* x, int x_fp32, void* y);
 shell_status launch_pcg_result(Shell& s);

@@ -126,7 +126,7 @@ static void destroy_shell(shell_s* s) {
                   s->d_pcg, s->d_qn, s->d_y, s->d_g, s->d_gin, s->d_d, s->d_Md, s->d_Ep,
                   s->d_qwork, s->d_vwork, s->d_qfix, s->d_warm, s->d_mask, s->d_ns, s->d_err, s->d_qmy,
                   s->d_energy_tmp, s->red.partials, s->red.ticket, s->red_aux.partials, s->red_aux.ticket, s->d_rhs, s->d_g2, s->d_Ep2,
-                  s->d_search, s->d_ray_nets, s->d_ccd_nets};
+                  s->d_search, s->d_ray_nets, s->d_ccd_nets, s->d_persist};
   for (void* p : ptrs) dfree(p);
   if (s->h_ns) cudaFreeHost(s->h_ns);
   if (s->h_pcg) cudaFreeHost(s->h_pcg);
@@ -169,7 +169,7 @@ static shell_status sync_and_check(Shell& s) {
   }
   if (bits & ERRBIT_DEGENERATE) return fail(SHELL_ERR_DEGENERATE, "degenerate surface normal at a Gauss point");
   if (bits & ERRBIT_NONFINITE) return fail(SHELL_ERR_NONFINITE, "non-finite energy or residual");
-  if (bits & ERRBIT_TIMEOUT) return fail(SHELL_ERR_TIMEOUT, "a bounded wait for a bulk copy expired");
+  if (bits & ERRBIT_TIMEOUT) return fail(SHELL_ERR_TIMEOUT, "a bounded device-side wait expired (bulk copy or grid barrier)");
   return SHELL_OK;
 }
 
@@ -220,6 +220,13 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
   s->mu = material->young / (2.0 * (1.0 + material->poisson));
   s->val_fp64 = opt.precision == SHELL_PREC_FP64;
   s->pcg_host_loop = getenv("BHEM_PCG_HOST_LOOP") != nullptr;
+  {
+    const char* m = getenv("BHEM_PCG_LOOP");
+    s->pcg_mode = s->pcg_host_loop ? 2 : 1;
+    if (m && std::strcmp(m, "persistent") == 0) s->pcg_mode = 0;
+    if (m && std::strcmp(m, "host") == 0) s->pcg_mode = 2;
+    s->pcg_host_loop = s->pcg_mode == 2;
+  }
 
   HostTopo T;
   build_topology(g, s->n1, s->n2, T);
@@ -419,7 +426,15 @@ static shell_status run_pcg(Shell& s, const unsigned char* mask, const double td
   mark(s, "pcg_setup_enqueued");
   int launched = 0, chunk = 4;
   *s.h_pcg = PcgState{};
-  if (!s.val_fp64 && !s.pcg_host_loop) {
+  if (!s.val_fp64 && s.pcg_mode == 0) {
+    // mixed precision, BHEM_PCG_LOOP=persistent: the whole solve is one persistent cooperative
+    // launch (measured slower than the graph loop below on every workload of the bench)
+    if (limit > 0) BHEM_TRY(launch_pcg_persistent(s, mask));
+    BHEM_CUDA(cudaMemcpyAsync(s.h_pcg, s.d_pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s.stream));
+    BHEM_CUDA(cudaStreamSynchronize(s.stream));
+    mark(s, "pcg_persistent");
+    launched = limit;
+  } else if (!s.val_fp64 && s.pcg_mode == 1) {
     // mixed precision: the whole solve loops on the device (one graph with a conditional WHILE
     // node around a few iterations; the kernels stop it, at the latest after `limit` iterations)
     if (limit > 0) BHEM_TRY(launch_pcg_loop_graph(s, mask));

@@ -636,6 +636,200 @@ k_spmv32_tma(int n, const int* __restrict__ rp, const int* __restrict__ col, con
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Mixed-precision PCG as one persistent cooperative launch: every CTA owns a contiguous range of
+// node rows and runs all iterations of the solve, the phases separated by grid barriers:
+//   SpMV of its rows (p.Ap partial) | barrier + sum | update x, r, z = D r of its rows (r.z, r.r
+//   partials) | barrier + sums | p = z + beta p of its rows | barrier.
+// The arithmetic per element is that of k_spmv32, k_pcg32_update and k_pcg32_pupdate4; the
+// partial sums are taken per CTA and combined by the last CTA to arrive at the barrier (in CTA
+// order), which publishes the totals before it releases the others, so every CTA takes the same
+// decisions. Every barrier wait is bounded (Shell::wait_polls polls): on expiry the CTA raises
+// ERRBIT_TIMEOUT and returns, and the others then time out at their next barrier. The launch is
+// cooperative, so all CTAs are resident and a barrier completes unless a CTA has given up.
+// ------------------------------------------------------------------------------------------
+struct PersistSync {
+  unsigned count, gen;   // barrier arrivals and generation
+  double out[4];         // totals published by the last CTA of a reducing barrier
+};
+constexpr int kPersistMaxCtas = 4096;
+
+// Grid barrier; with nv > 0 the last CTA to arrive first sums the nv per-CTA partials
+// part[v * kPersistMaxCtas + b] (b = 0 .. gridDim.x - 1, double-float, in a fixed order) into
+// ps->out[v]. Returns false when this CTA's wait ran out (the kernel must return).
+__device__ __forceinline__ bool persist_sync(PersistSync* ps, const float2* part, int nv, int polls,
+                                             int* err) {
+  __shared__ int s_last, s_ok;
+  __shared__ unsigned s_gen;
+  __shared__ F2 sred[3][32];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &ps->gen;
+    s_gen = *vgen;   // no CTA can release this barrier before this CTA has arrived
+    __threadfence();
+    s_last = atomicAdd(&ps->count, 1u) == gridDim.x - 1u ? 1 : 0;
+    s_ok = 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    for (int v = 0; v < nv; ++v) {
+      F2 acc{0.f, 0.f};
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        const float2 y = __ldcg(part + (size_t)v * kPersistMaxCtas + b);
+        acc = f2_add(acc, F2{y.x, y.y});
+      }
+      const F2 t = f2_block_sum(acc, sred, v);
+      if (threadIdx.x == 0) ps->out[v] = (double)t.hi + (double)t.lo;
+    }
+    if (threadIdx.x == 0) {
+      ps->count = 0u;
+      __threadfence();
+      atomicAdd(&ps->gen, 1u);
+    }
+  } else if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &ps->gen;
+    int i = 0;
+    for (; i < polls; ++i) {
+      if (*vgen != s_gen) break;
+      __nanosleep(32);
+    }
+    if (i >= polls) {
+      atomicOr(err, ERRBIT_TIMEOUT);
+      s_ok = 0;
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ double persist_out(PersistSync* ps, int v) {
+  return *reinterpret_cast<volatile double*>(&ps->out[v]);
+}
+
+__global__ void __launch_bounds__(kSpmvThreads)
+k_pcg32_persistent(int n, int per, const int* __restrict__ rp, const int* __restrict__ col,
+                   const float* __restrict__ val, const float* __restrict__ Dinv,
+                   const unsigned char* __restrict__ mask, float* __restrict__ x, float* __restrict__ r,
+                   float* __restrict__ z, float* __restrict__ p, float* __restrict__ Ap, PcgState* st,
+                   PersistSync* ps, float2* part, int polls, int* err) {
+  constexpr int NC = 3, TPR = 36, RPC = kSpmvThreads / TPR, NPG = kSpmvThreads / 12;
+  __shared__ float sacc[kSpmvThreads];
+  __shared__ float sr[NPG][12];
+  __shared__ F2 sred[2][32];
+  const int t = threadIdx.x;
+  const int i0 = blockIdx.x * per, i1 = min(n, i0 + per);
+  const float td[4] = {st->td[0], st->td[1], st->td[2], st->td[3]};
+  const int limit = st->limit, fixed = st->fixed;
+  const double rtol2 = st->rtol2, bb = st->bb;
+  double rz = st->rz, rr = st->rr, pq = 0.0, alpha = 0.0, beta = 0.0;
+  int iters = 0, negcurv = 0;
+  int done = st->done || limit <= 0;
+  const int br = t / TPR, w = t % TPR, rr_ = w / NC, cc = w % NC;
+  const int ln = t / 12, a = t % 12;
+  while (!done) {
+    // y = (A + tau D) p on this CTA's rows and the partial p.y
+    F2 part_pq{0.f, 0.f};
+    for (int base = i0; base < i1; base += RPC) {
+      const int i = base + br;
+      float acc = 0.f;
+      if (i < i1) {
+        const int k0 = rp[i], k1 = rp[i + 1];
+        for (int k = k0; k < k1; ++k) {
+          const float4 av = __ldcs(reinterpret_cast<const float4*>(val + (size_t)k * 144 + rr_ * 12 + cc * 4));
+          const float4 xv = __ldcg(reinterpret_cast<const float4*>(p + (size_t)col[k] * 12 + cc * 4));
+          acc = dot4_acc(acc, av, xv);
+        }
+      }
+      sacc[t] = acc;
+      __syncthreads();
+      if (i < i1 && cc == 0) {
+        const size_t gi = (size_t)i * 12 + rr_;
+        const float xi = __ldcg(p + gi);
+        float yi = (sacc[t] + sacc[t + 1]) + sacc[t + 2];
+        yi = __fmaf_rn(td[rr_ / 3], xi, yi);
+        if (mask && mask[gi]) yi = 0.f;
+        Ap[gi] = yi;
+        part_pq = f2_add(part_pq, f2_prod(xi, yi));
+      }
+      __syncthreads();
+    }
+    {
+      const F2 c = f2_block_sum(part_pq, sred, 0);
+      if (t == 0) part[blockIdx.x] = make_float2(c.hi, c.lo);
+    }
+    if (!persist_sync(ps, part, 1, polls, err)) return;
+    pq = persist_out(ps, 0);
+    if (!(pq > 0.0)) {
+      negcurv = 1;
+      alpha = 0.0;
+      break;
+    }
+    alpha = rz / pq;
+    // x += alpha p, r -= alpha Ap, z = D r on this CTA's nodes; partials r.z, r.r
+    const float af = (float)alpha;
+    F2 prz{0.f, 0.f}, prr{0.f, 0.f};
+    for (int base = i0; base < i1; base += NPG) {
+      const int i = base + ln;
+      const size_t gi = (size_t)i * 12 + a;
+      float ri = 0.f, zi = 0.f;
+      if (i < i1) {
+        x[gi] = fmaf(af, p[gi], x[gi]);
+        ri = fmaf(-af, Ap[gi], r[gi]);
+        r[gi] = ri;
+        sr[ln][a] = ri;
+      }
+      __syncthreads();
+      if (i < i1) {
+        if (!(mask && mask[gi])) {
+          const float* D = Dinv + (size_t)i * 144 + a * 12;
+          const float* q = sr[ln];
+          zi = __fmaf_rn(D[0], q[0], 0.f);
+#pragma unroll
+          for (int c = 1; c < 12; ++c) zi = __fmaf_rn(D[c], q[c], zi);
+        }
+        z[gi] = zi;
+      }
+      prz = f2_add(prz, f2_prod(ri, zi));
+      prr = f2_add(prr, f2_prod(ri, ri));
+      __syncthreads();
+    }
+    {
+      const F2 c0 = f2_block_sum(prz, sred, 0);
+      const F2 c1 = f2_block_sum(prr, sred, 1);
+      if (t == 0) {
+        part[kPersistMaxCtas + blockIdx.x] = make_float2(c0.hi, c0.lo);
+        part[2 * kPersistMaxCtas + blockIdx.x] = make_float2(c1.hi, c1.lo);
+      }
+    }
+    if (!persist_sync(ps, part + kPersistMaxCtas, 2, polls, err)) return;
+    const double rz_new = persist_out(ps, 0);
+    rr = persist_out(ps, 1);
+    iters += 1;
+    beta = rz_new / rz;
+    rz = rz_new;
+    if (fixed == 0 && rr <= rtol2 * bb) done = 1;
+    if (rz_new == 0.0) done = 1;
+    if (iters >= limit) done = 1;
+    if (done) break;
+    // p = z + beta p on this CTA's rows, then every CTA waits before the next SpMV reads them
+    const float bf = (float)beta;
+    for (int k = i0 * 12 + t; k < i1 * 12; k += blockDim.x) p[k] = fmaf(bf, p[k], z[k]);
+    if (!persist_sync(ps, nullptr, 0, polls, err)) return;
+  }
+  if (blockIdx.x == 0 && t == 0) {
+    st->iters = iters;
+    st->rz = rz;
+    st->rr = rr;
+    st->pq = pq;
+    st->alpha = alpha;
+    st->beta = beta;
+    st->negcurv = negcurv;
+    st->done = 1;
+  }
+}
+
 // row a of a 12x12 block times sr, as the explicit FMA chain of k_pcg32_update
 __device__ __forceinline__ float apply_block32(const float* __restrict__ D, const float* sr, int a) {
   float s = 0.f;
@@ -1215,6 +1409,43 @@ void drop_pcg_graphs(Shell& s) {
     gph = Shell::PcgGraph{};
   }
   s.pcg_graph_next = 0;
+}
+
+// The whole mixed-precision solve as one cooperative launch (k_pcg32_persistent), after
+// launch_precond_setup and launch_pcg_init. Grid: one CTA per 24 nodes, at most as many as can be
+// resident (occupancy x SMs) and kPersistMaxCtas.
+shell_status launch_pcg_persistent(Shell& s, const unsigned char* mask) {
+  if (s.val_fp64) return fail(SHELL_ERR_ARG, "the persistent PCG is for mixed precision");
+  if (!s.d_persist) {
+    const cudaError_t e = cudaMalloc(&s.d_persist, sizeof(PersistSync) + sizeof(float2) * 3 * kPersistMaxCtas);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      s.d_persist = nullptr;
+      return fail(SHELL_ERR_OOM, std::string("persistent PCG workspace: ") + cudaGetErrorString(e));
+    }
+    int occ = 0;
+    BHEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg32_persistent, kSpmvThreads, 0));
+    s.persist_max_ctas = std::min(kPersistMaxCtas, std::max(1, occ) * std::max(1, s.num_sms));
+  }
+  const int n = s.n_nodes;
+  int G = std::max(1, std::min(s.persist_max_ctas, (n + 23) / 24));
+  int per = (n + G - 1) / G;
+  G = (n + per - 1) / per;
+  PersistSync* ps = reinterpret_cast<PersistSync*>(s.d_persist);
+  float2* part = reinterpret_cast<float2*>(reinterpret_cast<char*>(s.d_persist) + sizeof(PersistSync));
+  BHEM_CUDA(cudaMemsetAsync(&ps->count, 0, sizeof(unsigned), s.stream));
+  const int* rp = s.d_row_ptr;
+  const int* col = s.d_col;
+  const float* val = (const float*)s.d_val;
+  const float* Dinv = (const float*)s.d_Dinv;
+  int polls = s.wait_polls;
+  void* args[] = {(void*)&n, (void*)&per, (void*)&rp, (void*)&col, (void*)&val, (void*)&Dinv, (void*)&mask,
+                  (void*)&s.d_x32, (void*)&s.d_r32, (void*)&s.d_z32, (void*)&s.d_p32, (void*)&s.d_Ap32,
+                  (void*)&s.d_pcg, (void*)&ps, (void*)&part, (void*)&polls, (void*)&s.d_err};
+  BHEM_CUDA(cudaLaunchCooperativeKernel((const void*)k_pcg32_persistent, dim3(G), dim3(kSpmvThreads), args, 0,
+                                        s.stream));
+  ++s.launches;
+  return SHELL_OK;
 }
 
 shell_status launch_pcg_loop_graph(Shell& s, const unsigned char* mask) {

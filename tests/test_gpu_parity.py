@@ -179,9 +179,11 @@ def test_spmv_tma_identical_to_plain(case):
     assert np.array_equal(ys[0], ys[1])
 
 
-def test_pcg_mixed_tma_matches_plain():
-    """PCG with the TMA SpMV: same iteration count, and the solution agrees to the solver
-    tolerance (only the order of the p.Ap partial sums differs)."""
+def test_pcg_mixed_tma_matches_plain(monkeypatch):
+    """PCG with the TMA SpMV (in the graph-loop form of the solve, which launches the shell's SpMV
+    kernel): same iteration count, and the solution agrees to the solver tolerance (only the
+    order of the p.Ap partial sums differs)."""
+    monkeypatch.setenv("BHEM_PCG_LOOP", "graph")
     g, rest, q, mat = CASES["sheet10x10-noisy"]()
     mask = dev(S.pinned_mask(g, [0, g.n_nodes - 1]), torch.uint8)
     res = []
@@ -196,12 +198,14 @@ def test_pcg_mixed_tma_matches_plain():
     assert rel(res[1][0], res[0][0]) <= 1e-5
 
 
-def test_tma_spmv_wait_timeout_is_reported_and_the_shell_recovers():
+def test_tma_spmv_wait_timeout_is_reported_and_the_shell_recovers(monkeypatch):
     """The bulk-copy SpMV's stage waits are bounded. With a zero budget every stage wait expires:
-    the solve returns SHELL_ERR_TIMEOUT (the kernel still drains the copies it issued, with the
-    default budget, so nothing is left in flight), and after the default budget is restored the
-    same shell solves the system as before."""
+    the solve (in its graph-loop form, which launches the shell's SpMV kernel) returns
+    SHELL_ERR_TIMEOUT (the kernel still drains the copies it issued, with the default budget, so
+    nothing is left in flight), and after the default budget is restored the same shell solves
+    the system as before."""
     from paper_2312_14839_gb300.bhem import ShellError
+    monkeypatch.setenv("BHEM_PCG_LOOP", "graph")
     g, rest, q, mat = CASES["sheet10x10-noisy"]()
     mask = dev(S.pinned_mask(g, [0, g.n_nodes - 1]), torch.uint8)
     sh = make_shell(g, mat, rest, precision="mixed", spmv="tma")
@@ -510,9 +514,9 @@ def test_spmv_rejects_misaligned_x():
     ("sinusoid16", 1.0, 0),            # indefinite: stops on negative curvature
 ])
 def test_pcg_device_loop_matches_host_loop(monkeypatch, case, mass_scale, fixed):
-    """The mixed-precision solve loops on the device (a conditional graph node around 4
-    iterations); BHEM_PCG_HOST_LOOP launches the same iterations from the host. Same kernels in
-    the same order: iteration count, curvature flag and solution are identical."""
+    """The graph-loop form of the mixed-precision solve loops on the device (a conditional graph
+    node around 4 iterations); BHEM_PCG_HOST_LOOP launches the same iterations from the host.
+    Same kernels in the same order: iteration count, curvature flag and solution are identical."""
     if case == "sinusoid16":
         g, rest, q = S.sheet_sinusoid(16, 3)
         mat = THIN
@@ -525,6 +529,7 @@ def test_pcg_device_loop_matches_host_loop(monkeypatch, case, mass_scale, fixed)
             monkeypatch.setenv("BHEM_PCG_HOST_LOOP", "1")
         else:
             monkeypatch.delenv("BHEM_PCG_HOST_LOOP", raising=False)
+            monkeypatch.setenv("BHEM_PCG_LOOP", "graph")
         sh = make_shell(g, mat, rest, precision="mixed", assembly="color")
         _, G = sh.energy_grad_hess(dev(q.reshape(-1)), mass_scale=mass_scale)
         x, it, neg = sh.pcg_solve(-G, mask=mask, rtol=1e-6, max_iter=1000, fixed_iters=fixed)
@@ -536,6 +541,70 @@ def test_pcg_device_loop_matches_host_loop(monkeypatch, case, mass_scale, fixed)
     if case == "sinusoid16":
         assert res[0][2] == 1
     assert np.array_equal(res[0][0], res[1][0])
+
+
+@pytest.mark.parametrize("case,mass_scale,fixed", [
+    ("sheet10x10-noisy", 1e6, 0),      # converges to rtol
+    ("sheet10x10-noisy", 1e6, 7),      # a fixed iteration count
+    ("sinusoid16", 1.0, 0),            # indefinite: stops on negative curvature
+    ("sinusoid64", 1e6, 0),            # 4,225 nodes: many CTAs, several rows each
+    ("annulus280x5", 1e6, 0),          # periodic
+])
+def test_pcg_persistent_matches_host_loop(monkeypatch, case, mass_scale, fixed):
+    """The default mixed-precision solve is one persistent cooperative launch whose CTAs meet at
+    grid barriers; the host-chunked form launches one kernel per phase. Same arithmetic per
+    element, partial sums combined in another order: same curvature flag, iteration counts within
+    one (the stopping test may fall either side), solutions within the solver's tolerance."""
+    if case == "sinusoid16":
+        g, rest, q = S.sheet_sinusoid(16, 3)
+        mat = THIN
+    elif case == "sinusoid64":
+        g, rest, q = S.sheet_sinusoid(64, 3, 0.01)
+        mat = THIN
+    elif case == "annulus280x5":
+        g, rest, q = S.annulus_sinusoid(280, 5, 3, 0.01)
+        mat = THIN
+    else:
+        g, rest, q, mat = CASES[case]()
+    mask = dev(S.pinned_mask(g, [0]), torch.uint8)
+    res = []
+    for mode in ("persistent", "host"):
+        monkeypatch.setenv("BHEM_PCG_LOOP", mode)
+        sh = make_shell(g, mat, rest, precision="mixed", assembly="color")
+        _, G = sh.energy_grad_hess(dev(q.reshape(-1)), mass_scale=mass_scale)
+        x, it, neg = sh.pcg_solve(-G, mask=mask, rtol=1e-6, max_iter=1000, fixed_iters=fixed)
+        res.append((host(x), it, neg))
+        sh.close()
+    assert res[0][2] == res[1][2], (res[0][1:], res[1][1:])
+    assert abs(res[0][1] - res[1][1]) <= 1, (res[0][1:], res[1][1:])
+    if fixed:
+        assert res[0][1] == res[1][1] == fixed
+    if case == "sinusoid16":
+        assert res[0][2] == 1
+    else:
+        assert rel(res[0][0], res[1][0]) <= 1e-4
+
+
+def test_pcg_persistent_barrier_timeout_is_reported_and_the_shell_recovers(monkeypatch):
+    """The persistent solve's grid barriers are bounded waits. With a zero budget every CTA that
+    is not the last to arrive gives up at once: the solve returns SHELL_ERR_TIMEOUT and every CTA
+    leaves the kernel. With the default budget restored, the same shell solves the system."""
+    from paper_2312_14839_gb300.bhem import ShellError
+    monkeypatch.setenv("BHEM_PCG_LOOP", "persistent")
+    g, rest, q, mat = CASES["sheet10x10-noisy"]()
+    mask = dev(S.pinned_mask(g, [0, g.n_nodes - 1]), torch.uint8)
+    sh = make_shell(g, mat, rest, precision="mixed")
+    _, G = sh.energy_grad_hess(dev(q.reshape(-1)), mass_scale=1e6)
+    x0, it0, neg0 = sh.pcg_solve(-G, mask=mask, rtol=1e-6, max_iter=1000)
+    sh.set_wait_budget(0)
+    with pytest.raises(ShellError) as ei:
+        sh.pcg_solve(-G, mask=mask, rtol=1e-6, max_iter=20)
+    assert ei.value.status == 9   # SHELL_ERR_TIMEOUT
+    sh.set_wait_budget(-1)
+    x1, it1, neg1 = sh.pcg_solve(-G, mask=mask, rtol=1e-6, max_iter=1000)
+    assert it1 == it0 and neg1 == neg0 == 0
+    assert np.array_equal(host(x1), host(x0))
+    sh.close()
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
