@@ -1105,6 +1105,10 @@ def step_workload_line(args, workload, dist, world, rank, full=True):
         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
         "traffic": traffic, "algorithmic_bytes_per_launch": spmv_bytes, "avg_launch_us": spmv_s * 1e6}
     line["alu_rooflines"] = alu_rooflines(sh, q0_d, P, g.n_patches, stream)
+    # the warp-level tensor-core rates beside the FP32 FMA peak: what a TF32 split of the element
+    # contraction could run at (three TF32 products per FP32-accurate product)
+    line["warp_mma_peaks_tflops"] = {"tf32_m16n8k8": bhem.measure_mma_peak(0, 2048, stream) / 1e12,
+                                     "bf16_m16n8k16": bhem.measure_mma_peak(1, 2048, stream) / 1e12}
     line["element_kernel_only"] = element_kernel_only(sh, q0_d, g.n_patches, stream)
     sh.close()
     return line

@@ -382,6 +382,14 @@ SHELL_API shell_status shell_mlp_warm_start(shell_mlp_t* mlp, shell_t* shell, co
    and frees a small device buffer. */
 SHELL_API shell_status shell_measure_fma_peak(int fp64, int iters, void* stream, double* flops_per_s);
 
+/* Measured warp-level tensor-core throughput of the current device (no paper counterpart; the
+   rate a TF32 tensor-core split of the element Hessian contraction of App. B.2 would run at).
+   kind 0: mma.sync m16n8k8 TF32 with FP32 accumulation, kind 1: mma.sync m16n8k16 BF16. Times one
+   launch of four independent accumulator tiles per warp, `iters` MMAs each, register operands,
+   4 CTAs of 8 warps per SM (after one warm-up launch). *flops_per_s receives 2 x MACs / elapsed
+   seconds. Synchronises; allocates and frees a small device buffer. */
+SHELL_API shell_status shell_measure_mma_peak(int kind, int iters, void* stream, double* flops_per_s);
+
 /* ------------------------------------------------------------------------------------------ */
 /* Static ray-patch intersection (Sec. 5, Eq. ray, Eq. ineqray)                                */
 /* ------------------------------------------------------------------------------------------ */

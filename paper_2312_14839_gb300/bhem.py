@@ -121,6 +121,7 @@ def load():
                 "shell_warm_targets": [ll, p, p, p, d, p, p],
                 "shell_mlp_warm_start": [p, p, p, p, d, p],
                 "shell_measure_fma_peak": [i, i, p, p],
+                "shell_measure_mma_peak": [i, i, p, p],
                 "shell_trace_rays": [p, p, ll, p, p, i, p, p, p, p, p],
                 "shell_ccd_points": [p, p, p, ll, p, p, i, p, p, p, p, p],
             }
@@ -549,6 +550,14 @@ def warm_targets(q_next, q, v, dt, T=None, stream=None):
     _, sh = _stream_handle(stream)
     _check(load().shell_warm_targets(int(q.numel()), _ptr(q_next), _ptr(q), _ptr(v), float(dt), _ptr(T), sh))
     return T
+
+
+def measure_mma_peak(kind: int, iters: int, stream=None) -> float:
+    """Measured mma.sync throughput in FLOP/s (shell_measure_mma_peak; 0: TF32, 1: BF16)."""
+    _, sh = _stream_handle(stream)
+    out = C.c_double()
+    _check(load().shell_measure_mma_peak(int(kind), int(iters), sh, C.byref(out)))
+    return out.value
 
 
 def measure_fma_peak(fp64: bool, iters: int, stream=None) -> float:
