@@ -11,7 +11,7 @@ of it: every function restates a textbook definition in plain numpy, one step af
 * Adam (Kingma and Ba, 2015, Algorithm 1) with bias-corrected moments.
 * Node features and warm-start targets of a shell state (the feature definition of the library's
   warm-start interface): u = q - q_rest, v, the mean of u_nb - u over present edge neighbours for
-  the position DOFs, and the present fraction of the 4-neighbour stencil; targets
+  the position DOFs, and the mean over the same neighbours of their position speed |v_nb|; targets
   q^{n+1} - q^n - dt v^n.
 
 ``bf16=True`` rounds, to the nearest bfloat16 (ties to even), exactly the quantities that the CUDA
@@ -148,7 +148,7 @@ def node_features(grid, rest, q, v):
             node = j * n1 + i
             X[node, 0:12] = u[node]
             X[node, 12:24] = vv[node]
-            diffs = []
+            diffs, speeds = [], []
             for di, dj in ((-1, 0), (1, 0), (0, -1), (0, 1)):
                 a, b = i + di, j + dj
                 if grid.periodic_u:
@@ -158,9 +158,10 @@ def node_features(grid, rest, q, v):
                 if not (0 <= a < n1 and 0 <= b < n2) or (a == i and b == j):
                     continue
                 diffs.append(u[b * n1 + a, 0:3] - u[node, 0:3])
+                speeds.append(np.linalg.norm(vv[b * n1 + a, 0:3]))
             if diffs:
                 X[node, 24:27] = np.mean(diffs, axis=0)
-            X[node, 27] = len(diffs) / 4.0
+                X[node, 27] = np.mean(speeds)
     return X
 
 

@@ -4,8 +4,9 @@
 // component; the implicit-Euler Newton solve of Sec. 6.1 stays the judge of every step.
 //
 // Node features (28, FP32): the node's 12 DOFs relative to rest (u = q - q_rest), its 12 velocity
-// DOFs, the mean over its present edge neighbours of u_nb - u_i for the position DOFs (a discrete
-// Laplacian of the displacement, 3 values) and the fraction of its 4-neighbour stencil that exists.
+// DOFs, and 4 means over its present edge neighbours: of u_nb - u_i for the position DOFs (a
+// discrete Laplacian of the displacement, 3 values), and of the neighbours' position speed |v_nb|
+// (their previous step's |dq| over dt, 1 value).
 // Output (12): the node's update beyond the inertial predictor, q^{n+1} - q^n - dt v^n.
 #include <cuda_bf16.h>
 
@@ -298,7 +299,7 @@ __device__ __forceinline__ void node_features_of(int i, int n1, int n2, int per_
   }
   const int ii = i % n1, jj = i / n1;
   const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
-  double lap[3] = {0.0, 0.0, 0.0};
+  double lap[3] = {0.0, 0.0, 0.0}, speed = 0.0;
   int cnt = 0;
   for (int e = 0; e < 4; ++e) {
     int a = ii + di[e], b = jj + dj[e];
@@ -307,10 +308,11 @@ __device__ __forceinline__ void node_features_of(int i, int n1, int n2, int per_
     if (a < 0 || a >= n1 || b < 0 || b >= n2 || (a == ii && b == jj)) continue;
     const size_t o = ((size_t)b * n1 + a) * 12;
     for (int c = 0; c < 3; ++c) lap[c] += (q[o + c] - rest[o + c]) - ui[c];
+    speed += sqrt(v[o] * v[o] + v[o + 1] * v[o + 1] + v[o + 2] * v[o + 2]);
     ++cnt;
   }
   for (int c = 0; c < 3; ++c) out[24 + c] = cnt ? (float)(lap[c] / cnt) : 0.f;
-  out[27] = 0.25f * (float)cnt;
+  out[27] = cnt ? (float)(speed / cnt) : 0.f;
 }
 
 __global__ void k_node_features(int n1, int n2, int per_u, int per_v, const double* __restrict__ q,

@@ -116,18 +116,30 @@ def test_round_bf16_ties_and_torch():
     np.testing.assert_array_equal(om.round_bf16(x), ref)
 
 
-def test_features_rest_state_stencil():
+def test_features_rest_state_and_neighbour_speed():
+    """At rest every feature is 0. A uniform position velocity c gives the neighbour-mean speed |c|
+    at every node (corners, edges, interior, and on the periodic annulus); a velocity linear in x,
+    v_x = (x, 0, 0) with x >= 0, gives the interior mean of x - h, x + h, x, x: x itself."""
     g, rest = S.flat_sheet(5, 3)
     X = om.node_features(g, rest, rest, np.zeros_like(rest))
-    assert np.abs(X[:, :27]).max() == 0.0
-    frac = X[:, 27].reshape(g.n2, g.n1)
-    assert frac[0, 0] == frac[-1, -1] == frac[0, -1] == frac[-1, 0] == 0.5
-    assert np.all(frac[0, 1:-1] == 0.75) and np.all(frac[1:-1, 0] == 0.75)
-    assert np.all(frac[1:-1, 1:-1] == 1.0)
-    ga, resta = S.annulus(8, 3)          # periodic in u: only the v-boundary rows miss a neighbour
-    Xa = om.node_features(ga, resta, resta, np.zeros_like(resta))
-    fa = Xa[:, 27].reshape(ga.n2, ga.n1)
-    assert np.all(fa[0] == 0.75) and np.all(fa[-1] == 0.75) and np.all(fa[1:-1] == 1.0)
+    assert np.abs(X).max() == 0.0
+    c = np.array([0.3, -0.4, 1.2])
+    v = np.zeros_like(rest)
+    v[:, 0:3] = c
+    v[:, 3:12] = 7.0                       # derivative velocities do not enter the speed feature
+    X = om.node_features(g, rest, rest, v)
+    np.testing.assert_allclose(X[:, 27], np.linalg.norm(c), rtol=1e-15)
+    ga, resta = S.annulus(8, 3)
+    va = np.zeros_like(resta)
+    va[:, 0:3] = c
+    Xa = om.node_features(ga, resta, resta, va)
+    np.testing.assert_allclose(Xa[:, 27], np.linalg.norm(c), rtol=1e-15)
+    r = rest.reshape(-1, 12)
+    vl = np.zeros_like(r)
+    vl[:, 0] = r[:, 0]
+    Xl = om.node_features(g, rest, rest, vl)
+    inner = np.array([(j * g.n1 + i) for j in range(1, g.n2 - 1) for i in range(1, g.n1 - 1)])
+    np.testing.assert_allclose(Xl[inner, 27], r[inner, 0], rtol=1e-14)
 
 
 def test_features_affine_and_quadratic_fields():
