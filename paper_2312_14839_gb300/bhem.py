@@ -371,7 +371,7 @@ class Batch:
     """Many shells stepped together (shell_batch_*): shells = [(grid, material, rest), ...].
     State arrays are the shells' arrays concatenated; ``node_offsets[s]`` is shell s's first node."""
 
-    def __init__(self, shells, stream=None):
+    def __init__(self, shells, stream=None, assembly="atomic"):
         import torch
         lib = load()
         S = len(shells)
@@ -385,7 +385,7 @@ class Batch:
         stream_obj, sh = (None, C.c_void_p(None)) if stream is None else _stream_handle(stream)
         self.stream = stream_obj
         self._h = C.c_void_p()
-        opts = shell_options(PREC["mixed"], HESS["exact"], ASM["atomic"], 0, 0)
+        opts = shell_options(PREC["mixed"], HESS["exact"], ASM[assembly], 0, 0)
         _check(lib.shell_batch_create(S, self.grids, self.mats, _ptr(rest), C.byref(opts), sh, C.byref(self._h)))
         self.n_shells = S
         self.node_offsets = np.zeros(S + 1, dtype=np.int32)

@@ -138,3 +138,28 @@ def test_direct_solver_rejects_unsupported_shells():
         with pytest.raises(ShellError) as ei:
             sh.newton_step(q, v, step_params(dt=1e-3), raise_on_error=True)
         assert ei.value.status == 1
+
+
+def test_direct_solver_rejects_a_grid_periodic_in_both_directions():
+    """A torus (periodic in u and v) couples the first and last node rows in both directions, so
+    no row ordering makes its matrix block tridiagonal: the direct step returns SHELL_ERR_ARG."""
+    import math
+    from paper_2312_14839_gb300.bhem import Shell, ShellError, step_params
+    nu, nv, R, r = 12, 8, 0.5, 0.2
+    g = S.Grid(nu, nv, True, True, 2 * math.pi / nu, 2 * math.pi / nv)
+    rest = np.zeros((g.n_nodes, 12))
+    for j in range(g.n2):
+        for i in range(g.n1):
+            th, ph = i * g.dxi1, j * g.dxi2
+            rho = R + r * math.cos(ph)
+            rest[j * g.n1 + i] = [rho * math.cos(th), rho * math.sin(th), r * math.sin(ph),
+                                  -rho * math.sin(th), rho * math.cos(th), 0.0,
+                                  -r * math.sin(ph) * math.cos(th), -r * math.sin(ph) * math.sin(th), r * math.cos(ph),
+                                  r * math.sin(ph) * math.sin(th), -r * math.sin(ph) * math.cos(th), 0.0]
+    with Shell(g, S.SHEET_MATERIAL, torch.as_tensor(rest.reshape(-1), device="cuda"), precision="fp64",
+               solver="direct") as sh:
+        q = torch.as_tensor(S.noisy(rest, 1e-3, 4).reshape(-1), device="cuda")
+        v = torch.zeros_like(q)
+        with pytest.raises(ShellError) as ei:
+            sh.newton_step(q, v, step_params(dt=1e-3, gravity=(0.0, 0.0, 0.0)), raise_on_error=True)
+        assert ei.value.status == 1
