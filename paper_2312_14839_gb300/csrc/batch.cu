@@ -1175,6 +1175,11 @@ void build_items(shell_batch_s& b, std::vector<int4>& items, std::vector<int4>& 
 }
 
 shell_status upload_items(shell_batch_s& b, int ppi) {
+  if (b.step_graph) {   // its element launches hold the previous items
+    cudaGraphExecDestroy(b.step_graph);
+    b.step_graph = nullptr;
+    b.step_key.clear();
+  }
   std::vector<int4> items, citems;
   std::vector<int> coff;
   build_items(b, items, citems, coff, std::vector<int>(), ppi);
