@@ -359,6 +359,8 @@ void og_trace_rays(const og_grid* g, const double* q, int n, const double* origi
   const int np = g->nu * g->nv;
   double (*P)[4][4][3] = (double(*)[4][4][3])malloc(sizeof(double) * 48 * (size_t)np);
   for (int p = 0; p < np; ++p) og_bezier_patch(g, q, p, P[p]);
+  /* queries are independent (each keeps its own heap): all host cores with OpenMP */
+#pragma omp parallel for schedule(dynamic, 16)
   for (int k = 0; k < n; ++k) {
     double t = INFINITY, u = 0.0, v = 0.0;
     int p = -1;
