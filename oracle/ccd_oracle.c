@@ -326,7 +326,7 @@ void og_ccd_points(const og_grid* g, const double* q, const double* dq, int n, c
     swept_box(P[p], dP[p], sw[p]);
   }
   /* queries are independent (each keeps its own heap): all host cores with OpenMP */
-#pragma omp parallel for schedule(dynamic, 16)
+#pragma omp parallel for schedule(dynamic, 16) if (n >= 256)
   for (int k = 0; k < n; ++k) {
     double t = INFINITY, u = 0.0, v = 0.0;
     int p = -1;

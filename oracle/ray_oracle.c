@@ -360,7 +360,7 @@ void og_trace_rays(const og_grid* g, const double* q, int n, const double* origi
   double (*P)[4][4][3] = (double(*)[4][4][3])malloc(sizeof(double) * 48 * (size_t)np);
   for (int p = 0; p < np; ++p) og_bezier_patch(g, q, p, P[p]);
   /* queries are independent (each keeps its own heap): all host cores with OpenMP */
-#pragma omp parallel for schedule(dynamic, 16)
+#pragma omp parallel for schedule(dynamic, 16) if (n >= 256)
   for (int k = 0; k < n; ++k) {
     double t = INFINITY, u = 0.0, v = 0.0;
     int p = -1;
