@@ -1,7 +1,8 @@
 // Learned Newton warm start: a per-node MLP 28 -> 256 -> 256 -> 256 -> 12 with GELU, BF16 weights
-// and activations, FP32 accumulation on the tensor cores (mma.sync m16n8k16, BF16 in, FP32 out),
-// trained with an MSE loss and Adam by the kernels of this file. The paper has no learning
-// component; the implicit-Euler Newton solve of Sec. 6.1 stays the judge of every step.
+// and activations, FP32 accumulation on the tensor cores (tcgen05.mma kind::f16 with TMEM
+// accumulators, operands staged by TMA; tc_gemm.cuh), trained with an MSE loss and Adam by the
+// kernels of this file. The paper has no learning component; the implicit-Euler Newton solve of
+// Sec. 6.1 stays the judge of every step.
 //
 // Node features (28, FP32): the node's 12 DOFs relative to rest (u = q - q_rest), its 12 velocity
 // DOFs, and 4 means over its present edge neighbours: of u_nb - u_i for the position DOFs (a
@@ -16,6 +17,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tc_gemm.cuh"
 
 namespace bhem {
 namespace mlp {
@@ -37,137 +39,115 @@ __device__ __forceinline__ float gelu_grad(float x) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Tensor-core GEMM: C[m][n] = sum_k A(m, k) B(n, k) (+ bias[n]); A, B BF16 with arbitrary element
-// strides, FP32 accumulation. 64 x 64 tile per CTA of 4 warps (32 x 32 each), K in chunks of 32,
-// split-K over gridDim.z with FP32 atomics into a zeroed C. Optional BF16 copy of GELU(C) or C.
+// Epilogues of the tensor-core GEMM (tc_gemm.cuh): called per row with 16 consecutive FP32
+// accumulator columns; every N here is a multiple of 16. A transposed BF16 copy ([column][row],
+// row stride ldt) is what the weight-gradient GEMMs read as their K-contiguous operands.
 // ------------------------------------------------------------------------------------------
-struct GemmArgs {
-  int M, N, K;
-  const bf16* A;
-  long long sAm, sAk;
-  const bf16* B;
-  long long sBn, sBk;
-  float* C;
-  long long ldc;
-  bf16* Cb;
-  long long ldcb;
+constexpr int kErrIndex = 1, kErrTimeout = 2;   // bits of the network's error word
+
+__device__ __forceinline__ void store_bf16x16(bf16* dst, const float (&x)[16]) {
+  unsigned w[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    w[j] = (unsigned)__bfloat16_as_ushort(__float2bfloat16(x[2 * j])) |
+           ((unsigned)__bfloat16_as_ushort(__float2bfloat16(x[2 * j + 1])) << 16);
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+__device__ __forceinline__ void store_f32x16(float* dst, const float (&x)[16]) {
+  float4* d = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) d[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+}
+
+// forward layer: Z = acc + bias (FP32 pre-activation); Ab = BF16 of GELU(Z) (hidden layers) and
+// its transpose AbT (training only)
+struct EpiForward {
+  float* Z;
+  int ldz;
   const float* bias;
-  int gelu;
-  int atomic;
+  bf16* Ab;
+  int lda;
+  bf16* AbT;
+  long long ldt;
+  __device__ void operator()(int row, int col0, const float (&acc)[16]) const {
+    float z[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) z[j] = acc[j] + bias[col0 + j];
+    store_f32x16(Z + (long long)row * ldz + col0, z);
+    if (!Ab) return;
+    float a[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = gelu(z[j]);
+    store_bf16x16(Ab + (long long)row * lda + col0, a);
+    if (AbT) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) AbT[(long long)(col0 + j) * ldt + row] = __float2bfloat16(a[j]);
+    }
+  }
 };
 
-constexpr int BM = 64, BN = 64, BK = 32, BKP = BK + 8;
-
-__device__ __forceinline__ unsigned pack2(bf16 lo, bf16 hi) {
-  return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// stage a 64 x 32 tile (rows r, columns k) of a strided operand; the loop order follows the unit
-// stride so that global loads coalesce
-__device__ __forceinline__ void stage_tile(bf16 (*S)[BKP], const bf16* __restrict__ P, long long s_row,
-                                           long long s_k, int row0, int rows, int k0, int K, int tid) {
-  const bf16 zero = __float2bfloat16(0.f);
-  if (s_k == 1) {
-    for (int e = tid; e < 64 * BK; e += 128) {
-      const int r = e / BK, k = e % BK, gr = row0 + r, gk = k0 + k;
-      S[r][k] = (gr < rows && gk < K) ? P[gr * s_row + gk] : zero;
-    }
-  } else {
-    for (int e = tid; e < 64 * BK; e += 128) {
-      const int r = e % 64, k = e / 64, gr = row0 + r, gk = k0 + k;
-      S[r][k] = (gr < rows && gk < K) ? P[gr * s_row + gk * s_k] : zero;
-    }
+// split-K weight gradient: C += acc (C zeroed before the launch)
+struct EpiAtomic {
+  float* C;
+  int ldc;
+  __device__ void operator()(int row, int col0, const float (&acc)[16]) const {
+    float* d = C + (long long)row * ldc + col0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) tc::red_add_v4(d + 4 * q, acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
   }
-}
+};
 
-__global__ void __launch_bounds__(128) k_gemm(GemmArgs G) {
-  __shared__ bf16 As[BM][BKP];
-  __shared__ bf16 Bs[BN][BKP];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1, g = lane >> 2, t = lane & 3;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int kchunks = (G.K + BK - 1) / BK;
-  const int per = (kchunks + gridDim.z - 1) / gridDim.z;
-  const int kc0 = blockIdx.z * per, kc1 = min(kchunks, kc0 + per);
-  float acc[2][4][4];
+// back-propagation through a hidden layer: dZ = (dZ_next W) * GELU'(Z) in FP32, BF16 and
+// transposed BF16
+struct EpiGeluBack {
+  const float* Z;
+  float* dZ;
+  bf16* dZb;
+  int ld;
+  bf16* dZbT;
+  long long ldt;
+  __device__ void operator()(int row, int col0, const float (&acc)[16]) const {
+    const long long o = (long long)row * ld + col0;
+    const float4* zp = reinterpret_cast<const float4*>(Z + o);
+    float d[16];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-  for (int kc = kc0; kc < kc1; ++kc) {
-    stage_tile(As, G.A, G.sAm, G.sAk, m0, G.M, kc * BK, G.K, tid);
-    stage_tile(Bs, G.B, G.sBn, G.sBk, n0, G.N, kc * BK, G.K, tid);
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; kk += 16) {
-      unsigned a[2][4], b[4][2];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int r = wm * 32 + mt * 16 + g;
-        a[mt][0] = pack2(As[r][kk + 2 * t], As[r][kk + 2 * t + 1]);
-        a[mt][1] = pack2(As[r + 8][kk + 2 * t], As[r + 8][kk + 2 * t + 1]);
-        a[mt][2] = pack2(As[r][kk + 2 * t + 8], As[r][kk + 2 * t + 9]);
-        a[mt][3] = pack2(As[r + 8][kk + 2 * t + 8], As[r + 8][kk + 2 * t + 9]);
-      }
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int c = wn * 32 + nt * 8 + g;
-        b[nt][0] = pack2(Bs[c][kk + 2 * t], Bs[c][kk + 2 * t + 1]);
-        b[nt][1] = pack2(Bs[c][kk + 2 * t + 8], Bs[c][kk + 2 * t + 9]);
-      }
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a[mt], b[nt]);
+    for (int q = 0; q < 4; ++q) {
+      const float4 z4 = zp[q];
+      d[4 * q] = acc[4 * q] * gelu_grad(z4.x);
+      d[4 * q + 1] = acc[4 * q + 1] * gelu_grad(z4.y);
+      d[4 * q + 2] = acc[4 * q + 2] * gelu_grad(z4.z);
+      d[4 * q + 3] = acc[4 * q + 3] * gelu_grad(z4.w);
     }
-    __syncthreads();
+    store_f32x16(dZ + o, d);
+    store_bf16x16(dZb + o, d);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) dZbT[(long long)(col0 + j) * ldt + row] = __float2bfloat16(d[j]);
   }
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int m = m0 + wm * 32 + mt * 16 + g + (e >= 2 ? 8 : 0);
-        const int n = n0 + wn * 32 + nt * 8 + 2 * t + (e & 1);
-        if (m >= G.M || n >= G.N) continue;
-        float v = acc[mt][nt][e];
-        if (G.bias && blockIdx.z == 0) v += G.bias[n];
-        if (G.C) {
-          if (G.atomic) atomicAdd(&G.C[m * G.ldc + n], v);
-          else G.C[m * G.ldc + n] = v;
-        }
-        if (G.Cb) G.Cb[m * G.ldcb + n] = __float2bfloat16(G.gelu ? gelu(v) : v);
-      }
-}
+};
 
 // ------------------------------------------------------------------------------------------
 // Element-wise kernels
 // ------------------------------------------------------------------------------------------
-// normalised BF16 input rows (gathered through idx when given); an index outside [0, data_rows)
-// gives a zero row and raises the error flag
+// normalised BF16 input rows (gathered through idx when given), and their transpose XbT
+// ([32][ldt]) when given; an index outside [0, data_rows) gives a zero row and raises the error flag
 __global__ void k_input(int rows, const float* __restrict__ X, long long data_rows, const int* __restrict__ idx,
-                        const float* __restrict__ norm, bf16* __restrict__ Xb, int* err) {
+                        const float* __restrict__ norm, bf16* __restrict__ Xb, bf16* __restrict__ XbT,
+                        long long ldt, int* err) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * kInPad; e += gridDim.x * blockDim.x) {
     const int r = e / kInPad, c = e % kInPad;
     float v = 0.f;
     const long long src = idx ? (long long)idx[r] : r;
     if (src < 0 || src >= data_rows) {
-      if (c == 0) atomicOr(err, 1);
+      if (c == 0) atomicOr(err, kErrIndex);
     } else if (c < kIn) {
       v = (X[src * kIn + c] - norm[kNormInMean + c]) * norm[kNormInIstd + c];
     }
-    Xb[e] = __float2bfloat16(v);
+    const bf16 b = __float2bfloat16(v);
+    Xb[e] = b;
+    if (XbT) XbT[c * ldt + r] = b;
   }
 }
 
@@ -180,10 +160,10 @@ __global__ void k_output(int rows, const float* __restrict__ Z, const float* __r
 }
 
 // MSE on normalised targets: loss = mean (Z - Tn)^2 over rows x 12; dZ = 2 (Z - Tn) / (rows x 12),
-// zero in the padded columns
+// zero in the padded columns (FP32, BF16, and BF16 transposed [16][ldt])
 __global__ void k_loss(int rows, const float* __restrict__ Z, const float* __restrict__ T, long long data_rows,
                        const int* __restrict__ idx, const float* __restrict__ norm, float* __restrict__ dZ,
-                       bf16* __restrict__ dZb, double* loss) {
+                       bf16* __restrict__ dZb, bf16* __restrict__ dZbT, long long ldt, double* loss) {
   __shared__ double sbuf[32];
   double part = 0.0;
   const float scale = 2.f / (float)(rows * kOut);
@@ -199,6 +179,7 @@ __global__ void k_loss(int rows, const float* __restrict__ Z, const float* __res
     }
     dZ[e] = d;
     dZb[e] = __float2bfloat16(d);
+    dZbT[c * ldt + r] = __float2bfloat16(d);
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
   if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = part;
@@ -207,17 +188,6 @@ __global__ void k_loss(int rows, const float* __restrict__ Z, const float* __res
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sbuf[w];
     atomicAdd(loss, s / (double)(rows * kOut));
-  }
-}
-
-// dZ = dA * GELU'(Z) (FP32 and BF16 copies)
-__global__ void k_gelu_back(long long count, const float* __restrict__ dA, const float* __restrict__ Z,
-                            float* __restrict__ dZ, bf16* __restrict__ dZb) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
-       e += (long long)gridDim.x * blockDim.x) {
-    const float d = dA[e] * gelu_grad(Z[e]);
-    dZ[e] = d;
-    dZb[e] = __float2bfloat16(d);
   }
 }
 
@@ -233,11 +203,12 @@ __global__ void k_colsum(int rows, int cols, const float* __restrict__ dZ, float
   atomicAdd(&db[n], s);
 }
 
-// Adam (Kingma and Ba) on FP32 master parameters, refreshing the BF16 copy when given. Padded
-// entries see zero gradients and stay zero.
+// Adam (Kingma and Ba) on FP32 master parameters, refreshing the BF16 copy and its transpose
+// (a [rows x cols] matrix stored [cols][rows]) when given. Padded entries see zero gradients and
+// stay zero.
 __global__ void k_adam(long long count, float* __restrict__ w, const float* __restrict__ grad, float* __restrict__ m,
-                       float* __restrict__ v, bf16* __restrict__ wb, float lr, float b1, float b2, float eps,
-                       float c1, float c2) {
+                       float* __restrict__ v, bf16* __restrict__ wb, bf16* __restrict__ wbT, int rows, int cols,
+                       float lr, float b1, float b2, float eps, float c1, float c2) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
        e += (long long)gridDim.x * blockDim.x) {
     const float gr = grad[e];
@@ -248,13 +219,20 @@ __global__ void k_adam(long long count, float* __restrict__ w, const float* __re
     const float wn = w[e] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
     w[e] = wn;
     if (wb) wb[e] = __float2bfloat16(wn);
+    if (wbT) wbT[(e % cols) * rows + e / cols] = __float2bfloat16(wn);
   }
 }
 
-__global__ void k_to_bf16(long long count, const float* __restrict__ a, bf16* __restrict__ b) {
+// BF16 copy of a [rows x cols] FP32 matrix, and its transpose [cols][rows] when bT is given
+__global__ void k_to_bf16(int rows, int cols, const float* __restrict__ a, bf16* __restrict__ b,
+                          bf16* __restrict__ bT) {
+  const long long count = (long long)rows * cols;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
-       e += (long long)gridDim.x * blockDim.x)
-    b[e] = __float2bfloat16(a[e]);
+       e += (long long)gridDim.x * blockDim.x) {
+    const bf16 h = __float2bfloat16(a[e]);
+    b[e] = h;
+    if (bT) bT[(e % cols) * rows + e / cols] = h;
+  }
 }
 
 // per-column sum and sum of squares (FP64) of a [rows x cols] FP32 matrix; one CTA per column
@@ -342,125 +320,163 @@ __global__ void k_compose(int n_nodes, const double* __restrict__ q, const doubl
 
 // ------------------------------------------------------------------------------------------
 // Fused warm start: features -> normalised BF16 input -> 4 layers -> q + dt v + output, one
-// launch. A CTA takes 32 nodes; activations stay in shared memory (BF16, as the GEMM path stores
-// them), weights are read from L2 (every CTA reads the same 280 KB). Each output element is
-// accumulated over K in the same k16 order and with the same epilogue as k_gemm, so the network
-// output equals the unfused path's.
+// launch. A CTA takes 128 nodes (one per TMEM lane). The activations stay in shared memory as the
+// next layer's A operand (128-byte swizzled K-major tiles, written by the epilogue); each layer's
+// weights arrive by TMA into one shared buffer as soon as the previous layer's MMAs are done, and
+// one thread issues the layer's tcgen05.mma into a 128 x 256 FP32 TMEM accumulator. Every output
+// is accumulated over the same K chunks, in the same order and with the same MMA shapes as the
+// GEMM path (shell_mlp_forward), and finished by the same epilogue arithmetic, so the network
+// output equals that path's.
 // ------------------------------------------------------------------------------------------
-constexpr int kFR = 32;                 // nodes per CTA
-constexpr int kLdX = kInPad + 8;        // padded row strides (bank-conflict-free fragment loads)
-constexpr int kLdA = kHid + 8;
+constexpr int kWarmThreads = 256;                 // 8 warps: TMEM lane quarter w % 4, column half w / 4
+constexpr int kActBytes = 4 * tc::kBM * 128;      // 4 K chunks of 128 rows x 128 bytes
+constexpr int kWgtBytes = 4 * kHid * 128;         // 4 K chunks of 256 rows x 128 bytes
+constexpr size_t kWarmSmem = (size_t)kActBytes + kWgtBytes + 1024;
 
-__device__ __forceinline__ unsigned lds_pair(const bf16* p) { return *reinterpret_cast<const unsigned*>(p); }
-__device__ __forceinline__ unsigned ldg_pair(const bf16* p) { return __ldg(reinterpret_cast<const unsigned*>(p)); }
+struct WarmArgs {
+  int n_nodes, n1, n2, per_u, per_v;
+  const double* q;
+  const double* rest;
+  const double* v;
+  double dt;
+  const float* bias[kLayers];
+  const float* norm;
+  double* warm;
+  int* err;
+  unsigned polls;
+};
 
-__global__ void __launch_bounds__(128)
-k_mlp_warm(int n_nodes, int n1, int n2, int per_u, int per_v, const double* __restrict__ q,
-           const double* __restrict__ rest, const double* __restrict__ v, double dt,
-           const bf16* __restrict__ W0, const bf16* __restrict__ W1, const bf16* __restrict__ W2,
-           const bf16* __restrict__ W3, const float* __restrict__ b0, const float* __restrict__ b1,
-           const float* __restrict__ b2, const float* __restrict__ b3, const float* __restrict__ norm,
-           double* __restrict__ warm) {
-  __shared__ __align__(16) bf16 sX[kFR * kLdX];
-  __shared__ __align__(16) bf16 sA[2][kFR * kLdA];
-  __shared__ float sY[kFR][kOutPad];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
-  const int r0 = blockIdx.x * kFR;
-  // features and normalisation (the arithmetic of k_node_features and k_input)
-  if (tid < kFR) {
+__device__ __forceinline__ uint4 pack_bf16x8(const float* x) {
+  unsigned w[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    w[j] = (unsigned)__bfloat16_as_ushort(__float2bfloat16(x[2 * j])) |
+           ((unsigned)__bfloat16_as_ushort(__float2bfloat16(x[2 * j + 1])) << 16);
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__global__ void __launch_bounds__(kWarmThreads, 1)
+k_mlp_warm(const __grid_constant__ CUtensorMap tw0, const __grid_constant__ CUtensorMap tw1,
+           const __grid_constant__ CUtensorMap tw2, const __grid_constant__ CUtensorMap tw3, WarmArgs A) {
+  extern __shared__ unsigned char warm_smem_raw[];
+  __shared__ __align__(8) uint64_t bar_w, bar_mma;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_abort;
+  volatile int* abort_flag = &s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t raw = tc::smem_addr(warm_smem_raw);
+  const uint32_t act = (raw + 1023u) & ~1023u, wgt = act + kActBytes;
+  unsigned char* act_g = warm_smem_raw + (act - raw);   // generic pointer to the activation tiles
+  const uint32_t bw = tc::smem_addr(&bar_w), bm = tc::smem_addr(&bar_mma);
+  const int r0 = blockIdx.x * tc::kBM;
+  if (tid == 0) {
+    tc::mbar_init(bw, 1);
+    tc::mbar_init(bm, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    s_abort = 0;
+  }
+  if (warp == 0) tc::tmem_alloc<kHid>(tc::smem_addr(&tmem_slot));
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  if (tid == 0) {   // layer-0 weights (K = 32: one 64-column chunk, the rest read as zeros)
+    tc::mbar_arrive_expect_tx(bw, kHid * 128);
+    tc::tma_load_2d(wgt, &tw0, bw, 0, 0);
+  }
+  // layer-0 input rows (the arithmetic of k_node_features and k_input): K chunk 0, columns 32..63 zero
+  if (tid < tc::kBM) {
     const int i = r0 + tid;
     float f[kIn];
-    if (i < n_nodes) node_features_of(i, n1, n2, per_u, per_v, q, rest, v, f);
-    for (int c = 0; c < kInPad; ++c) {
-      float x = 0.f;
-      if (i < n_nodes && c < kIn) x = (f[c] - norm[kNormInMean + c]) * norm[kNormInIstd + c];
-      sX[tid * kLdX + c] = __float2bfloat16(x);
-    }
+    if (i < A.n_nodes) node_features_of(i, A.n1, A.n2, A.per_u, A.per_v, A.q, A.rest, A.v, f);
+    float x[kInPad];
+#pragma unroll
+    for (int c = 0; c < kInPad; ++c)
+      x[c] = (i < A.n_nodes && c < kIn) ? (f[c] - A.norm[kNormInMean + c]) * A.norm[kNormInIstd + c] : 0.f;
+    uint4* row = reinterpret_cast<uint4*>(act_g + tid * 128);
+#pragma unroll
+    for (int p = 0; p < 8; ++p) row[p ^ (tid & 7)] = p < 4 ? pack_bf16x8(x + 8 * p) : make_uint4(0u, 0u, 0u, 0u);
   }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  tc::tc_fence_before();
   __syncthreads();
-  // hidden layers: warp w computes output columns [64 w, 64 w + 64) of all 32 rows
-  const bf16* in = sX;
-  int ldin = kLdX, K = kInPad;
-  for (int l = 0; l < kLayers - 1; ++l) {
-    const bf16* W = l == 0 ? W0 : l == 1 ? W1 : W2;
-    const float* bias = l == 0 ? b0 : l == 1 ? b1 : b2;
-    float acc[2][8][4];
+  tc::tc_fence_after();
+  const int quarter = warp & 3, half = warp >> 2, row = quarter * 32 + lane;
+  const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+  int w_inflight = 0;   // thread 0: the layer whose weight copy is in flight, or -1
+#pragma unroll 1
+  for (int l = 0; l < kLayers; ++l) {
+    const int N = l < kLayers - 1 ? kHid : kOutPad;
+    const int nch = l == 0 ? 1 : kHid / tc::kBK;
+    if (tid == 0) {
+      if (!tc::mbar_wait_parity(bw, l & 1, A.polls)) {
+        *abort_flag = 1;
+      } else {
+        w_inflight = -1;
+        tc::tc_fence_after();
+        const uint32_t idesc = tc::idesc_bf16(tc::kBM, N);
+        for (int c = 0; c < nch; ++c)
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
-    for (int kk = 0; kk < K; kk += 16) {
-      unsigned a[2][4];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const bf16* ar = in + (mt * 16 + g) * ldin + kk + 2 * t;
-        a[mt][0] = lds_pair(ar);
-        a[mt][1] = lds_pair(ar + 8 * ldin);
-        a[mt][2] = lds_pair(ar + 8);
-        a[mt][3] = lds_pair(ar + 8 * ldin + 8);
+          for (int j = 0; j < tc::kBK / 16; ++j)
+            tc::mma_bf16_ss(tmem, tc::smem_desc_sw128(act + c * (tc::kBM * 128) + 32 * j),
+                            tc::smem_desc_sw128(wgt + c * (N * 128) + 32 * j), idesc, c > 0 || j > 0);
       }
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        const bf16* br = W + (size_t)(warp * 64 + nt * 8 + g) * K + kk + 2 * t;
-        const unsigned b[2] = {ldg_pair(br), ldg_pair(br + 8)};
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) mma_bf16(acc[mt][nt], a[mt], b);
-      }
+      tc::mma_commit(bm);
     }
-    bf16* out = sA[l & 1];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int m = mt * 16 + g + (e >= 2 ? 8 : 0);
-          const int n = warp * 64 + nt * 8 + 2 * t + (e & 1);
-          out[m * kLdA + n] = __float2bfloat16(gelu(acc[mt][nt][e] + bias[n]));
-        }
+    if (!tc::mbar_wait_parity(bm, l & 1, A.polls)) *abort_flag = 1;
+    tc::tc_fence_after();
     __syncthreads();
-    in = out;
-    ldin = kLdA;
-    K = kHid;
-  }
-  // output layer (16 padded columns): warps 0 and 1 take 8 columns each
-  if (warp < 2) {
-    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-    for (int kk = 0; kk < kHid; kk += 16) {
-      unsigned a[2][4];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const bf16* ar = in + (mt * 16 + g) * kLdA + kk + 2 * t;
-        a[mt][0] = lds_pair(ar);
-        a[mt][1] = lds_pair(ar + 8 * kLdA);
-        a[mt][2] = lds_pair(ar + 8);
-        a[mt][3] = lds_pair(ar + 8 * kLdA + 8);
-      }
-      const bf16* br = W3 + (size_t)(warp * 8 + g) * kHid + kk + 2 * t;
-      const unsigned b[2] = {ldg_pair(br), ldg_pair(br + 8)};
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) mma_bf16(acc[mt], a[mt], b);
+    if (*abort_flag) break;
+    if (tid == 0 && l + 1 < kLayers) {   // the weight buffer is free: fetch the next layer's
+      const int N1 = l + 1 < kLayers - 1 ? kHid : kOutPad;
+      const CUtensorMap* m = l == 0 ? &tw1 : (l == 1 ? &tw2 : &tw3);
+      tc::mbar_arrive_expect_tx(bw, (kHid / tc::kBK) * N1 * 128);
+      for (int c = 0; c < kHid / tc::kBK; ++c) tc::tma_load_2d(wgt + c * N1 * 128, m, bw, c * tc::kBK, 0);
+      w_inflight = l + 1;
     }
+    const float* bias = A.bias[l];
+    if (l < kLayers - 1) {
+      // epilogue of a hidden layer (the arithmetic of EpiForward): GELU(acc + bias) in BF16,
+      // written over the activations as the next layer's A tiles
+#pragma unroll 1
+      for (int c0 = half * (kHid / 2); c0 < (half + 1) * (kHid / 2); c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
+        float a[16];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int m = mt * 16 + g + (e >= 2 ? 8 : 0);
-        const int n = warp * 8 + 2 * t + (e & 1);
-        sY[m][n] = acc[mt][e] + b3[n];
+        for (int j = 0; j < 16; ++j) a[j] = gelu(v[j] + bias[c0 + j]);
+        unsigned char* rp = act_g + (c0 / tc::kBK) * (tc::kBM * 128) + row * 128;
+        const int p = (c0 % tc::kBK) / 8;
+        *reinterpret_cast<uint4*>(rp + ((p ^ (row & 7)) * 16)) = pack_bf16x8(a);
+        *reinterpret_cast<uint4*>(rp + (((p + 1) ^ (row & 7)) * 16)) = pack_bf16x8(a + 8);
       }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      tc::tc_fence_before();
+      __syncthreads();
+      tc::tc_fence_after();
+    } else if (half == 0) {
+      // output layer: warm = q + dt v + out_std * (acc + bias) + out_mean (k_output, k_compose)
+      float v[16];
+      tc::tmem_ld16(lane_addr, v);
+      const int i = r0 + row;
+      if (i < A.n_nodes) {
+#pragma unroll
+        for (int c = 0; c < kOut; ++c) {
+          const float y = (v[c] + bias[c]) * A.norm[kNormOutStd + c] + A.norm[kNormOutMean + c];
+          const size_t gi = (size_t)i * 12 + c;
+          A.warm[gi] = A.q[gi] + A.dt * A.v[gi] + (double)y;
+        }
+      }
+    }
   }
+  if (tid == 0 && *abort_flag) {
+    atomicOr(A.err, kErrTimeout);
+    // a weight copy still in flight lands in shared memory: wait for it before the CTA exits
+    if (w_inflight >= 0) tc::mbar_wait_parity(bw, w_inflight & 1, A.polls);
+  }
+  tc::tc_fence_before();
   __syncthreads();
-  // warm = q + dt v + out_std * y + out_mean (the arithmetic of k_compose)
-  for (int e = tid; e < kFR * kOut; e += blockDim.x) {
-    const int r = e / kOut, c = e % kOut, i = r0 + r;
-    if (i >= n_nodes) continue;
-    const size_t gi = (size_t)i * 12 + c;
-    const float y = sY[r][c] * norm[kNormOutStd + c] + norm[kNormOutMean + c];
-    warm[gi] = q[gi] + dt * v[gi] + (double)y;
-  }
+  if (warp == 0) tc::tmem_dealloc<kHid>(tmem);
 }
 
 }  // namespace mlp
@@ -481,12 +497,16 @@ struct shell_mlp_s {
   float *W[kLayers] = {}, *b[kLayers] = {}, *gW[kLayers] = {}, *gb[kLayers] = {};
   float *mW[kLayers] = {}, *vW[kLayers] = {}, *mb[kLayers] = {}, *vb[kLayers] = {};
   bf16* Wb[kLayers] = {};
-  // activations of the last forward pass, and their gradients
-  bf16* Xb = nullptr;
+  bf16* WbT[kLayers] = {};   // transposed BF16 weights [fan_in][fan_out] (input-gradient GEMMs)
+  CUtensorMap warm_maps[kLayers];   // TMA maps of Wb for the fused warm start (box 64 x fan-out)
+  // activations of the last forward pass, and their gradients; the *T arrays are transposed
+  // copies [features][ldt] read by the weight-gradient GEMMs
+  long long ldt = 0;         // max_rows rounded up to 8 (16-byte rows for TMA)
+  bf16 *Xb = nullptr, *XbT = nullptr;
   float* Z[kLayers] = {};
-  bf16* Ab[kLayers] = {};
-  float *dZ[kLayers] = {}, *dA = nullptr;
-  bf16* dZb[kLayers] = {};
+  bf16 *Ab[kLayers] = {}, *AbT[kLayers] = {};
+  float* dZ[kLayers] = {};
+  bf16 *dZb[kLayers] = {}, *dZbT[kLayers] = {};
   float* Xraw = nullptr;  // [max_rows x 28] features of a warm-start call
   float* norm = nullptr;  // kNormSize floats
   double* loss = nullptr;
@@ -514,11 +534,11 @@ shell_status malloc_zero(T** p, size_t count, cudaStream_t s) {
 void free_mlp(shell_mlp_s* m) {
   for (int l = 0; l < kLayers; ++l) {
     void* ps[] = {m->W[l], m->b[l], m->gW[l], m->gb[l], m->mW[l], m->vW[l], m->mb[l], m->vb[l], m->Wb[l],
-                  m->Z[l], m->Ab[l], m->dZ[l], m->dZb[l]};
+                  m->WbT[l], m->Z[l], m->Ab[l], m->AbT[l], m->dZ[l], m->dZb[l], m->dZbT[l]};
     for (void* p : ps)
       if (p) cudaFree(p);
   }
-  void* ps[] = {m->Xb, m->dA, m->Xraw, m->norm, m->loss, m->stats, m->err};
+  void* ps[] = {m->Xb, m->XbT, m->Xraw, m->norm, m->loss, m->stats, m->err};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (m->h_loss) cudaFreeHost(m->h_loss);
@@ -528,90 +548,70 @@ void free_mlp(shell_mlp_s* m) {
 
 int eblocks(long long n) { return (int)std::min<long long>(4096, std::max(1LL, (n + 255) / 256)); }
 
-shell_status gemm(shell_mlp_s& M, const GemmArgs& G, int ksplit, cudaStream_t st) {
-  dim3 grid((G.N + BN - 1) / BN, (G.M + BM - 1) / BM, ksplit);
-  k_gemm<<<grid, 128, 0, st>>>(G);
-  BHEM_CUDA(cudaGetLastError());
+// C = A B^T on the tensor cores for A [m][k] (row stride lda) and B [n][k] (row stride ldb), both
+// BF16 with K contiguous; epilogue epi; K split over up to ksplit CTAs per output tile.
+template <int BN, class Epi>
+shell_status tc_gemm(shell_mlp_s& M, const bf16* A, long long lda, const bf16* B, long long ldb, int m, int n, int k,
+                     int ksplit, const Epi& epi, cudaStream_t st) {
+  CUtensorMap ma, mb;
+  if (!tc::encode_bf16_map(&ma, A, m, k, lda, tc::kBM) || !tc::encode_bf16_map(&mb, B, n, k, ldb, BN))
+    return fail(SHELL_ERR_CUDA, "tensor map encoding failed (cuTensorMapEncodeTiled)");
+  const cudaError_t e = tc::launch_gemm_tc<BN, Epi>(ma, mb, m, n, k, ksplit, epi, M.err, kErrTimeout,
+                                                    kDefaultWaitPolls, st);
+  BHEM_CUDA(e);
   ++M.launches;
   return SHELL_OK;
 }
 
-// forward pass of the rows staged in M.Xb: Z_l (FP32 pre-activation), Ab_l (BF16 GELU)
-shell_status forward(shell_mlp_s& M, int rows, cudaStream_t st) {
+// forward pass of the rows staged in M.Xb: Z_l (FP32 pre-activation), Ab_l (BF16 GELU) and, when
+// training, the transposed AbT_l
+shell_status forward(shell_mlp_s& M, int rows, bool training, cudaStream_t st) {
   const bf16* in = M.Xb;
   for (int l = 0; l < kLayers; ++l) {
-    GemmArgs G{};
-    G.M = rows;
-    G.N = kDout[l];
-    G.K = kDin[l];
-    G.A = in;
-    G.sAm = kDin[l];
-    G.sAk = 1;
-    G.B = M.Wb[l];
-    G.sBn = kDin[l];
-    G.sBk = 1;
-    G.C = M.Z[l];
-    G.ldc = kDout[l];
-    G.Cb = l < kLayers - 1 ? M.Ab[l] : nullptr;
-    G.ldcb = kDout[l];
-    G.bias = M.b[l];
-    G.gelu = l < kLayers - 1;
-    BHEM_TRY(gemm(M, G, 1, st));
+    const bool hidden = l < kLayers - 1;
+    const EpiForward e{M.Z[l], kDout[l], M.b[l], hidden ? M.Ab[l] : nullptr, kDout[l],
+                       hidden && training ? M.AbT[l] : nullptr, M.ldt};
+    if (kDout[l] == kHid) BHEM_TRY(tc_gemm<kHid>(M, in, kDin[l], M.Wb[l], kDin[l], rows, kHid, kDin[l], 1, e, st));
+    else BHEM_TRY(tc_gemm<kOutPad>(M, in, kDin[l], M.Wb[l], kDin[l], rows, kOutPad, kDin[l], 1, e, st));
     in = M.Ab[l];
   }
   return SHELL_OK;
 }
 
-// parameter gradients of the loss whose dZ (last layer) k_loss left in M.dZ[3] / M.dZb[3]
+// parameter gradients of the loss whose dZ (last layer) k_loss left in M.dZ[3], M.dZb[3], M.dZbT[3]
 shell_status backward(shell_mlp_s& M, int rows, cudaStream_t st) {
+  int dev = 0, nsm = 0;
+  BHEM_CUDA(cudaGetDevice(&dev));
+  BHEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int kchunks = (rows + tc::kBK - 1) / tc::kBK;
   for (int l = kLayers - 1; l >= 0; --l) {
     BHEM_CUDA(cudaMemsetAsync(M.gW[l], 0, sizeof(float) * kDout[l] * kDin[l], st));
     BHEM_CUDA(cudaMemsetAsync(M.gb[l], 0, sizeof(float) * kDout[l], st));
-    // dW_l = dZ_l^T A_{l-1}
-    GemmArgs G{};
-    G.M = kDout[l];
-    G.N = kDin[l];
-    G.K = rows;
-    G.A = M.dZb[l];
-    G.sAm = 1;
-    G.sAk = kDout[l];
-    G.B = l > 0 ? M.Ab[l - 1] : M.Xb;
-    G.sBn = 1;
-    G.sBk = kDin[l];
-    G.C = M.gW[l];
-    G.ldc = kDin[l];
-    G.atomic = 1;
-    BHEM_TRY(gemm(M, G, std::max(1, std::min(64, rows / 512)), st));
+    // dW_l = dZ_l^T A_{l-1}: M = fan-out, N = fan-in, K = rows, split over about one CTA per SM
+    const bf16* At = l > 0 ? M.AbT[l - 1] : M.XbT;
+    const int tiles = (kDout[l] + tc::kBM - 1) / tc::kBM;
+    const int ksplit = std::max(1, std::min(kchunks, nsm / tiles));
+    const EpiAtomic ea{M.gW[l], kDin[l]};
+    if (kDin[l] == kHid)
+      BHEM_TRY(tc_gemm<kHid>(M, M.dZbT[l], M.ldt, At, M.ldt, kDout[l], kHid, rows, ksplit, ea, st));
+    else
+      BHEM_TRY(tc_gemm<kInPad>(M, M.dZbT[l], M.ldt, At, M.ldt, kDout[l], kInPad, rows, ksplit, ea, st));
     dim3 cg((kDout[l] + 127) / 128, std::min(1024, (rows + 255) / 256));
     k_colsum<<<cg, 128, 0, st>>>(rows, kDout[l], M.dZ[l], M.gb[l]);
     BHEM_CUDA(cudaGetLastError());
     ++M.launches;
     if (l == 0) break;
-    // dA_{l-1} = dZ_l W_l, then dZ_{l-1} = dA_{l-1} GELU'(Z_{l-1})
-    GemmArgs H{};
-    H.M = rows;
-    H.N = kDin[l];
-    H.K = kDout[l];
-    H.A = M.dZb[l];
-    H.sAm = kDout[l];
-    H.sAk = 1;
-    H.B = M.Wb[l];
-    H.sBn = 1;
-    H.sBk = kDin[l];
-    H.C = M.dA;
-    H.ldc = kDin[l];
-    BHEM_TRY(gemm(M, H, 1, st));
-    const long long cnt = (long long)rows * kDout[l - 1];
-    k_gelu_back<<<eblocks(cnt), 256, 0, st>>>(cnt, M.dA, M.Z[l - 1], M.dZ[l - 1], M.dZb[l - 1]);
-    BHEM_CUDA(cudaGetLastError());
-    ++M.launches;
+    // dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1}): M = rows, N = fan-in, K = fan-out
+    const EpiGeluBack eg{M.Z[l - 1], M.dZ[l - 1], M.dZb[l - 1], kDout[l - 1], M.dZbT[l - 1], M.ldt};
+    BHEM_TRY(tc_gemm<kHid>(M, M.dZb[l], kDout[l], M.WbT[l], kDout[l], rows, kHid, kDout[l], 1, eg, st));
   }
   return SHELL_OK;
 }
 
 shell_status stage_input(shell_mlp_s& M, const float* X, long long data_rows, const int* idx, int rows,
-                         cudaStream_t st) {
-  k_input<<<eblocks((long long)rows * kInPad), 256, 0, st>>>(rows, X, data_rows, idx, M.norm, M.Xb, M.err);
+                         bool training, cudaStream_t st) {
+  k_input<<<eblocks((long long)rows * kInPad), 256, 0, st>>>(rows, X, data_rows, idx, M.norm, M.Xb,
+                                                             training ? M.XbT : nullptr, M.ldt, M.err);
   BHEM_CUDA(cudaGetLastError());
   ++M.launches;
   return SHELL_OK;
@@ -623,8 +623,10 @@ shell_status finish(shell_mlp_s& M, double* loss) {
   if (loss) BHEM_CUDA(cudaMemcpyAsync(M.h_loss, M.loss, sizeof(double), cudaMemcpyDeviceToHost, M.stream));
   BHEM_CUDA(cudaStreamSynchronize(M.stream));
   if (*M.h_err) {
+    const int e = *M.h_err;
     BHEM_CUDA(cudaMemsetAsync(M.err, 0, sizeof(int), M.stream));
     BHEM_CUDA(cudaStreamSynchronize(M.stream));
+    if (e & kErrTimeout) return fail(SHELL_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
     return fail(SHELL_ERR_ARG, "row index outside [0, data_rows)");
   }
   if (loss) *loss = *M.h_loss;
@@ -670,8 +672,9 @@ extern "C" shell_status shell_mlp_create(int max_rows, void* stream, shell_mlp_t
   shell_mlp_s* M = new shell_mlp_s();
   M->max_rows = max_rows;
   M->stream = (cudaStream_t)stream;
+  M->ldt = ((long long)max_rows + 7) / 8 * 8;
   shell_status st = SHELL_OK;
-  const size_t R = (size_t)max_rows;
+  const size_t R = (size_t)max_rows, RT = (size_t)M->ldt;
   for (int l = 0; l < kLayers && st == SHELL_OK; ++l) {
     const size_t nw = (size_t)kDout[l] * kDin[l], nb = kDout[l];
     float** f32w[] = {&M->W[l], &M->gW[l], &M->mW[l], &M->vW[l]};
@@ -681,13 +684,16 @@ extern "C" shell_status shell_mlp_create(int max_rows, void* stream, shell_mlp_t
     for (float** p : f32b)
       if (st == SHELL_OK) st = malloc_zero(p, nb, M->stream);
     if (st == SHELL_OK) st = malloc_zero(&M->Wb[l], nw, M->stream);
+    if (st == SHELL_OK && l > 0) st = malloc_zero(&M->WbT[l], nw, M->stream);
     if (st == SHELL_OK) st = malloc_zero(&M->Z[l], R * kDout[l], M->stream);
-    if (st == SHELL_OK) st = malloc_zero(&M->Ab[l], R * kDout[l], M->stream);
+    if (st == SHELL_OK && l < kLayers - 1) st = malloc_zero(&M->Ab[l], R * kDout[l], M->stream);
+    if (st == SHELL_OK && l < kLayers - 1) st = malloc_zero(&M->AbT[l], RT * kDout[l], M->stream);
     if (st == SHELL_OK) st = malloc_zero(&M->dZ[l], R * kDout[l], M->stream);
     if (st == SHELL_OK) st = malloc_zero(&M->dZb[l], R * kDout[l], M->stream);
+    if (st == SHELL_OK) st = malloc_zero(&M->dZbT[l], RT * kDout[l], M->stream);
   }
   if (st == SHELL_OK) st = malloc_zero(&M->Xb, R * kInPad, M->stream);
-  if (st == SHELL_OK) st = malloc_zero(&M->dA, R * kHid, M->stream);
+  if (st == SHELL_OK) st = malloc_zero(&M->XbT, RT * kInPad, M->stream);
   if (st == SHELL_OK) st = malloc_zero(&M->Xraw, R * kIn, M->stream);
   if (st == SHELL_OK) st = malloc_zero(&M->norm, kNormSize, M->stream);
   if (st == SHELL_OK) st = malloc_zero(&M->loss, 1, M->stream);
@@ -698,6 +704,9 @@ extern "C" shell_status shell_mlp_create(int max_rows, void* stream, shell_mlp_t
     cudaGetLastError();
     st = fail(SHELL_ERR_OOM, "cudaMallocHost failed");
   }
+  for (int l = 0; l < kLayers && st == SHELL_OK; ++l)
+    if (!tc::encode_bf16_map(&M->warm_maps[l], M->Wb[l], kDout[l], kDin[l], kDin[l], kDout[l]))
+      st = fail(SHELL_ERR_CUDA, "tensor map encoding failed (cuTensorMapEncodeTiled)");
   if (st == SHELL_OK) {
     // identity normalisation until shell_mlp_set_normalization
     float h[kNormSize] = {};
@@ -735,7 +744,7 @@ extern "C" shell_status shell_mlp_set_params(shell_mlp_t* M, const float* params
   BHEM_TRY(copy_params(*M, nullptr, params, 0));
   for (int l = 0; l < kLayers; ++l) {
     const long long n = (long long)kDout[l] * kDin[l];
-    k_to_bf16<<<eblocks(n), 256, 0, M->stream>>>(n, M->W[l], M->Wb[l]);
+    k_to_bf16<<<eblocks(n), 256, 0, M->stream>>>(kDout[l], kDin[l], M->W[l], M->Wb[l], M->WbT[l]);
     BHEM_CUDA(cudaGetLastError());
     ++M->launches;
     BHEM_CUDA(cudaMemsetAsync(M->mW[l], 0, sizeof(float) * n, M->stream));
@@ -794,8 +803,8 @@ extern "C" shell_status shell_mlp_column_stats(shell_mlp_t* M, const float* X, l
 
 extern "C" shell_status shell_mlp_forward(shell_mlp_t* M, const float* X, int rows, float* Y) {
   if (!M || !X || !Y || rows < 1 || rows > M->max_rows) return fail(SHELL_ERR_ARG, "invalid argument");
-  BHEM_TRY(stage_input(*M, X, rows, nullptr, rows, M->stream));
-  BHEM_TRY(forward(*M, rows, M->stream));
+  BHEM_TRY(stage_input(*M, X, rows, nullptr, rows, false, M->stream));
+  BHEM_TRY(forward(*M, rows, false, M->stream));
   k_output<<<eblocks((long long)rows * kOut), 256, 0, M->stream>>>(rows, M->Z[kLayers - 1], M->norm, Y);
   BHEM_CUDA(cudaGetLastError());
   ++M->launches;
@@ -806,12 +815,12 @@ extern "C" shell_status shell_mlp_gradients(shell_mlp_t* M, const float* X, cons
                                             const int* idx, int rows, double* loss) {
   if (!M || !X || !T || rows < 1 || rows > M->max_rows || data_rows < 1 || (!idx && rows > data_rows))
     return fail(SHELL_ERR_ARG, "invalid argument");
-  BHEM_TRY(stage_input(*M, X, data_rows, idx, rows, M->stream));
-  BHEM_TRY(forward(*M, rows, M->stream));
+  BHEM_TRY(stage_input(*M, X, data_rows, idx, rows, true, M->stream));
+  BHEM_TRY(forward(*M, rows, true, M->stream));
   BHEM_CUDA(cudaMemsetAsync(M->loss, 0, sizeof(double), M->stream));
-  k_loss<<<eblocks((long long)rows * kOutPad), 256, 0, M->stream>>>(rows, M->Z[kLayers - 1], T, data_rows, idx,
-                                                                    M->norm, M->dZ[kLayers - 1],
-                                                                    M->dZb[kLayers - 1], M->loss);
+  k_loss<<<eblocks((long long)rows * kOutPad), 256, 0, M->stream>>>(
+      rows, M->Z[kLayers - 1], T, data_rows, idx, M->norm, M->dZ[kLayers - 1], M->dZb[kLayers - 1],
+      M->dZbT[kLayers - 1], M->ldt, M->loss);
   BHEM_CUDA(cudaGetLastError());
   ++M->launches;
   BHEM_TRY(backward(*M, rows, M->stream));
@@ -826,10 +835,10 @@ extern "C" shell_status shell_mlp_train_step(shell_mlp_t* M, const float* X, con
   const float c1 = 1.f - std::pow(b1, (float)M->step), c2 = 1.f - std::pow(b2, (float)M->step);
   for (int l = 0; l < kLayers; ++l) {
     const long long nw = (long long)kDout[l] * kDin[l];
-    k_adam<<<eblocks(nw), 256, 0, M->stream>>>(nw, M->W[l], M->gW[l], M->mW[l], M->vW[l], M->Wb[l], lr, b1, b2, eps,
-                                               c1, c2);
-    k_adam<<<eblocks(kDout[l]), 256, 0, M->stream>>>(kDout[l], M->b[l], M->gb[l], M->mb[l], M->vb[l], nullptr, lr,
-                                                     b1, b2, eps, c1, c2);
+    k_adam<<<eblocks(nw), 256, 0, M->stream>>>(nw, M->W[l], M->gW[l], M->mW[l], M->vW[l], M->Wb[l], M->WbT[l],
+                                               kDout[l], kDin[l], lr, b1, b2, eps, c1, c2);
+    k_adam<<<eblocks(kDout[l]), 256, 0, M->stream>>>(kDout[l], M->b[l], M->gb[l], M->mb[l], M->vb[l], nullptr,
+                                                     nullptr, 1, kDout[l], lr, b1, b2, eps, c1, c2);
     M->launches += 2;
   }
   BHEM_CUDA(cudaGetLastError());
@@ -871,9 +880,28 @@ extern "C" shell_status shell_mlp_warm_start(shell_mlp_t* M, shell_t* shell, con
     ++s.launches;
     return SHELL_OK;
   }
-  k_mlp_warm<<<(s.n_nodes + kFR - 1) / kFR, 128, 0, s.stream>>>(
-      s.n_nodes, s.n1, s.n2, s.grid.periodic_u, s.grid.periodic_v, q, s.d_rest, v, dt, M->Wb[0], M->Wb[1],
-      M->Wb[2], M->Wb[3], M->b[0], M->b[1], M->b[2], M->b[3], M->norm, warm);
+  static bool attr_set[64] = {false};
+  if (!attr_set[s.device & 63]) {
+    BHEM_CUDA(cudaFuncSetAttribute(k_mlp_warm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarmSmem));
+    attr_set[s.device & 63] = true;
+  }
+  WarmArgs A{};
+  A.n_nodes = s.n_nodes;
+  A.n1 = s.n1;
+  A.n2 = s.n2;
+  A.per_u = s.grid.periodic_u;
+  A.per_v = s.grid.periodic_v;
+  A.q = q;
+  A.rest = s.d_rest;
+  A.v = v;
+  A.dt = dt;
+  for (int l = 0; l < kLayers; ++l) A.bias[l] = M->b[l];
+  A.norm = M->norm;
+  A.warm = warm;
+  A.err = M->err;
+  A.polls = (unsigned)kDefaultWaitPolls;
+  k_mlp_warm<<<(s.n_nodes + tc::kBM - 1) / tc::kBM, kWarmThreads, kWarmSmem, s.stream>>>(
+      M->warm_maps[0], M->warm_maps[1], M->warm_maps[2], M->warm_maps[3], A);
   BHEM_CUDA(cudaGetLastError());
   ++M->launches;
   return SHELL_OK;

@@ -232,9 +232,9 @@ def test_learned_warm_start_gains():
 @pytest.mark.parametrize("grid", [(11, 6), (64, 64)])
 def test_fused_warm_start_matches_gemm_path(grid):
     """shell_mlp_warm_start (one fused launch) against the unfused path: node features ->
-    shell_mlp_forward (tensor-core GEMM kernels) -> q + dt v + y. Both accumulate every output in
-    the same k16 order with the same epilogues, so the network outputs agree to the rounding of
-    the final FP64 sum."""
+    shell_mlp_forward (tensor-core GEMM kernels) -> q + dt v + y. Both issue the same tcgen05 MMAs
+    over the same K chunks in the same order and finish with the same epilogue arithmetic, so the
+    network outputs agree to the rounding of the final FP64 sum."""
     from paper_2312_14839_gb300 import bhem
     g, rest = S.flat_sheet(*grid)
     q = S.noisy(rest, 1e-2, 90).reshape(-1)
