@@ -47,6 +47,9 @@ WORKLOADS = {
                  "seeded rates U[-2,2] deg/step; warm-start MLP 28-256-256-256-12 (BF16, GELU) trained "
                  "on 10,000 steps of the plain solver (50 trajectories x 200 steps); 200 implicit-Euler "
                  "steps of an unseen trajectory, Newton to 1e-8 of the zero-guess residual, PCG to 1e-6",
+    "mlp16384": "warm-start network kernels alone (profiling size): MLP 28-256-256-256-12 (BF16, GELU) on "
+                "seeded N(0,1) features and targets; forward and training step of a 16,384-row batch, fused "
+                "warm start of the 64x64-patch sheet",
     "twist30": "30x30-patch 1 m sheet, centre node held and its x_,1, x_,2 rotated 2 deg per step about +z, "
                "no gravity, dt = 2 ms, 200 implicit-Euler steps to 1e-8 (PCG to 1e-6), mixed precision; "
                "exact Hessian against the pseudo Hessian (App. B)",
@@ -360,6 +363,31 @@ def batch_line(args, steps, warmup, plain_reps):
     }
 
 
+def run_mlp_bench(args):
+    """The warm-start network's kernels alone on seeded synthetic rows (no solver data): the JSON
+    line of network_timing, value = training-step GEMM TFLOP/s."""
+    import torch
+    from paper_2312_14839_gb300 import learned as L
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(7)
+    X = torch.as_tensor(rng.normal(size=(65536, 28)), dtype=torch.float32, device="cuda")
+    T = torch.as_tensor(rng.normal(size=(65536, 12)), dtype=torch.float32, device="cuda")
+    net = L.make_network(16384, 5)
+    with ClockSampler(0) as clk:
+        clk.wait_first()
+        clk.mark()
+        nk = network_timing(net, X, T, reps=max(1, args.steps))
+    net.close()
+    tr = nk["train_step_16384_rows"]
+    line = {"metric": "warm-start network GEMM throughput (training step)", "value": tr["tflops"],
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": max(1, args.steps), "warmup": 3,
+            "ms_per_step": tr["us"] / 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 (FP32 accumulation)", "data": "synthetic (seeded N(0,1) rows)",
+            "config": {"workload": WORKLOADS["mlp16384"], "batch_rows": 16384},
+            "network_kernels": nk, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_learned_bench(args):
     """Learned warm start vs the plain zero-guess Newton (and the inertial predictor) on the
     64x64 corner-twist sheet (one JSON line)."""
@@ -417,9 +445,63 @@ def learned_line(args):
                             "newton_iters_mean": float(data.newton_iters.mean()),
                             "trajectories_stopped_unconverged": data.dropped},
         "gpu_launches": l["launches"], "clocks": clk.summary(),
+        "network_kernels": network_timing(net, data.X, data.T),
     }
     net.close()
     return line
+
+
+# BF16 multiply-adds per row of one forward pass (padded fan-in x fan-out of the 4 layers)
+MLP_MAC_PER_ROW = 32 * 256 + 2 * 256 * 256 + 256 * 16
+
+
+def network_timing(net, X_all, T_all, n_sheet=64, reps=20):
+    """The warm-start network's tensor-core kernels (tcgen05 GEMM, fused warm start) timed with
+    CUDA events on the network's stream after 3 warm-up calls: forward of a 16,384-row batch (four
+    GEMM launches plus the input and output kernels), one training step of that batch (forward,
+    loss, backward, Adam), and the fused warm start of the 64x64 sheet (one launch, 4,225 nodes).
+    Rates are GEMM FLOPs over the whole call, against the measured BF16 peak."""
+    import torch
+    from paper_2312_14839_gb300 import bhem
+    from paper_2312_14839_gb300 import scenes as S
+    rows = 16384
+    X, T = X_all[:rows].contiguous(), T_all[:rows].contiguous()
+    idx = torch.arange(rows, dtype=torch.int32, device=X.device)
+    Y = torch.empty(rows, 12, dtype=torch.float32, device=X.device)
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops") \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps * 1e-3
+
+    def entry(sec, flop):
+        return {"us": sec * 1e6, "gemm_flop": flop, "tflops": flop / sec / 1e12,
+                "frac_of_bf16_peak": flop / sec / 1e12 / peak}
+
+    fwd_flop = 2 * rows * MLP_MAC_PER_ROW
+    train_flop = 2 * rows * (3 * MLP_MAC_PER_ROW - 32 * 256)
+    out = {"forward_16384_rows": entry(timed(lambda: net.forward(X, Y)), fwd_flop),
+           "train_step_16384_rows": entry(timed(lambda: net.train_step(X_all, T_all, idx, 0.0)), train_flop)}
+    g, rest = S.flat_sheet(n_sheet, n_sheet)
+    with bhem.Shell(g, S.SHEET_MATERIAL, rest.reshape(-1)) as sh:
+        q = torch.as_tensor(rest.reshape(-1), dtype=torch.float64, device="cuda")
+        v = torch.zeros_like(q)
+        w = torch.empty_like(q)
+        out["warm_start_64x64"] = entry(timed(lambda: net.warm_start(sh, q, v, 1e-3, w)),
+                                        2 * g.n_nodes * MLP_MAC_PER_ROW)
+    out["peak_source"] = "measured bf16_tflops (MEASURED_PEAKS.json), cuBLAS 8192^3 burst"
+    out["kernels"] = ("k_gemm_tc (tcgen05.mma kind::f16 into TMEM, TMA 128-byte-swizzled operands), "
+                      "k_mlp_warm (fused warm start, same MMA sequence)")
+    return out
 
 
 # Algorithmic work per patch of the two arithmetic-bound kernels (the units are stated in DESIGN):
@@ -928,6 +1010,9 @@ def main():
         return
     if args.workload == "batch512":
         run_batch_bench(args)
+        return
+    if args.workload == "mlp16384":
+        run_mlp_bench(args)
         return
     if args.workload == "learned64":
         run_learned_bench(args)

@@ -362,6 +362,13 @@ SHELL_API shell_status shell_mlp_train_step(shell_mlp_t* mlp, const float* X, co
                                             const int* idx, int rows, float lr, double* loss);
 /* Number of CUDA kernels this network has launched (host counter). */
 SHELL_API shell_status shell_mlp_kernel_launches(const shell_mlp_t* mlp, long long* count);
+/* Bound of the network's device-side waits: every mbarrier wait of its tensor-core kernels (TMA
+   stage arrivals, MMA completion) gives up after `polls` polls (< 0: the default, 2^20; 0: every
+   such wait expires at once). A kernel whose wait expires waits for the copies it issued itself,
+   frees its tensor memory, skips its output and raises an error bit that the next synchronising
+   call of this network (shell_mlp_gradients or shell_mlp_train_step with a loss pointer) returns
+   as SHELL_ERR_TIMEOUT. Synchronises the network's stream. */
+SHELL_API shell_status shell_mlp_set_wait_budget(shell_mlp_t* mlp, int polls);
 /* Node features of a shell state: q, v device [n_dof] FP64; X device [n_nodes x 28] FP32. Runs on
    the shell's stream. */
 SHELL_API shell_status shell_node_features(shell_t* shell, const double* q, const double* v, float* X);

@@ -117,6 +117,7 @@ def load():
                 "shell_mlp_gradients": [p, p, p, ll, p, i, p],
                 "shell_mlp_train_step": [p, p, p, ll, p, i, f, p],
                 "shell_mlp_kernel_launches": [p, p],
+                "shell_mlp_set_wait_budget": [p, C.c_int],
                 "shell_node_features": [p, p, p, p],
                 "shell_warm_targets": [ll, p, p, p, d, p, p],
                 "shell_mlp_warm_start": [p, p, p, p, d, p],
@@ -514,6 +515,10 @@ class Mlp:
         n = C.c_longlong()
         _check(load().shell_mlp_kernel_launches(self._h, C.byref(n)))
         return n.value
+
+    def set_wait_budget(self, polls: int) -> None:
+        """Bound of the tensor-core kernels' device-side waits (< 0: default; 0: every wait expires)."""
+        _check(load().shell_mlp_set_wait_budget(self._h, int(polls)))
 
     def warm_start(self, shell, q, v, dt, warm=None):
         """q + dt v + network(features) for a shell state (FP64 CUDA tensors), on the shell's stream."""

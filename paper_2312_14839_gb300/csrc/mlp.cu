@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -39,92 +40,58 @@ __device__ __forceinline__ float gelu_grad(float x) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Epilogues of the tensor-core GEMM (tc_gemm.cuh): called per row with 16 consecutive FP32
-// accumulator columns; every N here is a multiple of 16. A transposed BF16 copy ([column][row],
-// row stride ldt) is what the weight-gradient GEMMs read as their K-contiguous operands.
+// Epilogues of the tensor-core GEMM (tc_gemm.cuh): per row and 16 accumulator columns, the values
+// of the FP32 output channel (f) and of the BF16 channels (b: row-major and transposed). A
+// transposed BF16 copy ([column][row], row stride ldt) is what the weight-gradient GEMMs read as
+// their K-contiguous operands.
 // ------------------------------------------------------------------------------------------
 constexpr int kErrIndex = 1, kErrTimeout = 2;   // bits of the network's error word
 
-__device__ __forceinline__ void store_bf16x16(bf16* dst, const float (&x)[16]) {
-  unsigned w[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j)
-    w[j] = (unsigned)__bfloat16_as_ushort(__float2bfloat16(x[2 * j])) |
-           ((unsigned)__bfloat16_as_ushort(__float2bfloat16(x[2 * j + 1])) << 16);
-  uint4* d = reinterpret_cast<uint4*>(dst);
-  d[0] = make_uint4(w[0], w[1], w[2], w[3]);
-  d[1] = make_uint4(w[4], w[5], w[6], w[7]);
-}
-
-__device__ __forceinline__ void store_f32x16(float* dst, const float (&x)[16]) {
-  float4* d = reinterpret_cast<float4*>(dst);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) d[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
-}
-
-// forward layer: Z = acc + bias (FP32 pre-activation); Ab = BF16 of GELU(Z) (hidden layers) and
-// its transpose AbT (training only)
+// forward layer: Z = acc + bias (FP32 pre-activation; bias = the per-column vector) and, for a
+// hidden layer, GELU(Z) for the BF16 channels
 struct EpiForward {
-  float* Z;
-  int ldz;
-  const float* bias;
-  bf16* Ab;
-  int lda;
-  bf16* AbT;
-  long long ldt;
-  __device__ void operator()(int row, int col0, const float (&acc)[16]) const {
-    float z[16];
+  int hidden;
+  __device__ void operator()(int, int, const float* bias, const float (&acc)[16], float (&f)[16],
+                             float (&b)[16]) const {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) z[j] = acc[j] + bias[col0 + j];
-    store_f32x16(Z + (long long)row * ldz + col0, z);
-    if (!Ab) return;
-    float a[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) a[j] = gelu(z[j]);
-    store_bf16x16(Ab + (long long)row * lda + col0, a);
-    if (AbT) {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) AbT[(long long)(col0 + j) * ldt + row] = __float2bfloat16(a[j]);
+    for (int j = 0; j < 16; ++j) {
+      f[j] = acc[j] + bias[j];
+      b[j] = hidden ? gelu(f[j]) : f[j];
     }
   }
 };
 
-// split-K weight gradient: C += acc (C zeroed before the launch)
+// split-K weight gradient: the FP32 channel adds acc into the zeroed gradient
 struct EpiAtomic {
-  float* C;
-  int ldc;
-  __device__ void operator()(int row, int col0, const float (&acc)[16]) const {
-    float* d = C + (long long)row * ldc + col0;
+  __device__ void operator()(int, int, const float*, const float (&acc)[16], float (&f)[16], float (&b)[16]) const {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) tc::red_add_v4(d + 4 * q, acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    for (int j = 0; j < 16; ++j) f[j] = b[j] = acc[j];
   }
 };
 
-// back-propagation through a hidden layer: dZ = (dZ_next W) * GELU'(Z) in FP32, BF16 and
-// transposed BF16
+// back-propagation through a hidden layer: dZ = (dZ_next W) * GELU'(Z), for all three channels
 struct EpiGeluBack {
   const float* Z;
-  float* dZ;
-  bf16* dZb;
   int ld;
-  bf16* dZbT;
-  long long ldt;
-  __device__ void operator()(int row, int col0, const float (&acc)[16]) const {
-    const long long o = (long long)row * ld + col0;
-    const float4* zp = reinterpret_cast<const float4*>(Z + o);
-    float d[16];
+  int rows;
+  __device__ void operator()(int row, int col0, const float*, const float (&acc)[16], float (&f)[16],
+                             float (&b)[16]) const {
+    if (row >= rows) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) f[j] = b[j] = 0.f;
+      return;
+    }
+    const float4* zp = reinterpret_cast<const float4*>(Z + (long long)row * ld + col0);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float4 z4 = zp[q];
-      d[4 * q] = acc[4 * q] * gelu_grad(z4.x);
-      d[4 * q + 1] = acc[4 * q + 1] * gelu_grad(z4.y);
-      d[4 * q + 2] = acc[4 * q + 2] * gelu_grad(z4.z);
-      d[4 * q + 3] = acc[4 * q + 3] * gelu_grad(z4.w);
+      f[4 * q] = acc[4 * q] * gelu_grad(z4.x);
+      f[4 * q + 1] = acc[4 * q + 1] * gelu_grad(z4.y);
+      f[4 * q + 2] = acc[4 * q + 2] * gelu_grad(z4.z);
+      f[4 * q + 3] = acc[4 * q + 3] * gelu_grad(z4.w);
     }
-    store_f32x16(dZ + o, d);
-    store_bf16x16(dZb + o, d);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) dZbT[(long long)(col0 + j) * ldt + row] = __float2bfloat16(d[j]);
+    for (int j = 0; j < 16; ++j) b[j] = f[j];
   }
 };
 
@@ -191,35 +158,55 @@ __global__ void k_loss(int rows, const float* __restrict__ Z, const float* __res
   }
 }
 
-// db[n] += sum over rows of dZ[r][n]; CTA row y sums the 256-row slabs y, y + gridDim.y, ...
+// db[n] += sum over rows of dZ[r][n]: CTA (x, y) takes columns 128 x .. 128 x + 127 of the
+// 64-row slab y, with eight independent partial sums per thread (eight loads in flight), then one
+// atomic per column
+constexpr int kColsumRows = 64;
+
 __global__ void k_colsum(int rows, int cols, const float* __restrict__ dZ, float* __restrict__ db) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= cols) return;
-  float s = 0.f;
-  for (int r0 = blockIdx.y * 256; r0 < rows; r0 += gridDim.y * 256) {
-    const int r1 = min(rows, r0 + 256);
-    for (int r = r0; r < r1; ++r) s += dZ[(long long)r * cols + n];
-  }
-  atomicAdd(&db[n], s);
+  const int r0 = blockIdx.y * kColsumRows, r1 = min(rows, r0 + kColsumRows);
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int r = r0;
+  for (; r + 8 <= r1; r += 8)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] += dZ[(long long)(r + j) * cols + n];
+  for (; r < r1; ++r) acc[0] += dZ[(long long)r * cols + n];
+  atomicAdd(&db[n], ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7])));
 }
 
-// Adam (Kingma and Ba) on FP32 master parameters, refreshing the BF16 copy and its transpose
-// (a [rows x cols] matrix stored [cols][rows]) when given. Padded entries see zero gradients and
-// stay zero.
-__global__ void k_adam(long long count, float* __restrict__ w, const float* __restrict__ grad, float* __restrict__ m,
-                       float* __restrict__ v, bf16* __restrict__ wb, bf16* __restrict__ wbT, int rows, int cols,
-                       float lr, float b1, float b2, float eps, float c1, float c2) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+// Adam (Kingma and Ba) on the FP32 master parameters of every tensor of the network in one launch,
+// refreshing a tensor's BF16 copy and its transpose (a [rows x cols] matrix stored [cols][rows])
+// where given. Padded entries see zero gradients and stay zero.
+constexpr int kAdamTensors = 2 * kLayers;
+struct AdamSet {
+  float* w[kAdamTensors];
+  const float* g[kAdamTensors];
+  float* m[kAdamTensors];
+  float* v[kAdamTensors];
+  bf16* wb[kAdamTensors];
+  bf16* wbT[kAdamTensors];
+  int rows[kAdamTensors], cols[kAdamTensors];
+  long long end[kAdamTensors];   // cumulative element counts
+};
+
+__global__ void k_adam(AdamSet S, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const long long total = S.end[kAdamTensors - 1];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const float gr = grad[e];
-    const float mm = b1 * m[e] + (1.f - b1) * gr;
-    const float vv = b2 * v[e] + (1.f - b2) * gr * gr;
-    m[e] = mm;
-    v[e] = vv;
-    const float wn = w[e] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
-    w[e] = wn;
-    if (wb) wb[e] = __float2bfloat16(wn);
-    if (wbT) wbT[(e % cols) * rows + e / cols] = __float2bfloat16(wn);
+    int t = 0;
+    while (e >= S.end[t]) ++t;
+    const long long i = e - (t ? S.end[t - 1] : 0);
+    const float gr = S.g[t][i];
+    const float mm = b1 * S.m[t][i] + (1.f - b1) * gr;
+    const float vv = b2 * S.v[t][i] + (1.f - b2) * gr * gr;
+    S.m[t][i] = mm;
+    S.v[t][i] = vv;
+    const float wn = S.w[t][i] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+    S.w[t][i] = wn;
+    if (S.wb[t]) S.wb[t][i] = __float2bfloat16(wn);
+    if (S.wbT[t]) S.wbT[t][(i % S.cols[t]) * S.rows[t] + i / S.cols[t]] = __float2bfloat16(wn);
   }
 }
 
@@ -328,7 +315,7 @@ __global__ void k_compose(int n_nodes, const double* __restrict__ q, const doubl
 // GEMM path (shell_mlp_forward), and finished by the same epilogue arithmetic, so the network
 // output equals that path's.
 // ------------------------------------------------------------------------------------------
-constexpr int kWarmThreads = 256;                 // 8 warps: TMEM lane quarter w % 4, column half w / 4
+constexpr int kWarmThreads = 512;                 // 16 warps: TMEM lane quarter w % 4, column part w / 4
 constexpr int kActBytes = 4 * tc::kBM * 128;      // 4 K chunks of 128 rows x 128 bytes
 constexpr int kWgtBytes = 4 * kHid * 128;         // 4 K chunks of 256 rows x 128 bytes
 constexpr size_t kWarmSmem = (size_t)kActBytes + kWgtBytes + 1024;
@@ -401,11 +388,12 @@ k_mlp_warm(const __grid_constant__ CUtensorMap tw0, const __grid_constant__ CUte
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  const int quarter = warp & 3, half = warp >> 2, row = quarter * 32 + lane;
+  const int quarter = warp & 3, part = warp >> 2, row = quarter * 32 + lane;
   const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
   int w_inflight = 0;   // thread 0: the layer whose weight copy is in flight, or -1
+  int l = 0;
 #pragma unroll 1
-  for (int l = 0; l < kLayers; ++l) {
+  for (; l < kLayers; ++l) {
     const int N = l < kLayers - 1 ? kHid : kOutPad;
     const int nch = l == 0 ? 1 : kHid / tc::kBK;
     if (tid == 0) {
@@ -439,7 +427,7 @@ k_mlp_warm(const __grid_constant__ CUtensorMap tw0, const __grid_constant__ CUte
       // epilogue of a hidden layer (the arithmetic of EpiForward): GELU(acc + bias) in BF16,
       // written over the activations as the next layer's A tiles
 #pragma unroll 1
-      for (int c0 = half * (kHid / 2); c0 < (half + 1) * (kHid / 2); c0 += 16) {
+      for (int c0 = part * (kHid / 4); c0 < (part + 1) * (kHid / 4); c0 += 16) {
         float v[16];
         tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
         float a[16];
@@ -454,7 +442,7 @@ k_mlp_warm(const __grid_constant__ CUtensorMap tw0, const __grid_constant__ CUte
       tc::tc_fence_before();
       __syncthreads();
       tc::tc_fence_after();
-    } else if (half == 0) {
+    } else if (part == 0) {
       // output layer: warm = q + dt v + out_std * (acc + bias) + out_mean (k_output, k_compose)
       float v[16];
       tc::tmem_ld16(lane_addr, v);
@@ -471,8 +459,10 @@ k_mlp_warm(const __grid_constant__ CUtensorMap tw0, const __grid_constant__ CUte
   }
   if (tid == 0 && *abort_flag) {
     atomicOr(A.err, kErrTimeout);
-    // a weight copy still in flight lands in shared memory: wait for it before the CTA exits
-    if (w_inflight >= 0) tc::mbar_wait_parity(bw, w_inflight & 1, A.polls);
+    // a weight copy still in flight, and the commit of the stopped layer, land in shared memory:
+    // wait for them before the CTA exits
+    if (w_inflight >= 0) tc::mbar_wait_parity(bw, w_inflight & 1, tc::kDrainPolls);
+    tc::mbar_wait_parity(bm, l & 1, tc::kDrainPolls);
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -491,6 +481,7 @@ using namespace bhem::mlp;
 struct shell_mlp_s {
   int max_rows = 0;
   cudaStream_t stream = nullptr;
+  unsigned wait_polls = (unsigned)kDefaultWaitPolls;   // bound of the tensor-core pipeline waits
   long long launches = 0;
   int step = 0;
   // parameters (padded; FP32 master copies, BF16 copies for the GEMMs), Adam moments, gradients
@@ -548,16 +539,47 @@ void free_mlp(shell_mlp_s* m) {
 
 int eblocks(long long n) { return (int)std::min<long long>(4096, std::max(1LL, (n + 255) / 256)); }
 
+// N tile of the 256-column GEMMs: 128 columns, so that two CTAs share an SM
+constexpr int kTileN = 128;
+
+// Outputs of one GEMM (any may be null): FP32 (stored, or added for split K), BF16 row-major,
+// BF16 transposed; colvec: the per-column vector handed to the epilogue.
+struct GemmOut {
+  float* f32 = nullptr;
+  long long ldf = 0;
+  bool add = false;
+  bf16* b16 = nullptr;
+  long long ldb = 0;
+  bf16* b16t = nullptr;
+  long long ldt = 0;
+  const float* colvec = nullptr;
+};
+
 // C = A B^T on the tensor cores for A [m][k] (row stride lda) and B [n][k] (row stride ldb), both
-// BF16 with K contiguous; epilogue epi; K split over up to ksplit CTAs per output tile.
+// BF16 with K contiguous; K split over up to ksplit CTAs per output tile.
 template <int BN, class Epi>
 shell_status tc_gemm(shell_mlp_s& M, const bf16* A, long long lda, const bf16* B, long long ldb, int m, int n, int k,
-                     int ksplit, const Epi& epi, cudaStream_t st) {
+                     int ksplit, const GemmOut& o, const Epi& epi, cudaStream_t st) {
   CUtensorMap ma, mb;
-  if (!tc::encode_bf16_map(&ma, A, m, k, lda, tc::kBM) || !tc::encode_bf16_map(&mb, B, n, k, ldb, BN))
-    return fail(SHELL_ERR_CUDA, "tensor map encoding failed (cuTensorMapEncodeTiled)");
-  const cudaError_t e = tc::launch_gemm_tc<BN, Epi>(ma, mb, m, n, k, ksplit, epi, M.err, kErrTimeout,
-                                                    kDefaultWaitPolls, st);
+  tc::TcOut out;
+  std::memset(&out, 0, sizeof(out));
+  int mask = 0;
+  bool ok = tc::encode_bf16_map(&ma, A, m, k, lda, tc::kBM) && tc::encode_bf16_map(&mb, B, n, k, ldb, BN);
+  if (o.f32) {
+    ok = ok && tc::encode_out_f32(&out.f32, o.f32, m, n, o.ldf);
+    mask |= o.add ? tc::kOutF32Add : tc::kOutF32;
+  }
+  if (o.b16) {
+    ok = ok && tc::encode_out_b16(&out.b16, o.b16, m, n, o.ldb);
+    mask |= tc::kOutB16;
+  }
+  if (o.b16t) {
+    ok = ok && tc::encode_out_b16t(&out.b16t, o.b16t, n, m, o.ldt);
+    mask |= tc::kOutB16T;
+  }
+  if (!ok) return fail(SHELL_ERR_CUDA, "tensor map encoding failed (cuTensorMapEncodeTiled)");
+  const cudaError_t e = tc::launch_gemm_tc<BN, Epi>(ma, mb, out, mask, o.colvec, m, n, k, ksplit, epi, M.err,
+                                                    kErrTimeout, M.wait_polls, st);
   BHEM_CUDA(e);
   ++M.launches;
   return SHELL_OK;
@@ -569,10 +591,21 @@ shell_status forward(shell_mlp_s& M, int rows, bool training, cudaStream_t st) {
   const bf16* in = M.Xb;
   for (int l = 0; l < kLayers; ++l) {
     const bool hidden = l < kLayers - 1;
-    const EpiForward e{M.Z[l], kDout[l], M.b[l], hidden ? M.Ab[l] : nullptr, kDout[l],
-                       hidden && training ? M.AbT[l] : nullptr, M.ldt};
-    if (kDout[l] == kHid) BHEM_TRY(tc_gemm<kHid>(M, in, kDin[l], M.Wb[l], kDin[l], rows, kHid, kDin[l], 1, e, st));
-    else BHEM_TRY(tc_gemm<kOutPad>(M, in, kDin[l], M.Wb[l], kDin[l], rows, kOutPad, kDin[l], 1, e, st));
+    GemmOut o;
+    o.f32 = M.Z[l];
+    o.ldf = kDout[l];
+    o.colvec = M.b[l];
+    if (hidden) {
+      o.b16 = M.Ab[l];
+      o.ldb = kDout[l];
+      if (training) {
+        o.b16t = M.AbT[l];
+        o.ldt = M.ldt;
+      }
+    }
+    const EpiForward e{hidden ? 1 : 0};
+    if (kDout[l] == kHid) BHEM_TRY(tc_gemm<kTileN>(M, in, kDin[l], M.Wb[l], kDin[l], rows, kHid, kDin[l], 1, o, e, st));
+    else BHEM_TRY(tc_gemm<kOutPad>(M, in, kDin[l], M.Wb[l], kDin[l], rows, kOutPad, kDin[l], 1, o, e, st));
     in = M.Ab[l];
   }
   return SHELL_OK;
@@ -589,21 +622,32 @@ shell_status backward(shell_mlp_s& M, int rows, cudaStream_t st) {
     BHEM_CUDA(cudaMemsetAsync(M.gb[l], 0, sizeof(float) * kDout[l], st));
     // dW_l = dZ_l^T A_{l-1}: M = fan-out, N = fan-in, K = rows, split over about one CTA per SM
     const bf16* At = l > 0 ? M.AbT[l - 1] : M.XbT;
-    const int tiles = (kDout[l] + tc::kBM - 1) / tc::kBM;
-    const int ksplit = std::max(1, std::min(kchunks, nsm / tiles));
-    const EpiAtomic ea{M.gW[l], kDin[l]};
+    const int tiles = (kDout[l] + tc::kBM - 1) / tc::kBM * (kDin[l] == kHid ? kHid / kTileN : 1);
+    const int ksplit = std::max(1, std::min(kchunks, 2 * nsm / tiles));
+    GemmOut ow;
+    ow.f32 = M.gW[l];
+    ow.ldf = kDin[l];
+    ow.add = true;
+    const EpiAtomic ea{};
     if (kDin[l] == kHid)
-      BHEM_TRY(tc_gemm<kHid>(M, M.dZbT[l], M.ldt, At, M.ldt, kDout[l], kHid, rows, ksplit, ea, st));
+      BHEM_TRY(tc_gemm<kTileN>(M, M.dZbT[l], M.ldt, At, M.ldt, kDout[l], kHid, rows, ksplit, ow, ea, st));
     else
-      BHEM_TRY(tc_gemm<kInPad>(M, M.dZbT[l], M.ldt, At, M.ldt, kDout[l], kInPad, rows, ksplit, ea, st));
-    dim3 cg((kDout[l] + 127) / 128, std::min(1024, (rows + 255) / 256));
+      BHEM_TRY(tc_gemm<kInPad>(M, M.dZbT[l], M.ldt, At, M.ldt, kDout[l], kInPad, rows, ksplit, ow, ea, st));
+    dim3 cg((kDout[l] + 127) / 128, (rows + kColsumRows - 1) / kColsumRows);
     k_colsum<<<cg, 128, 0, st>>>(rows, kDout[l], M.dZ[l], M.gb[l]);
     BHEM_CUDA(cudaGetLastError());
     ++M.launches;
     if (l == 0) break;
     // dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1}): M = rows, N = fan-in, K = fan-out
-    const EpiGeluBack eg{M.Z[l - 1], M.dZ[l - 1], M.dZb[l - 1], kDout[l - 1], M.dZbT[l - 1], M.ldt};
-    BHEM_TRY(tc_gemm<kHid>(M, M.dZb[l], kDout[l], M.WbT[l], kDout[l], rows, kHid, kDout[l], 1, eg, st));
+    GemmOut og;
+    og.f32 = M.dZ[l - 1];
+    og.ldf = kDout[l - 1];
+    og.b16 = M.dZb[l - 1];
+    og.ldb = kDout[l - 1];
+    og.b16t = M.dZbT[l - 1];
+    og.ldt = M.ldt;
+    const EpiGeluBack eg{M.Z[l - 1], kDout[l - 1], rows};
+    BHEM_TRY(tc_gemm<kTileN>(M, M.dZb[l], kDout[l], M.WbT[l], kDout[l], rows, kHid, kDout[l], 1, og, eg, st));
   }
   return SHELL_OK;
 }
@@ -833,16 +877,38 @@ extern "C" shell_status shell_mlp_train_step(shell_mlp_t* M, const float* X, con
   M->step += 1;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const float c1 = 1.f - std::pow(b1, (float)M->step), c2 = 1.f - std::pow(b2, (float)M->step);
+  AdamSet S{};
+  long long end = 0;
   for (int l = 0; l < kLayers; ++l) {
-    const long long nw = (long long)kDout[l] * kDin[l];
-    k_adam<<<eblocks(nw), 256, 0, M->stream>>>(nw, M->W[l], M->gW[l], M->mW[l], M->vW[l], M->Wb[l], M->WbT[l],
-                                               kDout[l], kDin[l], lr, b1, b2, eps, c1, c2);
-    k_adam<<<eblocks(kDout[l]), 256, 0, M->stream>>>(kDout[l], M->b[l], M->gb[l], M->mb[l], M->vb[l], nullptr,
-                                                     nullptr, 1, kDout[l], lr, b1, b2, eps, c1, c2);
-    M->launches += 2;
+    const int t = 2 * l;   // weights, then bias
+    S.w[t] = M->W[l];
+    S.g[t] = M->gW[l];
+    S.m[t] = M->mW[l];
+    S.v[t] = M->vW[l];
+    S.wb[t] = M->Wb[l];
+    S.wbT[t] = M->WbT[l];
+    S.rows[t] = kDout[l];
+    S.cols[t] = kDin[l];
+    S.end[t] = end += (long long)kDout[l] * kDin[l];
+    S.w[t + 1] = M->b[l];
+    S.g[t + 1] = M->gb[l];
+    S.m[t + 1] = M->mb[l];
+    S.v[t + 1] = M->vb[l];
+    S.rows[t + 1] = 1;
+    S.cols[t + 1] = kDout[l];
+    S.end[t + 1] = end += kDout[l];
   }
+  k_adam<<<eblocks(end), 256, 0, M->stream>>>(S, lr, b1, b2, eps, c1, c2);
+  ++M->launches;
   BHEM_CUDA(cudaGetLastError());
   return loss ? finish(*M, loss) : SHELL_OK;
+}
+
+extern "C" shell_status shell_mlp_set_wait_budget(shell_mlp_t* M, int polls) {
+  if (!M) return fail(SHELL_ERR_ARG, "NULL argument");
+  BHEM_CUDA(cudaStreamSynchronize(M->stream));
+  M->wait_polls = polls < 0 ? (unsigned)kDefaultWaitPolls : (unsigned)polls;
+  return SHELL_OK;
 }
 
 extern "C" shell_status shell_mlp_kernel_launches(const shell_mlp_t* M, long long* count) {
@@ -899,7 +965,7 @@ extern "C" shell_status shell_mlp_warm_start(shell_mlp_t* M, shell_t* shell, con
   A.norm = M->norm;
   A.warm = warm;
   A.err = M->err;
-  A.polls = (unsigned)kDefaultWaitPolls;
+  A.polls = M->wait_polls;
   k_mlp_warm<<<(s.n_nodes + tc::kBM - 1) / tc::kBM, kWarmThreads, kWarmSmem, s.stream>>>(
       M->warm_maps[0], M->warm_maps[1], M->warm_maps[2], M->warm_maps[3], A);
   BHEM_CUDA(cudaGetLastError());

@@ -13,7 +13,9 @@
 // Pipeline (per CTA): thread 0 issues the TMA copies of up to S K chunks ahead (one mbarrier per
 // stage counts the bytes), thread 32 waits for each stage, issues its four MMAs and commits them
 // to the stage's "empty" mbarrier, which releases the stage to the producer. A final commit
-// signals the epilogue. Every wait is bounded: on expiry the CTA raises an error bit, waits
+// signals the epilogue, which all 8 warps share. With 128-column tiles two CTAs fit an SM, so one
+// CTA's epilogue (latency-bound: TMEM loads, staging stores, proxy fences, TMA store issue)
+// overlaps the other's loads and MMAs. Every wait is bounded: on expiry the CTA raises an error bit, waits
 // (bounded) for the copies it issued, skips the epilogue, frees its TMEM and returns.
 #pragma once
 
@@ -27,7 +29,11 @@ namespace bhem {
 namespace tc {
 
 constexpr int kBM = 128;          // rows per CTA tile (TMEM lanes)
+constexpr int kThreads = 256;     // 8 warps: warp w reads TMEM lanes 32 (w % 4) .. + 31, column part w / 4
 constexpr int kBK = 64;           // K columns per pipeline stage (four MMAs of K = 16), 128 bytes
+// Budget of the waits that drain a CTA's own copies after another wait expired: those copies are
+// bound to land, so they get the full budget whatever the caller's.
+constexpr unsigned kDrainPolls = 1u << 20;
 
 // ---------------------------------------------------------------------------------------------
 // PTX wrappers
@@ -106,23 +112,45 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
 // 16 consecutive FP32 accumulator columns of this thread's TMEM lane (warp w reads lanes
-// 32 w .. 32 w + 31); all lanes of the warp must execute it.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
+// 32 (w % 4) .. + 31), without waiting; all lanes of the warp must execute it.
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  tmem_ld16_async(taddr, r);
+  tmem_ld_wait();
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ void red_add_v4(float* dst, float a, float b, float c, float d) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(dst), "f"(a), "f"(b), "f"(c), "f"(d)
+// TMA tensor stores from shared memory (bulk groups): plain, and element-wise atomic FP32 add
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(src)
                : "memory");
 }
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
+  asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// all but the newest N groups have finished reading shared memory
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(N) : "memory");
+}
+// every group has completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------------------------------------
 // The kernel
@@ -134,7 +162,17 @@ struct TcShape {
   unsigned polls;         // bound of every mbarrier wait
   int* err;               // error word; err_bit is raised when a wait expires
   int err_bit;
+  int out_mask;           // TcOutChannel bits: which outputs the epilogue writes
+  const float* colvec;    // optional per-column vector [N] handed to the epilogue (e.g. a bias)
 };
+
+// Outputs of the epilogue, written by TMA tensor stores from per-warp shared-memory tiles of
+// 32 rows x 16 columns: FP32 [M][N] (stored, or added atomically for split K), BF16 [M][N], and
+// BF16 transposed [N][M]. Maps from encode_out_map (boxes 16 x 32, and 32 x 16 transposed).
+struct TcOut {
+  CUtensorMap f32, b16, b16t;
+};
+enum TcOutChannel : int { kOutF32 = 1, kOutF32Add = 2, kOutB16 = 4, kOutB16T = 8 };
 
 template <int BN>
 struct TcCfg {
@@ -144,15 +182,30 @@ struct TcCfg {
   static constexpr int kBytesB = BN * kBK * 2;
   static constexpr int kStage = kBytesA + kBytesB;
   static constexpr int kTmemCols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
-  static constexpr size_t kSmem = (size_t)kStages * kStage + 1024;   // + slack to align the base
   static_assert(kStage % 1024 == 0, "every operand tile starts on a 1024-byte swizzle atom");
+  // epilogue: the four warps of a TMEM lane quarter split the columns into kParts parts of whole
+  // 16-column groups; each epilogue warp stages two 4 KB slots in the freed operand stages
+  static constexpr int kMaxParts = kThreads / 128;
+  static constexpr int kParts = BN / 16 < kMaxParts ? BN / 16 : kMaxParts;
+  static constexpr int kPartCols = BN / kParts;
+  static_assert(kPartCols % 16 == 0, "column parts of whole 16-column TMEM loads");
+  static constexpr int kStageWarp = 2 * 4096;
+  static constexpr size_t kPipeBytes = (size_t)kStages * kStage;
+  static constexpr size_t kEpiBytes = (size_t)kParts * 4 * kStageWarp;
+  static constexpr size_t kSmem = (kPipeBytes > kEpiBytes ? kPipeBytes : kEpiBytes) + 1024;   // + base alignment
 };
 
-// Epi: a functor with __device__ void operator()(int row, int col0, const float (&acc)[16]) const,
-// called for every valid row and every 16-column group col0 < N of the CTA's tile.
+// Epi: a functor with
+//   __device__ void operator()(int row, int col0, const float* colvec, const float (&acc)[16],
+//                              float (&f32)[16], float (&b16)[16]) const
+// that turns accumulator columns col0 .. col0 + 15 of one row into the values of the FP32 channel
+// and of the BF16 channels; colvec points at the per-column vector's entry for col0 (shared
+// memory). Rows past M are clipped by the stores: for such a row (row >= M) the functor must not
+// read memory indexed by it.
 template <int BN, class Epi>
-__global__ void __launch_bounds__(128, 1)
-k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcShape sh, Epi epi) {
+__global__ void __launch_bounds__(kThreads, 2)
+k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          const __grid_constant__ TcOut out, TcShape sh, Epi epi) {
   using C = TcCfg<BN>;
   constexpr int S = C::kStages;
   extern __shared__ unsigned char tc_smem_raw[];
@@ -161,10 +214,13 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   __shared__ __align__(8) uint64_t bar_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_abort, s_consumed, s_issued;
+  __shared__ float s_colvec[BN];
   volatile int* abort_flag = &s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t base = (smem_addr(tc_smem_raw) + 1023u) & ~1023u;
+  const uint32_t raw = smem_addr(tc_smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
   const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
+  for (int c = tid; c < BN; c += kThreads) s_colvec[c] = (sh.colvec && n0 + c < sh.N) ? sh.colvec[n0 + c] : 0.f;
   const int kc0 = blockIdx.z * sh.kchunks_per_split;
   const int nk = min(sh.kchunks, kc0 + sh.kchunks_per_split) - kc0;
   if (tid == 0) {
@@ -232,20 +288,87 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   if (aborted) {
     if (tid == 0) {
       atomicOr(sh.err, sh.err_bit);
-      // copies issued but not consumed are still landing in shared memory: wait for them
+      // copies issued but not consumed, and the final commit, are still landing in shared
+      // memory: wait for them before the CTA exits
       for (int i = s_consumed; i < s_issued; ++i)
-        mbar_wait_parity(smem_addr(&bar_full[i % S]), (i / S) & 1, sh.polls);
+        mbar_wait_parity(smem_addr(&bar_full[i % S]), (i / S) & 1, kDrainPolls);
+      mbar_wait_parity(smem_addr(&bar_done), 0, kDrainPolls);
     }
   } else if (nk > 0) {
+    // epilogue: the four warps of a TMEM lane quarter share its columns (parts of >= 16 columns)
     tc_fence_after();
-    const int row = m0 + warp * 32 + lane;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    constexpr int kParts = C::kParts, kPartCols = C::kPartCols;
+    const int quarter = warp & 3, part = warp >> 2;
+    const int row = m0 + quarter * 32 + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+    if (part < kParts) {
+      // two 4 KB slots per warp, one per 16-column group of a 32-column step: FP32 tile [32][16]
+      // at 0, BF16 [32][16] at 2048, BF16 transposed [16][32] at 3072. A step reads its 32
+      // accumulator columns with two loads and one wait, fills both slots once the previous
+      // step's stores have read them, and publishes them with one proxy fence and one bulk group.
+      const uint32_t stg = base + (uint32_t)(part * 4 + quarter) * C::kStageWarp;
+      unsigned char* stg_g = tc_smem_raw + (stg - raw);
+      const int mask = sh.out_mask;
+      const int y = m0 + quarter * 32;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      if (n0 + c0 >= sh.N) break;
-      float v[16];
-      tmem_ld16(lane_addr + (uint32_t)c0, v);
-      if (row < sh.M) epi(row, n0 + c0, v);
+      for (int cb = part * kPartCols; cb < (part + 1) * kPartCols; cb += 32) {
+        if (n0 + cb >= sh.N) break;
+        const int ng = (cb + 16 < (part + 1) * kPartCols && n0 + cb + 16 < sh.N) ? 2 : 1;
+        uint32_t r[2][16];
+        tmem_ld16_async(lane_addr + (uint32_t)cb, r[0]);
+        if (ng == 2) tmem_ld16_async(lane_addr + (uint32_t)(cb + 16), r[1]);
+        tmem_ld_wait();
+        if (cb > part * kPartCols) {
+          if (lane == 0) bulk_wait_read<0>();
+          __syncwarp();
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h >= ng) break;
+          const int c0 = cb + 16 * h;
+          float v[16], f[16], b[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[h][j]);
+          epi(row, n0 + c0, s_colvec + c0, v, f, b);
+          unsigned char* sp = stg_g + h * 4096;
+          if (mask & (kOutF32 | kOutF32Add)) {
+            float4* d = reinterpret_cast<float4*>(sp + lane * 64);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+          }
+          if (mask & kOutB16) {
+            unsigned w[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              w[j] = (unsigned)__bfloat16_as_ushort(__float2bfloat16(b[2 * j])) |
+                     ((unsigned)__bfloat16_as_ushort(__float2bfloat16(b[2 * j + 1])) << 16);
+            uint4* d = reinterpret_cast<uint4*>(sp + 2048 + lane * 32);
+            d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+          }
+          if (mask & kOutB16T) {
+            __nv_bfloat16* d = reinterpret_cast<__nv_bfloat16*>(sp + 3072);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) d[j * 32 + lane] = __float2bfloat16(b[j]);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          for (int h = 0; h < ng; ++h) {
+            const uint32_t ss = stg + (uint32_t)h * 4096u;
+            const int x = n0 + cb + 16 * h;
+            if (mask & kOutF32) tma_store_2d(&out.f32, ss, x, y);
+            if (mask & kOutF32Add) tma_reduce_add_2d(&out.f32, ss, x, y);
+            if (mask & kOutB16) tma_store_2d(&out.b16, ss + 2048, x, y);
+            if (mask & kOutB16T) tma_store_2d(&out.b16t, ss + 3072, y, x);
+          }
+          bulk_commit();
+        }
+        __syncwarp();
+      }
+      if (lane == 0) bulk_wait_all();
+      __syncwarp();
     }
   }
   tc_fence_before();
@@ -271,30 +394,53 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// Tensor map of a row-major BF16 matrix [rows][cols] with row stride ld elements, read in boxes of
-// 64 columns x box_rows rows written to shared memory with the 128-byte swizzle; reads outside [0, cols) x [0, rows) return zeros. Returns false when
-// the driver entry point is missing, the layout breaks a TMA rule (16-byte aligned base, row
-// stride a multiple of 16 bytes) or the driver rejects it.
-inline bool encode_bf16_map(CUtensorMap* map, const void* base, long long rows, long long cols, long long ld,
-                            int box_rows) {
+// Tensor map of a row-major matrix [rows][cols] (row stride ld elements) with boxes of box_cols x
+// box_rows; reads outside [0, cols) x [0, rows) return zeros and stores there are dropped. Returns
+// false when the driver entry point is missing, the layout breaks a TMA rule (16-byte aligned
+// base, row stride a multiple of 16 bytes) or the driver rejects it.
+inline bool encode_map(CUtensorMap* map, CUtensorMapDataType type, int elem_bytes, const void* base, long long rows,
+                       long long cols, long long ld, int box_cols, int box_rows, CUtensorMapSwizzle swizzle) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc || !base || rows < 1 || cols < 1 || ld < cols || ((uintptr_t)base & 15) || ((ld * 2) & 15) ||
-      box_rows < 1 || box_rows > 256)
+  if (!enc || !base || rows < 1 || cols < 1 || ld < cols || ((uintptr_t)base & 15) || ((ld * elem_bytes) & 15) ||
+      box_rows < 1 || box_rows > 256 || box_cols < 1 || box_cols > 256)
     return false;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(ld * elem_bytes)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1u, 1u};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return enc(map, type, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// GEMM operand: BF16 [rows][cols], K = cols contiguous, read in 64-column boxes of box_rows rows
+// into the 128-byte swizzled layout.
+inline bool encode_bf16_map(CUtensorMap* map, const void* base, long long rows, long long cols, long long ld,
+                            int box_rows) {
+  return encode_map(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, rows, cols, ld, kBK, box_rows,
+                    CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+// Epilogue outputs (TcOut): FP32 or BF16 [rows][cols] in 16-column x 32-row boxes; the transposed
+// BF16 channel [cols of the GEMM][rows of the GEMM] in 32 x 16 boxes.
+inline bool encode_out_f32(CUtensorMap* map, const float* base, long long rows, long long cols, long long ld) {
+  return encode_map(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, rows, cols, ld, 16, 32, CU_TENSOR_MAP_SWIZZLE_NONE);
+}
+inline bool encode_out_b16(CUtensorMap* map, const void* base, long long rows, long long cols, long long ld) {
+  return encode_map(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, rows, cols, ld, 16, 32,
+                    CU_TENSOR_MAP_SWIZZLE_NONE);
+}
+inline bool encode_out_b16t(CUtensorMap* map, const void* base, long long rows, long long cols, long long ld) {
+  return encode_map(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, rows, cols, ld, 32, 16,
+                    CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
 // Launches C = A B^T for A [M][K] (map box 128 rows) and B [N][K] (map box BN rows), splitting K
-// over at most ksplit CTAs per output tile (the epilogue must then accumulate atomically).
+// over at most ksplit CTAs per output tile (then the FP32 channel must be kOutF32Add). N must be a
+// multiple of 16.
 template <int BN, class Epi>
-inline cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K, int ksplit,
-                                  const Epi& epi, int* err, int err_bit, unsigned polls, cudaStream_t st) {
+inline cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, const TcOut& out, int out_mask,
+                                  const float* colvec, int M, int N, int K, int ksplit, const Epi& epi, int* err,
+                                  int err_bit, unsigned polls, cudaStream_t st) {
   using C = TcCfg<BN>;
   static bool attr_set[64] = {false};
   int dev = 0;
@@ -306,13 +452,14 @@ inline cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, in
     attr_set[dev & 63] = true;
   }
   if (M < 1 || N < 1 || K < 1) return cudaSuccess;
+  if (N % 16) return cudaErrorInvalidValue;
   const int kchunks = (K + kBK - 1) / kBK;
   if (ksplit < 1) ksplit = 1;
   const int per = (kchunks + ksplit - 1) / ksplit;
   const int splits = (kchunks + per - 1) / per;
   const dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM, splits);
-  const TcShape sh{M, N, kchunks, per, polls, err, err_bit};
-  k_gemm_tc<BN, Epi><<<grid, 128, C::kSmem, st>>>(a, b, sh, epi);
+  const TcShape sh{M, N, kchunks, per, polls, err, err_bit, out_mask, colvec};
+  k_gemm_tc<BN, Epi><<<grid, kThreads, C::kSmem, st>>>(a, b, out, sh, epi);
   return cudaGetLastError();
 }
 

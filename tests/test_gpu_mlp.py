@@ -249,3 +249,40 @@ def test_fused_warm_start_matches_gemm_path(grid):
     scale = np.abs(Y).max()
     assert np.abs(y_fused - Y).max() <= 1e-9 * scale + 8 * 2.0 ** -52 * np.abs(q).max()
     net.close()
+
+
+def test_tensor_core_wait_timeout_is_reported_and_the_network_recovers():
+    """Every mbarrier wait of the network's tcgen05 kernels (the GEMM's TMA stages and MMA
+    completion, the fused warm start's weight copies and layers) is bounded. With a budget of 0
+    polls each wait expires at once: the kernel drains its own copies and commits, frees its tensor
+    memory, skips its output and raises an error bit that the next synchronising call returns as
+    SHELL_ERR_TIMEOUT. With the default budget restored the same network computes the same loss and
+    gradients as before, and its warm start equals one computed before the expired waits."""
+    from paper_2312_14839_gb300 import bhem
+    net, _, _ = _net(2000, 41, _norm(40))
+    rng = np.random.default_rng(42)
+    X = dev(rng.normal(0, 1.5, (2000, 28)), torch.float32)
+    T = dev(rng.normal(0, 1.0, (2000, 12)), torch.float32)
+    loss0 = net.gradients(X, T)
+    G0 = net.get_grads().astype(np.float64)
+    g, rest = S.flat_sheet(11, 6)
+    q = dev(S.noisy(rest, 1e-2, 43).reshape(-1))
+    v = dev(np.random.default_rng(44).normal(0, 0.1, g.n_dof))
+    with bhem.Shell(g, S.SHEET_MATERIAL, rest.reshape(-1)) as sh:
+        w0 = host(net.warm_start(sh, q, v, 1e-3))
+        net.set_wait_budget(0)
+        with pytest.raises(bhem.ShellError) as ei:
+            net.gradients(X, T)
+        assert ei.value.status == 9
+        net.warm_start(sh, q, v, 1e-3)
+        torch.cuda.synchronize()
+        net.set_wait_budget(-1)
+        with pytest.raises(bhem.ShellError) as ei:   # raised by the warm start's expired waits
+            net.gradients(X, T)
+        assert ei.value.status == 9
+        loss1 = net.gradients(X, T)
+        w1 = host(net.warm_start(sh, q, v, 1e-3))
+    assert loss1 == pytest.approx(loss0, rel=1e-12)
+    assert rel(net.get_grads().astype(np.float64), G0) <= 1e-5
+    np.testing.assert_array_equal(w1, w0)
+    net.close()
