@@ -311,11 +311,12 @@ SHELL_API shell_status shell_batch_newton_step(shell_batch_t* batch, const shell
    Learned Newton warm start. The paper has no learning component: this is an extension that
    predicts the initial Newton iterate of an implicit-Euler step (Sec. 6.1) per node. The
    network is a per-node MLP 28 -> 256 -> 256 -> 256 -> 12 with GELU after each hidden layer;
-   weights and activations are BF16, products accumulate in FP32 on the tensor cores; FP32
-   master weights are trained with an MSE loss and Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+   weights and activations are BF16, products accumulate in FP32 on the fifth-generation tensor
+   cores (tcgen05.mma into tensor memory, operands and outputs moved by TMA); FP32 master weights
+   are trained with an MSE loss and Adam (beta1 0.9, beta2 0.999, eps 1e-8).
    Node features (28 floats, written by shell_node_features): u = q - q_rest (12), v (12), the
    mean over the node's present edge neighbours of u_nb - u for the position DOFs (3), and the
-   present fraction of its 4-neighbour stencil (1). Target and output (12 floats): the update
+   mean over the same neighbours of their position speed |v_nb| (1). Target and output (12 floats): the update
    beyond the inertial predictor, q^{n+1} - q^n - dt v^n (shell_warm_targets). Inputs and
    targets are normalised per column by shell_mlp_set_normalization (x' = (x - mean) / std;
    a std of 0 is taken as 1); the loss is the mean of squared normalised errors.
@@ -330,7 +331,8 @@ SHELL_API shell_status shell_batch_newton_step(shell_batch_t* batch, const shell
 typedef struct shell_mlp_s shell_mlp_t;
 
 /* Creates a network with zero parameters for batches of up to max_rows rows (1 .. 2^24) of
-   features; stream: cudaStream_t or NULL. Device memory: about 10.6 KB per row plus 2.3 MB. */
+   features; stream: cudaStream_t or NULL. Device memory: about 12.7 KB per row plus 2.9 MB.
+   Fails with SHELL_ERR_CUDA when the driver cannot encode the network's TMA tensor maps. */
 SHELL_API shell_status shell_mlp_create(int max_rows, void* stream, shell_mlp_t** out);
 SHELL_API shell_status shell_mlp_destroy(shell_mlp_t* mlp);
 /* Number of floats of the packed parameter array (142,092). */
@@ -376,8 +378,10 @@ SHELL_API shell_status shell_node_features(shell_t* shell, const double* q, cons
 SHELL_API shell_status shell_warm_targets(long long n_dof, const double* q_next, const double* q, const double* v,
                                           double dt, float* T, void* stream);
 /* warm = q + dt v + network(features(q, v)) (device [n_dof] FP64), ready to pass as warm_start to
-   shell_newton_step with the same dt. The shell must have at most max_rows nodes. mlp may be NULL:
-   then warm = q + dt v, the inertial predictor alone. */
+   shell_newton_step with the same dt: one fused launch of 128 nodes per CTA, whose output equals
+   that of shell_node_features followed by shell_mlp_forward. mlp may be NULL: then warm = q + dt v,
+   the inertial predictor alone. An expired device-side wait (shell_mlp_set_wait_budget) leaves
+   warm unwritten and is reported by the network's next synchronising call. */
 SHELL_API shell_status shell_mlp_warm_start(shell_mlp_t* mlp, shell_t* shell, const double* q, const double* v,
                                             double dt, double* warm);
 
