@@ -331,13 +331,33 @@ struct ElemArgs {
 };
 
 // Builds M_g (15x15) and the per-point energy, gradient vectors and mass weight for Gauss
-// point g of the warp's patch. Called by lanes 0..15, lane = g.
+// point g of the warp's patch. Called by all 32 lanes: lane g and lane g + 16 share Gauss point
+// g. The energy is unchanged when the two parameter directions are exchanged, so its Hessian
+// blocks of the exchanged frame are those of the original one with the derivative kinds relabeled
+// (xi^1 <-> xi^2: a_1 <-> a_2, x_,11 <-> x_,22, x_,12 fixed; sigma(k) = 1, 0, 3, 2, 4). Half 0 (the
+// original frame) computes the blocks (k, l), k <= l, with k in {0, 2, 4}; half 1 runs the same
+// instructions in the exchanged frame, which gives the blocks (sigma(k), sigma(l)) with k in
+// {1, 3}: together all 15 blocks. Half 1 discards the three blocks that map onto themselves
+// ((0, 1), (2, 3), (4, 4)) and the by-products (energy, gradient vectors, mass weight).
 template <typename R>
-__device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W, int g,
+__device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W, int g, int half,
                                                    const ElemArgs& A) {
   V3<R> ub[5], uu[5];
   interp5<R, R>(sphi, W.qb, g, ub);   // rest a_bar_1, a_bar_2, x_bar_{,11}, x_bar_{,22}, x_bar_{,12}
   interp5<R, R>(sphi, W.u, g, uu);    // displacement derivatives
+  {
+    // half 1: exchange the parameter directions (selects, no divergent branch)
+    const bool x = half != 0;
+    const V3<R> b0 = ub[0], b2 = ub[2], d0 = uu[0], d2 = uu[2];
+    ub[0] = x ? ub[1] : b0;
+    ub[1] = x ? b0 : ub[1];
+    ub[2] = x ? ub[3] : b2;
+    ub[3] = x ? b2 : ub[3];
+    uu[0] = x ? uu[1] : d0;
+    uu[1] = x ? d0 : uu[1];
+    uu[2] = x ? uu[3] : d2;
+    uu[3] = x ? d2 : uu[3];
+  }
   const V3<R> ab1 = ub[0], ab2 = ub[1];
   const V3<R> a1 = ab1 + uu[0], a2 = ab2 + uu[1];
   V3<R> c[3] = {ub[2] + uu[2], ub[3] + uu[3], ub[4] + uu[4]};
@@ -382,9 +402,11 @@ __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W
   }
   const R wgt = sphi[kPhiSize + g] * sqab;
   const R s = h * h * h * ((R)1 / (R)12);
-  W.en[g] = wgt * ((R)0.5 * h * (al[0] * sg[0] + al[1] * sg[1] + al[2] * sg[2]) +
-                   s * (R)0.5 * (be[0] * mm[0] + be[1] * mm[1] + be[2] * mm[2]));
-  W.ms[g] = (R)(A.mass_scale * A.rho_h) * wgt;
+  if (!half) {
+    W.en[g] = wgt * ((R)0.5 * h * (al[0] * sg[0] + al[1] * sg[1] + al[2] * sg[2]) +
+                     s * (R)0.5 * (be[0] * mm[0] + be[1] * mm[1] + be[2] * mm[2]));
+    W.ms[g] = (R)(A.mass_scale * A.rho_h) * wgt;
+  }
   // first derivatives: B matrices (rows = Voigt component, columns = coordinate)
   V3<R> t1 = cross(a2, a3), t2 = cross(a3, a1);
   V3<R> up[3], vp[3];
@@ -408,9 +430,11 @@ __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W
     gk = s * gk;
     if (k < 2) gk = gk + h * (sg[0] * Ba[k][0] + sg[1] * Ba[k][1] + sg[2] * Ba[k][2]);
     gk = wgt * gk;
-    W.G[g][k * 3 + 0] = gk.x;
-    W.G[g][k * 3 + 1] = gk.y;
-    W.G[g][k * 3 + 2] = gk.z;
+    if (!half) {
+      W.G[g][k * 3 + 0] = gk.x;
+      W.G[g][k * 3 + 1] = gk.y;
+      W.G[g][k * 3 + 2] = gk.z;
+    }
   }
   // Q_l = H B_l
   V3<R> Qa[2][3], Qb[5][3];
@@ -438,6 +462,7 @@ __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W
       for (int x = 0; x < 3; ++x)
 #pragma unroll
         for (int y = 0; y < 3; ++y) {
+          if (k == 1 || k == 3) continue;   // half 1 produces these blocks in the exchanged frame
           if (k == l && y < x) continue;
           R v = s * (comp(Bb[k][0], x) * comp(Qb[l][0], y) + comp(Bb[k][1], x) * comp(Qb[l][1], y) +
                      comp(Bb[k][2], x) * comp(Qb[l][2], y));
@@ -479,7 +504,11 @@ __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W
             }
           }
           v *= wgt;
-          M[sym15(k * 3 + x, l * 3 + y)] = v;
+          // sigma: the kind index in the original frame of a kind of the exchanged frame
+          constexpr int kSig[5] = {1, 0, 3, 2, 4};
+          const bool self_mirror = (k == 0 && l == 1) || (k == 2 && l == 3) || (k == 4 && l == 4);
+          if (!half) M[sym15(k * 3 + x, l * 3 + y)] = v;
+          else if (!self_mirror) M[sym15(kSig[k] * 3 + x, kSig[l] * 3 + y)] = v;
         }
 }
 
@@ -696,7 +725,7 @@ __device__ __forceinline__ void element_patch(const R* sphi, const R* w1d, const
     }
   }
   __syncwarp();
-  if (lane < 16) gauss_point_matrix<R>(sphi, W, lane, A);
+  gauss_point_matrix<R>(sphi, W, lane & 15, lane >> 4, A);
   __syncwarp();
 
   // energy and gradient (by-products)
