@@ -171,6 +171,9 @@ struct Shell {
   int spmv_tma = 0, spmv_grid = 0, spmv_stage_floats = 0;
   size_t spmv_smem = 0;
   int wait_polls = kDefaultWaitPolls;   // budget of each bounded device-side wait (shell_set_wait_budget)
+  // mixed precision: a step's first residual and Hessian in one element launch (default; the
+  // environment variable BHEM_FUSE_FIRST_HESSIAN=0 at shell creation selects separate launches)
+  bool fuse_first_hessian = true;
 
   // CUDA graphs of the mixed-precision PCG loop, keyed by mask (iters = -1)
   struct PcgGraph { const unsigned char* mask; int iters; cudaGraphExec_t exec; };
@@ -220,6 +223,10 @@ struct ElemOutputs {
   void* bsr = nullptr;          // assembled values
   double mass_scale = 0.0;      // adds mass_scale * M to the assembled / unassembled Hessian
   int pseudo = 0;               // drop the second derivative of beta
+  // FP32 kernel only: also the FP64 patch energies and the assembled FP64 gradient at q (the
+  // results of launch_energy_grad64 without its energy total), in the same launch; grad64 zeroed
+  double* energy64 = nullptr;   // [np]
+  double* grad64 = nullptr;     // [n_dof]
 };
 shell_status launch_element_full(Shell& s, const double* q, bool fp64, const ElemOutputs& out);
 

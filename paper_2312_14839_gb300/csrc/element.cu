@@ -203,7 +203,49 @@ k_element_full(ElemArgs A) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpSmem<R>& W = Ws[wid];
   const int total = A.plist ? A.plist_n : A.np;
-  for (int it = blockIdx.x * NW + wid; it < total; it += gridDim.x * NW)
+  const int stride = gridDim.x * NW;
+  if constexpr (sizeof(R) == 4) {
+    if (A.grad64) {
+      // FP64 energy and gradient at the same q (the arithmetic of k_energy_grad64) in the warps of
+      // the FP32 Hessian: the FP64 pipe works while other warps issue the FP32 pass. Every second
+      // patch of a warp, its two half-warps evaluate that patch and the warp's next one, in the
+      // warp's Gauss-point-matrix area (free between patches; 2 x 432 doubles).
+      __shared__ double w1_64[kHerm1D], w2_64[kHerm1D];
+      build_hermite_1d<double>(w1_64, A.d1, threadIdx.x, blockDim.x);
+      build_hermite_1d<double>(w2_64, A.d2, threadIdx.x, blockDim.x);
+      __syncthreads();
+      static_assert(sizeof(W.M) >= 2 * 432 * sizeof(double), "FP64 scratch fits the M_g area");
+      const int hw = lane >> 4, g = lane & 15;
+      double* scratch = reinterpret_cast<double*>(&W.M[0][0]) + hw * 432;
+      int k = 0;
+      for (int it = blockIdx.x * NW + wid; it < total; it += stride, ++k) {
+        if ((k & 1) == 0) {
+          const int itp = it + hw * stride;
+          const bool active = itp < total;
+          const int pp = active ? (A.plist ? A.plist[itp] : itp) : 0;
+          int nd[4] = {0, 0, 0, 0};
+          if (active) {
+            const int4 pn = A.pnodes[pp];
+            nd[0] = pn.x;
+            nd[1] = pn.y;
+            nd[2] = pn.z;
+            nd[3] = pn.w;
+          }
+          const double ep = eg64_patch(w1_64, w2_64, scratch, scratch + 48,
+                                       reinterpret_cast<double(*)[15]>(scratch + 192), pp, active, g, nd, A.q,
+                                       nullptr, 0.0, A.restgp, (size_t)A.np * 16, A.h, A.grad64, A.err);
+          if (active && g == 0) {
+            if (!isfinite(ep)) atomicOr(A.err, ERRBIT_NONFINITE);
+            A.energy64[pp] = ep;
+          }
+          __syncwarp();
+        }
+        element_patch<R>(sphi, w1d, sphg, W, A.plist ? A.plist[it] : it, A, lane);
+      }
+      return;
+    }
+  }
+  for (int it = blockIdx.x * NW + wid; it < total; it += stride)
     element_patch<R>(sphi, w1d, sphg, W, A.plist ? A.plist[it] : it, A, lane);
 }
 
@@ -257,6 +299,11 @@ shell_status launch_element_full(Shell& s, const double* q, bool fp64, const Ele
   A.hess_p = out.hess_p;
   A.bsr = out.bsr;
   A.err = s.d_err;
+  if (!fp64 && out.grad64) {
+    A.restgp = s.d_restgp;
+    A.energy64 = out.energy64;
+    A.grad64 = out.grad64;
+  }
   if (out.bsr && s.opt.assembly == SHELL_ASM_COLOR) {
     // colour-ordered: patches of one colour share no node, plain read-modify-write
     A.bsr_atomic = 0;

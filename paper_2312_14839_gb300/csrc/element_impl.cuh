@@ -328,18 +328,24 @@ struct ElemArgs {
   void* bsr;
   int bsr_atomic;
   int* err;
+  // FP64 energy and gradient at the same q in the same warps (FP32 kernel only; grad64 null: off):
+  // energy64[p] = E_p, grad64 += dE/dq (zeroed by the caller); restgp: rest Gauss-point data [13][np][16]
+  const double* restgp;
+  double* energy64;
+  double* grad64;
 };
 
 // Builds M_g (15x15) and the per-point energy, gradient vectors and mass weight for Gauss
-// point g of the warp's patch. Called by all 32 lanes: lane g and lane g + 16 share Gauss point
-// g. The energy is unchanged when the two parameter directions are exchanged, so its Hessian
+// point g of the warp's patch. kSplit = false (FP64 kernel): lanes 0..15, lane = g, every block.
+// kSplit = true (FP32 kernel): all 32 lanes, lane g and lane g + 16 share Gauss point g. The
+// energy is unchanged when the two parameter directions are exchanged, so its Hessian
 // blocks of the exchanged frame are those of the original one with the derivative kinds relabeled
 // (xi^1 <-> xi^2: a_1 <-> a_2, x_,11 <-> x_,22, x_,12 fixed; sigma(k) = 1, 0, 3, 2, 4). Half 0 (the
 // original frame) computes the blocks (k, l), k <= l, with k in {0, 2, 4}; half 1 runs the same
 // instructions in the exchanged frame, which gives the blocks (sigma(k), sigma(l)) with k in
 // {1, 3}: together all 15 blocks. Half 1 discards the three blocks that map onto themselves
 // ((0, 1), (2, 3), (4, 4)) and the by-products (energy, gradient vectors, mass weight).
-template <typename R>
+template <typename R, bool kSplit>
 __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W, int g, int half,
                                                    const ElemArgs& A) {
   V3<R> ub[5], uu[5];
@@ -462,7 +468,7 @@ __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W
       for (int x = 0; x < 3; ++x)
 #pragma unroll
         for (int y = 0; y < 3; ++y) {
-          if (k == 1 || k == 3) continue;   // half 1 produces these blocks in the exchanged frame
+          if (kSplit && (k == 1 || k == 3)) continue;   // half 1 produces these in the exchanged frame
           if (k == l && y < x) continue;
           R v = s * (comp(Bb[k][0], x) * comp(Qb[l][0], y) + comp(Bb[k][1], x) * comp(Qb[l][1], y) +
                      comp(Bb[k][2], x) * comp(Qb[l][2], y));
@@ -725,7 +731,8 @@ __device__ __forceinline__ void element_patch(const R* sphi, const R* w1d, const
     }
   }
   __syncwarp();
-  gauss_point_matrix<R>(sphi, W, lane & 15, lane >> 4, A);
+  if constexpr (sizeof(R) == 4) gauss_point_matrix<R, true>(sphi, W, lane & 15, lane >> 4, A);
+  else if (lane < 16) gauss_point_matrix<R, false>(sphi, W, lane, 0, A);
   __syncwarp();
 
   // energy and gradient (by-products)

@@ -226,6 +226,8 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
     if (m && std::strcmp(m, "persistent") == 0) s->pcg_mode = 0;
     if (m && std::strcmp(m, "host") == 0) s->pcg_mode = 2;
     s->pcg_host_loop = s->pcg_mode == 2;
+    const char* f = getenv("BHEM_FUSE_FIRST_HESSIAN");
+    s->fuse_first_hessian = !(f && std::strcmp(f, "0") == 0);
   }
 
   HostTopo T;
@@ -529,6 +531,30 @@ static shell_status residual(Shell& s, const double* q, const shell_step_params&
   return SHELL_OK;
 }
 
+// |g| at q together with the first Hessian at q (mixed precision) in one element launch: the warps
+// of the FP32 Hessian also evaluate the FP64 patch energies and the FP64 elastic gradient, so the
+// FP64 pipe works under the FP32 pass instead of after it. The Hessian's diagonal statistics ride
+// on the residual's host copy of the Newton scalars. (The total elastic energy, unused by the step,
+// is not formed on this path.)
+static shell_status residual_with_hessian(Shell& s, const double* q, const shell_step_params& P,
+                                          const unsigned char* mask, double inv_dt2, double* gnorm) {
+  BHEM_CUDA(cudaMemsetAsync(s.d_g, 0, sizeof(double) * s.n_dof, s.stream));
+  BHEM_CUDA(cudaMemsetAsync(s.d_val, 0, (size_t)s.n_blocks * 144 * sizeof(float), s.stream));
+  ElemOutputs o;
+  o.bsr = s.d_val;
+  o.mass_scale = inv_dt2;
+  o.pseudo = s.opt.hessian == SHELL_HESS_PSEUDO;
+  o.energy64 = s.d_Ep;
+  o.grad64 = s.d_g;
+  BHEM_TRY(launch_element_full(s, q, false, o));
+  BHEM_TRY(launch_diag_check(s, mask, s.d_ns->diag_stats, true));
+  BHEM_TRY(launch_grad_finish(s, q, s.d_y, P.dt, P.gravity, mask, s.d_g, s.d_gin, &s.d_ns->gnorm2));
+  BHEM_CUDA(cudaMemcpyAsync(s.h_ns, s.d_ns, sizeof(NewtonScalars), cudaMemcpyDeviceToHost, s.stream));
+  BHEM_TRY(sync_and_check(s));
+  *gnorm = std::sqrt(s.h_ns->gnorm2);
+  return SHELL_OK;
+}
+
 // Residual at q = q_prev + d when the elastic gradient and patch energies at q are already in
 // d_g / d_Ep (from the accepted first line-search trial, alpha = 1): the inertial part follows from
 // the previous one and M d (d_Md, formed for the line search), without a second mass product.
@@ -566,8 +592,12 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
   // Only for large shells: on small ones every kernel is short, the step is launch- and sync-bound,
   // and the second stream's fixed costs outweigh the overlap (30 x 30 patches: 3% slower).
   constexpr int kOverlapMinPatches = 16384;
-  bool hess_pending = false;
-  if (!warm && P.newton_max > 0 && s.n_patches >= kOverlapMinPatches) {
+  bool hess_pending = false, hess_ready = false;
+  if (!warm && P.newton_max > 0 && !s.val_fp64 && s.fuse_first_hessian) {
+    // mixed precision: residual and first Hessian in one element launch (residual_with_hessian)
+    BHEM_TRY(residual_with_hessian(s, q, P, mask, inv_dt2, &gref));
+    hess_ready = true;
+  } else if (!warm && P.newton_max > 0 && s.n_patches >= kOverlapMinPatches) {
     if (!s.aux_stream) {
       BHEM_CUDA(cudaStreamCreateWithFlags(&s.aux_stream, cudaStreamNonBlocking));
       BHEM_CUDA(cudaEventCreateWithFlags(&s.ev_q, cudaEventDisableTiming));
@@ -586,7 +616,7 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
     BHEM_CUDA(cudaEventRecord(s.ev_hess, s.aux_stream));
     hess_pending = true;
   }
-  BHEM_TRY(residual(s, q, P, mask, &gref, hess_pending ? s.ev_hess : nullptr));
+  if (!hess_ready) BHEM_TRY(residual(s, q, P, mask, &gref, hess_pending ? s.ev_hess : nullptr));
   s.aux_unjoined = false;   // the residual's synchronised check waited for ev_hess
   mark(s, "residual0");
   st.res0 = gref;
@@ -609,10 +639,12 @@ static shell_status newton_core(Shell& s, const shell_step_params& P, const unsi
     // iteration's tau; each negative curvature met by PCG multiplies tau by 10 (at least 1e-8),
     // beyond 1e4 the step gives up.
     KindStats K;
-    const bool from_pending = hess_pending;
+    const bool from_pending = hess_pending || hess_ready;
     if (hess_pending) {   // assembled and its statistics read with the residual (joined there)
       BHEM_CUDA(cudaStreamWaitEvent(s.stream, s.ev_hess, 0));
       hess_pending = false;
+    } else if (hess_ready) {   // assembled in the residual's launch
+      hess_ready = false;
     } else {
       BHEM_TRY(assemble_hessian(s, q, inv_dt2));
     }
