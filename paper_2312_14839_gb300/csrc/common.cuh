@@ -174,6 +174,9 @@ struct Shell {
   // mixed precision: a step's first residual and Hessian in one element launch (default; the
   // environment variable BHEM_FUSE_FIRST_HESSIAN=0 at shell creation selects separate launches)
   bool fuse_first_hessian = true;
+  // mixed precision: shells of at most this many nodes solve PCG as one thread-block cluster
+  // (default 0: never, the graph loop was faster on every workload; BHEM_PCG_LOOP=cluster: always)
+  int pcg_cluster_max_nodes = 0;
 
   // CUDA graphs of the mixed-precision PCG loop, keyed by mask (iters = -1)
   struct PcgGraph { const unsigned char* mask; int iters; cudaGraphExec_t exec; };
@@ -256,6 +259,8 @@ shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, const dou
 // the whole mixed-precision solve as one graph: a conditional WHILE node around one iteration
 shell_status launch_pcg_loop_graph(Shell& s, const unsigned char* mask);
 shell_status launch_pcg_persistent(Shell& s, const unsigned char* mask);
+// the whole mixed-precision solve as one thread-block cluster (small shells)
+shell_status launch_pcg_cluster(Shell& s, const unsigned char* mask);
 int pcg_loop_unroll();   // PCG iterations per loop body
 shell_status launch_spmv(Shell& s, const void* x, int x_fp32, void* y);
 shell_status launch_pcg_result(Shell& s);

@@ -225,6 +225,8 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
     s->pcg_mode = s->pcg_host_loop ? 2 : 1;
     if (m && std::strcmp(m, "persistent") == 0) s->pcg_mode = 0;
     if (m && std::strcmp(m, "host") == 0) s->pcg_mode = 2;
+    if (m && std::strcmp(m, "graph") == 0) s->pcg_cluster_max_nodes = 0;
+    if (m && std::strcmp(m, "cluster") == 0) s->pcg_cluster_max_nodes = 1 << 30;
     s->pcg_host_loop = s->pcg_mode == 2;
     const char* f = getenv("BHEM_FUSE_FIRST_HESSIAN");
     s->fuse_first_hessian = !(f && std::strcmp(f, "0") == 0);
@@ -435,6 +437,13 @@ static shell_status run_pcg(Shell& s, const unsigned char* mask, const double td
     BHEM_CUDA(cudaMemcpyAsync(s.h_pcg, s.d_pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s.stream));
     BHEM_CUDA(cudaStreamSynchronize(s.stream));
     mark(s, "pcg_persistent");
+    launched = limit;
+  } else if (!s.val_fp64 && s.pcg_mode == 1 && s.n_nodes <= s.pcg_cluster_max_nodes) {
+    // mixed precision, small shell: the whole solve in one thread-block cluster
+    if (limit > 0) BHEM_TRY(launch_pcg_cluster(s, mask));
+    BHEM_CUDA(cudaMemcpyAsync(s.h_pcg, s.d_pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s.stream));
+    BHEM_CUDA(cudaStreamSynchronize(s.stream));
+    mark(s, "pcg_cluster");
     launched = limit;
   } else if (!s.val_fp64 && s.pcg_mode == 1) {
     // mixed precision: the whole solve loops on the device (one graph with a conditional WHILE

@@ -830,6 +830,221 @@ k_pcg32_persistent(int n, int per, const int* __restrict__ rp, const int* __rest
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Mixed-precision PCG of a small shell as one thread-block cluster: the cluster's CTAs (one per
+// SM, up to 16) own contiguous ranges of node rows and run all iterations, the phases separated
+// by the hardware cluster barrier (barrier.cluster, release/acquire at cluster scope, which also
+// orders the global-memory vectors the CTAs exchange). A reduction is one partial per CTA in its
+// own shared memory, read by every CTA through distributed shared memory in rank order after the
+// barrier, so every CTA holds the same totals and takes the same decisions; the partials are
+// double-buffered, since a CTA rewrites one only two barriers later. Per iteration, as in
+// k_pcg32_persistent: SpMV (p.Ap) | barrier | update x, r, z = D r (r.z, r.r) | barrier |
+// p = z + beta p | barrier. The arithmetic per element is that of k_spmv32, k_pcg32_update and
+// k_pcg32_pupdate4. Every CTA runs every barrier (control flow depends only on the shared totals
+// and the launch's state), so the barriers cannot wait on a CTA that has left.
+// ------------------------------------------------------------------------------------------
+constexpr int kClusterRows = 16;                        // node rows per SpMV pass of a CTA
+constexpr int kClusterThreads = kClusterRows * 36;      // 576
+constexpr int kClusterMaxCtas = 16;
+
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ unsigned cluster_ctas() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;\n" : "=r"(r));
+  return r;
+}
+
+// float2 at a shared-memory address of CTA `rank` of the cluster
+__device__ __forceinline__ float2 dsmem_ld_f2(const float2* local, unsigned rank) {
+  unsigned addr = (unsigned)__cvta_generic_to_shared(local), remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(remote) : "r"(addr), "r"(rank));
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(remote) : "memory");
+  return v;
+}
+
+// Totals over the cluster's CTAs of the nv partials in every CTA's slots: lane q of warp 0 reads
+// CTA q's slots through distributed shared memory (one remote load per lane, all in flight at
+// once), lane 0 sums them in rank order (so every CTA gets the same doubles) and the CTA reads them
+// from shared memory. All threads of the CTA must call it.
+__device__ __forceinline__ void cluster_totals(const float2* slots, int nv, unsigned nctas, double* s_tot,
+                                               double* out) {
+  if (threadIdx.x < 32) {
+    const unsigned q = threadIdx.x;
+    float2 y[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (q < nctas)
+      for (int v = 0; v < nv; ++v) y[v] = dsmem_ld_f2(slots + v, q);
+    for (int v = 0; v < nv; ++v) {
+      F2 acc{0.f, 0.f};
+      for (unsigned k = 0; k < nctas; ++k) {
+        const float hi = __shfl_sync(0xffffffffu, y[v].x, k), lo = __shfl_sync(0xffffffffu, y[v].y, k);
+        acc = f2_add(acc, F2{hi, lo});
+      }
+      if (q == 0) s_tot[v] = (double)acc.hi + (double)acc.lo;
+    }
+  }
+  __syncthreads();
+  for (int v = 0; v < nv; ++v) out[v] = s_tot[v];
+}
+
+__global__ void __launch_bounds__(kClusterThreads, 1)
+k_pcg32_cluster(int n, int per, const int* __restrict__ rp, const int* __restrict__ col,
+                const float* __restrict__ val, const float* __restrict__ Dinv,
+                const unsigned char* __restrict__ mask, float* __restrict__ x, float* __restrict__ r,
+                float* __restrict__ z, float* __restrict__ p, float* __restrict__ Ap, PcgState* st) {
+  constexpr int NC = 3, TPR = 36, NPG = kClusterThreads / 12;
+  __shared__ float sacc[kClusterThreads];
+  __shared__ float sr[NPG][12];
+  __shared__ F2 sred[2][32];
+  __shared__ float2 slots[2][2];   // [buffer][value]: this CTA's partials of a reduction
+  __shared__ double s_tot[2];
+  const int t = threadIdx.x;
+  const unsigned rank = cluster_rank(), nctas = cluster_ctas();
+  const int i0 = min(n, (int)rank * per), i1 = min(n, i0 + per);
+  const float td[4] = {st->td[0], st->td[1], st->td[2], st->td[3]};
+  const int limit = st->limit, fixed = st->fixed;
+  const double rtol2 = st->rtol2, bb = st->bb;
+  double rz = st->rz, rr = st->rr, pq = 0.0, alpha = 0.0, beta = 0.0;
+  int iters = 0, negcurv = 0, buf = 0;
+  int done = st->done || limit <= 0;
+  const int br = t / TPR, w = t % TPR, rr_ = w / NC, cc = w % NC;
+  const int ln = t / 12, a = t % 12;
+  while (!done) {
+    // y = (A + tau D) p on this CTA's rows and the partial p.y
+    F2 part_pq{0.f, 0.f};
+    for (int base = i0; base < i1; base += kClusterRows) {
+      const int i = base + br;
+      float acc = 0.f;
+      if (i < i1) {
+        // up to 9 blocks of the row in flight at once (a node row has at most 9), as in k_spmv32
+        const int k0 = rp[i], k1 = rp[i + 1];
+        constexpr int U = 9;
+        float4 v[U];
+        int j[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int k = k0 + u;
+          if (k < k1) {
+            j[u] = col[k];
+            v[u] = __ldcs(reinterpret_cast<const float4*>(val + (size_t)k * 144 + rr_ * 12 + cc * 4));
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (k0 + u < k1) {
+            const float4 xv = __ldcg(reinterpret_cast<const float4*>(p + (size_t)j[u] * 12 + cc * 4));
+            acc = dot4_acc(acc, v[u], xv);
+          }
+        for (int k = k0 + U; k < k1; ++k) {
+          const float4 av = __ldcs(reinterpret_cast<const float4*>(val + (size_t)k * 144 + rr_ * 12 + cc * 4));
+          const float4 xv = __ldcg(reinterpret_cast<const float4*>(p + (size_t)col[k] * 12 + cc * 4));
+          acc = dot4_acc(acc, av, xv);
+        }
+      }
+      sacc[t] = acc;
+      __syncthreads();
+      if (i < i1 && cc == 0) {
+        const size_t gi = (size_t)i * 12 + rr_;
+        const float xi = __ldcg(p + gi);
+        float yi = (sacc[t] + sacc[t + 1]) + sacc[t + 2];
+        yi = __fmaf_rn(td[rr_ / 3], xi, yi);
+        if (mask && mask[gi]) yi = 0.f;
+        Ap[gi] = yi;
+        part_pq = f2_add(part_pq, f2_prod(xi, yi));
+      }
+      __syncthreads();
+    }
+    {
+      const F2 c = f2_block_sum(part_pq, sred, 0);
+      if (t == 0) slots[buf][0] = make_float2(c.hi, c.lo);
+    }
+    cluster_barrier();
+    cluster_totals(slots[buf], 1, nctas, s_tot, &pq);
+    buf ^= 1;
+    if (!(pq > 0.0)) {
+      negcurv = 1;
+      alpha = 0.0;
+      break;
+    }
+    alpha = rz / pq;
+    // x += alpha p, r -= alpha Ap, z = D r on this CTA's nodes; partials r.z, r.r
+    const float af = (float)alpha;
+    F2 prz{0.f, 0.f}, prr{0.f, 0.f};
+    for (int base = i0; base < i1; base += NPG) {
+      const int i = base + ln;
+      const size_t gi = (size_t)i * 12 + a;
+      float ri = 0.f, zi = 0.f;
+      if (i < i1) {
+        x[gi] = fmaf(af, p[gi], x[gi]);
+        ri = fmaf(-af, Ap[gi], r[gi]);
+        r[gi] = ri;
+        sr[ln][a] = ri;
+      }
+      __syncthreads();
+      if (i < i1) {
+        if (!(mask && mask[gi])) {
+          const float* D = Dinv + (size_t)i * 144 + a * 12;
+          const float* q = sr[ln];
+          zi = __fmaf_rn(D[0], q[0], 0.f);
+#pragma unroll
+          for (int c = 1; c < 12; ++c) zi = __fmaf_rn(D[c], q[c], zi);
+        }
+        z[gi] = zi;
+      }
+      prz = f2_add(prz, f2_prod(ri, zi));
+      prr = f2_add(prr, f2_prod(ri, ri));
+      __syncthreads();
+    }
+    {
+      const F2 c0 = f2_block_sum(prz, sred, 0);
+      const F2 c1 = f2_block_sum(prr, sred, 1);
+      if (t == 0) {
+        slots[buf][0] = make_float2(c0.hi, c0.lo);
+        slots[buf][1] = make_float2(c1.hi, c1.lo);
+      }
+    }
+    cluster_barrier();
+    double tot[2];
+    cluster_totals(slots[buf], 2, nctas, s_tot, tot);
+    const double rz_new = tot[0];
+    rr = tot[1];
+    buf ^= 1;
+    iters += 1;
+    beta = rz_new / rz;
+    rz = rz_new;
+    if (fixed == 0 && rr <= rtol2 * bb) done = 1;
+    if (rz_new == 0.0) done = 1;
+    if (iters >= limit) done = 1;
+    if (done) break;
+    // p = z + beta p on this CTA's rows, then every CTA waits before the next SpMV reads them
+    const float bf = (float)beta;
+    for (int k = i0 * 12 + t; k < i1 * 12; k += blockDim.x) p[k] = fmaf(bf, p[k], z[k]);
+    cluster_barrier();
+  }
+  // no CTA leaves while another may still read its partials
+  cluster_barrier();
+  if (rank == 0 && t == 0) {
+    st->iters = iters;
+    st->rz = rz;
+    st->rr = rr;
+    st->pq = pq;
+    st->alpha = alpha;
+    st->beta = beta;
+    st->negcurv = negcurv;
+    st->done = 1;
+  }
+}
+
+
 // row a of a 12x12 block times sr, as the explicit FMA chain of k_pcg32_update
 __device__ __forceinline__ float apply_block32(const float* __restrict__ D, const float* sr, int a) {
   float s = 0.f;
@@ -1444,6 +1659,63 @@ shell_status launch_pcg_persistent(Shell& s, const unsigned char* mask) {
                   (void*)&s.d_pcg, (void*)&ps, (void*)&part, (void*)&polls, (void*)&s.d_err};
   BHEM_CUDA(cudaLaunchCooperativeKernel((const void*)k_pcg32_persistent, dim3(G), dim3(kSpmvThreads), args, 0,
                                         s.stream));
+  ++s.launches;
+  return SHELL_OK;
+}
+
+// Cluster size for the cluster PCG (16 where the device runs such a cluster, else 8; 0 if none),
+// decided once per device.
+static int cluster_pcg_ctas(int device) {
+  static int cached[64] = {0};
+  static bool known[64] = {false};
+  const int d = device & 63;
+  if (known[d]) return cached[d];
+  int best = 0;
+  if (cudaFuncSetAttribute(k_pcg32_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    cudaGetLastError();
+  for (int c : {kClusterMaxCtas, 8}) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(kClusterThreads);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = c;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_pcg32_cluster, &cfg) == cudaSuccess && nclusters > 0) {
+      best = c;
+      break;
+    }
+    cudaGetLastError();
+  }
+  cached[d] = best;
+  known[d] = true;
+  return best;
+}
+
+shell_status launch_pcg_cluster(Shell& s, const unsigned char* mask) {
+  if (s.val_fp64) return fail(SHELL_ERR_ARG, "the cluster PCG is for mixed precision");
+  const int C = cluster_pcg_ctas(s.device);
+  if (C <= 0) return fail(SHELL_ERR_CUDA, "no thread-block cluster fits this device");
+  const int n = s.n_nodes;
+  const int per = (n + C - 1) / C;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kClusterThreads);
+  cfg.stream = s.stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  BHEM_CUDA(cudaLaunchKernelEx(&cfg, k_pcg32_cluster, n, per, (const int*)s.d_row_ptr, (const int*)s.d_col,
+                               (const float*)s.d_val, (const float*)s.d_Dinv, mask, s.d_x32, s.d_r32, s.d_z32,
+                               s.d_p32, s.d_Ap32, s.d_pcg));
   ++s.launches;
   return SHELL_OK;
 }

@@ -549,6 +549,7 @@ def test_pcg_device_loop_matches_host_loop(monkeypatch, case, mass_scale, fixed)
     assert np.array_equal(res[0][0], res[1][0])
 
 
+@pytest.mark.parametrize("mode", ["persistent", "cluster"])
 @pytest.mark.parametrize("case,mass_scale,fixed", [
     ("sheet10x10-noisy", 1e6, 0),      # converges to rtol
     ("sheet10x10-noisy", 1e6, 7),      # a fixed iteration count
@@ -556,11 +557,12 @@ def test_pcg_device_loop_matches_host_loop(monkeypatch, case, mass_scale, fixed)
     ("sinusoid64", 1e6, 0),            # 4,225 nodes: many CTAs, several rows each
     ("annulus280x5", 1e6, 0),          # periodic
 ])
-def test_pcg_persistent_matches_host_loop(monkeypatch, case, mass_scale, fixed):
-    """The default mixed-precision solve is one persistent cooperative launch whose CTAs meet at
-    grid barriers; the host-chunked form launches one kernel per phase. Same arithmetic per
-    element, partial sums combined in another order: same curvature flag, iteration counts within
-    one (the stopping test may fall either side), solutions within the solver's tolerance."""
+def test_pcg_single_launch_forms_match_host_loop(monkeypatch, mode, case, mass_scale, fixed):
+    """Two mixed-precision solves run as one launch: the persistent cooperative kernel, whose CTAs
+    meet at software grid barriers, and the thread-block cluster kernel (BHEM_PCG_LOOP=cluster),
+    whose CTAs meet at the hardware cluster barrier and reduce through distributed shared memory. The host-chunked form launches one kernel per phase. Same arithmetic per element,
+    partial sums combined in another order: same curvature flag, iteration counts within one (the
+    stopping test may fall either side), solutions within the solver's tolerance."""
     if case == "sinusoid16":
         g, rest, q = S.sheet_sinusoid(16, 3)
         mat = THIN
@@ -574,8 +576,8 @@ def test_pcg_persistent_matches_host_loop(monkeypatch, case, mass_scale, fixed):
         g, rest, q, mat = CASES[case]()
     mask = dev(S.pinned_mask(g, [0]), torch.uint8)
     res = []
-    for mode in ("persistent", "host"):
-        monkeypatch.setenv("BHEM_PCG_LOOP", mode)
+    for m in (mode, "host"):
+        monkeypatch.setenv("BHEM_PCG_LOOP", m)
         sh = make_shell(g, mat, rest, precision="mixed", assembly="color")
         _, G = sh.energy_grad_hess(dev(q.reshape(-1)), mass_scale=mass_scale)
         x, it, neg = sh.pcg_solve(-G, mask=mask, rtol=1e-6, max_iter=1000, fixed_iters=fixed)
