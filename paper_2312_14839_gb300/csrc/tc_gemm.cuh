@@ -1,8 +1,8 @@
 // BF16 GEMM on the fifth-generation tensor cores: C[m][n] = sum_k A[m][k] B[n][k], FP32
 // accumulation in tensor memory (TMEM). Operands are K-contiguous BF16 matrices in global memory,
 // moved into shared memory by TMA tensor copies; one thread issues tcgen05.mma (kind::f16, BF16
-// inputs, FP32 accumulator), and the four warps of the CTA read the accumulator back with
-// tcgen05.ld for the epilogue.
+// inputs, FP32 accumulator), and the warps of the CTA read the accumulator back with tcgen05.ld
+// for the epilogue.
 //
 // Shared-memory operand layout (128-byte swizzle, K-major canonical form): a K chunk of 64 BF16
 // columns is one 128-byte row per matrix row, 8-row atoms of 1024 bytes, the 16-byte pieces of
@@ -15,8 +15,8 @@
 // to the stage's "empty" mbarrier, which releases the stage to the producer. A final commit
 // signals the epilogue, which all 8 warps share. With 128-column tiles two CTAs fit an SM, so one
 // CTA's epilogue (latency-bound: TMEM loads, staging stores, proxy fences, TMA store issue)
-// overlaps the other's loads and MMAs. Every wait is bounded: on expiry the CTA raises an error bit, waits
-// (bounded) for the copies it issued, skips the epilogue, frees its TMEM and returns.
+// overlaps the other's loads and MMAs. Every wait is bounded: on expiry the CTA raises an error
+// bit, waits (bounded) for the copies it issued, skips the epilogue, frees its TMEM and returns.
 #pragma once
 
 #include <cuda.h>
