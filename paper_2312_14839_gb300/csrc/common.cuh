@@ -177,6 +177,10 @@ struct Shell {
   // mixed precision: shells of at most this many nodes solve PCG as one thread-block cluster
   // (default 0: never, the graph loop was faster on every workload; BHEM_PCG_LOOP=cluster: always)
   int pcg_cluster_max_nodes = 0;
+  // mixed precision, plain SpMV, shells of at most 16,384 nodes: the p-update folded into the next
+  // iteration's SpMV (default; the environment variable BHEM_PCG_PUPDATE=1 at shell creation keeps
+  // the separate p-update kernel)
+  bool pcg_fold_pupdate = true;
 
   // CUDA graphs of the mixed-precision PCG loop, keyed by mask (iters = -1)
   struct PcgGraph { const unsigned char* mask; int iters; cudaGraphExec_t exec; };
@@ -259,6 +263,9 @@ shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, const dou
 // the whole mixed-precision solve as one graph: a conditional WHILE node around one iteration
 shell_status launch_pcg_loop_graph(Shell& s, const unsigned char* mask);
 shell_status launch_pcg_persistent(Shell& s, const unsigned char* mask);
+// kernels per mixed-precision PCG iteration, and whether the p-update rides in the SpMV
+bool pcg_folds_pupdate(const Shell& s);
+int pcg_kernels_per_iteration(const Shell& s);
 // the whole mixed-precision solve as one thread-block cluster (small shells)
 shell_status launch_pcg_cluster(Shell& s, const unsigned char* mask);
 int pcg_loop_unroll();   // PCG iterations per loop body

@@ -228,6 +228,8 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
     if (m && std::strcmp(m, "graph") == 0) s->pcg_cluster_max_nodes = 0;
     if (m && std::strcmp(m, "cluster") == 0) s->pcg_cluster_max_nodes = 1 << 30;
     s->pcg_host_loop = s->pcg_mode == 2;
+    const char* pu = getenv("BHEM_PCG_PUPDATE");
+    s->pcg_fold_pupdate = !(pu && std::strcmp(pu, "1") == 0);
     const char* f = getenv("BHEM_FUSE_FIRST_HESSIAN");
     s->fuse_first_hessian = !(f && std::strcmp(f, "0") == 0);
   }
@@ -451,8 +453,8 @@ static shell_status run_pcg(Shell& s, const unsigned char* mask, const double td
     if (limit > 0) BHEM_TRY(launch_pcg_loop_graph(s, mask));
     BHEM_CUDA(cudaMemcpyAsync(s.h_pcg, s.d_pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s.stream));
     BHEM_CUDA(cudaStreamSynchronize(s.stream));
-    // per body: SpMV, update and p-update per iteration, and the loop condition
-    s.launches += (3LL * pcg_loop_unroll() + 1) * s.h_pcg->bodies;
+    // per body: the PCG kernels of each iteration (2 with the folded p-update, else 3) and the loop condition
+    s.launches += ((long long)pcg_kernels_per_iteration(s) * pcg_loop_unroll() + 1) * s.h_pcg->bodies;
     mark(s, "pcg_loop");
     launched = limit;
   } else {

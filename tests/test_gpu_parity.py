@@ -722,3 +722,42 @@ def test_fused_first_residual_and_hessian_equal_separate_launches(grid, hessian,
     assert abs(s1["pcg_iters_total"] - s0["pcg_iters_total"]) <= s0["newton_iters"], (s1, s0)
     assert s1["res0"] == pytest.approx(s0["res0"], rel=1e-12)
     assert rel(q1 - q0.reshape(-1), q0_ - q0.reshape(-1)) <= 1e-5
+
+
+@pytest.mark.parametrize("case,mass_scale,fixed", [
+    ("sheet10x10-noisy", 1e6, 0),
+    ("sheet10x10-noisy", 1e6, 7),
+    ("sinusoid16", 1.0, 0),            # indefinite: negative curvature
+    ("annulus280x5", 1e6, 0),
+])
+def test_pcg_folded_direction_update_matches_separate_kernel(monkeypatch, case, mass_scale, fixed):
+    """Small shells fold the PCG's p = z + beta p into the next iteration's SpMV, which gathers z
+    and forms Ap as (A + tau D) z + beta Ap. Against the separate p-update kernel
+    (BHEM_PCG_PUPDATE=1): the same direction arithmetic, Ap by linearity instead of recomputed, so
+    the same curvature flag, iteration counts within one and solutions within the solver's
+    tolerance."""
+    if case == "sinusoid16":
+        g, rest, q = S.sheet_sinusoid(16, 3)
+        mat = THIN
+    elif case == "annulus280x5":
+        g, rest, q = S.annulus_sinusoid(280, 5, 3, 0.01)
+        mat = THIN
+    else:
+        g, rest, q, mat = CASES[case]()
+    mask = dev(S.pinned_mask(g, [0]), torch.uint8)
+    res = []
+    for v in ("0", "1"):
+        monkeypatch.setenv("BHEM_PCG_PUPDATE", v)
+        sh = make_shell(g, mat, rest, precision="mixed", assembly="color")
+        _, G = sh.energy_grad_hess(dev(q.reshape(-1)), mass_scale=mass_scale)
+        x, it, neg = sh.pcg_solve(-G, mask=mask, rtol=1e-6, max_iter=1000, fixed_iters=fixed)
+        res.append((host(x), it, neg))
+        sh.close()
+    assert res[0][2] == res[1][2], (res[0][1:], res[1][1:])
+    assert abs(res[0][1] - res[1][1]) <= 1, (res[0][1:], res[1][1:])
+    if fixed:
+        assert res[0][1] == res[1][1] == fixed
+    if case == "sinusoid16":
+        assert res[0][2] == 1
+    else:
+        assert rel(res[0][0], res[1][0]) <= 1e-4
