@@ -514,10 +514,13 @@ k_pcg_init(int n, const int* __restrict__ nshell, ShellState* st, const double* 
 __device__ __forceinline__ bool pcg_running(const ShellState& S) { return S.active && !S.pcg_done; }
 
 // y = (A + tau D) p on rows of running shells; acc[0] += p.y
+// x is z: per running shell's own rows, p = z + beta p (the first iteration of a solve: p = z)
+// and y = Ap = (A + tau D) z + beta Ap, equal to (A + tau D) p by linearity, so no separate
+// p-update launch follows the update
 __global__ void __launch_bounds__(kSpmvThreads)
 k_spmv(int n, const int* __restrict__ nshell, ShellState* st, const int* __restrict__ rp,
        const int* __restrict__ col, const float* __restrict__ val, const float* __restrict__ x,
-       const unsigned char* __restrict__ mask, float* __restrict__ y) {
+       const unsigned char* __restrict__ mask, float* __restrict__ p, float* __restrict__ y) {
   __shared__ float sacc[kSpmvThreads];
   const int t = threadIdx.x;
   const int br = t / 36, w = t % 36, r = w / 3, cc = w % 3;
@@ -546,12 +549,19 @@ k_spmv(int n, const int* __restrict__ nshell, ShellState* st, const int* __restr
   F2 part{0.f, 0.f};
   if (run && cc == 0) {
     const size_t gi = (size_t)i * 12 + r;
-    const float xi = x[gi];
-    float yi = (sacc[t] + sacc[t + 1]) + sacc[t + 2];
-    yi += st[sh].td[r / 3] * xi;
-    if (mask && mask[gi]) yi = 0.f;
-    y[gi] = yi;
-    part = f2_prod(xi, yi);
+    const float zi = x[gi];
+    float wi = (sacc[t] + sacc[t + 1]) + sacc[t + 2];
+    wi += st[sh].td[r / 3] * zi;
+    if (mask && mask[gi]) wi = 0.f;
+    float pi = zi, qi = wi;
+    if (st[sh].pcg_iters > 0) {
+      const float bf = (float)st[sh].beta;
+      pi = fmaf(bf, p[gi], zi);
+      qi = fmaf(bf, y[gi], wi);
+    }
+    p[gi] = pi;
+    y[gi] = qi;
+    part = f2_prod(pi, qi);
   }
   seg_add_f2(part, sh, s0, s1, run0, run1, st, 0);
 }
@@ -593,14 +603,6 @@ k_pcg_update(int n, const int* __restrict__ nshell, ShellState* st, float* __res
   seg_add_f2(f2_prod(ri, ri), sh, s0, s1, run0, run1, st, 1);
 }
 
-__global__ void k_pcg_pupdate(int n, const int* __restrict__ nshell, const ShellState* st,
-                              const float* __restrict__ z, float* __restrict__ p) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n * 12; k += gridDim.x * blockDim.x) {
-    const int s = nshell[k / 12];
-    if (!pcg_running(st[s])) continue;
-    p[k] = fmaf((float)st[s].beta, p[k], z[k]);
-  }
-}
 
 // ------------------------------------------------------------------------------------------
 // Controllers: one thread per shell
@@ -1221,15 +1223,16 @@ shell_status residual(shell_batch_s& b, const double* q, const shell_step_params
   return read_counters(b);
 }
 
+constexpr int kPcgKernels = 4;   // per PCG iteration: SpMV (with the p-update), alpha, update, beta
+
 shell_status pcg_chunk(shell_batch_s& b, const unsigned char* mask, int iters) {
   for (int k = 0; k < iters; ++k) {
     k_spmv<<<blocks_for(b.N, kRowNodes), kSpmvThreads, 0, b.stream>>>(b.N, b.nshell, b.st, b.row_ptr, b.col,
-                                                                        b.val, b.p32, mask, b.Ap32);
+                                                                        b.val, b.z32, mask, b.p32, b.Ap32);
     k_ctrl_alpha<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st);
     k_pcg_update<<<blocks_for(b.N, 16), kNodeThreads, 0, b.stream>>>(b.N, b.nshell, b.st, b.x32, b.r32, b.z32,
                                                                       b.p32, b.Ap32, b.Dinv, mask);
     k_ctrl_beta<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st);
-    k_pcg_pupdate<<<vblocks(b.M), 256, 0, b.stream>>>(b.N, b.nshell, b.st, b.z32, b.p32);
   }
   BHEM_CUDA(cudaGetLastError());
   return SHELL_OK;
@@ -1253,7 +1256,7 @@ shell_status pcg_chunk_graph(shell_batch_s& b, const unsigned char* mask, int it
     b.pcg_graph_mask = mask;
   }
   BHEM_CUDA(cudaGraphLaunch(b.pcg_graph, b.stream));
-  b.launches += 5LL * iters;
+  b.launches += (long long)kPcgKernels * iters;
   return SHELL_OK;
 }
 
@@ -1437,7 +1440,7 @@ shell_status enqueue_newton_body(shell_batch_s& b, const shell_step_params& P, c
     BHEM_TRY(cap_body(b, 3, pcg_body, [&]() -> shell_status {
       const long long p0 = b.launches;
       BHEM_TRY(pcg_chunk(b, mask, kGraphPcgChunk));
-      b.launches += 5LL * kGraphPcgChunk;
+      b.launches += (long long)kPcgKernels * kGraphPcgChunk;
       BHEM_TRY(zero_counters(b));
       k_ctrl_count_running<<<blocks_for(b.S, 128), 128, 0, b.stream>>>(b.S, b.st, b.cnt);
       k_cond_pcg<<<1, 1, 0, b.stream>>>(b.cnt, b.loop, limit, h_pcg, 0);
