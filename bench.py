@@ -511,6 +511,24 @@ def network_timing(net, X_all, T_all, n_sheet=64, reps=20):
 #    about 190 FMA of nonlinear point work at each of the 16 Gauss points = 6,112 FMA.
 ELEMENT_FLOP_PER_PATCH = 2 * (16 * 15 * 48 * 5 + 1176 * 80)
 ENERGY64_FLOP_PER_PATCH = 2 * (1536 + 1536 + 16 * 190)
+# The tensor-core form of the element pass (the default of a mixed-precision shell) issues per patch
+# 96 rows (6 component pairs x 16 J) x 16 columns x 96 K values (16 Gauss points x 6 kinds) TF32
+# multiply-adds, three times (head and tail products): 442,368 tensor MACs.
+ELEMENT_TC_TENSOR_FLOP_PER_PATCH = 2 * 3 * 96 * 16 * 96
+# dense TF32 against dense BF16 on the fifth-generation tensor cores (nominal 1.1 / 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def element_form():
+    """Which FP32 element pass a mixed-precision shell created now runs (BHEM_ELEMENT)."""
+    return "ffma" if os.environ.get("BHEM_ELEMENT") == "ffma" else "tc"
+
+
+def element_kernel_name():
+    if element_form() == "tc":
+        return ("k_element_tc (FP32 exact Hessian: Gauss-point matrices and T rows on the FMA pipe, "
+                "the contraction K = Psi^T T on tcgen05 kind::tf32 from tensor memory")
+    return "k_element_full<float> (FP32 exact Hessian on the FMA pipe"
 
 
 def alu_rooflines(sh, q_d, P, n_patches, stream, reps=5):
@@ -538,7 +556,7 @@ def alu_rooflines(sh, q_d, P, n_patches, stream, reps=5):
     t_eg = timed(lambda: sh.energy_grad_hess(q_d, want_hessian=False))
     out = []
     for kern, t, flop, pk, what in (
-            ("k_element_full<float> (FP32 exact Hessian + BSR scatter; the BSR clear is in the time)",
+            (element_kernel_name() + " + BSR scatter; the BSR clear is in the time)",
              t_el, ELEMENT_FLOP_PER_PATCH, peak32, "FP32"),
             ("k_energy_grad64 (FP64 energy + assembled gradient; the gradient clear is in the time)",
              t_eg, ENERGY64_FLOP_PER_PATCH, peak64, "FP64")):
@@ -546,6 +564,17 @@ def alu_rooflines(sh, q_d, P, n_patches, stream, reps=5):
         out.append({"kernel": kern, "bound": "alu", "achieved": ach, "peak": pk / 1e12, "unit": "TFLOP/s",
                     "frac": ach * 1e12 / pk, "flop_per_patch": flop, "avg_launch_us": t * 1e6,
                     "peak_source": f"measured {what} FMA microbenchmark (shell_measure_fma_peak)"})
+    if element_form() == "tc":
+        # the same pass's tensor-core work against the TF32 peak (measured BF16 x nominal ratio)
+        path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        bf16 = json.load(open(path)).get("bf16_tflops") if os.path.exists(path) else None
+        tf32 = (bf16 if bf16 else 1900.0) * TF32_PER_BF16
+        ach = ELEMENT_TC_TENSOR_FLOP_PER_PATCH * n_patches / t_el / 1e12
+        out.append({"kernel": "k_element_tc tensor-core work (TF32 head and tail products)", "bound": "tensor",
+                    "achieved": ach, "peak": tf32, "unit": "TFLOP/s", "frac": ach / tf32,
+                    "flop_per_patch": ELEMENT_TC_TENSOR_FLOP_PER_PATCH, "avg_launch_us": t_el * 1e6,
+                    "peak_source": ("measured bf16_tflops (MEASURED_PEAKS.json) x 1.1/2.25 (nominal dense "
+                                    "TF32/BF16)" if bf16 else "fallback 1.9 PFLOP/s bf16 x 1.1/2.25")})
     return out
 
 
@@ -573,7 +602,7 @@ def element_kernel_only(sh, q_d, n_patches, stream, reps=5):
     t = e0.elapsed_time(e1) / 1e3 / reps
     del H
     return {"patch_hessians_per_s": n_patches / t, "avg_launch_us": t * 1e6,
-            "what": "k_element_full<float> writing the 48x48 FP32 Hessians unassembled (no BSR clear or scatter)"}
+            "what": element_kernel_name() + ") writing the 48x48 FP32 Hessians unassembled (no BSR clear or scatter)"}
 
 
 # FP64 operations per step of the ray search (adds, multiplies, compares, min/max, divisions and

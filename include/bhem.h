@@ -152,11 +152,13 @@ SHELL_API shell_status shell_info(const shell_t* shell, shell_info_t* info);
 
 /* Budget of the library's bounded device-side waits on this shell: the grid barriers of the
    persistent mixed-precision PCG (one cooperative launch per solve; selected by the environment
-   variable BHEM_PCG_LOOP=persistent when the shell is created) and the mbarrier waits of
-   the bulk-copy SpMV (SHELL_SPMV_TMA) poll at most `polls` times before the waiting CTA gives
-   up. The call then returns SHELL_ERR_TIMEOUT (its results are void): a CTA that gave up at a
-   barrier leaves the kernel, the others give up at their next barrier, and the bulk-copy SpMV
-   still waits, with the default budget, for the copies it has issued, so that the device stays
+   variable BHEM_PCG_LOOP=persistent when the shell is created), the mbarrier waits of
+   the bulk-copy SpMV (SHELL_SPMV_TMA) and those of the tensor-core element pass (mixed
+   precision; each CTA waits for the MMAs it commits) poll at most `polls` times before the
+   waiting CTA gives up. The call then returns SHELL_ERR_TIMEOUT (its results are void): a CTA
+   that gave up at a barrier leaves the kernel, the others give up at their next barrier, and the
+   bulk-copy SpMV and the tensor-core element pass still wait, with the default budget, for the
+   copies or MMAs they have issued (then free their tensor memory), so that the device stays
    usable.
    polls < 0 restores the default (2^20 polls); 0 makes every such wait expire at once (a test
    of the timeout path). Synchronises the shell's stream and drops its cached PCG graphs. No paper
@@ -175,7 +177,10 @@ SHELL_API shell_status shell_grid_colours(const shell_grid* grid, int* colour);
 /* Element-by-element evaluation, unassembled (App. B): for every patch p, energy_p[p] (FP64),
    grad_p[p * 48 + l] (FP64) and hess_p[p * 2304 + l * 48 + m] (FP32 when precision is
    SHELL_PREC_MIXED, FP64 when SHELL_PREC_FP64), l, m patch-local DOF indices. q: device
-   [n_nodes * 12]. Any output may be NULL. Asynchronous. */
+   [n_nodes * 12]. Any output may be NULL. Asynchronous. The FP32 Hessian's contraction
+   K = sum_g Phi_g^T M_g Phi_g (App. B.2) runs on the tensor cores (TF32 head-and-tail products,
+   FP32 accuracy) unless the environment variable BHEM_ELEMENT=ffma was set when the shell was
+   created (then on the FP32 FMA pipe); this applies to every FP32 Hessian of the shell. */
 SHELL_API shell_status shell_element_egh(shell_t* shell, const double* q, int precision, double* energy_p,
                                double* grad_p, void* hess_p);
 

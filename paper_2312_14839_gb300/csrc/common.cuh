@@ -174,6 +174,10 @@ struct Shell {
   // mixed precision: a step's first residual and Hessian in one element launch (default; the
   // environment variable BHEM_FUSE_FIRST_HESSIAN=0 at shell creation selects separate launches)
   bool fuse_first_hessian = true;
+  // mixed precision: the FP32 element Hessian's contraction on the tensor cores (tcgen05, TF32
+  // head-and-tail products; default), or on the FP32 FMA pipe (the environment variable
+  // BHEM_ELEMENT=ffma at shell creation)
+  bool elem_tc = true;
   // mixed precision: shells of at most this many nodes solve PCG as one thread-block cluster
   // (default 0: never, the graph loop was faster on every workload; BHEM_PCG_LOOP=cluster: always)
   int pcg_cluster_max_nodes = 0;

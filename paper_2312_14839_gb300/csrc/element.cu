@@ -278,6 +278,17 @@ static shell_status launch_full_t(Shell& s, const ElemArgs& A, int work) {
   return SHELL_OK;
 }
 
+// element_tc.cu: the FP32 pass with the tensor-core contraction (same arguments and outputs)
+shell_status launch_full_tc(Shell& s, const ElemArgs& A, int work);
+
+template <typename R>
+static shell_status launch_full_pick(Shell& s, const ElemArgs& A, int work) {
+  if constexpr (sizeof(R) == 4) {
+    if (s.elem_tc) return launch_full_tc(s, A, work);
+  }
+  return launch_full_t<R>(s, A, work);
+}
+
 shell_status launch_element_full(Shell& s, const double* q, bool fp64, const ElemOutputs& out) {
   ElemArgs A{};
   A.np = s.n_patches;
@@ -313,12 +324,12 @@ shell_status launch_element_full(Shell& s, const double* q, bool fp64, const Ele
       ElemArgs Ac = A;
       Ac.plist = s.d_color_list + b;
       Ac.plist_n = e - b;
-      BHEM_TRY(fp64 ? launch_full_t<double>(s, Ac, e - b) : launch_full_t<float>(s, Ac, e - b));
+      BHEM_TRY(fp64 ? launch_full_t<double>(s, Ac, e - b) : launch_full_pick<float>(s, Ac, e - b));
     }
     return SHELL_OK;
   }
   A.bsr_atomic = 1;
-  return fp64 ? launch_full_t<double>(s, A, A.np) : launch_full_t<float>(s, A, A.np);
+  return fp64 ? launch_full_t<double>(s, A, A.np) : launch_full_pick<float>(s, A, A.np);
 }
 
 }  // namespace bhem

@@ -295,6 +295,26 @@ __device__ __forceinline__ int sym15(int i, int j) {
   return i * 15 - (i * (i - 1)) / 2 + (j - i);
 }
 
+// Component-pair block layout of M_g (tensor-core Hessian kernel): for the six pairs c <= d
+// (index cd: (0,0) 0, (0,1) 1, (0,2) 2, (1,1) 3, (1,2) 4, (2,2) 5) the 5x5 matrix
+// m^{cd}[k][l] = M_g[(k, c), (l, d)] over the derivative kinds, rows of 6 at cd * kBlk + 6 k + l
+// (kBlk = 32: rows k, k + 1 of even k start 16-byte aligned). The pairs c > d are the transposes.
+constexpr int kBlk = 32;
+constexpr int kBlkRow = 6;
+// floats per Gauss point: the six blocks (192) padded to 196, so that the 16 lanes that store the
+// matrices of 16 Gauss points at once fall in 8 distinct banks
+constexpr int kMbG = 6 * kBlk + 4;
+__host__ __device__ constexpr int cd_index(int x, int y) { return x * 3 - (x * (x - 1)) / 2 + (y - x); }
+struct BlkOff { int a, b; };
+// Offsets of the entry M[(K1, x), (L1, y)] in the block layout, and of its mirror in a diagonal
+// block (-1: none)
+__host__ __device__ constexpr BlkOff blk_off(int K1, int x, int L1, int y) {
+  return x < y   ? BlkOff{cd_index(x, y) * kBlk + K1 * kBlkRow + L1, -1}
+         : x > y ? BlkOff{cd_index(y, x) * kBlk + L1 * kBlkRow + K1, -1}
+                 : BlkOff{cd_index(x, x) * kBlk + K1 * kBlkRow + L1,
+                          K1 != L1 ? cd_index(x, x) * kBlk + L1 * kBlkRow + K1 : -1};
+}
+
 // Row stride of T: FP32 rows are padded to 52 (16-byte aligned, and the rows that 8 lanes read
 // together with 16-byte loads fall in distinct banks).
 template <typename R> struct TStride { static constexpr int v = 45; };
@@ -345,8 +365,8 @@ struct ElemArgs {
 // instructions in the exchanged frame, which gives the blocks (sigma(k), sigma(l)) with k in
 // {1, 3}: together all 15 blocks. Half 1 discards the three blocks that map onto themselves
 // ((0, 1), (2, 3), (4, 4)) and the by-products (energy, gradient vectors, mass weight).
-template <typename R, bool kSplit>
-__device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W, int g, int half,
+template <typename R, bool kSplit, bool kBlocks = false, class WS = WarpSmem<R>>
+__device__ __forceinline__ void gauss_point_matrix(const R* sphi, WS& W, int g, int half,
                                                    const ElemArgs& A) {
   V3<R> ub[5], uu[5];
   interp5<R, R>(sphi, W.qb, g, ub);   // rest a_bar_1, a_bar_2, x_bar_{,11}, x_bar_{,22}, x_bar_{,12}
@@ -459,7 +479,9 @@ __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W
   const R ia = isqa * isqa;
   const R a11 = dot(a1, a1), a22 = dot(a2, a2), a12 = dot(a1, a2);
   const R coef[3] = {mm[0], mm[1], (R)2 * mm[2]};
-  R* M = W.M[g];
+  R* M;
+  if constexpr (kBlocks) M = W.Mb[g];
+  else M = W.M[g];
 #pragma unroll
   for (int k = 0; k < 5; ++k)
 #pragma unroll
@@ -513,8 +535,19 @@ __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WarpSmem<R>& W
           // sigma: the kind index in the original frame of a kind of the exchanged frame
           constexpr int kSig[5] = {1, 0, 3, 2, 4};
           const bool self_mirror = (k == 0 && l == 1) || (k == 2 && l == 3) || (k == 4 && l == 4);
-          if (!half) M[sym15(k * 3 + x, l * 3 + y)] = v;
-          else if (!self_mirror) M[sym15(kSig[k] * 3 + x, kSig[l] * 3 + y)] = v;
+          if constexpr (kBlocks) {
+            const BlkOff o0 = blk_off(k, x, l, y), o1 = blk_off(kSig[k], x, kSig[l], y);
+            if (!half) {
+              M[o0.a] = v;
+              if (o0.b >= 0) M[o0.b] = v;
+            } else if (!self_mirror) {
+              M[o1.a] = v;
+              if (o1.b >= 0) M[o1.b] = v;
+            }
+          } else {
+            if (!half) M[sym15(k * 3 + x, l * 3 + y)] = v;
+            else if (!self_mirror) M[sym15(kSig[k] * 3 + x, kSig[l] * 3 + y)] = v;
+          }
         }
 }
 
@@ -587,6 +620,42 @@ __device__ __forceinline__ void t_stage(const R* w1d, const R* Mg, R* T, int g, 
 // staged in shared memory over the Gauss-point matrices (no longer needed), from which the
 // unassembled Hessian and the BSR rows are written as before.
 constexpr int kKStride = 52;   // row stride of the staged 48 x 48 Hessian (16-byte aligned rows)
+
+// Writes one patch's FP32 Hessian, staged in shared memory as K[(I, c) * kKStride + (J, c')], to
+// the unassembled output and/or scatters it into the BSR values (one warp).
+__device__ __forceinline__ void store_staged_hessian32(const float* K, int p, const ElemArgs& A, int lane) {
+  if (A.hess_p) {
+    float* Hp = reinterpret_cast<float*>(A.hess_p) + (size_t)p * 2304;
+    for (int e = lane; e < 2304; e += 32) Hp[e] = K[(e / 48) * kKStride + e % 48];
+  }
+  if (A.bsr) {
+    // lane (I, h): rows (I, c) of the node blocks (I >> 2, b), b = 2h, 2h + 1, 12 entries each
+    float* V = reinterpret_cast<float*>(A.bsr);
+    const int I = lane >> 1, h = lane & 1, a = I >> 2, r = I & 3;
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb) {
+      const int b = 2 * h + bb;
+      const int kb = A.pblocks[p * 16 + a * 4 + b];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float4* src = reinterpret_cast<const float4*>(K + (I * 3 + c) * kKStride + b * 12);
+        float row[12];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const float4 v4 = src[q];
+          row[4 * q] = v4.x;
+          row[4 * q + 1] = v4.y;
+          row[4 * q + 2] = v4.z;
+          row[4 * q + 3] = v4.w;
+        }
+        float* dst = V + (size_t)kb * 144 + (r * 3 + c) * 12;
+        if (A.bsr_atomic) atomic_add_row12<float>(dst, row);
+        else plain_add_row12<float>(dst, row);
+      }
+    }
+  }
+  __syncwarp();
+}
 
 __device__ __forceinline__ void hessian_sym32(const float* sphi, const float* w1d, const float* sphg,
                                               WarpSmem<float>& W, int p, const ElemArgs& A, int lane) {
@@ -671,46 +740,12 @@ __device__ __forceinline__ void hessian_sym32(const float* sphi, const float* w1
       }
   }
   __syncwarp();
-  if (A.hess_p) {
-    float* Hp = reinterpret_cast<float*>(A.hess_p) + (size_t)p * 2304;
-    for (int e = lane; e < 2304; e += 32) Hp[e] = K[(e / 48) * kKStride + e % 48];
-  }
-  if (A.bsr) {
-    // lane (I, h): rows (I, c) of the node blocks (I >> 2, b), b = 2h, 2h + 1, 12 entries each
-    float* V = reinterpret_cast<float*>(A.bsr);
-    const int I = lane >> 1, h = lane & 1, a = I >> 2, r = I & 3;
-#pragma unroll
-    for (int bb = 0; bb < 2; ++bb) {
-      const int b = 2 * h + bb;
-      const int kb = A.pblocks[p * 16 + a * 4 + b];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float4* src = reinterpret_cast<const float4*>(K + (I * 3 + c) * kKStride + b * 12);
-        float row[12];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const float4 v4 = src[q];
-          row[4 * q] = v4.x;
-          row[4 * q + 1] = v4.y;
-          row[4 * q + 2] = v4.z;
-          row[4 * q + 3] = v4.w;
-        }
-        float* dst = V + (size_t)kb * 144 + (r * 3 + c) * 12;
-        if (A.bsr_atomic) atomic_add_row12<float>(dst, row);
-        else plain_add_row12<float>(dst, row);
-      }
-    }
-  }
-  __syncwarp();
+  store_staged_hessian32(K, p, A, lane);
 }
 
-// One patch by one warp: gather, Gauss-point matrices M_g, energy/gradient by-products, and the
-// Hessian K = sum_g phi_g^T M_g phi_g written unassembled and/or scattered into the BSR.
-template <typename R>
-__device__ __forceinline__ void element_patch(const R* sphi, const R* w1d, const R* sphg, WarpSmem<R>& W, int p,
-                                              const ElemArgs& A, int lane) {
-  constexpr int JP = ElemCfg<R>::kJP;          // J columns per pass (16 / 2 / JP passes)
-  const int I = lane >> 1, h = lane & 1;
+// Gathers the warp's patch: displacement u = q - rest and rest DOFs qb (shared memory).
+template <typename R, class WS>
+__device__ __forceinline__ void gather_patch(WS& W, int p, const ElemArgs& A, int lane) {
   const int4 pn = A.pnodes[p];
   const int nd[4] = {pn.x, pn.y, pn.z, pn.w};
   // Value DOFs enter only through derivatives, whose value-kind shape functions sum to zero
@@ -730,12 +765,12 @@ __device__ __forceinline__ void element_patch(const R* sphi, const R* w1d, const
       W.qb[l] = (R)rv;
     }
   }
-  __syncwarp();
-  if constexpr (sizeof(R) == 4) gauss_point_matrix<R, true>(sphi, W, lane & 15, lane >> 4, A);
-  else if (lane < 16) gauss_point_matrix<R, false>(sphi, W, lane, 0, A);
-  __syncwarp();
+}
 
-  // energy and gradient (by-products)
+// Energy and gradient of the patch in the kernel's precision (by-products of the Gauss-point
+// matrices: per-point energies W.en and gradient vectors W.G).
+template <typename R, class WS>
+__device__ __forceinline__ void patch_byproducts(const R* sphi, const WS& W, int p, const ElemArgs& A, int lane) {
   if (A.energy_p) {
     R e = lane < 16 ? W.en[lane] : (R)0;
     for (int o = 8; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -751,6 +786,21 @@ __device__ __forceinline__ void element_patch(const R* sphi, const R* w1d, const
       A.grad_p[(size_t)p * 48 + l] = (double)sacc;
     }
   }
+}
+
+// One patch by one warp: gather, Gauss-point matrices M_g, energy/gradient by-products, and the
+// Hessian K = sum_g phi_g^T M_g phi_g written unassembled and/or scattered into the BSR.
+template <typename R>
+__device__ __forceinline__ void element_patch(const R* sphi, const R* w1d, const R* sphg, WarpSmem<R>& W, int p,
+                                              const ElemArgs& A, int lane) {
+  constexpr int JP = ElemCfg<R>::kJP;          // J columns per pass (16 / 2 / JP passes)
+  const int I = lane >> 1, h = lane & 1;
+  gather_patch<R>(W, p, A, lane);
+  __syncwarp();
+  if constexpr (sizeof(R) == 4) gauss_point_matrix<R, true>(sphi, W, lane & 15, lane >> 4, A);
+  else if (lane < 16) gauss_point_matrix<R, false>(sphi, W, lane, 0, A);
+  __syncwarp();
+  patch_byproducts<R>(sphi, W, p, A, lane);
 
   const bool want_h = A.hess_p || A.bsr;
   if constexpr (sizeof(R) == 4) {

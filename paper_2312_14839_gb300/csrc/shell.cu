@@ -169,7 +169,8 @@ static shell_status sync_and_check(Shell& s) {
   }
   if (bits & ERRBIT_DEGENERATE) return fail(SHELL_ERR_DEGENERATE, "degenerate surface normal at a Gauss point");
   if (bits & ERRBIT_NONFINITE) return fail(SHELL_ERR_NONFINITE, "non-finite energy or residual");
-  if (bits & ERRBIT_TIMEOUT) return fail(SHELL_ERR_TIMEOUT, "a bounded device-side wait expired (bulk copy or grid barrier)");
+  if (bits & ERRBIT_TIMEOUT)
+    return fail(SHELL_ERR_TIMEOUT, "a bounded device-side wait expired (bulk copy, grid barrier or tensor-core MMA)");
   return SHELL_OK;
 }
 
@@ -232,6 +233,8 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
     s->pcg_fold_pupdate = !(pu && std::strcmp(pu, "1") == 0);
     const char* f = getenv("BHEM_FUSE_FIRST_HESSIAN");
     s->fuse_first_hessian = !(f && std::strcmp(f, "0") == 0);
+    const char* el = getenv("BHEM_ELEMENT");
+    s->elem_tc = !(el && std::strcmp(el, "ffma") == 0);
   }
 
   HostTopo T;
