@@ -329,6 +329,12 @@ def _fp64_step_against_oracle(g, mat, rest, q0, P, Po, mask=None, qfix=None, v0=
     return st, so, host(q), qo
 
 
+def _q_bound(st, so):
+    """State bound of an FP64 step against the oracle: rounding when every PCG solve stopped at the
+    same iteration, else the Newton criterion's (see the test below)."""
+    return 1e-11 if st["pcg_iters_total"] == so["pcg_iters_total"] else 1e-9
+
+
 def test_newton_backtracking_and_regulariser_ladder_fp64_identical():
     """16x16 sheet relaxing from the 5 cm sinusoid under gravity: the FP64 step meets negative
     curvature (regulariser ladder) and rejects line-search trials (quadratic and cubic
@@ -337,7 +343,10 @@ def test_newton_backtracking_and_regulariser_ladder_fp64_identical():
     GPU's FP64 Hessian and gradient are sums of patch contributions in atomic order, so their last
     bits vary from run to run; over this step's ~600 PCG iterations a solve whose residual ends
     within rounding of its tolerance can stop one iteration apart (seen: 624 against 625 in one
-    of several runs), so the PCG totals may differ by at most one per Newton iteration."""
+    of several runs), so the PCG totals may differ by at most one per Newton iteration. The states
+    then agree to FP64 rounding (1e-11) when the PCG totals are equal; when one solve stopped an
+    iteration apart, the two iterates differ by that solve's remainder, which the step's Newton
+    criterion (relative residual 1e-8, with PCG at eta = 1e-6) bounds, and the bound is 1e-9."""
     from paper_2312_14839_gb300.bhem import step_params
     g, rest, q0 = S.sheet_sinusoid(16, 3, 0.05)
     st, so, qg, qo = _fp64_step_against_oracle(g, THIN, rest, q0, step_params(dt=1e-3, newton_max=50),
@@ -346,7 +355,7 @@ def test_newton_backtracking_and_regulariser_ladder_fp64_identical():
     for key in ("status", "newton_iters", "ls_backtracks", "regularizations", "diag_fixes"):
         assert st[key] == so[key], (key, st, so)
     assert abs(st["pcg_iters_total"] - so["pcg_iters_total"]) <= so["newton_iters"], (st, so)
-    assert rel(qg, qo) <= 1e-11
+    assert rel(qg, qo) <= _q_bound(st, so), (rel(qg, qo), st["pcg_iters_total"], so["pcg_iters_total"])
     assert so["tau_final"] > 0 and st["tau_final"] == pytest.approx(so["tau_final"], rel=1e-12)
     # the same step with a regulariser level carried in (the first solve starts at 0.1): the same
     # decisions on both sides
@@ -357,7 +366,7 @@ def test_newton_backtracking_and_regulariser_ladder_fp64_identical():
     for key in ("status", "newton_iters", "ls_backtracks", "regularizations", "diag_fixes"):
         assert st2[key] == so2[key], (key, st2, so2)
     assert abs(st2["pcg_iters_total"] - so2["pcg_iters_total"]) <= so2["newton_iters"], (st2, so2)
-    assert rel(qg2, qo2) <= 1e-11
+    assert rel(qg2, qo2) <= _q_bound(st2, so2), (rel(qg2, qo2), st2["pcg_iters_total"], so2["pcg_iters_total"])
 
 
 def test_newton_planar_twist_diagonal_fix_fp64_identical():
