@@ -1212,14 +1212,23 @@ def step_workload_line(args, workload, dist, world, rank, full=True):
     torch.cuda.nvtx.range_pop()
     spmv_s = e0.elapsed_time(e1) / 1e3 / args.spmv_reps
     nb, n = sh.n_blocks, sh.n_nodes
-    spmv_bytes = nb * 144 * 4 + nb * 4 + (n + 1) * 4 + m * 4 + m * 4
+    sym = args.spmv != "tma" and os.environ.get("BHEM_SPMV_SYM") == "1"
+    if sym:
+        # diagonal and upper blocks once, column indices, the transpose map of the lower blocks,
+        # row pointers, diagonal positions, x and y
+        spmv_bytes = ((nb + n) // 2) * 144 * 4 + nb * 4 + ((nb - n) // 2) * 4 + (n + 1) * 4 + n * 4 + m * 4 + m * 4
+    else:
+        spmv_bytes = nb * 144 * 4 + nb * 4 + (n + 1) * 4 + m * 4 + m * 4
     peak, peak_kind = measured_peaks()
     achieved = spmv_bytes / spmv_s / 1e9
     traffic = recorded_traffic(os.path.join(ROOT, "paper_2312_14839_gb300", "csrc", "solver.cu"),
-                               "k_spmv32_tma" if args.spmv == "tma" else "k_spmv32", workload)
+                               "k_spmv32_tma" if args.spmv == "tma" else "k_spmv32_sym" if sym else "k_spmv32",
+                               workload)
     line["roofline"] = {
-        "kernel": ("k_spmv32_tma (FP32 12x12 BSR SpMV of the PCG, bulk-copy pipelined)"
-                   if args.spmv == "tma" else "k_spmv32 (FP32 12x12 BSR SpMV of the PCG)"),
+        "kernel": ("k_spmv32_tma (FP32 12x12 BSR SpMV of the PCG, bulk-copy pipelined)" if args.spmv == "tma" else
+                   "k_spmv32_sym (FP32 12x12 BSR SpMV of the PCG: diagonal and upper blocks streamed, lower "
+                   "blocks read as their transposes through L2)" if sym else
+                   "k_spmv32 (FP32 12x12 BSR SpMV of the PCG, both triangles streamed)"),
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
         "traffic": traffic, "algorithmic_bytes_per_launch": spmv_bytes, "avg_launch_us": spmv_s * 1e6}

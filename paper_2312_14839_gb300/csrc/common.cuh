@@ -103,6 +103,7 @@ struct Shell {
   int* d_row_ptr = nullptr;         // [n_nodes + 1]
   int* d_col = nullptr;             // [n_blocks]
   int* d_diag_block = nullptr;      // [n_nodes]
+  int* d_tpos = nullptr;            // [n_nodes][8]: the blocks (j, i) of row i's blocks (i, j) left of its diagonal
   int* d_color_start = nullptr;     // unused by the atomic path
   int* h_color_patches = nullptr;   // host copy of the colour offsets (kColours + 1 ints)
   int* d_color_list = nullptr;      // [np] patches ordered by colour
@@ -178,6 +179,12 @@ struct Shell {
   // head-and-tail products; default), or on the FP32 FMA pipe (the environment variable
   // BHEM_ELEMENT=ffma at shell creation)
   bool elem_tc = true;
+  // mixed precision, plain SpMV: k_spmv32_sym reads each node row's diagonal and upper blocks and
+  // takes its lower blocks as the transposes of the upper blocks of earlier rows (d_tpos), which
+  // those rows have just brought into L2, so DRAM sees each off-diagonal pair once (the
+  // environment variable BHEM_SPMV_SYM=1 at shell creation); default k_spmv32, which streams both
+  // triangles and was faster (60 against 72 us per launch at 256 x 256)
+  bool spmv_sym = false;
   // mixed precision: shells of at most this many nodes solve PCG as one thread-block cluster
   // (default 0: never, the graph loop was faster on every workload; BHEM_PCG_LOOP=cluster: always)
   int pcg_cluster_max_nodes = 0;

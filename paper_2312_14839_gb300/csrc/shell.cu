@@ -55,7 +55,7 @@ static bool is_device_ptr(const void* p) {
 // ------------------------------------------------------------------------------------------
 struct HostTopo {
   std::vector<int4> pnodes;
-  std::vector<int> row_ptr, col, pblocks, diag, color_list;
+  std::vector<int> row_ptr, col, pblocks, diag, color_list, tpos;
   int color_off[10];
 };
 
@@ -95,6 +95,12 @@ static void build_topology(const shell_grid& g, int n1, int n2, HostTopo& T) {
   }
   T.diag.resize(n);
   for (int i = 0; i < n; ++i) T.diag[i] = find(i, i);
+  // transposed lower blocks: for node row i, slot u < (diag - row start) holds the index of block
+  // (col[row start + u], i), the transpose of the row's u-th block left of the diagonal (a row
+  // has at most 8 such blocks); 8 slots per row, so a kernel reads them with the row index alone
+  T.tpos.assign((size_t)n * 8, 0);
+  for (int i = 0; i < n; ++i)
+    for (int k = T.row_ptr[i]; k < T.diag[i]; ++k) T.tpos[(size_t)i * 8 + (k - T.row_ptr[i])] = find(T.col[k], i);
   // colours: patches of one colour share no node (patch_colour)
   std::vector<int> cnt(10, 0);
   std::vector<int> colr(np);
@@ -120,7 +126,7 @@ static void destroy_shell(shell_s* s) {
   if (s->ev_q) cudaEventDestroy(s->ev_q);
   if (s->ev_hess) cudaEventDestroy(s->ev_hess);
   destroy_direct(*s);
-  void* ptrs[] = {s->d_patch_nodes, s->d_patch_blocks, s->d_row_ptr, s->d_col, s->d_diag_block,
+  void* ptrs[] = {s->d_patch_nodes, s->d_patch_blocks, s->d_row_ptr, s->d_col, s->d_diag_block, s->d_tpos,
                   s->d_color_list, s->d_rest, s->d_restgp, s->d_mass, s->d_fgrav, s->d_val,
                   s->d_x, s->d_r, s->d_z, s->d_p, s->d_Ap, s->d_p32, s->d_x32, s->d_r32, s->d_z32, s->d_Ap32, s->d_Dinv, s->d_phi64, s->d_phi32,
                   s->d_pcg, s->d_qn, s->d_y, s->d_g, s->d_gin, s->d_d, s->d_Md, s->d_Ep,
@@ -235,6 +241,8 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
     s->fuse_first_hessian = !(f && std::strcmp(f, "0") == 0);
     const char* el = getenv("BHEM_ELEMENT");
     s->elem_tc = !(el && std::strcmp(el, "ffma") == 0);
+    const char* sy = getenv("BHEM_SPMV_SYM");
+    s->spmv_sym = sy && std::strcmp(sy, "1") == 0;
   }
 
   HostTopo T;
@@ -253,6 +261,7 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
   A(s->d_row_ptr, n + 1);
   A(s->d_col, nb);
   A(s->d_diag_block, n);
+  A(s->d_tpos, (size_t)n * 8);
   A(s->d_color_list, np);
   A(s->d_rest, m);
   A(s->d_restgp, (size_t)13 * np * 16);
@@ -310,6 +319,7 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
   if (e == cudaSuccess) e = up(s->d_row_ptr, T.row_ptr.data(), sizeof(int) * (n + 1));
   if (e == cudaSuccess) e = up(s->d_col, T.col.data(), sizeof(int) * nb);
   if (e == cudaSuccess) e = up(s->d_diag_block, T.diag.data(), sizeof(int) * n);
+  if (e == cudaSuccess) e = up(s->d_tpos, T.tpos.data(), sizeof(int) * T.tpos.size());
   if (e == cudaSuccess) e = up(s->d_color_list, T.color_list.data(), sizeof(int) * np);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(s->d_rest, rest_dofs, sizeof(double) * m, cudaMemcpyDefault, s->stream);

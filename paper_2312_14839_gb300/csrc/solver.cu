@@ -483,6 +483,119 @@ k_spmv32(int n, const int* __restrict__ rp, const int* __restrict__ col, const f
   }
 }
 
+// k_spmv32 reading each node row's blocks left of the diagonal as transposes (an opt-in form of
+// the mixed-precision plain SpMV; Shell::spmv_sym). The row's u-th block left of the diagonal is
+// the transpose of block kt[u] = (j, i) of row j < i (the row's transposed-block slots): the same
+// values when the assembled matrix is symmetric (exactly with the colour-ordered assembly, whose
+// sums over patches run in the same order for (i, j) and (j, i); to rounding with the atomic
+// one). Row j read those values moments before (rows run in order across the grid), so they come
+// from L2, and DRAM streams only the diagonal and upper blocks. Each thread copies its 16-byte
+// pieces of the row's blocks, and the row's first three threads the x pieces they multiply, into
+// shared memory with cp.async (L2 only, no registers held while the copies fly, blocks and x in
+// one group), and reads them back, the blocks left of the diagonal transposed. The arithmetic and its order per
+// row are those of k_spmv32, so the two agree bit for bit on an exactly symmetric matrix.
+constexpr int kSymBlocks = 9;   // blocks of a node row staged (a row has at most 9)
+// per CTA: the 8 rows' blocks and x pieces, 44,928 B (4 CTAs per SM)
+constexpr size_t kSpmvSymSmem = sizeof(float) * (kSpmvThreads / 36) * kSymBlocks * (144 + 12);
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kSpmvThreads)
+k_spmv32_sym(int n, const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ val,
+             const int* __restrict__ tpos, const int* __restrict__ dg, const float* __restrict__ x, Shift4f td,
+             const unsigned char* __restrict__ mask, float* __restrict__ y, PcgState* st, Reduce red) {
+  constexpr int NC = 3, TPR = 36, RPC = kSpmvThreads / TPR;
+  // the solve's stop flag is read together with the row pointers, which the block loads wait
+  // for anyway, and tested before those loads: a launch after the solve stopped streams nothing
+  // (the flag is written only by the last CTA of a launch, after every CTA read it)
+  const int done = st ? st->done : 0;
+  __shared__ float sacc[kSpmvThreads];
+  extern __shared__ __align__(16) float sblk[];   // [RPC][kSymBlocks][144]
+  const int t = threadIdx.x;
+  const int br = t / TPR, w = t % TPR, r = w / NC, cc = w % NC;
+  const int i = blockIdx.x * RPC + br;
+  const int k0 = i < n ? rp[i] : 0, k1 = i < n ? rp[i + 1] : 0;
+  // the diagonal block (blocks before it are left of it) and the row's transposed-block slots,
+  // read beside the row pointers
+  const int kd = i < n ? dg[i] : k0;
+  int4 t0 = make_int4(0, 0, 0, 0), t1 = t0;
+  if (i < n) {
+    t0 = __ldg(reinterpret_cast<const int4*>(tpos) + 2 * i);
+    t1 = __ldg(reinterpret_cast<const int4*>(tpos) + 2 * i + 1);
+  }
+  if (done) return;
+  float* rowb = sblk + (size_t)br * kSymBlocks * 144;
+  float* rowx = sblk + (size_t)RPC * kSymBlocks * 144 + (size_t)br * kSymBlocks * 12;
+  const int nlow = kd - k0;
+  if (i < n) {
+    const int kt[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+#pragma unroll
+    for (int u = 0; u < kSymBlocks; ++u) {
+      const int k = k0 + u;
+      if (k < k1) {
+        const int kb = (u < 8 && u < nlow) ? kt[u < 8 ? u : 0] : k;
+        cp_async16(rowb + u * 144 + r * 12 + cc * 4, val + (size_t)kb * 144 + r * 12 + cc * 4);
+        // the piece x_j[4 cc .. 4 cc + 3] that the row's threads of column piece cc share
+        if (r == 0) cp_async16(rowx + u * 12 + cc * 4, x + (size_t)col[k] * 12 + cc * 4);
+      }
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  float acc = 0.f;
+  if (i < n) {
+#pragma unroll
+    for (int u = 0; u < kSymBlocks; ++u)
+      if (k0 + u < k1) {
+        float4 a;
+        if (u < nlow) {
+          const float* b = rowb + u * 144 + cc * 48 + r;   // block (i, j) = (block (j, i))^T
+          a = make_float4(b[0], b[12], b[24], b[36]);
+        } else {
+          a = *reinterpret_cast<const float4*>(rowb + u * 144 + r * 12 + cc * 4);
+        }
+        const float4 xv = *reinterpret_cast<const float4*>(rowx + u * 12 + cc * 4);
+        acc = dot4_acc(acc, a, xv);
+      }
+    for (int k = k0 + kSymBlocks; k < k1; ++k) {
+      const float4 a = __ldcg(reinterpret_cast<const float4*>(val + (size_t)k * 144 + r * 12 + cc * 4));
+      const float4 xv = *reinterpret_cast<const float4*>(x + (size_t)col[k] * 12 + cc * 4);
+      acc = dot4_acc(acc, a, xv);
+    }
+  }
+  sacc[t] = acc;
+  __syncthreads();
+  F2 part{0.f, 0.f};
+  if (i < n && cc == 0) {
+    const size_t gi = (size_t)i * 12 + r;
+    const float xi = x[gi];
+    float yi = (sacc[t] + sacc[t + 1]) + sacc[t + 2];
+    yi = __fmaf_rn(st ? st->td[r / 3] : td.v[r / 3], xi, yi);   // PCG: the solve's shift
+    if (mask && mask[gi]) yi = 0.f;
+    y[gi] = yi;
+    part = f2_prod(xi, yi);
+  }
+  if (st) {
+    F2 v1[1] = {part};
+    double out[1];
+    if (grid_reduce_f2<1>(v1, red, out, gridDim.x) && threadIdx.x == 0) {
+      st->pq = out[0];
+      if (!(out[0] > 0.0)) {
+        st->negcurv = 1;
+        st->done = 1;
+        st->alpha = 0.0;
+      } else {
+        st->alpha = st->rz / out[0];
+      }
+    }
+  }
+}
+
 // The SpMV of a mixed-precision PCG iteration with the search-direction update folded in: it
 // gathers z instead of p and forms, per own row, p = z + beta p (the arithmetic of
 // k_pcg32_pupdate4) and Ap = (A + tau D) z + beta Ap, which equals (A + tau D) p by linearity, so
@@ -1646,8 +1759,12 @@ static shell_status launch_spmv32(Shell& s, const float* x, Shift4f sh, const un
   } else {
     const int blocks = grid_for(n, kSpmvThreads / 36);
     if (st && blocks > s.red.stride) return fail(SHELL_ERR_ARG, "too many nodes for one reduction");
-    k_spmv32<<<blocks, kSpmvThreads, 0, s.stream>>>(n, s.d_row_ptr, s.d_col, (const float*)s.d_val, x, sh, mask,
-                                                    y, st, s.red);
+    if (s.spmv_sym)
+      k_spmv32_sym<<<blocks, kSpmvThreads, kSpmvSymSmem, s.stream>>>(
+          n, s.d_row_ptr, s.d_col, (const float*)s.d_val, s.d_tpos, s.d_diag_block, x, sh, mask, y, st, s.red);
+    else
+      k_spmv32<<<blocks, kSpmvThreads, 0, s.stream>>>(n, s.d_row_ptr, s.d_col, (const float*)s.d_val, x, sh, mask,
+                                                      y, st, s.red);
   }
   BHEM_CUDA(cudaGetLastError());
   ++s.launches;

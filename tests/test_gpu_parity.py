@@ -164,10 +164,12 @@ SPMV_GRIDS = {
 
 
 @pytest.mark.parametrize("case", list(SPMV_GRIDS))
-def test_spmv_tma_identical_to_plain(case):
+def test_spmv_tma_identical_to_plain(case, monkeypatch):
     """The TMA-pipelined FP32 SpMV computes every row with the arithmetic and order of the plain
-    kernel: outputs are bit-identical (empty tail groups, one-group grids, full size). The
-    matrices come from the colour-ordered assembly, which is deterministic."""
+    kernel that streams both triangles (BHEM_SPMV_SYM=0): outputs are bit-identical (empty tail
+    groups, one-group grids, full size). The matrices come from the colour-ordered assembly,
+    which is deterministic."""
+    monkeypatch.setenv("BHEM_SPMV_SYM", "0")
     g, rest, q, mat = SPMV_GRIDS[case]()
     ys = []
     x32 = dev(np.random.default_rng(1).normal(size=g.n_dof), torch.float32)
@@ -177,6 +179,39 @@ def test_spmv_tma_identical_to_plain(case):
         ys.append(host(sh.spmv(x32)))
         sh.close()
     assert np.array_equal(ys[0], ys[1])
+
+
+@pytest.mark.parametrize("assembly", ["color", "atomic"])
+@pytest.mark.parametrize("case", ["annulus12x3", "sheet1x1", "sheet61x37", "sheet256-sinusoid"])
+def test_spmv_symmetric_reads_match_both_triangles(monkeypatch, case, assembly):
+    """The FP32 SpMV that reads each node row's blocks left of the diagonal as the transposes of
+    the blocks (j, i) of earlier rows (BHEM_SPMV_SYM=1) against the default one, which streams
+    both triangles (BHEM_SPMV_SYM=0). The colour-ordered assembly adds the patches into blocks
+    (i, j) and (j, i) in the same order and each patch's 48x48 Hessian is exactly symmetric, so that assembled
+    matrix is exactly symmetric (checked block by block) and the products, summed in the same
+    order by both kernels, are bit-identical; the atomic assembly's sums run in arbitrary order,
+    so its triangles, and the products, agree to FP32 rounding."""
+    g, rest, q, mat = SPMV_GRIDS[case]()
+    x32 = dev(np.random.default_rng(2).normal(size=g.n_dof), torch.float32)
+    ys = {}
+    for sym in ("1", "0"):
+        monkeypatch.setenv("BHEM_SPMV_SYM", sym)
+        sh = make_shell(g, mat, rest, precision="mixed", spmv="plain", assembly=assembly)
+        sh.energy_grad_hess(dev(q.reshape(-1)), mass_scale=1e6, want_energy=False, want_grad=False)
+        ys[sym] = host(sh.spmv(x32))
+        if sym == "1" and assembly == "color" and g.n_patches <= 4096:
+            rp, col, val = sh.bsr()
+            rp, col, val = host(rp).astype(np.int64), host(col).astype(np.int64), host(val)
+            for i in range(g.n_nodes):
+                for k in range(rp[i], rp[i + 1]):
+                    j = col[k]
+                    kt = rp[j] + int(np.searchsorted(col[rp[j]:rp[j + 1]], i))
+                    assert col[kt] == i and np.array_equal(val[k], val[kt].T), (i, j)
+        sh.close()
+    if assembly == "color":
+        assert np.array_equal(ys["1"], ys["0"])
+    else:
+        assert rel(ys["1"], ys["0"]) <= 1e-6
 
 
 def test_pcg_mixed_tma_matches_plain(monkeypatch):
