@@ -67,6 +67,12 @@ static_assert(sizeof(WarpSmemTc) % 16 == 0 && offsetof(WarpSmemTc, Mb) % 16 == 0
 
 constexpr size_t kSmemBytes =
     1024 + 2 * kPsiBytes + sizeof(float) * ((kPhiTable + 3) & ~3) + sizeof(WarpSmemTc) * kWarps;
+// the resident CTAs of an SM: their tensor memory (512 columns per SM), their shared memory
+// (228 KB per SM, 1 KB of it reserved per CTA, about 1 KB of static arrays each) and their
+// registers (64K per SM at the 168 the launch bounds allow)
+static_assert(kCtasPerSm * kTmemCols <= 512, "tensor memory of the resident CTAs");
+static_assert(kCtasPerSm * (kSmemBytes + 2048) <= 228 * 1024, "shared memory of the resident CTAs");
+static_assert(kCtasPerSm * kThreads * 168 <= 65536, "registers of the resident CTAs");
 
 // Instruction descriptor of kind::tf32: TF32 A and B, FP32 D, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
