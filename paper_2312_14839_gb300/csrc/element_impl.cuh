@@ -368,9 +368,24 @@ struct ElemArgs {
 template <typename R, bool kSplit, bool kBlocks = false, class WS = WarpSmem<R>>
 __device__ __forceinline__ void gauss_point_matrix(const R* sphi, WS& W, int g, int half,
                                                    const ElemArgs& A) {
-  V3<R> ub[5], uu[5];
-  interp5<R, R>(sphi, W.qb, g, ub);   // rest a_bar_1, a_bar_2, x_bar_{,11}, x_bar_{,22}, x_bar_{,12}
-  interp5<R, R>(sphi, W.u, g, uu);    // displacement derivatives
+  V3<R> ub[5], uu[5];   // rest a_bar_1, a_bar_2, x_bar_{,11}, x_bar_{,22}, x_bar_{,12}; displacement derivatives
+  if constexpr (kSplit) {
+    // both halves need both fields at the same Gauss point: half 0 interpolates the rest DOFs,
+    // half 1 the displacement, and they exchange (lane g <-> g + 16)
+    V3<R> mine[5];
+    interp5<R, R>(sphi, half ? W.u : W.qb, g, mine);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const V3<R> other = mk<R>(__shfl_xor_sync(0xffffffffu, mine[k].x, 16),
+                                __shfl_xor_sync(0xffffffffu, mine[k].y, 16),
+                                __shfl_xor_sync(0xffffffffu, mine[k].z, 16));
+      ub[k] = half ? other : mine[k];
+      uu[k] = half ? mine[k] : other;
+    }
+  } else {
+    interp5<R, R>(sphi, W.qb, g, ub);
+    interp5<R, R>(sphi, W.u, g, uu);
+  }
   {
     // half 1: exchange the parameter directions (selects, no divergent branch)
     const bool x = half != 0;
