@@ -308,6 +308,7 @@ shell_status launch_element_full(Shell& s, const double* q, bool fp64, const Ele
   A.energy_p = out.energy_p;
   A.grad_p = out.grad_p;
   A.hess_p = out.hess_p;
+  A.hess_vec = ((uintptr_t)out.hess_p & 15u) == 0;
   A.bsr = out.bsr;
   A.err = s.d_err;
   if (!fp64 && out.grad64) {

@@ -345,6 +345,7 @@ struct ElemArgs {
   double* energy_p;
   double* grad_p;
   void* hess_p;
+  int hess_vec;            // hess_p is 16-byte aligned (FP32 Hessians stored as float4)
   void* bsr;
   int bsr_atomic;
   int* err;
@@ -639,7 +640,13 @@ constexpr int kKStride = 52;   // row stride of the staged 48 x 48 Hessian (16-b
 // Writes one patch's FP32 Hessian, staged in shared memory as K[(I, c) * kKStride + (J, c')], to
 // the unassembled output and/or scatters it into the BSR values (one warp).
 __device__ __forceinline__ void store_staged_hessian32(const float* K, int p, const ElemArgs& A, int lane) {
-  if (A.hess_p) {
+  if (A.hess_p && A.hess_vec) {
+    // 16-byte pieces: staged rows of 52 floats and output rows of 48 both start 16-byte aligned
+    // (the output when its base is, which the host checked)
+    float4* Hp = reinterpret_cast<float4*>(reinterpret_cast<float*>(A.hess_p) + (size_t)p * 2304);
+    for (int e = lane; e < 576; e += 32)
+      Hp[e] = *reinterpret_cast<const float4*>(K + (e / 12) * kKStride + (e % 12) * 4);
+  } else if (A.hess_p) {
     float* Hp = reinterpret_cast<float*>(A.hess_p) + (size_t)p * 2304;
     for (int e = lane; e < 2304; e += 32) Hp[e] = K[(e / 48) * kKStride + e % 48];
   }

@@ -141,3 +141,42 @@ def test_tensor_core_wait_timeout_is_reported_and_the_shell_recovers(monkeypatch
     st = sh.newton_step(qd.clone(), torch.zeros_like(qd), step_params(dt=1e-3, newton_max=4))
     assert st["status"] == 0
     sh.close()
+
+
+def test_tensor_core_pass_reports_degenerate_and_nonfinite_inputs(monkeypatch):
+    """A mixed-precision step (the tensor-core pass with the fused FP64 residual) on a collapsed
+    state reports SHELL_ERR_DEGENERATE, on a state with a NaN SHELL_ERR_DEGENERATE or
+    SHELL_ERR_NONFINITE; the shell then steps normally."""
+    from paper_2312_14839_gb300.bhem import ShellError, step_params
+    g, rest, q, mat = CASES["sheet3x3-thick"]()
+    sh = shell(monkeypatch, "tc", g, mat, rest)
+    P = step_params(dt=1e-3, newton_max=4)
+    zero = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    with pytest.raises(ShellError) as e:
+        sh.newton_step(zero.clone(), zero.clone(), P)
+    assert e.value.status == 4
+    bad = dev(q.reshape(-1)).clone()
+    bad[5] = float("nan")
+    with pytest.raises(ShellError) as e:
+        sh.newton_step(bad, zero.clone(), P)
+    assert e.value.status in (4, 5)
+    st = sh.newton_step(dev(q.reshape(-1)), zero.clone(), P)
+    assert st["status"] == 0
+    sh.close()
+
+
+def test_unassembled_hessians_at_a_misaligned_address(monkeypatch):
+    """The FP32 patch Hessians are stored in 16-byte pieces when the output is 16-byte aligned
+    and element by element otherwise: an output 4 bytes off alignment receives the same values."""
+    from paper_2312_14839_gb300 import bhem
+    g, rest, q, mat = CASES["annulus10x3"]()
+    sh = shell(monkeypatch, "tc", g, mat, rest)
+    qd = dev(q.reshape(-1))
+    _, _, H0 = sh.element_egh(qd, want=("h",))
+    buf = torch.full((g.n_patches * 2304 + 1,), float("nan"), dtype=torch.float32, device="cuda")
+    H1 = buf[1:]
+    assert H1.data_ptr() % 16 == 4
+    bhem._check(bhem.load().shell_element_egh(sh._h, bhem._ptr(qd), 1, None, None, bhem._ptr(H1)))
+    torch.cuda.synchronize()
+    assert torch.equal(H1.view(g.n_patches, 48, 48), H0)
+    sh.close()
