@@ -185,6 +185,10 @@ struct Shell {
   // environment variable BHEM_SPMV_SYM=1 at shell creation); default k_spmv32, which streams both
   // triangles and was faster (60 against 72 us per launch at 256 x 256)
   bool spmv_sym = false;
+  // mixed-precision PCG iterations (plain SpMV, update, direction update) launched with
+  // programmatic dependent launch, so each kernel's CTAs are scheduled while the previous one
+  // finishes (default; the environment variable BHEM_PDL=0 at shell creation: plain launches)
+  bool pdl = true;
   // mixed precision: shells of at most this many nodes solve PCG as one thread-block cluster
   // (default 0: never, the graph loop was faster on every workload; BHEM_PCG_LOOP=cluster: always)
   int pcg_cluster_max_nodes = 0;

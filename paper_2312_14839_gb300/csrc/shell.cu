@@ -243,6 +243,8 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
     s->elem_tc = !(el && std::strcmp(el, "ffma") == 0);
     const char* sy = getenv("BHEM_SPMV_SYM");
     s->spmv_sym = sy && std::strcmp(sy, "1") == 0;
+    const char* pd = getenv("BHEM_PDL");
+    s->pdl = !(pd && std::strcmp(pd, "0") == 0);
   }
 
   HostTopo T;

@@ -405,6 +405,28 @@ __global__ void k_to_float(int m, const double* __restrict__ a, float* __restric
 // Mixed-precision PCG (FP32 matrix, FP32 vectors, dot products as exact FP32 products summed in
 // double-float): no FP64-pipe work per element. 36 threads per block row as in k_spmv.
 // ------------------------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel of the PCG iteration may be launched while the previous
+// kernel of its stream is still finishing (its CTAs are scheduled early); before it reads or
+// writes any memory it waits here until the previous kernel has completed and its writes are
+// visible. Without such a launch the wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+// Launch of kernel k, with programmatic dependent launch when pdl is set.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(bool pdl, void (*k)(KArgs...), unsigned grid, unsigned block, cudaStream_t st,
+                            Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 struct Shift4f { float v[4]; };
 
 // acc += a . x as an explicit FMA chain (both FP32 SpMV kernels round identically)
@@ -420,6 +442,7 @@ k_spmv32(int n, const int* __restrict__ rp, const int* __restrict__ col, const f
          const float* __restrict__ x, Shift4f td, const unsigned char* __restrict__ mask,
          float* __restrict__ y, PcgState* st, Reduce red) {
   constexpr int NC = 3, TPR = 36, RPC = kSpmvThreads / TPR;
+  pdl_wait();
   // the solve's stop flag is read together with the row pointers, which the block loads wait
   // for anyway, and tested before those loads: a launch after the solve stopped streams nothing
   // (the flag is written only by the last CTA of a launch, after every CTA read it)
@@ -1299,6 +1322,7 @@ k_pcg32_update(int n, float* __restrict__ x, float* __restrict__ r, float* __res
                const float* __restrict__ p, const float* __restrict__ Ap,
                const float* __restrict__ Dinv, const unsigned char* __restrict__ mask, PcgState* st,
                Reduce red) {
+  pdl_wait();
   if (st->done) return;
   const double alpha_d = st->alpha;
   __shared__ float sr[16][12];
@@ -1381,6 +1405,7 @@ k_pcg32_update(int n, float* __restrict__ x, float* __restrict__ r, float* __res
 
 __global__ void k_pcg32_pupdate(int m, const float* __restrict__ z, float* __restrict__ p,
                                 const PcgState* st) {
+  pdl_wait();
   // z and p (8 bytes a thread) are loaded while the stop flag and beta are in flight; a launch
   // after the solve stopped reads them for nothing
   const int done = st->done;
@@ -1396,6 +1421,7 @@ __global__ void k_pcg32_pupdate(int m, const float* __restrict__ z, float* __res
 // are cudaMalloc'd, so every float4 is aligned): a quarter of the threads for this short pass.
 __global__ void k_pcg32_pupdate4(int m4, const float4* __restrict__ z, float4* __restrict__ p,
                                  const PcgState* st) {
+  pdl_wait();
   const int done = st->done;
   const double beta_d = st->beta;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m4; k += gridDim.x * blockDim.x) {
@@ -1763,8 +1789,8 @@ static shell_status launch_spmv32(Shell& s, const float* x, Shift4f sh, const un
       k_spmv32_sym<<<blocks, kSpmvThreads, kSpmvSymSmem, s.stream>>>(
           n, s.d_row_ptr, s.d_col, (const float*)s.d_val, s.d_tpos, s.d_diag_block, x, sh, mask, y, st, s.red);
     else
-      k_spmv32<<<blocks, kSpmvThreads, 0, s.stream>>>(n, s.d_row_ptr, s.d_col, (const float*)s.d_val, x, sh, mask,
-                                                      y, st, s.red);
+      BHEM_CUDA(launch_k(s.pdl && st, k_spmv32, blocks, kSpmvThreads, s.stream, n, (const int*)s.d_row_ptr,
+                         (const int*)s.d_col, (const float*)s.d_val, x, sh, mask, y, st, s.red));
   }
   BHEM_CUDA(cudaGetLastError());
   ++s.launches;
@@ -1791,16 +1817,19 @@ shell_status launch_pcg_iteration(Shell& s, const unsigned char* mask, const dou
       BHEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg32_update, kNodeThreads, 0));
       s.update_grid = std::max(1, std::min(grid_for(n, 16), std::max(1, occ) * std::max(1, s.num_sms)));
     }
-    k_pcg32_update<<<s.update_grid, kNodeThreads, 0, s.stream>>>(
-        n, s.d_x32, s.d_r32, s.d_z32, s.d_p32, s.d_Ap32, (const float*)s.d_Dinv, mask, s.d_pcg, s.red);
+    BHEM_CUDA(launch_k(s.pdl, k_pcg32_update, s.update_grid, kNodeThreads, s.stream, n, s.d_x32, s.d_r32,
+                       s.d_z32, (const float*)s.d_p32, (const float*)s.d_Ap32, (const float*)s.d_Dinv, mask,
+                       s.d_pcg, s.red));
     BHEM_CUDA(cudaGetLastError());
     ++s.launches;
     if (fold) return SHELL_OK;   // the next iteration's SpMV forms p
     if (m % 4 == 0)
-      k_pcg32_pupdate4<<<vec_blocks(m / 4), 256, 0, s.stream>>>(m / 4, reinterpret_cast<const float4*>(s.d_z32),
-                                                                reinterpret_cast<float4*>(s.d_p32), s.d_pcg);
+      BHEM_CUDA(launch_k(s.pdl, k_pcg32_pupdate4, vec_blocks(m / 4), 256, s.stream, m / 4,
+                         reinterpret_cast<const float4*>(s.d_z32), reinterpret_cast<float4*>(s.d_p32),
+                         (const PcgState*)s.d_pcg));
     else
-      k_pcg32_pupdate<<<vec_blocks(m), 256, 0, s.stream>>>(m, s.d_z32, s.d_p32, s.d_pcg);
+      BHEM_CUDA(launch_k(s.pdl, k_pcg32_pupdate, vec_blocks(m), 256, s.stream, m, (const float*)s.d_z32, s.d_p32,
+                         (const PcgState*)s.d_pcg));
     BHEM_CUDA(cudaGetLastError());
     ++s.launches;
     return SHELL_OK;
