@@ -295,22 +295,16 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_element_tc(ElemArgs A,
       float* K = &W.Mb[0][0];
 #pragma unroll
       for (int t = 0; t < 3; ++t) {
+        // entry (I, c), (J, d) and its mirror; a diagonal pair (c = d) takes the entries I <= J of
+        // column J only (one path for both half-warps, whose pairs differ in kind)
         const int cd = 2 * t + cdl, c = cd_c(cd), d = cd_d(cd);
-        if (c < d) {
+        const bool off = c < d;
 #pragma unroll
-          for (int I = 0; I < 16; ++I) {
+        for (int I = 0; I < 16; ++I) {
+          if (off || I <= J) {
             const float v = __uint_as_float(r[t][I]);
             K[(I * 3 + c) * kKStride + J * 3 + d] = v;
             K[(J * 3 + d) * kKStride + I * 3 + c] = v;
-          }
-        } else {
-          // diagonal pair: the entries I <= J of column J, and their mirrors
-#pragma unroll
-          for (int I = 0; I < 16; ++I) {
-            if (I > J) continue;
-            const float v = __uint_as_float(r[t][I]);
-            K[(I * 3 + c) * kKStride + J * 3 + c] = v;
-            K[(J * 3 + c) * kKStride + I * 3 + c] = v;
           }
         }
       }
