@@ -263,7 +263,7 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
   A(s->d_row_ptr, n + 1);
   A(s->d_col, nb);
   A(s->d_diag_block, n);
-  A(s->d_tpos, (size_t)n * 8);
+  if (s->spmv_sym) A(s->d_tpos, (size_t)n * 8);   // read by the opt-in symmetric SpMV only
   A(s->d_color_list, np);
   A(s->d_rest, m);
   A(s->d_restgp, (size_t)13 * np * 16);
@@ -321,7 +321,7 @@ extern "C" shell_status shell_create(const shell_grid* grid, const shell_materia
   if (e == cudaSuccess) e = up(s->d_row_ptr, T.row_ptr.data(), sizeof(int) * (n + 1));
   if (e == cudaSuccess) e = up(s->d_col, T.col.data(), sizeof(int) * nb);
   if (e == cudaSuccess) e = up(s->d_diag_block, T.diag.data(), sizeof(int) * n);
-  if (e == cudaSuccess) e = up(s->d_tpos, T.tpos.data(), sizeof(int) * T.tpos.size());
+  if (e == cudaSuccess && s->d_tpos) e = up(s->d_tpos, T.tpos.data(), sizeof(int) * T.tpos.size());
   if (e == cudaSuccess) e = up(s->d_color_list, T.color_list.data(), sizeof(int) * np);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(s->d_rest, rest_dofs, sizeof(double) * m, cudaMemcpyDefault, s->stream);
