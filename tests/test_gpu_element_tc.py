@@ -180,3 +180,22 @@ def test_unassembled_hessians_at_a_misaligned_address(monkeypatch):
     torch.cuda.synchronize()
     assert torch.equal(H1.view(g.n_patches, 48, 48), H0)
     sh.close()
+
+
+def test_tensor_core_hessians_match_ffma_on_every_patch_at_full_size(monkeypatch):
+    """The bench's 256x256 sheet: all 65,536 tensor-core patch Hessians against the FFMA form's
+    (which the oracle pins patch by patch on smaller grids and on samples of this one), normwise
+    per patch, compared on the device."""
+    g, rest, q = S.sheet_sinusoid(256, 3)
+    Hs = {}
+    for form in ("tc", "ffma"):
+        sh = shell(monkeypatch, form, g, THIN, rest)
+        _, _, H = sh.element_egh(dev(q.reshape(-1)), want=("h",))
+        torch.cuda.synchronize()
+        Hs[form] = H
+        sh.close()
+    d = torch.linalg.norm((Hs["tc"] - Hs["ffma"]).double().reshape(g.n_patches, -1), dim=1)
+    ref = torch.linalg.norm(Hs["ffma"].double().reshape(g.n_patches, -1), dim=1)
+    worst = float((d / ref).max())
+    print(f"full-size tensor-core against FFMA: worst patch {worst:.2e}")
+    assert worst <= 5e-6, worst
